@@ -1,0 +1,404 @@
+"""Benchmark of the equirectangular splatting hot path on GB300.
+
+Workload (default "egocentric"): 1,000,000 Gaussians in a seeded 10 x 3 x 8 m room (70 % on the walls, 30 % inside),
+8 camera poses within 1 m of the room centre with random yaw, 2048 x 1024 equirectangular views, 16 x 16 tiles,
+FP32. One step = preprocess -> bin -> sort -> ranges -> render_fwd -> L1 loss -> render_bwd -> preprocess_bwd for all
+8 views (every stage of the path), against a target rendered once from a perturbed copy of the scene.
+
+Metric: forward + backward milliseconds per iteration (lower is better). Under torchrun each rank renders its own
+8 poses of the same scene (views are independent: weak scaling, no collective on the data path); the timed
+region is bracketed by barriers and the slowest rank's time is reported.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, views, W, H, tile, scene builder, pose builder)
+    "egocentric": dict(n=1_000_000, views=8, width=2048, height=1024, tile=16, scene="room"),
+    "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
+}
+
+# Algorithmic work per unit, used for the roofline (see the design doc for the derivations).
+FWD_FLOP_PER_PAIR = 22       # render_fwd: per evaluated (pixel, entry) pair
+BWD_FLOP_PER_PAIR = 62       # render_bwd: per processed (pixel, entry) pair (eval + adjoint)
+SORT_BYTES_PER_KEY = 24      # sort_downsweep: 8 B key + 4 B value read, the same written, per pass
+PRE_BYTES_PER_GAUSS = 236    # preprocess: 59 parameter floats read once
+PRE_BYTES_PER_SPLAT = 48     # preprocess: one 48 B splat written per (view, Gaussian)
+
+
+def build_scene(wl: dict, seed: int = 0):
+    if wl["scene"] == "room":
+        return synth.room_scene(wl["n"], seed)
+    return synth.shell_scene(wl["n"], seed)
+
+
+def build_poses(wl: dict, rank: int):
+    if wl["scene"] == "room":
+        return synth.room_viewmats(wl["views"], 1000 + rank)
+    return synth.identity_viewmats(wl["views"])
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = f"/tmp/omnigs_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng):
+    """One bounded oracle sample of a step, extrapolated to the whole step (ms). Returns (ms, description)."""
+    import oracle
+    W, H, T, V = wl["width"], wl["height"], wl["tile"], wl["views"]
+    tiles = (W // T) * (H // T)
+    n = scene.n
+    # Gaussian fraction for the full-list stages (bin + sort, ~n log n, taken as linear) and tile sample for blending
+    frac = float(min(1.0, max(0.02, budget_s / 12.0)))
+    k_tiles = int(max(4, min(64, 32 * budget_s / 12.0)))
+    v = int(rng.integers(V))
+    idx = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False)) if frac < 1.0 else np.arange(n)
+    sub = scene.subset(idx)
+    t0 = time.perf_counter()
+    rec = oracle.preprocess(scene, viewmats[v:v + 1], W, H)
+    t_pre = time.perf_counter() - t0
+    sp = oracle.splats_from_records(rec)
+    t0 = time.perf_counter()
+    rec_s = oracle.preprocess(sub, viewmats[v:v + 1], W, H)
+    oracle.bin_sort(oracle.splats_from_records(rec_s), 1, W, H, T)
+    t_sort = (time.perf_counter() - t0) / frac
+    mask = np.zeros(tiles, bool)
+    mask[rng.choice(tiles, k_tiles, replace=False)] = True
+    t0 = time.perf_counter()
+    rg, lst = oracle.bin_sort(sp, 1, W, H, T, tile_mask=mask)
+    rgb, Tf, nc, _ = oracle.blend_fwd(sp, rg, lst, 1, W, H, T)
+    d = rgb - target[v:v + 1]
+    g = (np.sign(d) / (V * d.size)).astype(np.float64)
+    g2 = oracle.blend_bwd(sp, rg, lst, g, 1, W, H, T)
+    t_blend = (time.perf_counter() - t0) * tiles / k_tiles
+    t0 = time.perf_counter()
+    oracle.preprocess_bwd(scene, viewmats[v:v + 1], g2, W, H)
+    t_pbwd = time.perf_counter() - t0
+    ms = 1e3 * V * (t_pre + t_sort + t_blend + t_pbwd)
+    desc = (f"1 of {V} views: preprocess + preprocess_bwd of all {n} Gaussians, bin + sort of a {frac:.0%} Gaussian "
+            f"sample (scaled 1/frac), blend fwd + bwd of {k_tiles} of {tiles} tiles (scaled), times {V} views")
+    return ms, desc
+
+
+def run_reference(args, wl):
+    """FP64 CPU oracle on bounded samples of the workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    scene = build_scene(wl)
+    vm = build_poses(wl, 0)
+    rng = np.random.default_rng(7)
+    target = synth.random_image(wl["views"], wl["width"], wl["height"], 5)
+    budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    times, desc = [], ""
+    for i in range(args.warmup + args.steps):
+        ms, desc = oracle_step_sample(scene, vm, wl, target, budget, rng)
+        if i >= args.warmup:
+            times.append(ms)
+    value = float(np.mean(times))
+    out = {"metric": "fwd+bwd ms/iter", "value": value, "unit": "ms/iter", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "impl": "reference",
+           "dtype": "f64", "data": "synthetic", "config": workload_config(wl, args),
+           "cpu_baseline": {"value": value, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "vs_baseline": None}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def workload_config(wl, args):
+    return {"workload": f"{args.workload}: {wl['n']} Gaussians, {wl['views']} views of {wl['width']}x{wl['height']} "
+                        f"equirect, {wl['tile']}x{wl['tile']} tiles, fwd+bwd with L1 loss",
+            "gaussians": wl["n"], "views_per_step": wl["views"], "width": wl["width"], "height": wl["height"],
+            "tile": wl["tile"], "parallelism": f"replica x{args.gpus} (views per rank)",
+            "l2": "inputs larger than L2 (several GB touched per step)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="egocentric", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2404_03202_gb300 as og
+    from paper_2404_03202_gb300 import _cabi as C
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    scene = build_scene(wl)
+    vm_np = build_poses(wl, rank)
+    V, W, H = wl["views"], wl["width"], wl["height"]
+    settings = og.Settings(width=W, height=H, tile=wl["tile"], num_views=V, sh_degree=scene.sh_degree)
+    params = [torch.from_numpy(a).to(dev) for a in scene.arrays()]
+    vm = torch.from_numpy(vm_np).to(dev)
+
+    # target image: rendered once from a perturbed copy (means + N(0, 0.01), SH DC + N(0, 0.05))
+    pert = synth.perturbed_copy(scene, 11)
+    probe = og.Rasterizer(settings, device=dev)
+    target = probe.forward(*[torch.from_numpy(a).to(dev) for a in pert.arrays()], vm).clone()
+    probe.forward(*params, vm)
+    count = probe.count
+    del probe
+    torch.cuda.synchronize()
+    r = og.Rasterizer(settings, device=dev, capacity=int(count * 1.05) + 4096, grow=False)
+
+    def step():
+        r.forward(*params, vm)
+        r.l1_loss(target)
+        r.backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    r.check()
+
+    # ---------------------------------------------------------------- timed region (device time, all stages)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    C.omnigs_profiler_enable(True)
+    C.omnigs_profiler_collect()
+    with sampler:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+    prof = C.omnigs_profiler_collect(64)
+    C.omnigs_profiler_enable(False)
+    r.check()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.summary()
+    kernel_launches = int(sum(p[1] for p in prof) / args.steps)
+
+    # ---------------------------------------------------------------- graph replay of the same step
+    graph_ms = None
+    try:
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(args.steps):
+            graph.replay()
+        g1.record()
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        r.check()
+        del graph
+    except Exception as e:  # reported, never silently replaces the eager number
+        graph_ms = f"failed: {type(e).__name__}: {e}"
+
+    # ---------------------------------------------------------------- end to end through the public API
+    e2e = None
+    if not args.no_e2e:
+        host_params = [torch.from_numpy(a).pin_memory() for a in scene.arrays()]
+        host_vm = torch.from_numpy(vm_np).pin_memory()
+        host_target = target.cpu().pin_memory()
+        dev_params = [torch.empty_like(p, device=dev) for p in host_params]
+        dev_vm = torch.empty_like(host_vm, device=dev)
+        dev_target = torch.empty_like(host_target, device=dev)
+        out_names = ["means", "scales", "quats", "opacity", "sh", "screen"]
+        host_out = {k: torch.empty(tuple(getattr(r, "d_" + k).shape), dtype=torch.float32).pin_memory()
+                    for k in out_names}
+        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            for d, h in zip(dev_params, host_params):
+                d.copy_(h, non_blocking=True)
+            dev_vm.copy_(host_vm, non_blocking=True)
+            dev_target.copy_(host_target, non_blocking=True)
+            r.forward(*dev_params, dev_vm)
+            r.l1_loss(dev_target)
+            grads = r.backward()
+            for k in out_names:
+                host_out[k].copy_(grads[k], non_blocking=True)
+            host_loss.copy_(r.loss, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        h2d = sum(h.numel() * h.element_size() for h in host_params) + host_vm.numel() * 4 + host_target.numel() * 4
+        d2h = sum(h.numel() * h.element_size() for h in host_out.values()) + 4
+        e2e = {"value": e_ms, "unit": "ms/iter", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        r.check()
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    peaks, peak_src = read_peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tflops = n_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    pairs = int(r.ncontrib.to(torch.int64).sum().item())
+    count = r.instance_count()
+    per_kernel = {p[0]: {"launches": p[1], "total_ms": p[2], "avg_ms": p[2] / max(p[1], 1)} for p in prof}
+    dom = max(prof, key=lambda p: p[2])[0]
+    k = per_kernel[dom]
+    sort_passes = per_kernel.get("sort_downsweep", {}).get("launches", 0) // args.steps
+    if dom == "render_bwd":
+        flops = pairs * BWD_FLOP_PER_PAIR
+        roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
+                "unit": "TFLOP/s"}
+    elif dom == "render_fwd":
+        flops = pairs * FWD_FLOP_PER_PAIR
+        roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
+                "unit": "TFLOP/s"}
+    elif dom == "sort_downsweep":
+        roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["kernel"] = dom
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
+    roof["traffic"] = None
+    roof["peak_source"] = f"{peak_src}" + (" (ALU peak: SMs x 128 FP32 lanes x 2 x median SM clock)"
+                                           if roof["bound"] == "alu" else "")
+
+    # ---------------------------------------------------------------- CPU baseline (oracle), rank 0, N = 1
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            ms_cpu, desc = oracle_step_sample(scene, vm_np, wl, synth.random_image(V, W, H, 5), 12.0,
+                                              np.random.default_rng(3))
+            cpu = {"value": ms_cpu, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": desc}
+        except Exception as e:
+            cpu = {"value": None, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        out = {"metric": "fwd+bwd ms/iter", "value": ms * 1.0, "unit": "ms/iter", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": workload_config(wl, args) | {"views_per_s": 1e3 * V * world / ms,
+                                                      "graph_ms_per_step": graph_ms,
+                                                      "instances_per_step": count, "pairs_per_step": pairs,
+                                                      "sort_passes": sort_passes},
+               "gpu_launches": kernel_launches * args.steps, "kernels_per_step": per_kernel,
+               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * omnigs.h -- C ABI of the GB300 (sm_103a) equirectangular Gaussian-splatting rasterizer.
+ *
+ * The library renders 3D Gaussians directly onto an equirectangular (spherical-camera) image and back-propagates
+ * through that rendering, following OmniGS (arXiv 2404.03202): projection onto longitude / latitude (Sec. 3.2,
+ * Eqs. 1, 3-5), the spherical-camera Jacobian and EWA covariance (Sec. 3.3, Eqs. 9-16), tile-based alpha blending
+ * sorted by the camera distance t_r (Sec. 3.3, Eqs. 6-8 and the tile procedure that closes Sec. 3.3), and the
+ * gradients of Sec. 3.4 (Eqs. 18-20).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named as device buffers must be device memory (or managed memory) of the current device. All
+ *     arrays are C-contiguous; float arrays are IEEE float32; "[a, b]" gives the shape.
+ *   - The caller owns every buffer, including the workspace. The library never allocates device memory and never
+ *     synchronises, except in omnigs_instance_count and omnigs_last_error, which say so.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL means the legacy default stream) and runs asynchronously.
+ *   - Invalid arguments are rejected before any work is enqueued, with OMNIGS_E_INVALID. A failed launch returns
+ *     OMNIGS_E_CUDA. Conditions found on the device (instance capacity exceeded) set a sticky error word in the
+ *     workspace; omnigs_last_error returns and clears it. Outputs are undefined after any error.
+ *   - Gradient outputs are overwritten, not accumulated.
+ *   - A sequence of calls for one frame must use one workspace and one stream; concurrent frames need separate
+ *     workspaces.
+ */
+#ifndef OMNIGS_H
+#define OMNIGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *omnigs_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    OMNIGS_OK = 0,
+    OMNIGS_E_INVALID = 1,  /* bad argument; nothing was enqueued */
+    OMNIGS_E_CAPACITY = 2, /* more tile instances than the capacity given to omnigs_bin */
+    OMNIGS_E_CUDA = 3,     /* a CUDA launch or call failed */
+    OMNIGS_E_TIMEOUT = 4   /* a bounded device-side wait ran out */
+} omnigs_status;
+
+/* Image and camera set-up shared by all calls of one frame. */
+typedef struct {
+    int32_t width;     /* W, equirectangular width in pixels; a multiple of `tile` */
+    int32_t height;    /* H, height in pixels; a multiple of `tile` (W = 2H is the usual equirect shape) */
+    int32_t tile;      /* square tile side in pixels: 8, 16 or 32 */
+    int32_t num_views; /* V >= 1 camera poses rendered in one call */
+    int32_t sh_degree; /* 0..3; the SH array holds K = (sh_degree + 1)^2 coefficients per colour channel */
+    float near_r;      /* a Gaussian is culled when its camera distance t_r <= near_r */
+    float bg[3];       /* background colour added with the final transmittance */
+} omnigs_config;
+
+/* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).
+ * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H]. (c0, c1, c2): inverse of the 2x2 covariance
+ * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. radius: half-side in pixels of the square whose tiles
+ * receive an instance (ceil(3 sqrt(lambda_max))), 0 when the Gaussian is culled in this view. */
+typedef struct {
+    float px, py;
+    float c0, c1, c2;
+    float opacity;
+    float r, g, b;
+    float depth;
+    int32_t radius;
+    uint32_t reserved; /* written as 0 */
+} omnigs_splat;
+
+/* Gradient of the loss with respect to one omnigs_splat's differentiable fields (48 bytes, 16-byte aligned). */
+typedef struct {
+    float px, py;
+    float c0, c1, c2;
+    float opacity;
+    float r, g, b;
+    float reserved[3]; /* written as 0 */
+} omnigs_splat_grad;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int omnigs_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *omnigs_status_string(omnigs_status status);
+
+/* Bytes of device workspace needed for n Gaussians in cfg->num_views views with room for `capacity` tile
+ * instances (one instance per (view, Gaussian, covered tile); Sec. 3.3). Returns 0 for invalid arguments.
+ * The workspace is 256-byte aligned by the caller and need not be initialised; omnigs_bin initialises it. */
+size_t omnigs_workspace_size(const omnigs_config *cfg, int64_t n, int64_t capacity);
+
+/* Per-(view, Gaussian) projection, Sec. 3.2-3.3: t = W m + t_cw (Eq. 1); lon, lat (Eq. 3); s (Eq. 4); p (Eq. 5);
+ * J (Eqs. 10-16); Sigma~ = J W Sigma W^T J^T + 0.3 I (Eq. 9), Sigma = R(q) diag(s)^2 R(q)^T; conic = Sigma~^-1;
+ * radius; colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m (Sec. 3.1).
+ *   means   [n, 3]  world positions m                     scales  [n, 3]  linear scales S (> 0)
+ *   quats   [n, 4]  rotations q as (w, x, y, z), any norm  opacity [n]     opacities o in [0, 1]
+ *   sh      [n, K, 3] SH coefficients                     viewmats [V, 4, 4] row-major world-to-camera T_cw
+ *   splats  [V, n]  output (device), index v * n + g
+ * All inputs are device buffers. n = 0 is valid and enqueues nothing. */
+omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float *means, const float *scales,
+                                const float *quats, const float *opacity, const float *sh, const float *viewmats,
+                                omnigs_splat *splats, omnigs_stream_t stream);
+
+/* Tile binning, Sec. 3.3 ("one instance per influence"): for every splat with radius > 0, one instance per tile
+ * covered by the square of half-side `radius` around pixel floor(p). Tile columns wrap modulo W / tile (the
+ * longitude seam; a square at least as wide as the image covers every column once); rows are clipped to the image.
+ *   splats   [V * n] input (device)
+ *   offsets  [V * n + 1] output (device): exclusive prefix sum of per-splat instance counts; offsets[V * n] = total
+ *   keys, values [capacity] output (device): instance i of splat j = v * n + g gets
+ *            keys[i] = ((v * TILES + tile) << 31) | (float bits of depth), values[i] = j,
+ *            where TILES = (W / tile) * (H / tile) and instances of a splat are listed row by row, columns in
+ *            seam order. The total stays on the device (workspace); if it exceeds `capacity`, only the first
+ *            `capacity` instances are written and OMNIGS_E_CAPACITY is raised in the workspace.
+ *   capacity must be < 2^32 and equal to the value given to omnigs_workspace_size. */
+omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *offsets,
+                         uint64_t *keys, uint32_t *values, int64_t capacity, void *workspace, omnigs_stream_t stream);
+
+/* Sort of the instances written by omnigs_bin by key, i.e. by (view, tile) and then by t_r (Sec. 3.3: blending
+ * order is by t_r, nearest first), stable, so equal keys keep splat order. Sorts keys/values in place (using the
+ * workspace) and writes ranges [V * TILES, 2] (device): ranges[2t], ranges[2t+1] = first and one-past-last sorted
+ * position of tile t (both 0 for an empty tile). */
+omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t capacity, uint64_t *keys, uint32_t *values,
+                          uint32_t *ranges, void *workspace, omnigs_stream_t stream);
+
+/* Forward blending, Eqs. 6-8 with the tile procedure of Sec. 3.3: pixel (x, y) of view v is sampled at
+ * (x + 0.5, y + 0.5) and blends its tile's sorted list front to back: dx taken as the minimal image in
+ * [-W/2, W/2); alpha = min(0.99, o exp(-1/2 dp^T conic dp)); entries with exponent > 0 or alpha < 1/255 are
+ * skipped; blending stops before an entry that would bring T below 1e-4; finally C += T bg.
+ *   splats [V * n], ranges [V * TILES, 2], values [capacity] (sorted, from omnigs_sort): inputs (device)
+ *   out_rgb [V, 3, H, W], out_T [V, H, W] (final transmittance), out_ncontrib [V, H, W] (list position after the
+ *   last contributor): outputs (device). out_T and out_ncontrib feed omnigs_render_bwd. */
+omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
+                                const uint32_t *ranges, const uint32_t *values, float *out_rgb, float *out_T,
+                                uint32_t *out_ncontrib, omnigs_stream_t stream);
+
+/* L1 term of the photometric loss (Eq. 17 with lambda = 0): loss = mean |rgb - target| over [V, 3, H, W];
+ * dL_drgb = sign(rgb - target) / (V * 3 * H * W) (0 where equal). rgb, target: inputs; dL_drgb [V, 3, H, W] and
+ * loss [1]: outputs (device). */
+omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const float *target, float *dL_drgb,
+                             float *loss, void *workspace, omnigs_stream_t stream);
+
+/* Adjoint of omnigs_render_fwd (Sec. 3.4, the blending part of Eqs. 18-20): per pixel, back to front from its
+ * last contributor, recovering T by division by (1 - alpha). Writes grads [V * n] (device): dL/d(px, py, c0, c1,
+ * c2, opacity, r, g, b) of every splat, summed over the pixels it reaches. The derivative of alpha is 0 where it is
+ * clamped at 0.99. Inputs are those of omnigs_render_fwd plus its out_T, out_ncontrib and dL_drgb [V, 3, H, W]. */
+omnigs_status omnigs_render_bwd(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
+                                const uint32_t *ranges, const uint32_t *values, const float *out_T,
+                                const uint32_t *ncontrib, const float *dL_drgb, omnigs_splat_grad *grads,
+                                omnigs_stream_t stream);
+
+/* Adjoint of omnigs_preprocess (Sec. 3.4, Eqs. 18-20): chain rule from the splat gradients through conic,
+ * Sigma~ (dSigma~/dSigma), the spherical Jacobian (dJ/dt), p (dp/ds, ds/dt), t = W m + t_cw, R(q), S and the SH
+ * colour (dc/dm), summed over views. Same parameter inputs as omnigs_preprocess, plus grads [V * n].
+ *   d_means [n, 3], d_scales [n, 3], d_quats [n, 4], d_opacity [n], d_sh [n, K, 3]: outputs (device)
+ *   d_screen [n, 2]: dL/ds, the gradient with respect to the uniform screen-space position s of Eq. 4 (which
+ *   drives densification, Sec. 4), summed over views; output (device). */
+omnigs_status omnigs_preprocess_bwd(const omnigs_config *cfg, int64_t n, const float *means, const float *scales,
+                                    const float *quats, const float *opacity, const float *sh,
+                                    const float *viewmats, const omnigs_splat_grad *grads, float *d_means,
+                                    float *d_scales, float *d_quats, float *d_opacity, float *d_sh,
+                                    float *d_screen, omnigs_stream_t stream);
+
+/* Total instance count of the last omnigs_bin on this workspace (may exceed the capacity). Synchronises `stream`. */
+omnigs_status omnigs_instance_count(const void *workspace, int64_t *count, omnigs_stream_t stream);
+
+/* Returns and clears the sticky device-side error of the workspace (OMNIGS_OK if none), after synchronising
+ * `stream`; also reports a pending CUDA error as OMNIGS_E_CUDA. */
+omnigs_status omnigs_last_error(void *workspace, omnigs_stream_t stream);
+
+/* Kernel timing. While enabled, every kernel the library launches is bracketed by CUDA events on its launching
+ * stream. omnigs_profiler_collect synchronises those events, writes up to `max` per-kernel totals (launches and
+ * summed milliseconds, in first-launch order) and clears the record; it returns the number of kernels. Host-side
+ * state is global to the process and not thread-safe; use it from one thread, outside CUDA graph capture. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} omnigs_kernel_time;
+omnigs_status omnigs_profiler_enable(int enable);
+int omnigs_profiler_collect(omnigs_kernel_time *out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMNIGS_H */

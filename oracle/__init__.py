@@ -53,7 +53,7 @@ def _load():
         lib.orc_rect.argtypes = [f64, f64, i32, i32, i32, i32, P]
         lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P]
         lib.orc_count_instances.restype = i64
-        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
+        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P]
         lib.orc_bin_sort.restype = i64
         lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
@@ -148,17 +148,21 @@ def count_instances(splats: dict, V: int, width: int, height: int, tile: int) ->
     return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rad)))
 
 
-def bin_sort(splats: dict, V: int, width: int, height: int, tile: int):
-    """Instances sorted by (view, tile, t_r, Gaussian): returns ranges [V*tiles, 2] and the list of (v*N + g)."""
+def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None):
+    """Instances sorted by (view, tile, t_r, Gaussian): returns ranges [V*tiles, 2] and the list of (v*N + g).
+    With `tile_mask` ([V*tiles] bool), only the lists of the masked tiles are built."""
     lib = _load()
     px, py, depth = _f64(splats["px"]), _f64(splats["py"]), _f64(splats["depth"])
     rad = np.ascontiguousarray(splats["radius"], dtype=np.int32)
     n = px.shape[0] // V
     tiles = (width // tile) * (height // tile)
-    total = lib.orc_count_instances(V, n, width, height, tile, _p(px), _p(py), _p(rad))
+    mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
     ranges = np.zeros((V * tiles, 2), dtype=np.int64)
+    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rad), _p(depth), _p(ranges), None,
+                                 None if mask is None else _p(mask)))
     lst = np.zeros(max(total, 1), dtype=np.int64)
-    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rad), _p(depth), _p(ranges), _p(lst))
+    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rad), _p(depth), _p(ranges), _p(lst),
+                     None if mask is None else _p(mask))
     return ranges, lst[:total]
 
 

@@ -361,12 +361,30 @@ int64_t orc_count_instances(int V, int64_t n, int W, int H, int T, const double 
 }
 
 /* One instance per (Gaussian, covered tile); order by (view, tile), then t_r, then Gaussian index (the order a
- * stable sort by (tile, t_r) gives when instances are generated Gaussian by Gaussian). ranges: [V*TX*TY][2]. */
+ * stable sort by (tile, t_r) gives when instances are generated Gaussian by Gaussian). ranges: [V*TX*TY][2].
+ * tile_mask (optional, [V*TX*TY]): when given, only instances of tiles whose mask byte is non-zero are listed
+ * (the lists of those tiles are the same as without a mask). Returns the number of listed instances; with
+ * list_vg == NULL it only counts them. */
 int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                     const int32_t *radius, const double *depth, int64_t *ranges, int64_t *list_vg)
+                     const int32_t *radius, const double *depth, int64_t *ranges, int64_t *list_vg,
+                     const uint8_t *tile_mask)
 {
     int64_t TX = W / T, TY = H / T, tiles = TX * TY;
-    int64_t total = orc_count_instances(V, n, W, H, T, px, py, radius);
+    int64_t total = 0;
+    if (!tile_mask) {
+        total = orc_count_instances(V, n, W, H, T, px, py, radius);
+    } else {
+        for (int v = 0; v < V; v++)
+            for (int64_t g = 0; g < n; g++) {
+                int64_t i = v * n + g, r[4];
+                if (radius[i] <= 0) continue;
+                orc_rect(px[i], py[i], radius[i], W, H, T, r);
+                for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
+                    for (int64_t c = 0; c < r[1]; c++)
+                        total += tile_mask[v * tiles + ty * TX + ((r[0] + c) % TX + TX) % TX] != 0;
+            }
+    }
+    if (!list_vg) return total; /* count only */
     orc_inst *inst = (orc_inst *)malloc(sizeof(orc_inst) * (total > 0 ? total : 1));
     int64_t k = 0;
     for (int v = 0; v < V; v++)
@@ -378,6 +396,7 @@ int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, co
             for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
                 for (int64_t c = 0; c < r[1]; c++) {
                     int64_t tx = ((r[0] + c) % TX + TX) % TX;
+                    if (tile_mask && !tile_mask[v * tiles + ty * TX + tx]) continue;
                     inst[k].tile = v * tiles + ty * TX + tx;
                     inst[k].depth = depth[i];
                     inst[k].vg = i;

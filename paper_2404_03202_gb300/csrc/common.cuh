@@ -1,0 +1,121 @@
+// Shared device definitions of the sm_103a rasterizer: constants of the method, the tile rectangle of a splat,
+// the workspace layout and the kernel-launch helpers. Arithmetic of the individual stages lives in its own .cu file.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "omnigs.h"
+
+namespace omnigs {
+
+// Method constants (3DGS conventions the paper inherits, Sec. 3.3).
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kDilation = 0.3f;        // low-pass dilation added to the 2x2 covariance
+constexpr float kAlphaMax = 0.99f;       // alpha clamp
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTStop = 1e-4f;          // stop once accumulated alpha would reach 0.9999
+constexpr float kPoleGuard = 1e-6f;      // rho is kept >= 1e-6 t_r inside J
+constexpr int kMaxRadius = 1 << 24;      // radii beyond W + H change nothing; kept finite for integer maths
+
+constexpr uint32_t kErrCapacity = 1u;
+
+// Workspace header (first 256 bytes of every workspace).
+struct WsHeader {
+    unsigned long long count;  // total instances of the last bin (may exceed capacity)
+    unsigned int error;        // sticky device-side error bits
+    unsigned int pad0;
+    float loss;
+    unsigned int pad1[3];
+};
+
+struct Rect {
+    int x0, nx, y0, ny;
+};
+
+__host__ __device__ inline int floordiv_int(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+// Tiles covered by the square of half-side r around pixel floor(p): columns x0 .. x0 + nx - 1 modulo the column
+// count (all columns, from 0, once the square is at least as wide as the image), rows clipped to the image.
+__device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int tiles_y, int tile) {
+    Rect R;
+    int ix = (int)floorf(px), iy = (int)floorf(py);
+    int x0 = floordiv_int(ix - r, tile), x1 = floordiv_int(ix + r, tile);
+    int nx = x1 - x0 + 1;
+    if (nx >= tiles_x) {
+        x0 = 0;
+        nx = tiles_x;
+    }
+    int y0 = floordiv_int(iy - r, tile), y1 = floordiv_int(iy + r, tile);
+    y0 = y0 < 0 ? 0 : y0;
+    y1 = y1 > tiles_y - 1 ? tiles_y - 1 : y1;
+    R.x0 = x0;
+    R.nx = nx;
+    R.y0 = y0;
+    R.ny = y1 >= y0 ? y1 - y0 + 1 : 0;
+    return R;
+}
+
+// Workspace layout (all offsets 256-byte aligned).
+struct WsLayout {
+    size_t header, block_sums, block_offsets, alt_keys, alt_values, hist, loss_partials, total;
+    int bin_blocks, sort_blocks, loss_blocks;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr int kBinThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort tile
+constexpr int kSortRadixMax = 256;
+constexpr int kLossThreads = 256;
+constexpr int kLossBlocks = 1024;
+
+int num_sms();
+WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
+
+// Kernel launches report their name and stream to the optional profiler.
+struct ProfScope {
+    int slot;
+    cudaStream_t stream;
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+};
+
+// Stage launchers (defined in preprocess.cu, binsort.cu, render.cu). Each returns cudaGetLastError().
+cudaError_t launch_preprocess(const omnigs_config &cfg, int64_t n, const float *means, const float *scales,
+                              const float *quats, const float *opacity, const float *sh, const float *viewmats,
+                              omnigs_splat *splats, cudaStream_t stream);
+cudaError_t launch_preprocess_bwd(const omnigs_config &cfg, int64_t n, const float *means, const float *scales,
+                                  const float *quats, const float *opacity, const float *sh, const float *viewmats,
+                                  const omnigs_splat_grad *grads, float *d_means, float *d_scales, float *d_quats,
+                                  float *d_opacity, float *d_sh, float *d_screen, cudaStream_t stream);
+cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *offsets,
+                       uint64_t *keys, uint32_t *values, int64_t capacity, const WsLayout &L, char *ws,
+                       cudaStream_t stream);
+cudaError_t launch_sort(const omnigs_config &cfg, int64_t capacity, uint64_t *keys, uint32_t *values,
+                        uint32_t *ranges, const WsLayout &L, char *ws, cudaStream_t stream);
+cudaError_t launch_render_fwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
+                              const uint32_t *ranges, const uint32_t *values, float *out_rgb, float *out_T,
+                              uint32_t *out_nc, cudaStream_t stream);
+cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
+                              const uint32_t *ranges, const uint32_t *values, const float *out_T,
+                              const uint32_t *nc, const float *dL_drgb, omnigs_splat_grad *grads,
+                              cudaStream_t stream);
+cudaError_t launch_l1(const omnigs_config &cfg, const float *rgb, const float *target, float *dL_drgb, float *loss,
+                      const WsLayout &L, char *ws, cudaStream_t stream);
+
+// Radix-sort geometry: number of key bits in use, passes (even, so the result lands back in the caller's
+// buffers) and bits per pass (<= 8).
+struct SortPlan {
+    int bits, passes, digit_bits;
+};
+SortPlan sort_plan(const omnigs_config &cfg);
+
+}  // namespace omnigs

@@ -1,0 +1,269 @@
+// C-ABI entry points of the rasterizer: argument validation, workspace layout, the optional kernel profiler and the
+// dispatch to the stage launchers. See include/omnigs.h for the contract of every call.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace omnigs {
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 148;
+    return sms;
+}
+
+// Layout order: fixed-size regions, then those sized by the capacity, then those sized by n, so that calls which do
+// not take n (sort) or neither n nor the capacity (loss) find their regions at the same offsets.
+WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
+    WsLayout L;
+    const int64_t total = n * cfg.num_views;
+    L.bin_blocks = (int)std::max<int64_t>(1, (total + kBinThreads - 1) / kBinThreads);
+    const int64_t sort_tiles = (capacity + kSortTile - 1) / kSortTile;
+    L.sort_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sort_tiles, 2 * (int64_t)num_sms()));
+    L.loss_blocks = kLossBlocks;
+    size_t off = 0;
+    L.header = off;        off += align256(sizeof(WsHeader));
+    L.loss_partials = off; off += align256(sizeof(float) * L.loss_blocks);
+    L.hist = off;          off += align256(sizeof(unsigned) * kSortRadixMax * (size_t)L.sort_blocks);
+    L.alt_keys = off;      off += align256(sizeof(unsigned long long) * (size_t)capacity);
+    L.alt_values = off;    off += align256(sizeof(unsigned) * (size_t)capacity);
+    L.block_sums = off;    off += align256(sizeof(unsigned) * L.bin_blocks);
+    L.block_offsets = off; off += align256(sizeof(unsigned long long) * L.bin_blocks);
+    L.total = off;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------------------ profiler
+
+namespace {
+struct ProfRecord {
+    std::string name;
+    cudaEvent_t start, stop;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRecord> g_prof_records;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_pool;
+size_t g_prof_used = 0;
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return true;
+    return st != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+    if (!g_prof_on || capturing(s)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_used == g_prof_pool.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+        g_prof_pool.push_back({a, b});
+    }
+    auto ev = g_prof_pool[g_prof_used++];
+    g_prof_records.push_back({name, ev.first, ev.second});
+    slot = (int)g_prof_records.size() - 1;
+    cudaEventRecord(ev.first, s);
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof_records[slot].stop, stream);
+}
+
+}  // namespace omnigs
+
+using namespace omnigs;
+
+namespace {
+
+bool valid_cfg(const omnigs_config* c) {
+    if (!c) return false;
+    if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
+    if (c->width <= 0 || c->height <= 0 || c->width % c->tile || c->height % c->tile) return false;
+    if (c->width > (1 << 20) || c->height > (1 << 20)) return false;
+    if (c->num_views < 1 || c->num_views > 4096) return false;
+    if (c->sh_degree < 0 || c->sh_degree > 3) return false;
+    if (!std::isfinite(c->near_r) || c->near_r < 0.f) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(c->bg[i])) return false;
+    const uint64_t tiles = (uint64_t)(c->width / c->tile) * (uint64_t)(c->height / c->tile) * (uint64_t)c->num_views;
+    return tiles < (1ull << 31);
+}
+
+bool valid_n(const omnigs_config* c, int64_t n) {
+    return n >= 0 && (uint64_t)n * (uint64_t)c->num_views < (1ull << 32) && n < (1ll << 31);
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+omnigs_status from_cuda(cudaError_t e) { return e == cudaSuccess ? OMNIGS_OK : OMNIGS_E_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int omnigs_version(void) { return 100; }
+
+const char* omnigs_status_string(omnigs_status s) {
+    switch (s) {
+        case OMNIGS_OK: return "ok";
+        case OMNIGS_E_INVALID: return "invalid argument";
+        case OMNIGS_E_CAPACITY: return "instance capacity exceeded";
+        case OMNIGS_E_CUDA: return "CUDA error";
+        case OMNIGS_E_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+size_t omnigs_workspace_size(const omnigs_config* cfg, int64_t n, int64_t capacity) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return 0;
+    return ws_layout(*cfg, n, capacity).total;
+}
+
+omnigs_status omnigs_preprocess(const omnigs_config* cfg, int64_t n, const float* means, const float* scales,
+                                const float* quats, const float* opacity, const float* sh, const float* viewmats,
+                                omnigs_splat* splats, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!means || !scales || !quats || !opacity || !sh || !viewmats || !splats) return OMNIGS_E_INVALID;
+    if (!aligned(quats, 16) || !aligned(splats, 16)) return OMNIGS_E_INVALID;
+    return from_cuda(launch_preprocess(*cfg, n, means, scales, quats, opacity, sh, viewmats, splats,
+                                       (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats, uint32_t* offsets,
+                         uint64_t* keys, uint32_t* values, int64_t capacity, void* workspace,
+                         omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
+    if (!offsets || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, n, capacity);
+    return from_cuda(launch_bin(*cfg, n, splats, offsets, keys, values, capacity, L, (char*)workspace,
+                                (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t capacity, uint64_t* keys, uint32_t* values,
+                          uint32_t* ranges, void* workspace, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
+    if (!ranges || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, 0, capacity);  // the sort's regions do not depend on n
+    return from_cuda(launch_sort(*cfg, capacity, keys, values, ranges, L, (char*)workspace, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_render_fwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
+                                const uint32_t* ranges, const uint32_t* values, float* out_rgb, float* out_T,
+                                uint32_t* out_ncontrib, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (!ranges || !out_rgb || !out_T || !out_ncontrib) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !values || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, values, out_rgb, out_T, out_ncontrib,
+                                       (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_l1_loss(const omnigs_config* cfg, const float* rgb, const float* target, float* dL_drgb,
+                             float* loss, void* workspace, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg)) return OMNIGS_E_INVALID;
+    if (!rgb || !target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (!aligned(rgb, 16) || !aligned(target, 16) || !aligned(dL_drgb, 16)) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, 0, 0);  // header and loss partials sit at fixed offsets
+    return from_cuda(launch_l1(*cfg, rgb, target, dL_drgb, loss, L, (char*)workspace, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
+                                const uint32_t* ranges, const uint32_t* values, const float* out_T,
+                                const uint32_t* ncontrib, const float* dL_drgb, omnigs_splat_grad* grads,
+                                omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (!ranges || !out_T || !ncontrib || !dL_drgb) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !values || !grads || !aligned(splats, 16) || !aligned(grads, 16))) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    return from_cuda(launch_render_bwd(*cfg, n, splats, ranges, values, out_T, ncontrib, dL_drgb, grads,
+                                       (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_preprocess_bwd(const omnigs_config* cfg, int64_t n, const float* means, const float* scales,
+                                    const float* quats, const float* opacity, const float* sh,
+                                    const float* viewmats, const omnigs_splat_grad* grads, float* d_means,
+                                    float* d_scales, float* d_quats, float* d_opacity, float* d_sh,
+                                    float* d_screen, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!means || !scales || !quats || !opacity || !sh || !viewmats || !grads) return OMNIGS_E_INVALID;
+    if (!d_means || !d_scales || !d_quats || !d_opacity || !d_sh || !d_screen) return OMNIGS_E_INVALID;
+    if (!aligned(quats, 16) || !aligned(grads, 16) || !aligned(d_quats, 16) || !aligned(d_screen, 8))
+        return OMNIGS_E_INVALID;
+    return from_cuda(launch_preprocess_bwd(*cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means,
+                                           d_scales, d_quats, d_opacity, d_sh, d_screen, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_instance_count(const void* workspace, int64_t* count, omnigs_stream_t stream) {
+    if (!workspace || !count || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    WsHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return OMNIGS_E_CUDA;
+    *count = (int64_t)h.count;
+    return OMNIGS_OK;
+}
+
+omnigs_status omnigs_last_error(void* workspace, omnigs_stream_t stream) {
+    if (!workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    WsHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return OMNIGS_E_CUDA;
+    if (h.error == 0) return OMNIGS_OK;
+    const unsigned zero = 0;
+    e = cudaMemcpyAsync((char*)workspace + offsetof(WsHeader, error), &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                        (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (h.error & kErrCapacity) return OMNIGS_E_CAPACITY;
+    return OMNIGS_E_TIMEOUT;
+}
+
+omnigs_status omnigs_profiler_enable(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+    return OMNIGS_OK;
+}
+
+int omnigs_profiler_collect(omnigs_kernel_time* out, int max) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<omnigs_kernel_time> agg;
+    for (auto& r : g_prof_records) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&ms, r.start, r.stop) != cudaSuccess)
+            ms = 0.f;
+        size_t k = 0;
+        while (k < agg.size() && std::strncmp(agg[k].name, r.name.c_str(), sizeof(agg[k].name)) != 0) ++k;
+        if (k == agg.size()) {
+            omnigs_kernel_time t;
+            std::memset(&t, 0, sizeof(t));
+            std::strncpy(t.name, r.name.c_str(), sizeof(t.name) - 1);
+            agg.push_back(t);
+        }
+        agg[k].launches += 1;
+        agg[k].total_ms += ms;
+    }
+    g_prof_records.clear();
+    g_prof_used = 0;
+    const int m = (int)std::min<size_t>(agg.size(), (size_t)std::max(max, 0));
+    for (int i = 0; i < m; ++i) out[i] = agg[i];
+    return (int)agg.size();
+}
+
+}  // extern "C"

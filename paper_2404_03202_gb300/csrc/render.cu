@@ -1,0 +1,377 @@
+// Tile-based alpha blending onto the equirectangular image (Sec. 3.3, Eqs. 6-8) and its adjoint (Sec. 3.4).
+//
+// One CTA per (view, tile), one thread per pixel. The tile's sorted instance list is walked in batches of one
+// entry per thread: each thread gathers one splat (two 16-byte loads and one 4-byte load) into shared memory, with
+// the conic pre-scaled by -log2(e)/2 so that G = 2^(dx (c0' dx + c1' dy) + c2' dy^2) costs one ex2 on the SFU, and
+// with the longitude-seam shift decided once per (entry, tile): 0 or +-W for the whole tile, or a flag for the rare
+// splat whose minimal-image boundary falls inside the tile. The CTA leaves the list as soon as every pixel has
+// stopped (__syncthreads_count).
+//
+// The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
+// (1 - alpha), reduces the 9 per-pixel partial derivatives of an entry over each warp with shuffles (skipped when no
+// lane of the warp touched the entry), then over the CTA in shared memory, and adds the CTA's sum to the splat's
+// gradient with 16-byte vector atomics (red.global.add.v4.f32). Forward and adjoint evaluate alpha with the same
+// inlined function, so their skip / stop decisions agree.
+#include "common.cuh"
+
+namespace omnigs {
+namespace {
+
+constexpr float kPerPixelWrap = 1.0f;  // seam-shift value meaning "wrap per pixel" (real shifts are 0 or +-W)
+
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct Staged {
+    float4 a;  // px, py, c0', c1'   (c' = conic scaled to base-2 exponent)
+    float4 b;  // c2', opacity, r, g
+    float2 c;  // b, seam shift
+};
+
+__device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats, unsigned vg, float x_first,
+                                              float x_last, float halfW, float fW) {
+    const float4 a = __ldg(splats + 3 * (size_t)vg);
+    const float4 b = __ldg(splats + 3 * (size_t)vg + 1);
+    const float blue = __ldg(reinterpret_cast<const float*>(splats + 3 * (size_t)vg + 2));
+    const float hi = a.x - x_first, lo = a.x - x_last;  // extreme dx over the tile's pixel columns
+    float shift;
+    if (lo >= -halfW && hi < halfW) shift = 0.f;
+    else if (lo >= halfW) shift = -fW;
+    else if (hi < -halfW) shift = fW;
+    else shift = kPerPixelWrap;
+    Staged s;
+    s.a = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
+    s.b = make_float4(-0.5f * kLog2e * b.x, b.y, b.z, b.w);
+    s.c = make_float2(blue, shift);
+    return s;
+}
+
+struct PairEval {
+    float dx, dy, G, raw, alpha;
+    bool skip;
+};
+
+// Eqs. 7-8 for one (pixel, entry): minimal-image dx, exponent, G, alpha and the skip decision.
+__device__ __forceinline__ PairEval eval_pair(const float4& A, const float4& B, float shift, float xs, float ys,
+                                              float halfW, float fW) {
+    PairEval e;
+    float dx = A.x - xs;
+    if (shift != kPerPixelWrap) {
+        dx += shift;
+    } else {
+        if (dx >= halfW) dx -= fW;
+        else if (dx < -halfW) dx += fW;
+    }
+    const float dy = A.y - ys;
+    const float p2 = fmaf(dx, fmaf(A.z, dx, A.w * dy), B.x * dy * dy);
+    e.dx = dx;
+    e.dy = dy;
+    e.G = fast_ex2(p2);
+    e.raw = B.y * e.G;
+    e.alpha = fminf(kAlphaMax, e.raw);
+    e.skip = (p2 > 0.f) || (e.alpha < kAlphaMin);
+    return e;
+}
+
+template <int TS>
+__global__ void __launch_bounds__(TS * TS)
+render_fwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
+                  const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                  const uint32_t* __restrict__ values, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                  uint32_t* __restrict__ out_nc) {
+    constexpr int NT = TS * TS;
+    __shared__ float4 s_a[NT];
+    __shared__ float4 s_b[NT];
+    __shared__ float2 s_c[NT];
+    const int tile_id = blockIdx.x;
+    const int v = tile_id / tiles, t = tile_id - v * tiles;
+    const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
+    const int x = txi * TS + (int)threadIdx.x % TS, y = tyi * TS + (int)threadIdx.x / TS;
+    const float xs = x + 0.5f, ys = y + 0.5f;
+    const float halfW = 0.5f * (float)W, fW = (float)W;
+    const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
+    const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0;
+    int done = 0;
+    for (uint32_t b = start; b < end; b += NT) {
+        if (__syncthreads_count(done) == NT) break;
+        const uint32_t s = b + threadIdx.x;
+        if (s < end) {
+            const Staged st = stage_entry(splats, __ldg(values + s), x_first, x_last, halfW, fW);
+            s_a[threadIdx.x] = st.a;
+            s_b[threadIdx.x] = st.b;
+            s_c[threadIdx.x] = st.c;
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)NT, end - b);
+        for (int j = 0; j < nb && !done; ++j) {
+            const float4 A = s_a[j];
+            const float4 B = s_b[j];
+            const float2 Cc = s_c[j];
+            const PairEval e = eval_pair(A, B, Cc.y, xs, ys, halfW, fW);
+            if (e.skip) continue;
+            const float Tn = T * (1.f - e.alpha);
+            if (Tn < kTStop) {
+                done = 1;
+                break;
+            }
+            const float w = e.alpha * T;
+            C0 = fmaf(w, B.z, C0);
+            C1 = fmaf(w, B.w, C1);
+            C2 = fmaf(w, Cc.x, C2);
+            T = Tn;
+            last = b - start + j + 1;
+        }
+    }
+    const size_t HW = (size_t)H * W;
+    const size_t pix = (size_t)y * W + x;
+    out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(T, bg0, C0);
+    out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(T, bg1, C1);
+    out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T, bg2, C2);
+    out_T[(size_t)v * HW + pix] = T;
+    out_nc[(size_t)v * HW + pix] = last;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+constexpr int kGradFields = 9;
+
+template <int TS>
+__global__ void __launch_bounds__(TS * TS)
+render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
+                  const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                  const uint32_t* __restrict__ values, const float* __restrict__ out_T,
+                  const uint32_t* __restrict__ ncontrib, const float* __restrict__ dL_drgb,
+                  float4* __restrict__ grads) {
+    constexpr int NT = TS * TS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s_a = reinterpret_cast<float4*>(smem_raw);
+    float4* s_b = s_a + NT;
+    float4* s_k = s_b + NT;                            // raw conic c0, c1, c2 and blue
+    float* s_shift = reinterpret_cast<float*>(s_k + NT);
+    unsigned* s_vg = reinterpret_cast<unsigned*>(s_shift + NT);
+    float* s_acc = reinterpret_cast<float*>(s_vg + NT);  // [NT][kGradFields]
+    __shared__ unsigned s_max;
+
+    const int tile_id = blockIdx.x;
+    const int v = tile_id / tiles, t = tile_id - v * tiles;
+    const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
+    const int x = txi * TS + (int)threadIdx.x % TS, y = tyi * TS + (int)threadIdx.x / TS;
+    const float xs = x + 0.5f, ys = y + 0.5f;
+    const float halfW = 0.5f * (float)W, fW = (float)W;
+    const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
+    const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
+    const size_t HW = (size_t)H * W;
+    const size_t pix = (size_t)y * W + x;
+    const uint32_t last = min(ncontrib[(size_t)v * HW + pix], len);
+    float T = out_T[(size_t)v * HW + pix];
+    const float g0 = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
+    const float g1 = dL_drgb[(3 * (size_t)v + 1) * HW + pix];
+    const float g2 = dL_drgb[(3 * (size_t)v + 2) * HW + pix];
+    float B0 = bg0, B1 = bg1, B2 = bg2;  // colour behind the current entry, per unit of its transmittance
+
+    if (threadIdx.x == 0) s_max = 0;
+    for (int i = threadIdx.x; i < NT * kGradFields; i += NT) s_acc[i] = 0.f;
+    __syncthreads();
+    atomicMax(&s_max, last);
+    __syncthreads();
+    const uint32_t maxlast = s_max;
+    const unsigned lane = threadIdx.x & 31;
+
+    for (int64_t bend = (int64_t)maxlast; bend > 0; bend -= NT) {
+        const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
+        const int nb = (int)(bend - bbeg);
+        if ((int)threadIdx.x < nb) {
+            const unsigned vg = __ldg(values + start + bbeg + threadIdx.x);
+            const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
+            const float4 raw0 = __ldg(splats + 3 * (size_t)vg);
+            const float4 raw1 = __ldg(splats + 3 * (size_t)vg + 1);
+            s_a[threadIdx.x] = st.a;
+            s_b[threadIdx.x] = st.b;
+            s_k[threadIdx.x] = make_float4(raw0.z, raw0.w, raw1.x, st.c.x);
+            s_shift[threadIdx.x] = st.c.y;
+            s_vg[threadIdx.x] = vg;
+        }
+        __syncthreads();
+        for (int j = nb - 1; j >= 0; --j) {
+            const uint32_t pos = (uint32_t)(bbeg + j);  // position in the tile list
+            const float4 A = s_a[j];
+            const float4 Bv = s_b[j];
+            const float4 K = s_k[j];
+            float gv[kGradFields];
+            bool contrib = false;
+            if (pos < last) {
+                const PairEval e = eval_pair(A, Bv, s_shift[j], xs, ys, halfW, fW);
+                if (!e.skip) {
+                    contrib = true;
+                    const float one_m = 1.f - e.alpha;
+                    T = T / one_m;  // transmittance in front of this entry
+                    const float cr = Bv.z, cg = Bv.w, cb = K.w;
+                    const float dalpha = T * (g0 * (cr - B0) + g1 * (cg - B1) + g2 * (cb - B2));
+                    const float w = e.alpha * T;
+                    gv[6] = w * g0;
+                    gv[7] = w * g1;
+                    gv[8] = w * g2;
+                    B0 = fmaf(e.alpha, cr, one_m * B0);
+                    B1 = fmaf(e.alpha, cg, one_m * B1);
+                    B2 = fmaf(e.alpha, cb, one_m * B2);
+                    if (e.raw < kAlphaMax) {
+                        gv[5] = dalpha * e.G;
+                        const float gp = dalpha * e.raw;  // dL/d(exponent)
+                        const float dx = e.dx, dy = e.dy;
+                        gv[2] = -0.5f * dx * dx * gp;
+                        gv[3] = -dx * dy * gp;
+                        gv[4] = -0.5f * dy * dy * gp;
+                        gv[0] = -(K.x * dx + K.y * dy) * gp;
+                        gv[1] = -(K.z * dy + K.y * dx) * gp;
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < 6; ++f) gv[f] = 0.f;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                if (!contrib) {
+#pragma unroll
+                    for (int f = 0; f < kGradFields; ++f) gv[f] = 0.f;
+                }
+#pragma unroll
+                for (int f = 0; f < kGradFields; ++f) gv[f] = warp_sum(gv[f]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int f = 0; f < kGradFields; ++f) atomicAdd(&s_acc[j * kGradFields + f], gv[f]);
+                }
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            float* acc = s_acc + threadIdx.x * kGradFields;
+            bool any = false;
+#pragma unroll
+            for (int f = 0; f < kGradFields; ++f) any |= (acc[f] != 0.f);
+            if (any) {
+                float4* gdst = grads + 3 * (size_t)s_vg[threadIdx.x];
+                atomicAdd(gdst, make_float4(acc[0], acc[1], acc[2], acc[3]));
+                atomicAdd(gdst + 1, make_float4(acc[4], acc[5], acc[6], acc[7]));
+                atomicAdd(reinterpret_cast<float*>(gdst + 2), acc[8]);
+            }
+#pragma unroll
+            for (int f = 0; f < kGradFields; ++f) acc[f] = 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+size_t bwd_smem(int nt) { return (size_t)nt * (3 * sizeof(float4) + sizeof(float) + sizeof(unsigned) + kGradFields * sizeof(float)); }
+
+template <int TS>
+cudaError_t render_fwd_t(const omnigs_config& cfg, const omnigs_splat* splats, const uint32_t* ranges,
+                         const uint32_t* values, float* out_rgb, float* out_T, uint32_t* out_nc, cudaStream_t stream) {
+    const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
+    ProfScope prof("render_fwd", stream);
+    render_fwd_kernel<TS><<<tiles * cfg.num_views, TS * TS, 0, stream>>>(
+        cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
+        ranges, values, out_rgb, out_T, out_nc);
+    return cudaGetLastError();
+}
+
+template <int TS>
+cudaError_t render_bwd_t(const omnigs_config& cfg, const omnigs_splat* splats, const uint32_t* ranges,
+                         const uint32_t* values, const float* out_T, const uint32_t* nc, const float* dL_drgb,
+                         omnigs_splat_grad* grads, cudaStream_t stream) {
+    const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
+    const size_t smem = bwd_smem(TS * TS);
+    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope prof("render_bwd", stream);
+    render_bwd_kernel<TS><<<tiles * cfg.num_views, TS * TS, smem, stream>>>(
+        cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
+        ranges, values, out_T, nc, dL_drgb, reinterpret_cast<float4*>(grads));
+    return cudaGetLastError();
+}
+
+// mean |rgb - target| and its gradient; float4 over the [V, 3, H, W] buffers (size a multiple of 4)
+__global__ void __launch_bounds__(kLossThreads)
+l1_kernel(size_t n4, const float4* __restrict__ rgb, const float4* __restrict__ target, float4* __restrict__ dL,
+          float inv_total, float* __restrict__ partials) {
+    float acc = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(rgb + i), b = __ldg(target + i);
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        auto sg = [inv_total](float d) { return d > 0.f ? inv_total : (d < 0.f ? -inv_total : 0.f); };
+        dL[i] = make_float4(sg(d0), sg(d1), sg(d2), sg(d3));
+    }
+    __shared__ float red[kLossThreads / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < kLossThreads / 32; ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void l1_finish_kernel(const float* __restrict__ partials, int nb, float inv_total, float* __restrict__ loss) {
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += partials[i];
+        *loss = (float)(s * inv_total);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
+                              const uint32_t* ranges, const uint32_t* values, float* out_rgb, float* out_T,
+                              uint32_t* out_nc, cudaStream_t stream) {
+    (void)n;
+    switch (cfg.tile) {
+        case 8: return render_fwd_t<8>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
+        case 32: return render_fwd_t<32>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
+        default: return render_fwd_t<16>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
+    }
+}
+
+cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
+                              const uint32_t* ranges, const uint32_t* values, const float* out_T,
+                              const uint32_t* nc, const float* dL_drgb, omnigs_splat_grad* grads,
+                              cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(omnigs_splat_grad) * (size_t)n * cfg.num_views, stream);
+    if (e != cudaSuccess) return e;
+    switch (cfg.tile) {
+        case 8: return render_bwd_t<8>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
+        case 32: return render_bwd_t<32>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
+        default: return render_bwd_t<16>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
+    }
+}
+
+cudaError_t launch_l1(const omnigs_config& cfg, const float* rgb, const float* target, float* dL_drgb, float* loss,
+                      const WsLayout& L, char* ws, cudaStream_t stream) {
+    const size_t total = (size_t)cfg.num_views * 3 * cfg.height * cfg.width;
+    const float inv = (float)(1.0 / (double)total);
+    float* partials = reinterpret_cast<float*>(ws + L.loss_partials);
+    {
+        ProfScope prof("l1_loss", stream);
+        l1_kernel<<<L.loss_blocks, kLossThreads, 0, stream>>>(total / 4, reinterpret_cast<const float4*>(rgb),
+                                                              reinterpret_cast<const float4*>(target),
+                                                              reinterpret_cast<float4*>(dL_drgb), inv, partials);
+    }
+    {
+        ProfScope prof("l1_finish", stream);
+        l1_finish_kernel<<<1, 32, 0, stream>>>(partials, L.loss_blocks, inv, loss);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace omnigs

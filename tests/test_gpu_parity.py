@@ -1,0 +1,229 @@
+"""GPU path vs the FP64 oracle, stage by stage and end to end, through the C ABI (marked gpu).
+
+Tolerances (written in each test):
+  * tile lists and sort order: bit-exact, given identical splats;
+  * blended images: |dC| <= 1e-5 per channel, given identical splats, outside pixels where a skip / stop decision
+    lies within 1e-5 (relative) of its threshold (the oracle flags them; at most 1e-3 of the pixels);
+  * blend and preprocess gradients: normwise relative error <= 1e-4 and elementwise <= 1e-4 * max|g*|;
+  * preprocess outputs (FP32 vs FP64 from identical parameters): see test_preprocess_matches_oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import assert_grad_close, dev, normwise, pack_splats, scene_to_device, unpack_splats
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2404_03202_gb300 as og  # noqa: E402
+from paper_2404_03202_gb300 import _cabi as C  # noqa: E402
+
+
+def _settings(W, H, tile=16, V=1, deg=3, bg=(0.0, 0.0, 0.0)):
+    return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=deg, bg=bg)
+
+
+def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):
+    """bin + sort + render_fwd on given splats (numpy [V*n, 12])."""
+    r = og.Rasterizer(s, capacity=capacity)
+    m = sp_packed.shape[0]
+    n = m // s.num_views
+    r._ensure(n, (s.sh_degree + 1) ** 2)
+    r.splats.copy_(dev(sp_packed))
+    C.omnigs_bin(r.cfg, n, r.splats, r.offsets, r.keys, r.values, r.capacity, r.ws)
+    cnt = r.instance_count()
+    if cnt > r.capacity:
+        r._alloc_instances(cnt)
+        r._ensure(n, (s.sh_degree + 1) ** 2)
+        r.splats.copy_(dev(sp_packed))
+        C.omnigs_bin(r.cfg, n, r.splats, r.offsets, r.keys, r.values, r.capacity, r.ws)
+    C.omnigs_sort(r.cfg, r.capacity, r.keys, r.values, r.ranges, r.ws)
+    C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.values, r.rgb, r.T, r.ncontrib)
+    torch.cuda.synchronize()
+    assert r.check() is None
+    return r, cnt
+
+
+# ------------------------------------------------------------------ S1 preprocess
+
+@pytest.mark.parametrize("deg", [3, 1])
+def test_preprocess_matches_oracle(deg):
+    W, H = 512, 256
+    sc = synth.shell_scene(10000, seed=1, sh_degree=deg)
+    vm = np.concatenate([synth.identity_viewmats(1), synth.random_viewmats(2, 5)])
+    s = _settings(W, H, V=3, deg=deg)
+    r = og.Rasterizer(s)
+    params = scene_to_device(sc)
+    r._ensure(sc.n, sc.sh.shape[1])
+    C.omnigs_preprocess(r.cfg, sc.n, *params, dev(vm), r.splats)
+    got = unpack_splats(r.splats.cpu().numpy())
+    rec = oracle.preprocess(sc, vm, W, H)
+    ref = oracle.splats_from_records(rec)
+    # culling agrees except within 1e-6 (relative) of the near distance
+    near_edge = np.abs(ref["depth"] - 0.2) < 1e-6 * 0.2
+    alive = ref["radius"] > 0
+    assert np.array_equal((got["radius"] > 0)[~near_edge], alive[~near_edge])
+    a = alive & (got["radius"] > 0)
+    np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6)
+    # p: atan2f / asinf carry a few ulp of the angle (< 1e-6 rad here); times W/(2 pi) and H/pi px per radian;
+    # longitude differences are taken across the seam
+    dpx = (got["px"][a] - ref["px"][a] + W / 2) % W - W / 2
+    dpy = got["py"][a] - ref["py"][a]
+    print(f"preprocess: max|dpx| {np.abs(dpx).max():.3e} max|dpy| {np.abs(dpy).max():.3e}")
+    assert np.abs(dpx).max() <= 2e-6 * W and np.abs(dpy).max() <= 2e-6 * H
+    # conic: relative to its norm; the FP32 determinant is formed without cancellation
+    cg = np.stack([got["c0"], got["c1"], got["c2"]], 1)[a]
+    cr = np.stack([ref["c0"], ref["c1"], ref["c2"]], 1)[a]
+    cerr = np.abs(cg - cr).max(1) / np.abs(cr).max(1)
+    print(f"preprocess: conic max rel {cerr.max():.3e}")
+    assert cerr.max() <= 1e-4
+    rgb_err = max(np.abs(got[k][a] - ref[k][a]).max() for k in ("r", "g", "b"))
+    print(f"preprocess: rgb max abs {rgb_err:.3e}")
+    assert rgb_err <= 1e-5
+    assert np.array_equal(got["opacity"][a], sc.opacity[np.nonzero(a)[0] % sc.n])
+    # radius = ceil(3 sqrt(lambda_max)): exact unless 3 sqrt(lambda) is within 1e-4 of an integer
+    margin_ok = rec[:, oracle.R_RMARGIN][a] > 1e-4 * np.maximum(1.0, ref["radius"][a])
+    assert np.array_equal(got["radius"][a][margin_ok], ref["radius"][a][margin_ok])
+
+
+# ------------------------------------------------------------------ S2-S4 bin, sort, ranges
+
+@pytest.mark.parametrize("tile,V,n", [(16, 2, 3000), (8, 1, 1500), (32, 3, 1000)])
+def test_bin_sort_bitexact(tile, V, n):
+    W, H = 256, 128
+    sp = synth.random_splats(V, n, W, H, seed=100 + tile, max_radius=30)
+    packed = pack_splats(sp)
+    s = _settings(W, H, tile=tile, V=V)
+    r, cnt = _run_splats(packed, s)
+    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
+    assert cnt == len(list_ref)
+    # offsets: exclusive prefix of per-splat instance counts
+    per = np.array([0 if sp["radius"][i] <= 0 else
+                    np.prod(oracle.rect(sp["px"][i], sp["py"][i], sp["radius"][i], W, H, tile)[1::2])
+                    for i in range(V * n)])
+    off = r.offsets.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(off[:-1], np.concatenate([[0], np.cumsum(per)[:-1]])) and off[-1] == per.sum()
+    ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    assert np.array_equal(ranges, ranges_ref)
+    vals = r.values[:cnt].cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(vals, list_ref)
+    keys = r.keys[:cnt].cpu().numpy().view(np.uint64)
+    depth_bits = sp["depth"].view(np.uint32).astype(np.uint64)
+    assert np.array_equal(keys & np.uint64(0x7FFFFFFF), depth_bits[vals])
+
+
+def test_sort_many_ties_and_all_columns():
+    """Every splat at one depth (order decided by index alone) and some wider than the image."""
+    W, H, V, n = 128, 64, 2, 800
+    sp = synth.random_splats(V, n, W, H, seed=9, max_radius=20, wide_frac=0.2)
+    sp["depth"][:] = np.float32(3.0)
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, V=V))
+    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, 16)
+    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_ref)
+    assert np.array_equal(r.values[:cnt].cpu().numpy().view(np.uint32), list_ref)
+
+
+# ------------------------------------------------------------------ S5 render forward
+
+def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0)):
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V, bg=bg))
+    sp64 = {k: (np.asarray(v, np.float64) if k != "radius" else v) for k, v in sp.items()}
+    ranges, lst = oracle.bin_sort(sp64, V, W, H, tile)
+    rgb, T, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5)
+    return r, (rgb, T, nc, near), (ranges, lst, sp64)
+
+
+@pytest.mark.parametrize("tile,V", [(16, 2), (8, 1), (32, 1)])
+def test_render_fwd_matches_oracle(tile, V):
+    W, H = 256, 128
+    sp = synth.random_splats(V, 2500, W, H, seed=200 + tile, max_radius=24)
+    bg = (0.25, 0.5, 0.75)
+    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, tile, bg)
+    mask = (near & 1) == 0
+    frac = 1.0 - mask.mean()
+    got = r.rgb.cpu().numpy()
+    err = np.abs(got - rgb).max(axis=1)[mask]
+    print(f"render_fwd tile {tile}: max|dC| {err.max():.3e}, masked {frac:.2e}, mean T {T.mean():.3f}")
+    assert frac <= 1e-3
+    assert err.max() <= 1e-5
+    assert np.abs(r.T.cpu().numpy() - T)[mask].max() <= 1e-5
+    assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+
+
+def test_render_fwd_opaque_stacks_stop_rule():
+    """Dense opaque splats: most pixels stop at T < 1e-4 (the 0.9999 rule)."""
+    W, H, V = 128, 64, 1
+    sp = synth.random_splats(V, 3000, W, H, seed=3, max_radius=16, opacity_range=(0.9, 1.0), cull_frac=0.0)
+    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, 16)
+    mask = (near & 1) == 0
+    assert (T[mask] < 1e-2).mean() > 0.5
+    assert np.abs(r.rgb.cpu().numpy() - rgb).max(axis=1)[mask].max() <= 1e-5
+    assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+
+
+# ------------------------------------------------------------------ S7 render backward
+
+@pytest.mark.parametrize("tile,V,opac", [(16, 2, (0.05, 0.99)), (8, 1, (0.5, 1.0)), (32, 1, (0.05, 0.99))])
+def test_render_bwd_matches_oracle(tile, V, opac):
+    W, H = 256, 128
+    sp = synth.random_splats(V, 2000, W, H, seed=300 + tile, max_radius=24, opacity_range=opac)
+    bg = (0.1, 0.2, 0.3)
+    r, (rgb, T, nc, near), (ranges, lst, sp64) = _fwd_compare(sp, V, W, H, tile, bg)
+    g = synth.random_image_grad(V, W, H, 7)
+    g[np.repeat((near != 0)[:, None], 3, axis=1)] = 0.0  # pixels near a decision threshold carry no gradient
+    ref = oracle.blend_bwd(sp64, ranges, lst, g.astype(np.float64), V, W, H, tile, bg)
+    got = r.backward_2d(dev(g)).cpu().numpy()
+    for j, name in enumerate(["px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b"]):
+        nw, el = assert_grad_close(got[:, j], ref[:, j], name)
+        print(f"render_bwd tile {tile} {name}: normwise {nw:.2e} elementwise {el:.2e}")
+    assert np.all(got[:, 9:] == 0)
+
+
+# ------------------------------------------------------------------ S8 preprocess backward
+
+@pytest.mark.parametrize("deg", [3, 0])
+def test_preprocess_bwd_matches_oracle(deg):
+    W, H = 512, 256
+    sc = synth.shell_scene(4000, seed=11, sh_degree=deg)
+    vm = np.concatenate([synth.identity_viewmats(1), synth.random_viewmats(1, 12)])
+    V = vm.shape[0]
+    rng = np.random.default_rng(13)
+    g2 = rng.normal(size=(V * sc.n, 9))
+    g2[:, 2:5] *= 10.0  # conic gradients are larger in practice (dL/dconic ~ dx^2 dL/dpower)
+    s = _settings(W, H, V=V, deg=deg)
+    r = og.Rasterizer(s)
+    params = scene_to_device(sc)
+    r._ensure(sc.n, sc.sh.shape[1])
+    grads = np.zeros((V * sc.n, 12), np.float32)
+    grads[:, :9] = g2
+    r.grads2d.copy_(dev(grads))
+    r._params = (*params, dev(vm))
+    C.omnigs_preprocess_bwd(r.cfg, sc.n, *params, dev(vm), r.grads2d, r.d_means, r.d_scales, r.d_quats,
+                            r.d_opacity, r.d_sh, r.d_screen)
+    ref = oracle.preprocess_bwd(sc, vm, grads[:, :9].astype(np.float64), W, H)
+    for name, got in [("means", r.d_means), ("scales", r.d_scales), ("quats", r.d_quats), ("opacity", r.d_opacity),
+                      ("sh", r.d_sh), ("screen", r.d_screen)]:
+        nw, el = assert_grad_close(got.cpu().numpy(), ref[name], name, rel=1e-4)
+        print(f"preprocess_bwd {name}: normwise {nw:.2e} elementwise {el:.2e}")
+
+
+# ------------------------------------------------------------------ S6 loss
+
+def test_l1_loss_matches_numpy():
+    W, H, V = 256, 128, 2
+    rgb = synth.random_image(V, W, H, 1)
+    tgt = synth.random_image(V, W, H, 2)
+    tgt[0, 0, :4, :4] = rgb[0, 0, :4, :4]  # equal entries: zero gradient
+    r = og.Rasterizer(_settings(W, H, V=V))
+    r._ensure(1, 16)
+    r.rgb.copy_(dev(rgb))
+    loss = r.l1_loss(dev(tgt)).item()
+    d = rgb.astype(np.float64) - tgt
+    assert abs(loss - np.abs(d).mean()) <= 1e-6 * np.abs(d).mean()
+    exp = np.sign(d) / d.size
+    assert np.array_equal(r.dL_drgb.cpu().numpy(), exp.astype(np.float32))
