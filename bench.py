@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--workload", default="egocentric", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -274,6 +275,8 @@ def main():
     # ---------------------------------------------------------------- graph replay of the same step
     graph_ms = None
     try:
+        if args.no_graph:
+            raise RuntimeError("skipped (--no-graph)")
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
