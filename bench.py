@@ -30,6 +30,7 @@ import synth  # noqa: E402
 WORKLOADS = {
     # name: (n, views, W, H, tile, scene builder, pose builder)
     "egocentric": dict(n=1_000_000, views=8, width=2048, height=1024, tile=16, scene="room"),
+    "egocentric-1view": dict(n=1_000_000, views=1, width=2048, height=1024, tile=16, scene="room"),
     "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
 }
 
