@@ -100,23 +100,24 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
 /* Tile binning, Sec. 3.3 ("one instance per influence"): for every splat with radius > 0, one instance per tile
  * covered by the square of half-side `radius` around pixel floor(p). Tile columns wrap modulo W / tile (the
  * longitude seam; a square at least as wide as the image covers every column once); rows are clipped to the image.
- *   splats   [V * n] input (device)
- *   offsets  [V * n + 1] output (device): exclusive prefix sum of per-splat instance counts; offsets[V * n] = total
- *   keys, values [capacity] output (device): instance i of splat j = v * n + g gets
- *            keys[i] = ((v * TILES + tile) << 31) | (float bits of depth), values[i] = j,
- *            where TILES = (W / tile) * (H / tile) and instances of a splat are listed row by row, columns in
- *            seam order. The total stays on the device (workspace); if it exceeds `capacity`, only the first
- *            `capacity` instances are written and OMNIGS_E_CAPACITY is raised in the workspace.
- *   capacity must be < 2^32 and equal to the value given to omnigs_workspace_size. */
-omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *offsets,
-                         uint64_t *keys, uint32_t *values, int64_t capacity, void *workspace, omnigs_stream_t stream);
+ * Splats whose centre lies outside [0, W] x [0, H] are ignored.
+ *   splats  [V * n] input (device)
+ *   ranges  [V * TILES, 2] output (device), TILES = (W / tile) * (H / tile): ranges[2t], ranges[2t+1] = first and
+ *           one-past-last position of tile t = v * TILES + ty * (W / tile) + tx in keys / values; tiles follow each
+ *           other in that order (both values clipped to `capacity`).
+ *   keys, values [capacity] output (device): the instances of tile t occupy [ranges[2t], ranges[2t+1]), in an
+ *           unspecified order; keys[i] = float bits of the splat's depth t_r, values[i] = splat index v * n + g.
+ * The total instance count stays on the device (workspace); if it exceeds `capacity`, instances beyond it are dropped
+ * and OMNIGS_E_CAPACITY is raised in the workspace. capacity < 2^32, the value given to omnigs_workspace_size. */
+omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *keys,
+                         uint32_t *values, int64_t capacity, uint32_t *ranges, void *workspace,
+                         omnigs_stream_t stream);
 
-/* Sort of the instances written by omnigs_bin by key, i.e. by (view, tile) and then by t_r (Sec. 3.3: blending
- * order is by t_r, nearest first), stable, so equal keys keep splat order. Sorts keys/values in place (using the
- * workspace) and writes ranges [V * TILES, 2] (device): ranges[2t], ranges[2t+1] = first and one-past-last sorted
- * position of tile t (both 0 for an empty tile). */
-omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t capacity, uint64_t *keys, uint32_t *values,
-                          uint32_t *ranges, void *workspace, omnigs_stream_t stream);
+/* Orders every tile's instances for blending (Sec. 3.3: nearest first by t_r): by depth, and by splat index among
+ * equal depths, i.e. the order a stable sort of (tile, t_r) keys gives to instances generated splat by splat. Sorts
+ * keys / values in place within the ranges written by omnigs_bin (using the workspace). */
+omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t capacity, uint32_t *keys, uint32_t *values,
+                          const uint32_t *ranges, void *workspace, omnigs_stream_t stream);
 
 /* Forward blending, Eqs. 6-8 with the tile procedure of Sec. 3.3: pixel (x, y) of view v is sampled at
  * (x + 0.5, y + 0.5) and blends its tile's sorted list front to back: dx taken as the minimal image in

@@ -53,7 +53,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_workspace_size.argtypes = [cfgp, i64, i64]
         lib.omnigs_workspace_size.restype = ctypes.c_size_t
         lib.omnigs_preprocess.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
-        lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, P, i64, P, P]
+        lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P, P]
         lib.omnigs_sort.argtypes = [cfgp, i64, P, P, P, P, P]
         lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
@@ -121,8 +121,8 @@ def omnigs_preprocess(cfg, n, means, scales, quats, opacity, sh, viewmats, splat
                                     _ptr(sh), _ptr(viewmats), _ptr(splats), _stream(stream)), "omnigs_preprocess")
 
 
-def omnigs_bin(cfg, n, splats, offsets, keys, values, capacity, workspace, stream=None):
-    _check(load().omnigs_bin(ctypes.byref(cfg), n, _ptr(splats), _ptr(offsets), _ptr(keys), _ptr(values), capacity,
+def omnigs_bin(cfg, n, splats, keys, values, capacity, ranges, workspace, stream=None):
+    _check(load().omnigs_bin(ctypes.byref(cfg), n, _ptr(splats), _ptr(keys), _ptr(values), capacity, _ptr(ranges),
                              _ptr(workspace), _stream(stream)), "omnigs_bin")
 
 

@@ -61,24 +61,20 @@ __device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int ti
     return R;
 }
 
-// Workspace layout (all offsets 256-byte aligned).
+// Workspace layout (all offsets 256-byte aligned). Every region depends on the configuration and the capacity only.
 struct WsLayout {
-    size_t header, block_sums, block_offsets, alt_keys, alt_values, hist, loss_partials, total;
-    int bin_blocks, sort_blocks, loss_blocks;
+    size_t header, loss_partials, tile_grid, tile_grid_bytes, scan_blocks, cursors, alt_keys, alt_values, total;
+    int loss_blocks;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kBinThreads = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort tile
-constexpr int kSortRadixMax = 256;
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocks = 1024;
 
 int num_sms();
-WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
+WsLayout ws_layout(const omnigs_config &cfg, int64_t capacity);
 
 // Kernel launches report their name and stream to the optional profiler.
 struct ProfScope {
@@ -96,11 +92,11 @@ cudaError_t launch_preprocess_bwd(const omnigs_config &cfg, int64_t n, const flo
                                   const float *quats, const float *opacity, const float *sh, const float *viewmats,
                                   const omnigs_splat_grad *grads, float *d_means, float *d_scales, float *d_quats,
                                   float *d_opacity, float *d_sh, float *d_screen, cudaStream_t stream);
-cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *offsets,
-                       uint64_t *keys, uint32_t *values, int64_t capacity, const WsLayout &L, char *ws,
+cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *keys,
+                       uint32_t *values, int64_t capacity, uint32_t *ranges, const WsLayout &L, char *ws,
                        cudaStream_t stream);
-cudaError_t launch_sort(const omnigs_config &cfg, int64_t capacity, uint64_t *keys, uint32_t *values,
-                        uint32_t *ranges, const WsLayout &L, char *ws, cudaStream_t stream);
+cudaError_t launch_sort(const omnigs_config &cfg, int64_t capacity, uint32_t *keys, uint32_t *values,
+                        const uint32_t *ranges, const WsLayout &L, char *ws, cudaStream_t stream);
 cudaError_t launch_render_fwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
                               const uint32_t *ranges, const uint32_t *values, float *out_rgb, float *out_T,
                               uint32_t *out_nc, cudaStream_t stream);
@@ -110,12 +106,5 @@ cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_
                               cudaStream_t stream);
 cudaError_t launch_l1(const omnigs_config &cfg, const float *rgb, const float *target, float *dL_drgb, float *loss,
                       const WsLayout &L, char *ws, cudaStream_t stream);
-
-// Radix-sort geometry: number of key bits in use, passes (even, so the result lands back in the caller's
-// buffers) and bits per pass (<= 8).
-struct SortPlan {
-    int bits, passes, digit_bits;
-};
-SortPlan sort_plan(const omnigs_config &cfg);
 
 }  // namespace omnigs

@@ -19,23 +19,21 @@ int num_sms() {
     return sms;
 }
 
-// Layout order: fixed-size regions, then those sized by the capacity, then those sized by n, so that calls which do
-// not take n (sort) or neither n nor the capacity (loss) find their regions at the same offsets.
-WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
+WsLayout ws_layout(const omnigs_config& cfg, int64_t capacity) {
     WsLayout L;
-    const int64_t total = n * cfg.num_views;
-    L.bin_blocks = (int)std::max<int64_t>(1, (total + kBinThreads - 1) / kBinThreads);
-    const int64_t sort_tiles = (capacity + kSortTile - 1) / kSortTile;
-    L.sort_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sort_tiles, 2 * (int64_t)num_sms()));
+    const size_t tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile, V = cfg.num_views;
+    const size_t ntiles = tx * ty * V;
+    const size_t scan_blocks = (ntiles + 4095) / 4096;
     L.loss_blocks = kLossBlocks;
+    L.tile_grid_bytes = sizeof(int) * V * (tx + 1) * (ty + 1);
     size_t off = 0;
     L.header = off;        off += align256(sizeof(WsHeader));
     L.loss_partials = off; off += align256(sizeof(float) * L.loss_blocks);
-    L.hist = off;          off += align256(sizeof(unsigned) * kSortRadixMax * (size_t)L.sort_blocks);
-    L.alt_keys = off;      off += align256(sizeof(unsigned long long) * (size_t)capacity);
-    L.alt_values = off;    off += align256(sizeof(unsigned) * (size_t)capacity);
-    L.block_sums = off;    off += align256(sizeof(unsigned) * L.bin_blocks);
-    L.block_offsets = off; off += align256(sizeof(unsigned long long) * L.bin_blocks);
+    L.tile_grid = off;     off += align256(L.tile_grid_bytes);
+    L.scan_blocks = off;   off += align256(sizeof(unsigned long long) * scan_blocks);
+    L.cursors = off;       off += align256(sizeof(uint32_t) * ntiles);
+    L.alt_keys = off;      off += align256(sizeof(uint32_t) * (size_t)capacity);
+    L.alt_values = off;    off += align256(sizeof(uint32_t) * (size_t)capacity);
     L.total = off;
     return L;
 }
@@ -128,7 +126,7 @@ const char* omnigs_status_string(omnigs_status s) {
 
 size_t omnigs_workspace_size(const omnigs_config* cfg, int64_t n, int64_t capacity) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return 0;
-    return ws_layout(*cfg, n, capacity).total;
+    return ws_layout(*cfg, capacity).total;
 }
 
 omnigs_status omnigs_preprocess(const omnigs_config* cfg, int64_t n, const float* means, const float* scales,
@@ -142,24 +140,24 @@ omnigs_status omnigs_preprocess(const omnigs_config* cfg, int64_t n, const float
                                        (cudaStream_t)stream));
 }
 
-omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats, uint32_t* offsets,
-                         uint64_t* keys, uint32_t* values, int64_t capacity, void* workspace,
+omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats, uint32_t* keys,
+                         uint32_t* values, int64_t capacity, uint32_t* ranges, void* workspace,
                          omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
-    if (!offsets || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (!ranges || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
     if (n > 0 && (!splats || !aligned(splats, 16))) return OMNIGS_E_INVALID;
     if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, n, capacity);
-    return from_cuda(launch_bin(*cfg, n, splats, offsets, keys, values, capacity, L, (char*)workspace,
+    const WsLayout L = ws_layout(*cfg, capacity);
+    return from_cuda(launch_bin(*cfg, n, splats, keys, values, capacity, ranges, L, (char*)workspace,
                                 (cudaStream_t)stream));
 }
 
-omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t capacity, uint64_t* keys, uint32_t* values,
-                          uint32_t* ranges, void* workspace, omnigs_stream_t stream) {
+omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t capacity, uint32_t* keys, uint32_t* values,
+                          const uint32_t* ranges, void* workspace, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
     if (!ranges || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
     if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, 0, capacity);  // the sort's regions do not depend on n
+    const WsLayout L = ws_layout(*cfg, capacity);
     return from_cuda(launch_sort(*cfg, capacity, keys, values, ranges, L, (char*)workspace, (cudaStream_t)stream));
 }
 
@@ -178,7 +176,7 @@ omnigs_status omnigs_l1_loss(const omnigs_config* cfg, const float* rgb, const f
     if (!valid_cfg(cfg)) return OMNIGS_E_INVALID;
     if (!rgb || !target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
     if (!aligned(rgb, 16) || !aligned(target, 16) || !aligned(dL_drgb, 16)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, 0, 0);  // header and loss partials sit at fixed offsets
+    const WsLayout L = ws_layout(*cfg, 0);  // header and loss partials sit at capacity-independent offsets
     return from_cuda(launch_l1(*cfg, rgb, target, dL_drgb, loss, L, (char*)workspace, (cudaStream_t)stream));
 }
 

@@ -11,7 +11,9 @@
 // (1 - alpha), reduces the 9 per-pixel partial derivatives of an entry over each warp with shuffles (skipped when no
 // lane of the warp touched the entry), then over the CTA in shared memory, and adds the CTA's sum to the splat's
 // gradient with 16-byte vector atomics (red.global.add.v4.f32). Forward and adjoint evaluate alpha with the same
-// inlined function, so their skip / stop decisions agree.
+// arithmetic, written identically in both kernels, so their skip / stop decisions agree. Each thread owns PPT
+// vertically adjacent pixels: they share dx and the entry loads, and the adjoint sums them before the warp
+// reduction, which halves its cost per pixel.
 #include "common.cuh"
 
 namespace omnigs {
@@ -49,54 +51,45 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     return s;
 }
 
-struct PairEval {
-    float dx, dy, G, raw, alpha;
-    bool skip;
+// Pixels of a thread: column lx = t % TS, rows (t / TS) * PPT + k for k < PPT, so a warp covers a compact
+// TS x (32 / TS * PPT) block and the PPT pixels of a thread share dx and every shared-memory load of an entry.
+template <int TS, int PPT>
+struct PixelMap {
+    static constexpr int NT = TS * TS / PPT;  // threads per CTA
+    static_assert(NT % 32 == 0, "a CTA must hold whole warps");
+    int x, y0;
+    __device__ PixelMap(int txi, int tyi) {
+        x = txi * TS + (int)threadIdx.x % TS;
+        y0 = tyi * TS + ((int)threadIdx.x / TS) * PPT;
+    }
 };
 
-// Eqs. 7-8 for one (pixel, entry): minimal-image dx, exponent, G, alpha and the skip decision.
-__device__ __forceinline__ PairEval eval_pair(const float4& A, const float4& B, float shift, float xs, float ys,
-                                              float halfW, float fW) {
-    PairEval e;
-    float dx = A.x - xs;
-    if (shift != kPerPixelWrap) {
-        dx += shift;
-    } else {
-        if (dx >= halfW) dx -= fW;
-        else if (dx < -halfW) dx += fW;
-    }
-    const float dy = A.y - ys;
-    const float p2 = fmaf(dx, fmaf(A.z, dx, A.w * dy), B.x * dy * dy);
-    e.dx = dx;
-    e.dy = dy;
-    e.G = fast_ex2(p2);
-    e.raw = B.y * e.G;
-    e.alpha = fminf(kAlphaMax, e.raw);
-    e.skip = (p2 > 0.f) || (e.alpha < kAlphaMin);
-    return e;
-}
-
-template <int TS>
-__global__ void __launch_bounds__(TS * TS)
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT)
 render_fwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
                   const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const uint32_t* __restrict__ values, float* __restrict__ out_rgb, float* __restrict__ out_T,
                   uint32_t* __restrict__ out_nc) {
-    constexpr int NT = TS * TS;
+    constexpr int NT = PixelMap<TS, PPT>::NT;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
     __shared__ float2 s_c[NT];
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    const int x = txi * TS + (int)threadIdx.x % TS, y = tyi * TS + (int)threadIdx.x / TS;
-    const float xs = x + 0.5f, ys = y + 0.5f;
+    const PixelMap<TS, PPT> pm(txi, tyi);
+    const float xs = pm.x + 0.5f;
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t last[PPT];
+    bool live[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; live[k] = true;
+    }
     int done = 0;
     for (uint32_t b = start; b < end; b += NT) {
         if (__syncthreads_count(done) == NT) break;
@@ -113,28 +106,49 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
             const float4 A = s_a[j];
             const float4 B = s_b[j];
             const float2 Cc = s_c[j];
-            const PairEval e = eval_pair(A, B, Cc.y, xs, ys, halfW, fW);
-            if (e.skip) continue;
-            const float Tn = T * (1.f - e.alpha);
-            if (Tn < kTStop) {
-                done = 1;
-                break;
+            float dx = A.x - xs;
+            if (Cc.y != kPerPixelWrap) {
+                dx += Cc.y;
+            } else {
+                if (dx >= halfW) dx -= fW;
+                else if (dx < -halfW) dx += fW;
             }
-            const float w = e.alpha * T;
-            C0 = fmaf(w, B.z, C0);
-            C1 = fmaf(w, B.w, C1);
-            C2 = fmaf(w, Cc.x, C2);
-            T = Tn;
-            last = b - start + j + 1;
+            const float u = A.z * dx;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!live[k]) continue;
+                const float dy = A.y - (pm.y0 + k + 0.5f);
+                const float p2 = fmaf(dx, fmaf(A.w, dy, u), B.x * dy * dy);
+                const float alpha = fminf(kAlphaMax, B.y * fast_ex2(p2));
+                if (p2 > 0.f || alpha < kAlphaMin) continue;
+                const float Tn = T[k] * (1.f - alpha);
+                if (Tn < kTStop) {
+                    live[k] = false;
+                    continue;
+                }
+                const float w = alpha * T[k];
+                C0[k] = fmaf(w, B.z, C0[k]);
+                C1[k] = fmaf(w, B.w, C1[k]);
+                C2[k] = fmaf(w, Cc.x, C2[k]);
+                T[k] = Tn;
+                last[k] = b - start + j + 1;
+            }
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) any |= live[k];
+            done = !any;
         }
     }
     const size_t HW = (size_t)H * W;
-    const size_t pix = (size_t)y * W + x;
-    out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(T, bg0, C0);
-    out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(T, bg1, C1);
-    out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T, bg2, C2);
-    out_T[(size_t)v * HW + pix] = T;
-    out_nc[(size_t)v * HW + pix] = last;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
+        out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(T[k], bg0, C0[k]);
+        out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(T[k], bg1, C1[k]);
+        out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T[k], bg2, C2[k]);
+        out_T[(size_t)v * HW + pix] = T[k];
+        out_nc[(size_t)v * HW + pix] = last[k];
+    }
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -145,14 +159,14 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 constexpr int kGradFields = 9;
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS)
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT)
 render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
                   const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const uint32_t* __restrict__ values, const float* __restrict__ out_T,
                   const uint32_t* __restrict__ ncontrib, const float* __restrict__ dL_drgb,
                   float4* __restrict__ grads) {
-    constexpr int NT = TS * TS;
+    constexpr int NT = PixelMap<TS, PPT>::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* s_a = reinterpret_cast<float4*>(smem_raw);
     float4* s_b = s_a + NT;
@@ -165,24 +179,32 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    const int x = txi * TS + (int)threadIdx.x % TS, y = tyi * TS + (int)threadIdx.x / TS;
-    const float xs = x + 0.5f, ys = y + 0.5f;
+    const PixelMap<TS, PPT> pm(txi, tyi);
+    const float xs = pm.x + 0.5f;
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
     const size_t HW = (size_t)H * W;
-    const size_t pix = (size_t)y * W + x;
-    const uint32_t last = min(ncontrib[(size_t)v * HW + pix], len);
-    float T = out_T[(size_t)v * HW + pix];
-    const float g0 = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
-    const float g1 = dL_drgb[(3 * (size_t)v + 1) * HW + pix];
-    const float g2 = dL_drgb[(3 * (size_t)v + 2) * HW + pix];
-    float B0 = bg0, B1 = bg1, B2 = bg2;  // colour behind the current entry, per unit of its transmittance
+
+    uint32_t last[PPT];
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], B0[PPT], B1[PPT], B2[PPT];
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
+        last[k] = min(ncontrib[(size_t)v * HW + pix], len);
+        T[k] = out_T[(size_t)v * HW + pix];
+        g0[k] = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
+        g1[k] = dL_drgb[(3 * (size_t)v + 1) * HW + pix];
+        g2[k] = dL_drgb[(3 * (size_t)v + 2) * HW + pix];
+        B0[k] = bg0; B1[k] = bg1; B2[k] = bg2;  // colour behind the current entry, per unit of its transmittance
+        mylast = max(mylast, last[k]);
+    }
 
     if (threadIdx.x == 0) s_max = 0;
     for (int i = threadIdx.x; i < NT * kGradFields; i += NT) s_acc[i] = 0.f;
     __syncthreads();
-    atomicMax(&s_max, last);
+    atomicMax(&s_max, mylast);
     __syncthreads();
     const uint32_t maxlast = s_max;
     const unsigned lane = threadIdx.x & 31;
@@ -204,46 +226,56 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
         __syncthreads();
         for (int j = nb - 1; j >= 0; --j) {
             const uint32_t pos = (uint32_t)(bbeg + j);  // position in the tile list
+            if (__all_sync(0xffffffffu, pos >= mylast)) continue;
             const float4 A = s_a[j];
             const float4 Bv = s_b[j];
             const float4 K = s_k[j];
+            const float shift = s_shift[j];
             float gv[kGradFields];
-            bool contrib = false;
-            if (pos < last) {
-                const PairEval e = eval_pair(A, Bv, s_shift[j], xs, ys, halfW, fW);
-                if (!e.skip) {
-                    contrib = true;
-                    const float one_m = 1.f - e.alpha;
-                    T = T / one_m;  // transmittance in front of this entry
-                    const float cr = Bv.z, cg = Bv.w, cb = K.w;
-                    const float dalpha = T * (g0 * (cr - B0) + g1 * (cg - B1) + g2 * (cb - B2));
-                    const float w = e.alpha * T;
-                    gv[6] = w * g0;
-                    gv[7] = w * g1;
-                    gv[8] = w * g2;
-                    B0 = fmaf(e.alpha, cr, one_m * B0);
-                    B1 = fmaf(e.alpha, cg, one_m * B1);
-                    B2 = fmaf(e.alpha, cb, one_m * B2);
-                    if (e.raw < kAlphaMax) {
-                        gv[5] = dalpha * e.G;
-                        const float gp = dalpha * e.raw;  // dL/d(exponent)
-                        const float dx = e.dx, dy = e.dy;
-                        gv[2] = -0.5f * dx * dx * gp;
-                        gv[3] = -dx * dy * gp;
-                        gv[4] = -0.5f * dy * dy * gp;
-                        gv[0] = -(K.x * dx + K.y * dy) * gp;
-                        gv[1] = -(K.z * dy + K.y * dx) * gp;
-                    } else {
 #pragma unroll
-                        for (int f = 0; f < 6; ++f) gv[f] = 0.f;
-                    }
+            for (int f = 0; f < kGradFields; ++f) gv[f] = 0.f;
+            bool contrib = false;
+            float dx = A.x - xs;
+            if (shift != kPerPixelWrap) {
+                dx += shift;
+            } else {
+                if (dx >= halfW) dx -= fW;
+                else if (dx < -halfW) dx += fW;
+            }
+            const float u = A.z * dx;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (pos >= last[k]) continue;
+                const float dy = A.y - (pm.y0 + k + 0.5f);
+                const float p2 = fmaf(dx, fmaf(A.w, dy, u), Bv.x * dy * dy);
+                const float G = fast_ex2(p2);
+                const float raw = Bv.y * G;
+                const float alpha = fminf(kAlphaMax, raw);
+                if (p2 > 0.f || alpha < kAlphaMin) continue;
+                contrib = true;
+                const float one_m = 1.f - alpha;
+                T[k] = __fdividef(T[k], one_m);  // transmittance in front of this entry
+                const float cr = Bv.z, cg = Bv.w, cb = K.w;
+                const float dalpha = T[k] * (g0[k] * (cr - B0[k]) + g1[k] * (cg - B1[k]) + g2[k] * (cb - B2[k]));
+                const float w = alpha * T[k];
+                gv[6] = fmaf(w, g0[k], gv[6]);
+                gv[7] = fmaf(w, g1[k], gv[7]);
+                gv[8] = fmaf(w, g2[k], gv[8]);
+                B0[k] = fmaf(alpha, cr, one_m * B0[k]);
+                B1[k] = fmaf(alpha, cg, one_m * B1[k]);
+                B2[k] = fmaf(alpha, cb, one_m * B2[k]);
+                if (raw < kAlphaMax) {
+                    gv[5] = fmaf(dalpha, G, gv[5]);
+                    const float gp = dalpha * raw;  // dL/d(exponent)
+                    const float gdx = gp * dx, gdy = gp * dy;
+                    gv[2] = fmaf(-0.5f * dx, gdx, gv[2]);
+                    gv[3] = fmaf(-dx, gdy, gv[3]);
+                    gv[4] = fmaf(-0.5f * dy, gdy, gv[4]);
+                    gv[0] -= K.x * gdx + K.y * gdy;
+                    gv[1] -= K.z * gdy + K.y * gdx;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                if (!contrib) {
-#pragma unroll
-                    for (int f = 0; f < kGradFields; ++f) gv[f] = 0.f;
-                }
 #pragma unroll
                 for (int f = 0; f < kGradFields; ++f) gv[f] = warp_sum(gv[f]);
                 if (lane == 0) {
@@ -271,6 +303,8 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
     }
 }
 
+constexpr int kPPT = 2;  // pixels per thread
+
 size_t bwd_smem(int nt) { return (size_t)nt * (3 * sizeof(float4) + sizeof(float) + sizeof(unsigned) + kGradFields * sizeof(float)); }
 
 template <int TS>
@@ -278,7 +312,7 @@ cudaError_t render_fwd_t(const omnigs_config& cfg, const omnigs_splat* splats, c
                          const uint32_t* values, float* out_rgb, float* out_T, uint32_t* out_nc, cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     ProfScope prof("render_fwd", stream);
-    render_fwd_kernel<TS><<<tiles * cfg.num_views, TS * TS, 0, stream>>>(
+    render_fwd_kernel<TS, kPPT><<<tiles * cfg.num_views, PixelMap<TS, kPPT>::NT, 0, stream>>>(
         cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
         ranges, values, out_rgb, out_T, out_nc);
     return cudaGetLastError();
@@ -289,11 +323,13 @@ cudaError_t render_bwd_t(const omnigs_config& cfg, const omnigs_splat* splats, c
                          const uint32_t* values, const float* out_T, const uint32_t* nc, const float* dL_drgb,
                          omnigs_splat_grad* grads, cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
-    const size_t smem = bwd_smem(TS * TS);
-    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int NT = PixelMap<TS, kPPT>::NT;
+    const size_t smem = bwd_smem(NT);
+    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, kPPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope prof("render_bwd", stream);
-    render_bwd_kernel<TS><<<tiles * cfg.num_views, TS * TS, smem, stream>>>(
+    render_bwd_kernel<TS, kPPT><<<tiles * cfg.num_views, NT, smem, stream>>>(
         cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
         ranges, values, out_T, nc, dL_drgb, reinterpret_cast<float4*>(grads));
     return cudaGetLastError();

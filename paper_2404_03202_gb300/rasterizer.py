@@ -71,7 +71,7 @@ class Rasterizer:
     def _alloc_instances(self, capacity: int):
         self.capacity = int(capacity)
         cap = max(self.capacity, 1)
-        self.keys = _empty((cap,), torch.int64, self.device)
+        self.keys = _empty((cap,), torch.int32, self.device)
         self.values = _empty((cap,), torch.int32, self.device)
         self.ws = None
 
@@ -82,7 +82,6 @@ class Rasterizer:
             m = max(V * n, 1)
             self.splats = _empty((m, C.SPLAT_FLOATS), torch.float32, self.device)
             self.grads2d = _empty((m, C.GRAD_FLOATS), torch.float32, self.device)
-            self.offsets = _empty((V * n + 1,), torch.int32, self.device)
             self.d_means = _empty((max(n, 1), 3), torch.float32, self.device)
             self.d_scales = _empty((max(n, 1), 3), torch.float32, self.device)
             self.d_quats = _empty((max(n, 1), 4), torch.float32, self.device)
@@ -92,7 +91,7 @@ class Rasterizer:
         if getattr(self, "d_sh", None) is None or self.d_sh.shape[0] != max(n, 1) or self.d_sh.shape[1] != K:
             self.d_sh = _empty((max(n, 1), K, 3), torch.float32, self.device)
         if self.ws is None:
-            nbytes = C.omnigs_workspace_size(self.cfg, n, self.capacity)
+            nbytes = C.omnigs_workspace_size(self.cfg, max(n, 0), self.capacity)
             if nbytes == 0:
                 raise C.OmnigsError(C.OMNIGS_E_INVALID, "omnigs_workspace_size")
             self.ws = _empty((nbytes,), torch.uint8, self.device)
@@ -106,13 +105,13 @@ class Rasterizer:
         self._ensure(n, K)
         self._params = (means, scales, quats, opacity, sh, viewmats)
         C.omnigs_preprocess(self.cfg, n, means, scales, quats, opacity, sh, viewmats, self.splats, stream)
-        C.omnigs_bin(self.cfg, n, self.splats, self.offsets, self.keys, self.values, self.capacity, self.ws, stream)
+        C.omnigs_bin(self.cfg, n, self.splats, self.keys, self.values, self.capacity, self.ranges, self.ws, stream)
         if self.grow:
             self.count = C.omnigs_instance_count(self.ws, stream)
             if self.count > self.capacity:
                 self._alloc_instances(int(math.ceil(self.count * self.headroom)))
                 self._ensure(n, K)
-                C.omnigs_bin(self.cfg, n, self.splats, self.offsets, self.keys, self.values, self.capacity, self.ws,
+                C.omnigs_bin(self.cfg, n, self.splats, self.keys, self.values, self.capacity, self.ranges, self.ws,
                              stream)
         C.omnigs_sort(self.cfg, self.capacity, self.keys, self.values, self.ranges, self.ws, stream)
         C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.values, self.rgb, self.T, self.ncontrib,

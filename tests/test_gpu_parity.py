@@ -35,13 +35,13 @@ def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):
     n = m // s.num_views
     r._ensure(n, (s.sh_degree + 1) ** 2)
     r.splats.copy_(dev(sp_packed))
-    C.omnigs_bin(r.cfg, n, r.splats, r.offsets, r.keys, r.values, r.capacity, r.ws)
+    C.omnigs_bin(r.cfg, n, r.splats, r.keys, r.values, r.capacity, r.ranges, r.ws)
     cnt = r.instance_count()
     if cnt > r.capacity:
         r._alloc_instances(cnt)
         r._ensure(n, (s.sh_degree + 1) ** 2)
         r.splats.copy_(dev(sp_packed))
-        C.omnigs_bin(r.cfg, n, r.splats, r.offsets, r.keys, r.values, r.capacity, r.ws)
+        C.omnigs_bin(r.cfg, n, r.splats, r.keys, r.values, r.capacity, r.ranges, r.ws)
     C.omnigs_sort(r.cfg, r.capacity, r.keys, r.values, r.ranges, r.ws)
     C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.values, r.rgb, r.T, r.ncontrib)
     torch.cuda.synchronize()
@@ -93,28 +93,22 @@ def test_preprocess_matches_oracle(deg):
 
 # ------------------------------------------------------------------ S2-S4 bin, sort, ranges
 
-@pytest.mark.parametrize("tile,V,n", [(16, 2, 3000), (8, 1, 1500), (32, 3, 1000)])
-def test_bin_sort_bitexact(tile, V, n):
-    W, H = 256, 128
+@pytest.mark.parametrize("tile,V,n,W,H", [(16, 2, 3000, 256, 128), (8, 1, 1500, 256, 128), (32, 3, 1000, 256, 128),
+                                         (16, 1, 60000, 512, 256), (8, 2, 20000, 128, 64)])
+def test_bin_sort_bitexact(tile, V, n, W, H):
+    """Includes lists longer than one shared-memory chunk (sorted in chunks and merged) and many depth ties."""
     sp = synth.random_splats(V, n, W, H, seed=100 + tile, max_radius=30)
     packed = pack_splats(sp)
     s = _settings(W, H, tile=tile, V=V)
     r, cnt = _run_splats(packed, s)
     ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
     assert cnt == len(list_ref)
-    # offsets: exclusive prefix of per-splat instance counts
-    per = np.array([0 if sp["radius"][i] <= 0 else
-                    np.prod(oracle.rect(sp["px"][i], sp["py"][i], sp["radius"][i], W, H, tile)[1::2])
-                    for i in range(V * n)])
-    off = r.offsets.cpu().numpy().view(np.uint32).astype(np.int64)
-    assert np.array_equal(off[:-1], np.concatenate([[0], np.cumsum(per)[:-1]])) and off[-1] == per.sum()
     ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
     assert np.array_equal(ranges, ranges_ref)
     vals = r.values[:cnt].cpu().numpy().view(np.uint32).astype(np.int64)
     assert np.array_equal(vals, list_ref)
-    keys = r.keys[:cnt].cpu().numpy().view(np.uint64)
-    depth_bits = sp["depth"].view(np.uint32).astype(np.uint64)
-    assert np.array_equal(keys & np.uint64(0x7FFFFFFF), depth_bits[vals])
+    keys = r.keys[:cnt].cpu().numpy().view(np.uint32)
+    assert np.array_equal(keys, sp["depth"].view(np.uint32)[vals])
 
 
 def test_sort_many_ties_and_all_columns():
