@@ -37,7 +37,7 @@ WORKLOADS = {
 # Algorithmic work per unit, used for the roofline (see the design doc for the derivations).
 FWD_FLOP_PER_PAIR = 22       # render_fwd: per evaluated (pixel, entry) pair
 BWD_FLOP_PER_PAIR = 62       # render_bwd: per processed (pixel, entry) pair (eval + adjoint)
-SORT_BYTES_PER_KEY = 24      # sort_downsweep: 8 B key + 4 B value read, the same written, per pass
+SORT_BYTES_PER_KEY = 16      # segment_sort: 4 B key + 4 B value read and written once per instance
 PRE_BYTES_PER_GAUSS = 236    # preprocess: 59 parameter floats read once
 PRE_BYTES_PER_SPLAT = 48     # preprocess: one 48 B splat written per (view, Gaussian)
 
@@ -358,7 +358,6 @@ def main():
     per_kernel = {p[0]: {"launches": p[1], "total_ms": p[2], "avg_ms": p[2] / max(p[1], 1)} for p in prof}
     dom = max(prof, key=lambda p: p[2])[0]
     k = per_kernel[dom]
-    sort_passes = per_kernel.get("sort_downsweep", {}).get("launches", 0) // args.steps
     if dom == "render_bwd":
         flops = pairs * BWD_FLOP_PER_PAIR
         roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
@@ -367,7 +366,7 @@ def main():
         flops = pairs * FWD_FLOP_PER_PAIR
         roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
                 "unit": "TFLOP/s"}
-    elif dom == "sort_downsweep":
+    elif dom == "segment_sort":
         roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     else:
@@ -394,8 +393,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": workload_config(wl, args) | {"views_per_s": 1e3 * V * world / ms,
                                                       "graph_ms_per_step": graph_ms,
-                                                      "instances_per_step": count, "pairs_per_step": pairs,
-                                                      "sort_passes": sort_passes},
+                                                      "instances_per_step": count, "pairs_per_step": pairs},
                "gpu_launches": kernel_launches * args.steps, "kernels_per_step": per_kernel,
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
