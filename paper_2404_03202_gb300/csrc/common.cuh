@@ -63,7 +63,7 @@ __device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int ti
 
 // Workspace layout (all offsets 256-byte aligned). Every region depends on the configuration and the capacity only.
 struct WsLayout {
-    size_t header, loss_partials, tile_grid, tile_grid_bytes, scan_blocks, cursors, alt_keys, alt_values, total;
+    size_t header, loss_partials, tile_counts, scan_blocks, cursors, alt_keys, alt_values, total;
     int loss_blocks;
 };
 

@@ -25,11 +25,10 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t capacity) {
     const size_t ntiles = tx * ty * V;
     const size_t scan_blocks = (ntiles + 4095) / 4096;
     L.loss_blocks = kLossBlocks;
-    L.tile_grid_bytes = sizeof(int) * V * (tx + 1) * (ty + 1);
     size_t off = 0;
     L.header = off;        off += align256(sizeof(WsHeader));
     L.loss_partials = off; off += align256(sizeof(float) * L.loss_blocks);
-    L.tile_grid = off;     off += align256(L.tile_grid_bytes);
+    L.tile_counts = off;   off += align256(sizeof(uint32_t) * ntiles);
     L.scan_blocks = off;   off += align256(sizeof(unsigned long long) * scan_blocks);
     L.cursors = off;       off += align256(sizeof(uint32_t) * ntiles);
     L.alt_keys = off;      off += align256(sizeof(uint32_t) * (size_t)capacity);
