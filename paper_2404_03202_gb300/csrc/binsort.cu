@@ -2,7 +2,7 @@
 //
 // The order produced is that of a stable sort of (view * TILES + tile, t_r) keys, i.e. a two-digit radix sort whose
 // most significant digit is the tile. The tile digit is resolved by counting instead of by key passes over HBM:
-//   1. tile_count: CTAs walk chunks of 8192 splats of one view, enumerate their instances warp-cooperatively,
+//   1. tile_count: CTAs walk chunks of 2048 splats of one view, enumerate their instances warp-cooperatively,
 //      count them per tile in shared memory and add the counts to the global per-tile counts (one atomic per touched
 //      tile and chunk instead of one per instance);
 //   2. scan_*: an exclusive scan of the counts gives each tile's [start, end) range (the ranges the blend kernels
@@ -80,7 +80,7 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
 // Splats are processed in chunks of kChunk consecutive splats of one view. The warps of a CTA take 32 splats at a
 // time and enumerate their instances together (one per lane per round, owner found by a binary search over the
 // warp's exclusive prefix of counts), calling fn(local_tile, depth_bits, splat_index) for each.
-constexpr int kChunk = 8192;
+constexpr int kChunk = 2048;
 constexpr int kBinCtaThreads = 512;
 constexpr int kAggTiles = 16384;  // tiles per view up to which per-tile counts are aggregated in shared memory
 
@@ -290,6 +290,11 @@ bin_emit_kernel(int64_t nchunks, int n, int chunks_per_view, const float4* __res
 // (digit, warp) its output offset, the items are scattered to shared memory and read back in element order.
 constexpr int kRadix = 256;
 
+// Counter of (digit d, warp w), digit-major with the warp index XOR-swizzled by the digit, so that lanes ranking
+// different digits hit different banks while one digit's NW counters stay contiguous for the scan.
+template <int NW>
+__device__ __forceinline__ unsigned cnt_index(unsigned d, unsigned w) { return d * NW + (w ^ (d & (NW - 1))); }
+
 template <int NT, int ITEMS>
 struct TileSortSmem {
     static constexpr int NW = NT / 32;
@@ -347,7 +352,7 @@ __device__ void tile_sort(uint32_t* __restrict__ gk, uint32_t* __restrict__ gv, 
             const int e = (warp * ITEMS + j) * 32 + lane;
             const unsigned d = e < n ? (key[j] >> shift) & 0xffu : (unsigned)kRadix;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
-            unsigned* c = &S.cnt[d * NW + warp];
+            unsigned* c = &S.cnt[cnt_index<NW>(d, warp)];
             const unsigned before = *c;
             __syncwarp();
             if (lane == (unsigned)(__ffs(peers) - 1)) *c = before + __popc(peers);
@@ -360,14 +365,16 @@ __device__ void tile_sort(uint32_t* __restrict__ gk, uint32_t* __restrict__ gv, 
             unsigned loc[PER], sum = 0;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                loc[q] = S.cnt[tid * PER + q];
+                const unsigned idx = tid * PER + q;  // logical digit-major position
+                loc[q] = S.cnt[cnt_index<NW>(idx / NW, idx % NW)];
                 sum += loc[q];
             }
             unsigned tot;
             unsigned run = block_exclusive_scan<unsigned>(sum, S.scratch, &tot);
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                S.cnt[tid * PER + q] = run;
+                const unsigned idx = tid * PER + q;
+                S.cnt[cnt_index<NW>(idx / NW, idx % NW)] = run;
                 run += loc[q];
             }
         }
@@ -376,7 +383,7 @@ __device__ void tile_sort(uint32_t* __restrict__ gk, uint32_t* __restrict__ gv, 
         for (int j = 0; j < ITEMS; ++j) {
             const int e = (warp * ITEMS + j) * 32 + lane;
             if (e < n) {
-                const unsigned pos = S.cnt[((key[j] >> shift) & 0xffu) * NW + warp] + rk[j];
+                const unsigned pos = S.cnt[cnt_index<NW>((key[j] >> shift) & 0xffu, warp)] + rk[j];
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
             }
@@ -489,7 +496,7 @@ __device__ void merge_runs(const unsigned* __restrict__ keys, const unsigned* __
 // One CTA per tile (grid-stride). Segments of up to NT * ITEMS pairs are sorted in registers and shared memory;
 // longer ones are sorted in chunks of that size and merged pairwise through the scratch buffers.
 template <int NT, int ITEMS>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 16 / ITEMS)
 segment_sort_kernel(u64 ntiles, const uint32_t* __restrict__ ranges, uint32_t* __restrict__ keys,
                     uint32_t* __restrict__ values, uint32_t* __restrict__ scratch_k, uint32_t* __restrict__ scratch_v,
                     int min_len, int max_len) {
@@ -525,7 +532,7 @@ segment_sort_kernel(u64 ntiles, const uint32_t* __restrict__ ranges, uint32_t* _
     }
 }
 
-constexpr int kSmallNT = 256, kSmallItems = 16;  // lists up to 4096
+constexpr int kSmallNT = 512, kSmallItems = 8;   // lists up to 4096
 constexpr int kLargeNT = 512, kLargeItems = 16;  // lists up to 8192 at once, longer ones merged
 
 }  // namespace
