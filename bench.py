@@ -37,7 +37,7 @@ WORKLOADS = {
 # Algorithmic work per unit, used for the roofline (see the design doc for the derivations).
 FWD_FLOP_PER_PAIR = 22       # render_fwd: per evaluated (pixel, entry) pair
 BWD_FLOP_PER_PAIR = 62       # render_bwd: per processed (pixel, entry) pair (eval + adjoint)
-SORT_BYTES_PER_KEY = 16      # segment_sort: 4 B key + 4 B value read and written once per instance
+SORT_BYTES_PER_KEY = 16      # sort_downsweep: one 8 B key read and written per instance and pass
 PRE_BYTES_PER_GAUSS = 236    # preprocess: 59 parameter floats read once
 PRE_BYTES_PER_SPLAT = 48     # preprocess: one 48 B splat written per (view, Gaussian)
 
@@ -366,7 +366,7 @@ def main():
         flops = pairs * FWD_FLOP_PER_PAIR
         roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
                 "unit": "TFLOP/s"}
-    elif dom == "segment_sort":
+    elif dom == "sort_downsweep":
         roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     else:

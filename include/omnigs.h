@@ -81,8 +81,9 @@ int omnigs_version(void);
 const char *omnigs_status_string(omnigs_status status);
 
 /* Bytes of device workspace needed for n Gaussians in cfg->num_views views with room for `capacity` tile
- * instances (one instance per (view, Gaussian, covered tile); Sec. 3.3). Returns 0 for invalid arguments.
- * The workspace is 256-byte aligned by the caller and need not be initialised; omnigs_bin initialises it. */
+ * instances (one instance per (view, Gaussian, covered tile); Sec. 3.3). Returns 0 for invalid arguments. The size
+ * depends on the device (it is queried on the current one). The workspace is 256-byte aligned by the caller and
+ * need not be initialised; omnigs_bin initialises it. */
 size_t omnigs_workspace_size(const omnigs_config *cfg, int64_t n, int64_t capacity);
 
 /* Per-(view, Gaussian) projection, Sec. 3.2-3.3: t = W m + t_cw (Eq. 1); lon, lat (Eq. 3); s (Eq. 4); p (Eq. 5);
@@ -102,33 +103,34 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  * longitude seam; a square at least as wide as the image covers every column once); rows are clipped to the image.
  * Splats whose centre lies outside [0, W] x [0, H] are ignored.
  *   splats  [V * n] input (device)
- *   ranges  [V * TILES, 2] output (device), TILES = (W / tile) * (H / tile): ranges[2t], ranges[2t+1] = first and
- *           one-past-last position of tile t = v * TILES + ty * (W / tile) + tx in keys / values; tiles follow each
- *           other in that order (both values clipped to `capacity`).
- *   keys, values [capacity] output (device): the instances of tile t occupy [ranges[2t], ranges[2t+1]), in an
- *           unspecified order; keys[i] = float bits of the splat's depth t_r, values[i] = splat index v * n + g.
+ *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:
+ *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r).
+ *   keys    [capacity] output (device): one key per instance, generated splat by splat (tiles row by row, columns in
+ *           seam order): ((v * TILES + tile) << R) | r, with TILES = (W / tile) * (H / tile), tile = ty * (W / tile)
+ *           + tx, r the splat's depth rank and R = max(1, ceil(log2(n))) rank bits.
  * The total instance count stays on the device (workspace); if it exceeds `capacity`, instances beyond it are dropped
  * and OMNIGS_E_CAPACITY is raised in the workspace. capacity < 2^32, the value given to omnigs_workspace_size. */
-omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *keys,
-                         uint32_t *values, int64_t capacity, uint32_t *ranges, void *workspace,
-                         omnigs_stream_t stream);
+omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
+                         uint64_t *keys, int64_t capacity, void *workspace, omnigs_stream_t stream);
 
-/* Orders every tile's instances for blending (Sec. 3.3: nearest first by t_r): by depth, and by splat index among
- * equal depths, i.e. the order a stable sort of (tile, t_r) keys gives to instances generated splat by splat. Sorts
- * keys / values in place within the ranges written by omnigs_bin (using the workspace). */
-omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t capacity, uint32_t *keys, uint32_t *values,
-                          const uint32_t *ranges, void *workspace, omnigs_stream_t stream);
+/* Sort of the instance keys written by omnigs_bin, in place: by (view, tile), then by depth rank, i.e. the blending
+ * order of Sec. 3.3 (nearest first by t_r) with equal depths in splat order, the order a stable sort of (tile, t_r)
+ * keys gives to instances generated splat by splat. Writes ranges [V * TILES, 2] (device): ranges[2t], ranges[2t+1] =
+ * first and one-past-last sorted position of tile t (both 0 for an empty tile). n and capacity as for omnigs_bin. */
+omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t n, int64_t capacity, uint64_t *keys, uint32_t *ranges,
+                          void *workspace, omnigs_stream_t stream);
 
 /* Forward blending, Eqs. 6-8 with the tile procedure of Sec. 3.3: pixel (x, y) of view v is sampled at
  * (x + 0.5, y + 0.5) and blends its tile's sorted list front to back: dx taken as the minimal image in
  * [-W/2, W/2); alpha = min(0.99, o exp(-1/2 dp^T conic dp)); entries with exponent > 0 or alpha < 1/255 are
  * skipped; blending stops before an entry that would bring T below 1e-4; finally C += T bg.
- *   splats [V * n], ranges [V * TILES, 2], values [capacity] (sorted, from omnigs_sort): inputs (device)
+ *   splats [V * n], ranges [V * TILES, 2] and keys [capacity] (from omnigs_sort), order [V * n] (from omnigs_bin):
+ *   inputs (device); the splat of sorted position s of view v is order[v * n + (keys[s] & (2^R - 1))].
  *   out_rgb [V, 3, H, W], out_T [V, H, W] (final transmittance), out_ncontrib [V, H, W] (list position after the
  *   last contributor): outputs (device). out_T and out_ncontrib feed omnigs_render_bwd. */
 omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
-                                const uint32_t *ranges, const uint32_t *values, float *out_rgb, float *out_T,
-                                uint32_t *out_ncontrib, omnigs_stream_t stream);
+                                const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
+                                float *out_T, uint32_t *out_ncontrib, omnigs_stream_t stream);
 
 /* L1 term of the photometric loss (Eq. 17 with lambda = 0): loss = mean |rgb - target| over [V, 3, H, W];
  * dL_drgb = sign(rgb - target) / (V * 3 * H * W) (0 where equal). rgb, target: inputs; dL_drgb [V, 3, H, W] and
@@ -141,9 +143,9 @@ omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const f
  * c2, opacity, r, g, b) of every splat, summed over the pixels it reaches. The derivative of alpha is 0 where it is
  * clamped at 0.99. Inputs are those of omnigs_render_fwd plus its out_T, out_ncontrib and dL_drgb [V, 3, H, W]. */
 omnigs_status omnigs_render_bwd(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
-                                const uint32_t *ranges, const uint32_t *values, const float *out_T,
-                                const uint32_t *ncontrib, const float *dL_drgb, omnigs_splat_grad *grads,
-                                omnigs_stream_t stream);
+                                const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
+                                const float *out_T, const uint32_t *ncontrib, const float *dL_drgb,
+                                omnigs_splat_grad *grads, omnigs_stream_t stream);
 
 /* Adjoint of omnigs_preprocess (Sec. 3.4, Eqs. 18-20): chain rule from the splat gradients through conic,
  * Sigma~ (dSigma~/dSigma), the spherical Jacobian (dJ/dt), p (dp/ds, ds/dt), t = W m + t_cw, R(q), S and the SH

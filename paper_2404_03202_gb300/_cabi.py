@@ -33,6 +33,11 @@ class omnigs_kernel_time(ctypes.Structure):
 
 
 SPLAT_FLOATS = 12  # sizeof(omnigs_splat) / 4
+
+
+def rank_bits(n: int) -> int:
+    """Bits of the depth rank in an instance key (max(1, ceil(log2(n))))."""
+    return max(1, (max(int(n), 1) - 1).bit_length())
 GRAD_FLOATS = 12   # sizeof(omnigs_splat_grad) / 4
 
 _lib = None
@@ -53,11 +58,11 @@ def load() -> ctypes.CDLL:
         lib.omnigs_workspace_size.argtypes = [cfgp, i64, i64]
         lib.omnigs_workspace_size.restype = ctypes.c_size_t
         lib.omnigs_preprocess.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
-        lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P, P]
-        lib.omnigs_sort.argtypes = [cfgp, i64, P, P, P, P, P]
-        lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P]
+        lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P]
+        lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
+        lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
-        lib.omnigs_render_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
+        lib.omnigs_render_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_preprocess_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.omnigs_instance_count.argtypes = [P, ctypes.POINTER(i64), P]
         lib.omnigs_last_error.argtypes = [P, P]
@@ -121,19 +126,19 @@ def omnigs_preprocess(cfg, n, means, scales, quats, opacity, sh, viewmats, splat
                                     _ptr(sh), _ptr(viewmats), _ptr(splats), _stream(stream)), "omnigs_preprocess")
 
 
-def omnigs_bin(cfg, n, splats, keys, values, capacity, ranges, workspace, stream=None):
-    _check(load().omnigs_bin(ctypes.byref(cfg), n, _ptr(splats), _ptr(keys), _ptr(values), capacity, _ptr(ranges),
-                             _ptr(workspace), _stream(stream)), "omnigs_bin")
+def omnigs_bin(cfg, n, splats, order, keys, capacity, workspace, stream=None):
+    _check(load().omnigs_bin(ctypes.byref(cfg), n, _ptr(splats), _ptr(order), _ptr(keys), capacity, _ptr(workspace),
+                             _stream(stream)), "omnigs_bin")
 
 
-def omnigs_sort(cfg, capacity, keys, values, ranges, workspace, stream=None):
-    _check(load().omnigs_sort(ctypes.byref(cfg), capacity, _ptr(keys), _ptr(values), _ptr(ranges), _ptr(workspace),
+def omnigs_sort(cfg, n, capacity, keys, ranges, workspace, stream=None):
+    _check(load().omnigs_sort(ctypes.byref(cfg), n, capacity, _ptr(keys), _ptr(ranges), _ptr(workspace),
                               _stream(stream)), "omnigs_sort")
 
 
-def omnigs_render_fwd(cfg, n, splats, ranges, values, out_rgb, out_T, out_ncontrib, stream=None):
-    _check(load().omnigs_render_fwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(values), _ptr(out_rgb),
-                                    _ptr(out_T), _ptr(out_ncontrib), _stream(stream)), "omnigs_render_fwd")
+def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, stream=None):
+    _check(load().omnigs_render_fwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(keys), _ptr(order),
+                                    _ptr(out_rgb), _ptr(out_T), _ptr(out_ncontrib), _stream(stream)), "omnigs_render_fwd")
 
 
 def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):
@@ -141,9 +146,10 @@ def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):
                                  _ptr(workspace), _stream(stream)), "omnigs_l1_loss")
 
 
-def omnigs_render_bwd(cfg, n, splats, ranges, values, out_T, ncontrib, dL_drgb, grads, stream=None):
-    _check(load().omnigs_render_bwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(values), _ptr(out_T),
-                                    _ptr(ncontrib), _ptr(dL_drgb), _ptr(grads), _stream(stream)), "omnigs_render_bwd")
+def omnigs_render_bwd(cfg, n, splats, ranges, keys, order, out_T, ncontrib, dL_drgb, grads, stream=None):
+    _check(load().omnigs_render_bwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(keys), _ptr(order),
+                                    _ptr(out_T), _ptr(ncontrib), _ptr(dL_drgb), _ptr(grads), _stream(stream)),
+           "omnigs_render_bwd")
 
 
 def omnigs_preprocess_bwd(cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means, d_scales, d_quats,

@@ -1,20 +1,19 @@
-// Tile binning ("one instance per influence", Sec. 3.3) and the ordering of every tile's list by t_r (Sec. 3.3).
+// Tile binning ("one instance per influence", Sec. 3.3) and the sort of every tile's list by t_r (Sec. 3.3).
 //
-// The order produced is that of a stable sort of (view * TILES + tile, t_r) keys, i.e. a two-digit radix sort whose
-// most significant digit is the tile. The tile digit is resolved by counting instead of by key passes over HBM:
-//   1. tile_count: CTAs walk chunks of 2048 splats of one view, enumerate their instances warp-cooperatively,
-//      count them per tile in shared memory and add the counts to the global per-tile counts (one atomic per touched
-//      tile and chunk instead of one per instance);
-//   2. scan_*: an exclusive scan of the counts gives each tile's [start, end) range (the ranges the blend kernels
-//      read) and a write cursor per tile; the 64-bit total is checked against the capacity;
-//   3. bin_emit: the same walk reserves one block of slots per touched tile and chunk, then writes every instance
-//      (t_r bits, splat index) into it;
-//   4. segment_sort: one CTA per tile sorts its segment in shared memory by the t_r bits that vary within it (LSD,
-//      8-bit digits, stable ranking with warp match-any), then orders runs of equal t_r by splat index, which gives
-//      exactly the stable-sort order whatever order the atomics left; segments larger than shared memory are sorted
-//      in chunks and merged along merge paths.
-// HBM traffic is ~8 B written by the emit and 8 B read + 8 B written by the segment sort per instance, instead of
-// ~32 B per instance per pass of a device-wide radix sort. There are no inter-CTA waits.
+// The blending order is that of a stable sort of (view * TILES + tile, t_r) keys over instances generated splat by
+// splat. Here that order is produced with short keys and coalesced passes only:
+//   1. depth_keys + LSD sort: the V * N splats are sorted once by (view, t_r bits), stable, so ties keep splat order.
+//      order[v * N + r] is the r-th nearest splat of view v; rank[v * N + g] is the inverse. Ranks are unique, so
+//      comparing ranks equals comparing (t_r, splat index).
+//   2. bin_count / bin_scan / bin_emit: per-splat instance counts, a 64-bit exclusive scan (overflow checked against
+//      the capacity) and a warp-cooperative emission that writes, in generation order and fully coalesced, one key
+//      per instance: ((v * TILES + tile) << rank_bits) | rank.
+//   3. LSD radix sort of the instance keys over the ceil(log2(V * TILES)) + rank_bits bits in use, in an even
+//      number of <= 9-bit passes (upsweep: per-CTA digit counts; one-CTA scan; downsweep: stable in-CTA ranking with
+//      warp match-any, staging in shared memory in digit order, and runs of equal digits written to HBM). The keys
+//      carry no payload: the splat is order[v * N + rank].
+//   4. tile_ranges: [start, end) of every tile from the sorted keys.
+// No pass waits on another CTA, so there are no spin loops.
 #include <algorithm>
 
 #include "common.cuh"
@@ -56,7 +55,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
 }
 
 struct SplatPos {
-    float px, py;
+    float px, py, depth;
     int radius;
 };
 
@@ -69,129 +68,58 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
     SplatPos p;
     p.px = a.x;
     p.py = a.y;
+    p.depth = c.y;
     p.radius = __float_as_int(c.z);
     const bool inside = a.x >= 0.f && a.x <= (float)(tiles_x * tile) && a.y >= 0.f && a.y <= (float)(tiles_y * tile);
     if (!inside || p.radius > kMaxRadius) p.radius = 0;
     return p;
 }
 
-// ------------------------------------------------------------------------------------------- instance walk
-
-// Splats are processed in chunks of kChunk consecutive splats of one view. The warps of a CTA take 32 splats at a
-// time and enumerate their instances together (one per lane per round, owner found by a binary search over the
-// warp's exclusive prefix of counts), calling fn(local_tile, depth_bits, splat_index) for each.
-constexpr int kChunk = 2048;
-constexpr int kBinCtaThreads = 512;
-constexpr int kAggTiles = 16384;  // tiles per view up to which per-tile counts are aggregated in shared memory
-
-struct ChunkSpan {
-    int v;
-    int64_t begin, end;  // splat indices v * n + g
-};
-
-__device__ __forceinline__ ChunkSpan chunk_span(int64_t c, int n, int chunks_per_view) {
-    ChunkSpan cs;
-    cs.v = (int)(c / chunks_per_view);
-    const int64_t g0 = (c - (int64_t)cs.v * chunks_per_view) * kChunk;
-    cs.begin = (int64_t)cs.v * n + g0;
-    cs.end = (int64_t)cs.v * n + min((int64_t)n, g0 + kChunk);
-    return cs;
-}
-
-template <typename Fn>
-__device__ __forceinline__ void for_each_instance(const ChunkSpan& cs, const float4* __restrict__ splats, int tiles_x,
-                                                  int tiles_y, int tile, Fn&& fn) {
-    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int64_t g0 = cs.begin + (int64_t)warp * 32; g0 < cs.end; g0 += (int64_t)nwarps * 32) {
-        const int64_t i = g0 + lane;
-        unsigned cnt = 0, dbits = 0;
-        Rect r = {0, 1, 0, 0};
-        if (i < cs.end) {
-            const SplatPos p = load_pos(splats, (size_t)i, tiles_x, tiles_y, tile);
-            if (p.radius > 0) {
-                r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
-                cnt = (unsigned)(r.nx * r.ny);
-                dbits = __float_as_uint(__ldg(reinterpret_cast<const float*>(splats + 3 * i + 2) + 1));
-            }
-        }
-        unsigned incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (unsigned)o) incl += y;
-        }
-        const unsigned excl = incl - cnt;
-        const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
-        for (unsigned base = 0; base < wtotal; base += 32) {
-            const unsigned e = base + lane;
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const unsigned ex = __shfl_sync(0xffffffffu, excl, (j + step) & 31);
-                if (j + step < 32 && ex <= e) j += step;
-            }
-            const unsigned k = e - __shfl_sync(0xffffffffu, excl, j);
-            const int x0 = __shfl_sync(0xffffffffu, r.x0, j);
-            const int nx = __shfl_sync(0xffffffffu, r.nx, j);
-            const int y0 = __shfl_sync(0xffffffffu, r.y0, j);
-            const unsigned db = __shfl_sync(0xffffffffu, dbits, j);
-            if (e < wtotal) {
-                const int row = (int)(k / (unsigned)nx);
-                const int col = (int)(k - (unsigned)row * (unsigned)nx);
-                int tx = (x0 + col) % tiles_x;
-                tx += tx < 0 ? tiles_x : 0;
-                fn((unsigned)((y0 + row) * tiles_x + tx), db, (unsigned)(g0 + j));
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------------------------------- 1: tile counts
-
-template <bool kAgg>
-__global__ void __launch_bounds__(kBinCtaThreads)
-tile_count_kernel(int64_t nchunks, int n, int chunks_per_view, const float4* __restrict__ splats, int tiles_x,
-                  int tiles_y, int tile, uint32_t* __restrict__ counts) {
-    extern __shared__ unsigned s_cnt[];
-    const int tpv = tiles_x * tiles_y;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const ChunkSpan cs = chunk_span(c, n, chunks_per_view);
-        uint32_t* vcounts = counts + (size_t)cs.v * tpv;
-        if (kAgg) {
-            for (int t = threadIdx.x; t < tpv; t += blockDim.x) s_cnt[t] = 0;
-            __syncthreads();
-            for_each_instance(cs, splats, tiles_x, tiles_y, tile,
-                              [&](unsigned t, unsigned, unsigned) { atomicAdd(&s_cnt[t], 1u); });
-            __syncthreads();
-            for (int t = threadIdx.x; t < tpv; t += blockDim.x)
-                if (s_cnt[t]) atomicAdd(vcounts + t, s_cnt[t]);
-            __syncthreads();
-        } else {
-            for_each_instance(cs, splats, tiles_x, tiles_y, tile,
-                              [&](unsigned t, unsigned, unsigned) { atomicAdd(vcounts + t, 1u); });
-        }
-    }
-}
-
-// ------------------------------------------------------------------------------------------- 2: scan
-
-constexpr int kScanItems = 16;
-constexpr int kScanBlock = kBinThreads * kScanItems;
+// ------------------------------------------------------------------------------------------- 1: splat depth order
 
 __global__ void __launch_bounds__(kBinThreads)
-scan_reduce_kernel(u64 ntiles, const uint32_t* __restrict__ counts, u64* __restrict__ block_sums) {
-    __shared__ u64 scratch[32];
-    const u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
-    u64 s = 0;
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < ntiles) s += counts[base + k];
-    u64 tot;
-    block_exclusive_scan<u64>(s, scratch, &tot);
+depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* __restrict__ keys,
+                  uint32_t* __restrict__ vals, u64* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if (i == 0) *count = (u64)total;
+    if (i >= total) return;
+    const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 2) + 1);
+    keys[i] = ((u64)(i / n) << 32) | (u64)__float_as_uint(d);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+rank_kernel(int64_t total, int n, const uint32_t* __restrict__ order, uint32_t* __restrict__ rank) {
+    const int64_t p = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if (p >= total) return;
+    const uint32_t vg = order[p];
+    rank[vg] = (uint32_t)(p - (p / n) * n);
+}
+
+// ------------------------------------------------------------------------------------------- 2: instances
+
+__global__ void __launch_bounds__(kBinThreads)
+bin_count_kernel(int64_t total, const float4* __restrict__ splats, int tiles_x, int tiles_y, int tile,
+                 unsigned* __restrict__ block_sums) {
+    __shared__ unsigned scratch[32];
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    unsigned cnt = 0;
+    if (i < total) {
+        const SplatPos p = load_pos(splats, (size_t)i, tiles_x, tiles_y, tile);
+        if (p.radius > 0) {
+            const Rect r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
+            cnt = (unsigned)(r.nx * r.ny);
+        }
+    }
+    unsigned tot;
+    block_exclusive_scan<unsigned>(cnt, scratch, &tot);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
+// One CTA: exclusive scan of the per-CTA sums in 64 bits; total to the header, overflow flagged.
 __global__ void __launch_bounds__(1024)
-scan_blocks_kernel(int nblocks, u64* __restrict__ block_sums, WsHeader* __restrict__ hdr, u64 capacity) {
+bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __restrict__ block_offsets,
+                WsHeader* __restrict__ hdr, u64 capacity) {
     __shared__ u64 scratch[32];
     const int per = (nblocks + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblocks);
@@ -200,9 +128,8 @@ scan_blocks_kernel(int nblocks, u64* __restrict__ block_sums, WsHeader* __restri
     u64 tot;
     u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
     for (int b = b0; b < b1; ++b) {
-        const u64 c = block_sums[b];
-        block_sums[b] = run;  // becomes the exclusive offset of the block
-        run += c;
+        block_offsets[b] = run;
+        run += block_sums[b];
     }
     if (threadIdx.x == 0) {
         hdr->count = tot;
@@ -210,411 +137,377 @@ scan_blocks_kernel(int nblocks, u64* __restrict__ block_sums, WsHeader* __restri
     }
 }
 
+// The 32 splats of a warp own one contiguous output range; each lane writes every 32nd instance of it (owner found
+// by a binary search over the warp's exclusive prefix of counts), so stores are coalesced even for splats that cover
+// thousands of tiles. Instances of a splat are listed row by row, columns in seam order.
 __global__ void __launch_bounds__(kBinThreads)
-scan_write_kernel(u64 ntiles, const uint32_t* __restrict__ counts, const u64* __restrict__ block_offsets,
-                  u64 capacity, uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursors) {
-    __shared__ u64 scratch[32];
-    const u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
-    unsigned c[kScanItems];
-    u64 s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        c[k] = base + k < ntiles ? counts[base + k] : 0u;
-        s += c[k];
+bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, int tiles_x, int tiles_y, int tile,
+                int rank_bits, const uint32_t* __restrict__ rank, const u64* __restrict__ block_offsets,
+                u64* __restrict__ keys, u64 capacity) {
+    __shared__ unsigned scratch[32];
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const int tiles = tiles_x * tiles_y;
+    unsigned cnt = 0;
+    Rect r = {0, 1, 0, 0};
+    u64 low = 0, tbase = 0;
+    if (i < total) {
+        const SplatPos p = load_pos(splats, (size_t)i, tiles_x, tiles_y, tile);
+        if (p.radius > 0) {
+            r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
+            cnt = (unsigned)(r.nx * r.ny);
+            low = rank[i];
+            tbase = (u64)(i / n) * (u64)tiles;
+        }
     }
-    u64 tot;
-    u64 run = block_offsets[blockIdx.x] + block_exclusive_scan<u64>(s, scratch, &tot);
+    unsigned blk_total;
+    const unsigned local = block_exclusive_scan<unsigned>(cnt, scratch, &blk_total);
+    const u64 off = block_offsets[blockIdx.x] + local;
+    const unsigned lane = lane_id();
+    unsigned incl = cnt;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < ntiles) {
-            const u64 e = run + c[k];
-            ranges[2 * (base + k)] = (uint32_t)min(run, capacity);
-            ranges[2 * (base + k) + 1] = (uint32_t)min(e, capacity);
-            cursors[base + k] = (uint32_t)min(run, capacity);
-            run = e;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+    }
+    const unsigned excl = incl - cnt;
+    const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    const u64 woff = __shfl_sync(0xffffffffu, off - excl, 0);
+    for (unsigned base = 0; base < wtotal; base += 32) {
+        const unsigned e = base + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const unsigned ex = __shfl_sync(0xffffffffu, excl, (j + step) & 31);
+            if (j + step < 32 && ex <= e) j += step;
+        }
+        const unsigned k = e - __shfl_sync(0xffffffffu, excl, j);
+        const int x0 = __shfl_sync(0xffffffffu, r.x0, j);
+        const int nx = __shfl_sync(0xffffffffu, r.nx, j);
+        const int y0 = __shfl_sync(0xffffffffu, r.y0, j);
+        const u64 lo = __shfl_sync(0xffffffffu, low, j);
+        const u64 tb = __shfl_sync(0xffffffffu, tbase, j);
+        if (e < wtotal) {
+            const int row = (int)(k / (unsigned)nx);
+            const int col = (int)(k - (unsigned)row * (unsigned)nx);
+            int tx = (x0 + col) % tiles_x;
+            tx += tx < 0 ? tiles_x : 0;
+            const u64 idx = woff + e;
+            if (idx < capacity) keys[idx] = ((tb + (u64)((y0 + row) * tiles_x + tx)) << rank_bits) | lo;
         }
     }
 }
 
-// ------------------------------------------------------------------------------------------- 3: emission
+// ------------------------------------------------------------------------------------------- 3: LSD radix sort
 
-// Each CTA counts its chunk's instances per tile in shared memory, reserves one block of slots per touched tile with
-// a single global atomic, then writes every instance (t_r bits, splat index) into its tile's block.
-template <bool kAgg>
-__global__ void __launch_bounds__(kBinCtaThreads)
-bin_emit_kernel(int64_t nchunks, int n, int chunks_per_view, const float4* __restrict__ splats, int tiles_x,
-                int tiles_y, int tile, uint32_t* __restrict__ cursors, uint32_t* __restrict__ keys,
-                uint32_t* __restrict__ values, uint32_t capacity) {
-    extern __shared__ unsigned s_mem[];
-    const int tpv = tiles_x * tiles_y;
-    unsigned* s_cnt = s_mem;
-    unsigned* s_base = s_mem + tpv;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const ChunkSpan cs = chunk_span(c, n, chunks_per_view);
-        uint32_t* vcur = cursors + (size_t)cs.v * tpv;
-        auto put = [&](unsigned pos, unsigned db, unsigned vg) {
-            if (pos < capacity) {
-                keys[pos] = db;
-                values[pos] = vg;
-            }
-        };
-        if (kAgg) {
-            for (int t = threadIdx.x; t < tpv; t += blockDim.x) s_cnt[t] = 0;
-            __syncthreads();
-            for_each_instance(cs, splats, tiles_x, tiles_y, tile,
-                              [&](unsigned t, unsigned, unsigned) { atomicAdd(&s_cnt[t], 1u); });
-            __syncthreads();
-            for (int t = threadIdx.x; t < tpv; t += blockDim.x) {
-                const unsigned k = s_cnt[t];
-                s_base[t] = k ? atomicAdd(vcur + t, k) : 0u;
-                s_cnt[t] = 0;
-            }
-            __syncthreads();
-            for_each_instance(cs, splats, tiles_x, tiles_y, tile, [&](unsigned t, unsigned db, unsigned vg) {
-                put(s_base[t] + atomicAdd(&s_cnt[t], 1u), db, vg);
-            });
-            __syncthreads();
-        } else {
-            for_each_instance(cs, splats, tiles_x, tiles_y, tile,
-                              [&](unsigned t, unsigned db, unsigned vg) { put(atomicAdd(vcur + t, 1u), db, vg); });
-        }
-    }
-}
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per CTA tile
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kHistRow = kRadixMax + 1;  // + one bucket for the padding past the end
 
-// ------------------------------------------------------------------------------------------- 4: segment sort
-
-// Stable LSD radix sort of one tile's (t_r bits, splat) pairs, NT threads x ITEMS pairs, keys held in registers
-// between passes. Element e = warp * ITEMS * 32 + j * 32 + lane lives in register j of that lane, so the order of
-// (warp, j, lane) is the element order. Per pass: every warp ranks its items with match-any (rank = peers below the
-// lane + running per-warp count of the digit), one CTA scan over the digit-major [digit][warp] counts gives every
-// (digit, warp) its output offset, the items are scattered to shared memory and read back in element order.
-constexpr int kRadix = 256;
-
-// Counter of (digit d, warp w), digit-major with the warp index XOR-swizzled by the digit, so that lanes ranking
-// different digits hit different banks while one digit's NW counters stay contiguous for the scan.
-template <int NW>
-__device__ __forceinline__ unsigned cnt_index(unsigned d, unsigned w) { return d * NW + (w ^ (d & (NW - 1))); }
-
-template <int NT, int ITEMS>
-struct TileSortSmem {
-    static constexpr int NW = NT / 32;
-    unsigned keys[NT * ITEMS];
-    unsigned vals[NT * ITEMS];
-    unsigned cnt[(kRadix + 1) * NW];  // [digit][warp]; digit kRadix collects the padding past the end
-    unsigned scratch[32];
-    unsigned red[2];
-    unsigned flag;
+struct TileSpan {
+    u64 begin, end;
 };
 
-template <int NT, int ITEMS>
-__device__ void tile_sort(uint32_t* __restrict__ gk, uint32_t* __restrict__ gv, int n, TileSortSmem<NT, ITEMS>& S) {
-    constexpr int NW = NT / 32;
-    constexpr int PER = (kRadix * NW) / NT;  // scan entries per thread
-    const unsigned tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned key[ITEMS], val[ITEMS];
-    unsigned kand = 0xffffffffu, kor = 0u;
+__device__ __forceinline__ TileSpan cta_tiles(u64 cnt, int G) {
+    const u64 tiles_total = (cnt + kSortTile - 1) / kSortTile;
+    const u64 tpb = (tiles_total + G - 1) / G;
+    TileSpan s;
+    s.begin = min((u64)blockIdx.x * tpb, tiles_total);
+    s.end = min(s.begin + tpb, tiles_total);
+    return s;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+lsd_upsweep_kernel(const u64* __restrict__ keys, const u64* __restrict__ count, u64 capacity, int shift, int dbits,
+                   unsigned* __restrict__ hist, int G) {
+    __shared__ unsigned s_hist[kWarps][kRadixMax];
+    const unsigned R = 1u << dbits, mask = R - 1;
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    for (unsigned d = lane; d < R; d += 32) s_hist[warp][d] = 0;
+    __syncwarp();
+    const u64 cnt = min(*count, capacity);
+    const TileSpan span = cta_tiles(cnt, G);
+    for (u64 t = span.begin; t < span.end; ++t) {
+        const u64 base = t * kSortTile + warp * (kSortItems * 32) + lane;
+        unsigned d[kSortItems];
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int e = (warp * ITEMS + j) * 32 + lane;
-        const bool ok = e < n;
-        key[j] = ok ? gk[e] : 0xffffffffu;
-        val[j] = ok ? gv[e] : 0u;
-        if (ok) {
-            kand &= key[j];
-            kor |= key[j];
+        for (int j = 0; j < kSortItems; ++j) {
+            const u64 idx = base + (u64)j * 32;
+            d[j] = idx < cnt ? (unsigned)(__ldg(keys + idx) >> shift) & mask : R;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            // one shared-memory add per distinct digit of the warp
+            const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
+            if (d[j] < R && lane == (unsigned)(__ffs(peers) - 1)) s_hist[warp][d[j]] += __popc(peers);
+            __syncwarp();
         }
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        kand &= __shfl_xor_sync(0xffffffffu, kand, o);
-        kor |= __shfl_xor_sync(0xffffffffu, kor, o);
-    }
-    if (tid == 0) {
-        S.red[0] = 0xffffffffu;
-        S.red[1] = 0u;
-        S.flag = 0u;
-    }
     __syncthreads();
-    if (lane == 0) {
-        atomicAnd(&S.red[0], kand);
-        atomicOr(&S.red[1], kor);
-    }
-    __syncthreads();
-    const unsigned diff = S.red[1] & ~S.red[0];
-    const int nbits = diff ? 32 - __clz(diff) : 0;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        for (int i = tid; i < (kRadix + 1) * NW; i += NT) S.cnt[i] = 0;
-        __syncthreads();
-        unsigned rk[ITEMS];
+    for (unsigned d = threadIdx.x; d < R; d += blockDim.x) {
+        unsigned s = 0;
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int e = (warp * ITEMS + j) * 32 + lane;
-            const unsigned d = e < n ? (key[j] >> shift) & 0xffu : (unsigned)kRadix;
+        for (int w = 0; w < kWarps; ++w) s += s_hist[w][d];
+        hist[(size_t)d * G + blockIdx.x] = s;
+    }
+}
+
+// One CTA: exclusive scan over the digit-major histogram [R * G].
+__global__ void __launch_bounds__(1024) lsd_scan_kernel(unsigned* __restrict__ hist, int total) {
+    __shared__ unsigned scratch[32];
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, total);
+    unsigned local = 0;
+    for (int b = b0; b < b1; ++b) local += hist[b];
+    unsigned tot;
+    unsigned run = block_exclusive_scan<unsigned>(local, scratch, &tot);
+    for (int b = b0; b < b1; ++b) {
+        const unsigned c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+}
+
+template <bool kVals>
+size_t downsweep_smem() {
+    return sizeof(u64) * kSortTile + (kVals ? sizeof(unsigned) * kSortTile : 0) +
+           sizeof(unsigned) * (kWarps * kHistRow + 3 * kRadixMax + 32);
+}
+
+template <bool kVals>
+__global__ void __launch_bounds__(kSortThreads)
+lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict__ vals_in, u64* __restrict__ keys_out,
+                     unsigned* __restrict__ vals_out, const u64* __restrict__ count, u64 capacity, int shift, int dbits,
+                     const unsigned* __restrict__ hist, int G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64* s_keys = reinterpret_cast<u64*>(smem_raw);
+    unsigned* s_vals = reinterpret_cast<unsigned*>(s_keys + kSortTile);
+    unsigned* s_whist = kVals ? s_vals + kSortTile : s_vals;
+    unsigned* s_start = s_whist + kWarps * kHistRow;
+    unsigned* s_tot = s_start + kRadixMax;
+    unsigned* s_gbase = s_tot + kRadixMax;
+    unsigned* s_scratch = s_gbase + kRadixMax;
+
+    const unsigned R = 1u << dbits, mask = R - 1;
+    const unsigned tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const u64 cnt = min(*count, capacity);
+    const TileSpan span = cta_tiles(cnt, G);
+    for (unsigned d = tid; d < R; d += kSortThreads) s_gbase[d] = hist[(size_t)d * G + blockIdx.x];
+    unsigned* my_hist = s_whist + warp * kHistRow;
+
+    for (u64 t = span.begin; t < span.end; ++t) {
+        for (unsigned d = lane; d <= R; d += 32) my_hist[d] = 0;
+        __syncwarp();
+        const u64 base = t * kSortTile + warp * (kSortItems * 32) + lane;
+        u64 k[kSortItems];
+        unsigned val[kSortItems], rk[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const u64 idx = base + (u64)j * 32;
+            const bool ok = idx < cnt;
+            k[j] = ok ? __ldg(keys_in + idx) : ~0ull;
+            if (kVals) val[j] = ok ? __ldg(vals_in + idx) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const u64 idx = base + (u64)j * 32;
+            const unsigned d = idx < cnt ? (unsigned)(k[j] >> shift) & mask : R;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
-            unsigned* c = &S.cnt[cnt_index<NW>(d, warp)];
-            const unsigned before = *c;
+            const unsigned before = my_hist[d];
             __syncwarp();
-            if (lane == (unsigned)(__ffs(peers) - 1)) *c = before + __popc(peers);
+            if (lane == (unsigned)(__ffs(peers) - 1)) my_hist[d] = before + __popc(peers);
             __syncwarp();
-            rk[j] = before + __popc(peers & lt);
+            rk[j] = before + __popc(peers & lt_mask);
         }
         __syncthreads();
-        // exclusive scan over the digit-major counts of the kRadix real digits
+        for (unsigned d = tid; d < R; d += kSortThreads) {
+            unsigned acc = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const unsigned c = s_whist[w * kHistRow + d];
+                s_whist[w * kHistRow + d] = acc;
+                acc += c;
+            }
+            s_tot[d] = acc;
+        }
+        __syncthreads();
         {
+            constexpr int PER = kRadixMax / kSortThreads;
             unsigned loc[PER], sum = 0;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                const unsigned idx = tid * PER + q;  // logical digit-major position
-                loc[q] = S.cnt[cnt_index<NW>(idx / NW, idx % NW)];
+                const unsigned d = tid * PER + q;
+                loc[q] = d < R ? s_tot[d] : 0u;
                 sum += loc[q];
             }
-            unsigned tot;
-            unsigned run = block_exclusive_scan<unsigned>(sum, S.scratch, &tot);
+            unsigned tile_total;
+            unsigned run = block_exclusive_scan<unsigned>(sum, s_scratch, &tile_total);
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                const unsigned idx = tid * PER + q;
-                S.cnt[cnt_index<NW>(idx / NW, idx % NW)] = run;
+                const unsigned d = tid * PER + q;
+                if (d < R) s_start[d] = run;
                 run += loc[q];
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int e = (warp * ITEMS + j) * 32 + lane;
-            if (e < n) {
-                const unsigned pos = S.cnt[cnt_index<NW>((key[j] >> shift) & 0xffu, warp)] + rk[j];
-                S.keys[pos] = key[j];
-                S.vals[pos] = val[j];
+        for (int j = 0; j < kSortItems; ++j) {
+            const u64 idx = base + (u64)j * 32;
+            if (idx < cnt) {
+                const unsigned d = (unsigned)(k[j] >> shift) & mask;
+                const unsigned pos = s_start[d] + my_hist[d] + rk[j];
+                s_keys[pos] = k[j];
+                if (kVals) s_vals[pos] = val[j];
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int e = (warp * ITEMS + j) * 32 + lane;
-            if (e < n) {
-                key[j] = S.keys[e];
-                val[j] = S.vals[e];
-            }
+        const unsigned nvalid = (unsigned)min((u64)kSortTile, cnt - t * kSortTile);
+        for (unsigned i = tid; i < nvalid; i += kSortThreads) {
+            const u64 key = s_keys[i];
+            const unsigned d = (unsigned)(key >> shift) & mask;
+            const unsigned gpos = s_gbase[d] + (i - s_start[d]);
+            keys_out[gpos] = key;
+            if (kVals) vals_out[gpos] = s_vals[i];
         }
         __syncthreads();
-    }
-    // equal t_r: order by splat index (a run of equal keys keeps the unspecified bucket order until here)
-    bool tie = false;
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int e = (warp * ITEMS + j) * 32 + lane;
-        const unsigned nxt = __shfl_down_sync(0xffffffffu, key[j], 1);
-        if (lane < 31 && e + 1 < n && nxt == key[j]) tie = true;
-        if (e < n) S.keys[e] = key[j];  // element order (already there unless no pass ran)
-    }
-    if (__any_sync(0xffffffffu, tie) && lane == 0) S.flag = 1u;
-    __syncthreads();
-    // pairs straddling two lanes' registers of different rounds are checked in shared memory
-    if (!S.flag) {
-        for (int e = tid; e + 1 < n; e += NT)
-            if (((e + 1) & 31) == 0 && S.keys[e] == S.keys[e + 1]) S.flag = 1u;
-    }
-    __syncthreads();
-    if (S.flag) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int e = (warp * ITEMS + j) * 32 + lane;
-            if (e < n) S.vals[e] = val[j];
-        }
+        for (unsigned d = tid; d < R; d += kSortThreads) s_gbase[d] += s_tot[d];
         __syncthreads();
-        for (int i = tid; i < n; i += NT) {
-            if (i > 0 && S.keys[i - 1] == S.keys[i]) continue;      // not a run start
-            if (i + 1 >= n || S.keys[i + 1] != S.keys[i]) continue;  // run of length 1
-            int e = i + 1;
-            while (e < n && S.keys[e] == S.keys[i]) ++e;
-            for (int a = i + 1; a < e; ++a) {
-                const unsigned x = S.vals[a];
-                int b = a - 1;
-                while (b >= i && S.vals[b] > x) {
-                    S.vals[b + 1] = S.vals[b];
-                    --b;
-                }
-                S.vals[b + 1] = x;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int e = (warp * ITEMS + j) * 32 + lane;
-            if (e < n) val[j] = S.vals[e];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const int e = (warp * ITEMS + j) * 32 + lane;
-        if (e < n) {
-            gk[e] = key[j];
-            gv[e] = val[j];
-        }
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ bool pair_less(unsigned ka, unsigned va, unsigned kb, unsigned vb) {
-    return ka < kb || (ka == kb && va < vb);
-}
-
-// Merge sorted runs a = [a0, a0 + la) and b = [b0, b0 + lb) of (keys, vals) into (ok, ov) starting at o0, along merge
-// paths: thread t produces outputs [t P, (t + 1) P).
-__device__ void merge_runs(const unsigned* __restrict__ keys, const unsigned* __restrict__ vals, int64_t a0, int la,
-                           int64_t b0, int lb, unsigned* __restrict__ ok, unsigned* __restrict__ ov, int64_t o0) {
-    const int total = la + lb;
-    const int P = (total + blockDim.x - 1) / blockDim.x;
-    const int d0 = min((int)threadIdx.x * P, total), d1 = min(d0 + P, total);
-    if (d0 >= d1) return;
-    int lo = max(0, d0 - lb), hi = min(d0, la);  // smallest i with b[d0 - 1 - i] < a[i]
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int j = d0 - 1 - mid;
-        if (pair_less(keys[b0 + j], vals[b0 + j], keys[a0 + mid], vals[a0 + mid])) hi = mid;
-        else lo = mid + 1;
-    }
-    int i = lo, j = d0 - lo;
-    for (int d = d0; d < d1; ++d) {
-        bool take_a;
-        if (i >= la) take_a = false;
-        else if (j >= lb) take_a = true;
-        else take_a = !pair_less(keys[b0 + j], vals[b0 + j], keys[a0 + i], vals[a0 + i]);
-        if (take_a) {
-            ok[o0 + d] = keys[a0 + i];
-            ov[o0 + d] = vals[a0 + i];
-            ++i;
-        } else {
-            ok[o0 + d] = keys[b0 + j];
-            ov[o0 + d] = vals[b0 + j];
-            ++j;
-        }
     }
 }
 
-// One CTA per tile (grid-stride). Segments of up to NT * ITEMS pairs are sorted in registers and shared memory;
-// longer ones are sorted in chunks of that size and merged pairwise through the scratch buffers.
-template <int NT, int ITEMS>
-__global__ void __launch_bounds__(NT, 16 / ITEMS)
-segment_sort_kernel(u64 ntiles, const uint32_t* __restrict__ ranges, uint32_t* __restrict__ keys,
-                    uint32_t* __restrict__ values, uint32_t* __restrict__ scratch_k, uint32_t* __restrict__ scratch_v,
-                    int min_len, int max_len) {
-    constexpr int CAP = NT * ITEMS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSortSmem<NT, ITEMS>& S = *reinterpret_cast<TileSortSmem<NT, ITEMS>*>(smem_raw);
-    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-        const int n = (int)(end - start);
-        if (n < min_len || n > max_len || n < 2) continue;
-        uint32_t* gk = keys + start;
-        uint32_t* gv = values + start;
-        for (int c0 = 0; c0 < n; c0 += CAP) tile_sort<NT, ITEMS>(gk + c0, gv + c0, min(CAP, n - c0), S);
-        if (n <= CAP) continue;
-        uint32_t *sk = keys, *sv = values, *dk = scratch_k, *dv = scratch_v;
-        for (int width = CAP; width < n; width *= 2) {
-            for (int a0 = 0; a0 < n; a0 += 2 * width) {
-                const int la = min(width, n - a0);
-                const int lb = max(0, min(width, n - a0 - la));
-                merge_runs(sk, sv, (int64_t)start + a0, la, (int64_t)start + a0 + la, lb, dk, dv, (int64_t)start + a0);
-            }
-            __syncthreads();
-            uint32_t* tk = sk; sk = dk; dk = tk;
-            uint32_t* tv = sv; sv = dv; dv = tv;
-        }
-        if (sk != keys) {
-            for (int i = threadIdx.x; i < n; i += NT) {
-                keys[start + i] = sk[start + i];
-                values[start + i] = sv[start + i];
-            }
-            __syncthreads();
-        }
+// ------------------------------------------------------------------------------------------- 4: tile ranges
+
+__global__ void ranges_kernel(const u64* __restrict__ keys, const WsHeader* __restrict__ hdr, u64 capacity,
+                              int rank_bits, u64 ntiles, uint32_t* __restrict__ ranges) {
+    const u64 cnt = min(hdr->count, capacity);
+    for (u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x; s < cnt; s += (u64)gridDim.x * blockDim.x) {
+        const u64 t = __ldg(keys + s) >> rank_bits;
+        if (t >= ntiles) continue;  // cannot happen for keys written by bin_emit
+        if (s == 0 || (__ldg(keys + s - 1) >> rank_bits) != t) ranges[2 * t] = (uint32_t)s;
+        if (s + 1 == cnt || (__ldg(keys + s + 1) >> rank_bits) != t) ranges[2 * t + 1] = (uint32_t)(s + 1);
     }
 }
 
-constexpr int kSmallNT = 512, kSmallItems = 8;   // lists up to 4096
-constexpr int kLargeNT = 512, kLargeItems = 16;  // lists up to 8192 at once, longer ones merged
+// Radix-sort geometry: `bits` key bits in an even number of passes of <= 9 bits.
+struct Plan {
+    int passes, digit;
+};
 
-}  // namespace
+Plan plan_for(int bits) {
+    Plan p;
+    p.passes = (bits + 8) / 9;
+    if (p.passes < 2) p.passes = 2;
+    if (p.passes % 2) ++p.passes;
+    p.digit = (bits + p.passes - 1) / p.passes;
+    return p;
+}
 
-cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, uint32_t* keys,
-                       uint32_t* values, int64_t capacity, uint32_t* ranges, const WsLayout& L, char* ws,
-                       cudaStream_t stream) {
-    const int tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile, tpv = tx * ty;
-    const u64 ntiles = (u64)tpv * cfg.num_views;
-    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.tile_counts);
-    u64* bsums = reinterpret_cast<u64*>(ws + L.scan_blocks);
-    uint32_t* cursors = reinterpret_cast<uint32_t*>(ws + L.cursors);
-    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ntiles, stream);
+// Sorts `count` (device) keys (and values) in (k0, v0) through (k1, v1); the result lands back in (k0, v0).
+template <bool kVals>
+cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* count, u64 capacity, int bits, int G,
+                     unsigned* hist, cudaStream_t stream, const char* tag_up, const char* tag_down) {
+    const Plan P = plan_for(bits);
+    const size_t smem = downsweep_smem<kVals>();
+    cudaError_t e = cudaFuncSetAttribute(lsd_downsweep_kernel<kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    const float4* sp = reinterpret_cast<const float4*>(splats);
-    const int chunks_per_view = (int)((n + kChunk - 1) / kChunk);
-    const int64_t nchunks = (int64_t)chunks_per_view * cfg.num_views;
-    const bool agg = tpv <= kAggTiles;
-    const int grid = (int)std::min<int64_t>(std::max<int64_t>(nchunks, 1), (int64_t)num_sms() * 4);
-    if (nchunks > 0) {
-        ProfScope prof("tile_count", stream);
-        const size_t smem = agg ? sizeof(unsigned) * tpv : 0;
-        if (agg) {
-            e = cudaFuncSetAttribute(tile_count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            tile_count_kernel<true><<<grid, kBinCtaThreads, smem, stream>>>(nchunks, (int)n, chunks_per_view, sp, tx,
-                                                                            ty, cfg.tile, counts);
-        } else {
-            tile_count_kernel<false><<<grid, kBinCtaThreads, 0, stream>>>(nchunks, (int)n, chunks_per_view, sp, tx,
-                                                                          ty, cfg.tile, counts);
+    for (int p = 0; p < P.passes; ++p) {
+        const int shift = p * P.digit;
+        const int db = std::max(1, std::min(P.digit, bits - shift));
+        {
+            ProfScope prof(tag_up, stream);
+            lsd_upsweep_kernel<<<G, kSortThreads, 0, stream>>>(k0, count, capacity, shift, db, hist, G);
+            lsd_scan_kernel<<<1, 1024, 0, stream>>>(hist, (1 << db) * G);
         }
-    }
-    const int nb = (int)((ntiles + kScanBlock - 1) / kScanBlock);
-    {
-        ProfScope prof("tile_scan", stream);
-        scan_reduce_kernel<<<nb, kBinThreads, 0, stream>>>(ntiles, counts, bsums);
-        scan_blocks_kernel<<<1, 1024, 0, stream>>>(nb, bsums, hdr, (u64)capacity);
-        scan_write_kernel<<<nb, kBinThreads, 0, stream>>>(ntiles, counts, bsums, (u64)capacity, ranges, cursors);
-    }
-    if (nchunks > 0 && capacity > 0) {
-        ProfScope prof("bin_emit", stream);
-        const size_t smem = agg ? 2 * sizeof(unsigned) * tpv : 0;
-        if (agg) {
-            e = cudaFuncSetAttribute(bin_emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            bin_emit_kernel<true><<<grid, kBinCtaThreads, smem, stream>>>(nchunks, (int)n, chunks_per_view, sp, tx,
-                                                                          ty, cfg.tile, cursors, keys, values,
-                                                                          (uint32_t)capacity);
-        } else {
-            bin_emit_kernel<false><<<grid, kBinCtaThreads, 0, stream>>>(nchunks, (int)n, chunks_per_view, sp, tx,
-                                                                        ty, cfg.tile, cursors, keys, values,
-                                                                        (uint32_t)capacity);
+        {
+            ProfScope prof(tag_down, stream);
+            lsd_downsweep_kernel<kVals><<<G, kSortThreads, smem, stream>>>(k0, v0, k1, v1, count, capacity, shift, db,
+                                                                            hist, G);
         }
+        std::swap(k0, k1);
+        std::swap(v0, v1);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const omnigs_config& cfg, int64_t capacity, uint32_t* keys, uint32_t* values,
-                        const uint32_t* ranges, const WsLayout& L, char* ws, cudaStream_t stream) {
-    if (capacity == 0) return cudaSuccess;
-    const u64 ntiles = (u64)(cfg.width / cfg.tile) * (cfg.height / cfg.tile) * cfg.num_views;
-    uint32_t* sk = reinterpret_cast<uint32_t*>(ws + L.alt_keys);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(ws + L.alt_values);
-    constexpr size_t small_smem = sizeof(TileSortSmem<kSmallNT, kSmallItems>);
-    constexpr size_t large_smem = sizeof(TileSortSmem<kLargeNT, kLargeItems>);
-    auto ks = segment_sort_kernel<kSmallNT, kSmallItems>;
-    auto kl = segment_sort_kernel<kLargeNT, kLargeItems>;
-    cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
-    if (e != cudaSuccess) return e;
-    const u64 max_grid = (u64)num_sms() * 16;
-    const unsigned grid = (unsigned)(ntiles < max_grid ? ntiles : max_grid);
+int ceil_log2(uint64_t x) {
+    int b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+int sort_grid(u64 elems) {
+    const u64 tiles = (elems + kSortTile - 1) / kSortTile;
+    return (int)std::max<u64>(1, std::min<u64>(tiles, (u64)num_sms() * kSortCtasPerSm));
+}
+
+}  // namespace
+
+int rank_bits_for(int64_t n) { return std::max(1, ceil_log2((uint64_t)std::max<int64_t>(n, 1))); }
+
+int instance_key_bits(const omnigs_config& cfg, int64_t n) {
+    const uint64_t tiles = (uint64_t)(cfg.width / cfg.tile) * (cfg.height / cfg.tile) * cfg.num_views;
+    return ceil_log2(tiles) + rank_bits_for(n);
+}
+
+cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, uint32_t* order,
+                       uint64_t* keys, int64_t capacity, const WsLayout& L, char* ws, cudaStream_t stream) {
+    const int64_t total = n * cfg.num_views;
+    const int tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
+    if (e != cudaSuccess || total == 0) return e;
+    const float4* sp = reinterpret_cast<const float4*>(splats);
+    u64* dk0 = reinterpret_cast<u64*>(ws + L.depth_keys);
+    u64* dk1 = reinterpret_cast<u64*>(ws + L.depth_keys_alt);
+    unsigned* dv1 = reinterpret_cast<unsigned*>(ws + L.depth_vals_alt);
+    uint32_t* rank = reinterpret_cast<uint32_t*>(ws + L.rank);
+    unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
+    unsigned* bsums = reinterpret_cast<unsigned*>(ws + L.block_sums);
+    u64* boffs = reinterpret_cast<u64*>(ws + L.block_offsets);
+    const unsigned nb = (unsigned)((total + kBinThreads - 1) / kBinThreads);
     {
-        ProfScope prof("segment_sort", stream);
-        ks<<<grid, kSmallNT, small_smem, stream>>>(ntiles, ranges, keys, values, sk, sv, 0, kSmallNT * kSmallItems);
+        ProfScope prof("depth_keys", stream);
+        depth_keys_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
+    }
+    e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 32 + ceil_log2(cfg.num_views),
+                       sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope prof("depth_rank", stream);
+        rank_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, order, rank);
     }
     {
-        ProfScope prof("segment_sort_large", stream);
-        kl<<<grid, kLargeNT, large_smem, stream>>>(ntiles, ranges, keys, values, sk, sv, kSmallNT * kSmallItems + 1,
-                                                   0x7fffffff);
+        ProfScope prof("bin_count", stream);
+        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, tx, ty, cfg.tile, bsums);
+        bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
+    }
+    if (capacity > 0) {
+        ProfScope prof("bin_emit", stream);
+        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, tx, ty, cfg.tile, rank_bits_for(n), rank,
+                                                         boffs, reinterpret_cast<u64*>(keys), (u64)capacity);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, uint64_t* keys, uint32_t* ranges,
+                        const WsLayout& L, char* ws, cudaStream_t stream) {
+    const u64 ntiles = (u64)(cfg.width / cfg.tile) * (cfg.height / cfg.tile) * cfg.num_views;
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * ntiles, stream);
+    if (e != cudaSuccess || capacity == 0 || n == 0) return e;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
+    u64* alt = reinterpret_cast<u64*>(ws + L.alt_keys);
+    unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
+    e = lsd_sort<false>(reinterpret_cast<u64*>(keys), nullptr, alt, nullptr, &hdr->count, (u64)capacity,
+                        instance_key_bits(cfg, n), sort_grid((u64)capacity), hist, stream, "sort_upsweep",
+                        "sort_downsweep");
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope prof("tile_ranges", stream);
+        ranges_kernel<<<num_sms() * 8, 256, 0, stream>>>(reinterpret_cast<const u64*>(keys), hdr, (u64)capacity,
+                                                         rank_bits_for(n), ntiles, ranges);
     }
     return cudaGetLastError();
 }

@@ -23,11 +23,12 @@ constexpr uint32_t kErrCapacity = 1u;
 
 // Workspace header (first 256 bytes of every workspace).
 struct WsHeader {
-    unsigned long long count;  // total instances of the last bin (may exceed capacity)
-    unsigned int error;        // sticky device-side error bits
+    unsigned long long count;        // total instances of the last bin (may exceed capacity)
+    unsigned long long splat_count;  // V * n of the last bin
+    unsigned int error;              // sticky device-side error bits
     unsigned int pad0;
     float loss;
-    unsigned int pad1[3];
+    unsigned int pad1;
 };
 
 struct Rect {
@@ -62,19 +63,25 @@ __device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int ti
 }
 
 // Workspace layout (all offsets 256-byte aligned). Every region depends on the configuration and the capacity only.
+// Order: fixed-size regions, then those sized by the capacity, then those sized by n, so that calls which do not take
+// n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
-    size_t header, loss_partials, tile_counts, scan_blocks, cursors, alt_keys, alt_values, total;
+    size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, rank, block_sums,
+        block_offsets, total;
     int loss_blocks;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kBinThreads = 256;
+constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
+constexpr int kSortCtasPerSm = 4;    // radix-sort grid: up to this many CTAs per SM
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocks = 1024;
 
 int num_sms();
-WsLayout ws_layout(const omnigs_config &cfg, int64_t capacity);
+WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
+int rank_bits_for(int64_t n);
 
 // Kernel launches report their name and stream to the optional profiler.
 struct ProfScope {
@@ -92,18 +99,17 @@ cudaError_t launch_preprocess_bwd(const omnigs_config &cfg, int64_t n, const flo
                                   const float *quats, const float *opacity, const float *sh, const float *viewmats,
                                   const omnigs_splat_grad *grads, float *d_means, float *d_scales, float *d_quats,
                                   float *d_opacity, float *d_sh, float *d_screen, cudaStream_t stream);
-cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *keys,
-                       uint32_t *values, int64_t capacity, uint32_t *ranges, const WsLayout &L, char *ws,
-                       cudaStream_t stream);
-cudaError_t launch_sort(const omnigs_config &cfg, int64_t capacity, uint32_t *keys, uint32_t *values,
-                        const uint32_t *ranges, const WsLayout &L, char *ws, cudaStream_t stream);
+cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
+                       uint64_t *keys, int64_t capacity, const WsLayout &L, char *ws, cudaStream_t stream);
+cudaError_t launch_sort(const omnigs_config &cfg, int64_t n, int64_t capacity, uint64_t *keys, uint32_t *ranges,
+                        const WsLayout &L, char *ws, cudaStream_t stream);
 cudaError_t launch_render_fwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
-                              const uint32_t *ranges, const uint32_t *values, float *out_rgb, float *out_T,
-                              uint32_t *out_nc, cudaStream_t stream);
+                              const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
+                              float *out_T, uint32_t *out_nc, cudaStream_t stream);
 cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
-                              const uint32_t *ranges, const uint32_t *values, const float *out_T,
-                              const uint32_t *nc, const float *dL_drgb, omnigs_splat_grad *grads,
-                              cudaStream_t stream);
+                              const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
+                              const float *out_T, const uint32_t *nc, const float *dL_drgb,
+                              omnigs_splat_grad *grads, cudaStream_t stream);
 cudaError_t launch_l1(const omnigs_config &cfg, const float *rgb, const float *target, float *dL_drgb, float *loss,
                       const WsLayout &L, char *ws, cudaStream_t stream);
 

@@ -19,20 +19,22 @@ int num_sms() {
     return sms;
 }
 
-WsLayout ws_layout(const omnigs_config& cfg, int64_t capacity) {
+WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     WsLayout L;
-    const size_t tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile, V = cfg.num_views;
-    const size_t ntiles = tx * ty * V;
-    const size_t scan_blocks = (ntiles + 4095) / 4096;
+    const size_t total = (size_t)n * cfg.num_views;
+    const size_t nb = std::max<size_t>(1, (total + kBinThreads - 1) / kBinThreads);
     L.loss_blocks = kLossBlocks;
     size_t off = 0;
-    L.header = off;        off += align256(sizeof(WsHeader));
-    L.loss_partials = off; off += align256(sizeof(float) * L.loss_blocks);
-    L.tile_counts = off;   off += align256(sizeof(uint32_t) * ntiles);
-    L.scan_blocks = off;   off += align256(sizeof(unsigned long long) * scan_blocks);
-    L.cursors = off;       off += align256(sizeof(uint32_t) * ntiles);
-    L.alt_keys = off;      off += align256(sizeof(uint32_t) * (size_t)capacity);
-    L.alt_values = off;    off += align256(sizeof(uint32_t) * (size_t)capacity);
+    L.header = off;         off += align256(sizeof(WsHeader));
+    L.loss_partials = off;  off += align256(sizeof(float) * L.loss_blocks);
+    L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * (size_t)num_sms() * kSortCtasPerSm);
+    L.alt_keys = off;       off += align256(sizeof(unsigned long long) * (size_t)capacity);
+    L.depth_keys = off;     off += align256(sizeof(unsigned long long) * total);
+    L.depth_keys_alt = off; off += align256(sizeof(unsigned long long) * total);
+    L.depth_vals_alt = off; off += align256(sizeof(uint32_t) * total);
+    L.rank = off;           off += align256(sizeof(uint32_t) * total);
+    L.block_sums = off;     off += align256(sizeof(unsigned) * nb);
+    L.block_offsets = off;  off += align256(sizeof(unsigned long long) * nb);
     L.total = off;
     return L;
 }
@@ -125,7 +127,7 @@ const char* omnigs_status_string(omnigs_status s) {
 
 size_t omnigs_workspace_size(const omnigs_config* cfg, int64_t n, int64_t capacity) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return 0;
-    return ws_layout(*cfg, capacity).total;
+    return ws_layout(*cfg, n, capacity).total;
 }
 
 omnigs_status omnigs_preprocess(const omnigs_config* cfg, int64_t n, const float* means, const float* scales,
@@ -139,34 +141,32 @@ omnigs_status omnigs_preprocess(const omnigs_config* cfg, int64_t n, const float
                                        (cudaStream_t)stream));
 }
 
-omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats, uint32_t* keys,
-                         uint32_t* values, int64_t capacity, uint32_t* ranges, void* workspace,
-                         omnigs_stream_t stream) {
+omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats, uint32_t* order,
+                         uint64_t* keys, int64_t capacity, void* workspace, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
-    if (!ranges || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
-    if (n > 0 && (!splats || !aligned(splats, 16))) return OMNIGS_E_INVALID;
-    if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, capacity);
-    return from_cuda(launch_bin(*cfg, n, splats, keys, values, capacity, ranges, L, (char*)workspace,
-                                (cudaStream_t)stream));
+    if (!workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !order || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    if (capacity > 0 && (!keys || !aligned(keys, 8))) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, n, capacity);
+    return from_cuda(launch_bin(*cfg, n, splats, order, keys, capacity, L, (char*)workspace, (cudaStream_t)stream));
 }
 
-omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t capacity, uint32_t* keys, uint32_t* values,
-                          const uint32_t* ranges, void* workspace, omnigs_stream_t stream) {
-    if (!valid_cfg(cfg) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
+omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t n, int64_t capacity, uint64_t* keys, uint32_t* ranges,
+                          void* workspace, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
     if (!ranges || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
-    if (capacity > 0 && (!keys || !values)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, capacity);
-    return from_cuda(launch_sort(*cfg, capacity, keys, values, ranges, L, (char*)workspace, (cudaStream_t)stream));
+    if (capacity > 0 && (!keys || !aligned(keys, 8))) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, n, capacity);
+    return from_cuda(launch_sort(*cfg, n, capacity, keys, ranges, L, (char*)workspace, (cudaStream_t)stream));
 }
 
 omnigs_status omnigs_render_fwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
-                                const uint32_t* ranges, const uint32_t* values, float* out_rgb, float* out_T,
-                                uint32_t* out_ncontrib, omnigs_stream_t stream) {
+                                const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
+                                float* out_T, uint32_t* out_ncontrib, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
     if (!ranges || !out_rgb || !out_T || !out_ncontrib) return OMNIGS_E_INVALID;
-    if (n > 0 && (!splats || !values || !aligned(splats, 16))) return OMNIGS_E_INVALID;
-    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, values, out_rgb, out_T, out_ncontrib,
+    if (n > 0 && (!splats || !keys || !order || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib,
                                        (cudaStream_t)stream));
 }
 
@@ -175,19 +175,20 @@ omnigs_status omnigs_l1_loss(const omnigs_config* cfg, const float* rgb, const f
     if (!valid_cfg(cfg)) return OMNIGS_E_INVALID;
     if (!rgb || !target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
     if (!aligned(rgb, 16) || !aligned(target, 16) || !aligned(dL_drgb, 16)) return OMNIGS_E_INVALID;
-    const WsLayout L = ws_layout(*cfg, 0);  // header and loss partials sit at capacity-independent offsets
+    const WsLayout L = ws_layout(*cfg, 0, 0);  // the header and the loss partials sit at fixed offsets
     return from_cuda(launch_l1(*cfg, rgb, target, dL_drgb, loss, L, (char*)workspace, (cudaStream_t)stream));
 }
 
 omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
-                                const uint32_t* ranges, const uint32_t* values, const float* out_T,
-                                const uint32_t* ncontrib, const float* dL_drgb, omnigs_splat_grad* grads,
-                                omnigs_stream_t stream) {
+                                const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
+                                const float* out_T, const uint32_t* ncontrib, const float* dL_drgb,
+                                omnigs_splat_grad* grads, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
     if (!ranges || !out_T || !ncontrib || !dL_drgb) return OMNIGS_E_INVALID;
-    if (n > 0 && (!splats || !values || !grads || !aligned(splats, 16) || !aligned(grads, 16))) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !keys || !order || !grads || !aligned(splats, 16) || !aligned(grads, 16)))
+        return OMNIGS_E_INVALID;
     if (n == 0) return OMNIGS_OK;
-    return from_cuda(launch_render_bwd(*cfg, n, splats, ranges, values, out_T, ncontrib, dL_drgb, grads,
+    return from_cuda(launch_render_bwd(*cfg, n, splats, ranges, keys, order, out_T, ncontrib, dL_drgb, grads,
                                        (cudaStream_t)stream));
 }
 

@@ -33,6 +33,13 @@ struct Staged {
     float2 c;  // b, seam shift
 };
 
+// Splat of sorted list position s: the key's low rank_bits are the splat's depth rank within its view.
+__device__ __forceinline__ unsigned entry_splat(const unsigned long long* __restrict__ keys,
+                                                const uint32_t* __restrict__ view_order, uint32_t s,
+                                                unsigned long long rank_mask) {
+    return __ldg(view_order + (__ldg(keys + s) & rank_mask));
+}
+
 __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats, unsigned vg, float x_first,
                                               float x_last, float halfW, float fW) {
     const float4 a = __ldg(splats + 3 * (size_t)vg);
@@ -66,10 +73,10 @@ struct PixelMap {
 
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS * TS / PPT)
-render_fwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
-                  const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
-                  const uint32_t* __restrict__ values, float* __restrict__ out_rgb, float* __restrict__ out_T,
-                  uint32_t* __restrict__ out_nc) {
+render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
+                  float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                  const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
+                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
@@ -95,7 +102,8 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
         if (__syncthreads_count(done) == NT) break;
         const uint32_t s = b + threadIdx.x;
         if (s < end) {
-            const Staged st = stage_entry(splats, __ldg(values + s), x_first, x_last, halfW, fW);
+            const Staged st = stage_entry(splats, entry_splat(keys, order + (size_t)v * n, s, rank_mask), x_first,
+                                          x_last, halfW, fW);
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
@@ -161,9 +169,10 @@ constexpr int kGradFields = 9;
 
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS * TS / PPT)
-render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, float bg2,
-                  const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
-                  const uint32_t* __restrict__ values, const float* __restrict__ out_T,
+render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
+                  float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                  const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
+                  const float* __restrict__ out_T,
                   const uint32_t* __restrict__ ncontrib, const float* __restrict__ dL_drgb,
                   float4* __restrict__ grads) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
@@ -213,7 +222,8 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, float bg0, float bg1, fl
         const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
         const int nb = (int)(bend - bbeg);
         if ((int)threadIdx.x < nb) {
-            const unsigned vg = __ldg(values + start + bbeg + threadIdx.x);
+            const unsigned vg = entry_splat(keys, order + (size_t)v * n, (uint32_t)(start + bbeg + threadIdx.x),
+                                            rank_mask);
             const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
             const float4 raw0 = __ldg(splats + 3 * (size_t)vg);
             const float4 raw1 = __ldg(splats + 3 * (size_t)vg + 1);
@@ -308,20 +318,24 @@ constexpr int kPPT = 2;  // pixels per thread
 size_t bwd_smem(int nt) { return (size_t)nt * (3 * sizeof(float4) + sizeof(float) + sizeof(unsigned) + kGradFields * sizeof(float)); }
 
 template <int TS>
-cudaError_t render_fwd_t(const omnigs_config& cfg, const omnigs_splat* splats, const uint32_t* ranges,
-                         const uint32_t* values, float* out_rgb, float* out_T, uint32_t* out_nc, cudaStream_t stream) {
+cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
+                         const uint64_t* keys, const uint32_t* order, float* out_rgb, float* out_T, uint32_t* out_nc,
+                         cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
+    const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     ProfScope prof("render_fwd", stream);
     render_fwd_kernel<TS, kPPT><<<tiles * cfg.num_views, PixelMap<TS, kPPT>::NT, 0, stream>>>(
-        cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
-        ranges, values, out_rgb, out_T, out_nc);
+        cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
+        reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
+        out_rgb, out_T, out_nc);
     return cudaGetLastError();
 }
 
 template <int TS>
-cudaError_t render_bwd_t(const omnigs_config& cfg, const omnigs_splat* splats, const uint32_t* ranges,
-                         const uint32_t* values, const float* out_T, const uint32_t* nc, const float* dL_drgb,
-                         omnigs_splat_grad* grads, cudaStream_t stream) {
+cudaError_t render_bwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
+                         const uint64_t* keys, const uint32_t* order, const float* out_T, const uint32_t* nc,
+                         const float* dL_drgb, omnigs_splat_grad* grads, cudaStream_t stream) {
+    const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     constexpr int NT = PixelMap<TS, kPPT>::NT;
     const size_t smem = bwd_smem(NT);
@@ -330,8 +344,9 @@ cudaError_t render_bwd_t(const omnigs_config& cfg, const omnigs_splat* splats, c
     if (e != cudaSuccess) return e;
     ProfScope prof("render_bwd", stream);
     render_bwd_kernel<TS, kPPT><<<tiles * cfg.num_views, NT, smem, stream>>>(
-        cfg.width, cfg.height, tx, tiles, cfg.bg[0], cfg.bg[1], cfg.bg[2], reinterpret_cast<const float4*>(splats),
-        ranges, values, out_T, nc, dL_drgb, reinterpret_cast<float4*>(grads));
+        cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
+        reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order, out_T,
+        nc, dL_drgb, reinterpret_cast<float4*>(grads));
     return cudaGetLastError();
 }
 
@@ -369,26 +384,25 @@ __global__ void l1_finish_kernel(const float* __restrict__ partials, int nb, flo
 }  // namespace
 
 cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
-                              const uint32_t* ranges, const uint32_t* values, float* out_rgb, float* out_T,
-                              uint32_t* out_nc, cudaStream_t stream) {
-    (void)n;
+                              const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
+                              float* out_T, uint32_t* out_nc, cudaStream_t stream) {
     switch (cfg.tile) {
-        case 8: return render_fwd_t<8>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
-        case 32: return render_fwd_t<32>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
-        default: return render_fwd_t<16>(cfg, splats, ranges, values, out_rgb, out_T, out_nc, stream);
+        case 8: return render_fwd_t<8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
+        case 32: return render_fwd_t<32>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
+        default: return render_fwd_t<16>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
     }
 }
 
 cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
-                              const uint32_t* ranges, const uint32_t* values, const float* out_T,
-                              const uint32_t* nc, const float* dL_drgb, omnigs_splat_grad* grads,
-                              cudaStream_t stream) {
+                              const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
+                              const float* out_T, const uint32_t* nc, const float* dL_drgb,
+                              omnigs_splat_grad* grads, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(omnigs_splat_grad) * (size_t)n * cfg.num_views, stream);
     if (e != cudaSuccess) return e;
     switch (cfg.tile) {
-        case 8: return render_bwd_t<8>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
-        case 32: return render_bwd_t<32>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
-        default: return render_bwd_t<16>(cfg, splats, ranges, values, out_T, nc, dL_drgb, grads, stream);
+        case 8: return render_bwd_t<8>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+        case 32: return render_bwd_t<32>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+        default: return render_bwd_t<16>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
     }
 }
 

@@ -71,8 +71,7 @@ class Rasterizer:
     def _alloc_instances(self, capacity: int):
         self.capacity = int(capacity)
         cap = max(self.capacity, 1)
-        self.keys = _empty((cap,), torch.int32, self.device)
-        self.values = _empty((cap,), torch.int32, self.device)
+        self.keys = _empty((cap,), torch.int64, self.device)
         self.ws = None
 
     def _ensure(self, n: int, K: int):
@@ -81,6 +80,7 @@ class Rasterizer:
             self.n = n
             m = max(V * n, 1)
             self.splats = _empty((m, C.SPLAT_FLOATS), torch.float32, self.device)
+            self.order = _empty((m,), torch.int32, self.device)
             self.grads2d = _empty((m, C.GRAD_FLOATS), torch.float32, self.device)
             self.d_means = _empty((max(n, 1), 3), torch.float32, self.device)
             self.d_scales = _empty((max(n, 1), 3), torch.float32, self.device)
@@ -105,17 +105,16 @@ class Rasterizer:
         self._ensure(n, K)
         self._params = (means, scales, quats, opacity, sh, viewmats)
         C.omnigs_preprocess(self.cfg, n, means, scales, quats, opacity, sh, viewmats, self.splats, stream)
-        C.omnigs_bin(self.cfg, n, self.splats, self.keys, self.values, self.capacity, self.ranges, self.ws, stream)
+        C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
         if self.grow:
             self.count = C.omnigs_instance_count(self.ws, stream)
             if self.count > self.capacity:
                 self._alloc_instances(int(math.ceil(self.count * self.headroom)))
                 self._ensure(n, K)
-                C.omnigs_bin(self.cfg, n, self.splats, self.keys, self.values, self.capacity, self.ranges, self.ws,
-                             stream)
-        C.omnigs_sort(self.cfg, self.capacity, self.keys, self.values, self.ranges, self.ws, stream)
-        C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.values, self.rgb, self.T, self.ncontrib,
-                            stream)
+                C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
+        C.omnigs_sort(self.cfg, n, self.capacity, self.keys, self.ranges, self.ws, stream)
+        C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.keys, self.order, self.rgb, self.T,
+                            self.ncontrib, stream)
         return self.rgb
 
     def l1_loss(self, target, stream=None):
@@ -127,8 +126,8 @@ class Rasterizer:
     def backward_2d(self, dL_drgb=None, stream=None):
         """Blend adjoint only: per-(view, Gaussian) splat gradients [V * n, 12]."""
         g = self.dL_drgb if dL_drgb is None else dL_drgb
-        C.omnigs_render_bwd(self.cfg, self.n, self.splats, self.ranges, self.values, self.T, self.ncontrib, g,
-                            self.grads2d, stream)
+        C.omnigs_render_bwd(self.cfg, self.n, self.splats, self.ranges, self.keys, self.order, self.T, self.ncontrib,
+                            g, self.grads2d, stream)
         return self.grads2d
 
     def backward(self, dL_drgb=None, stream=None):
@@ -149,6 +148,15 @@ class Rasterizer:
 
     def instance_count(self, stream=None) -> int:
         return C.omnigs_instance_count(self.ws, stream)
+
+    def sorted_splats(self, count: int):
+        """Splat index (v * n + g) of every sorted instance position [0, count) (host copy, for inspection)."""
+        keys = self.keys[:count].cpu().numpy().view("uint64")
+        order = self.order.cpu().numpy().view("uint32").astype("int64")
+        rb = C.rank_bits(self.n)
+        tiles = self.s.tiles
+        view = (keys >> rb).astype("int64") // tiles
+        return order[view * self.n + (keys & ((1 << rb) - 1)).astype("int64")]
 
 
 class OmniRender(torch.autograd.Function):

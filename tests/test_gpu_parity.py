@@ -35,15 +35,15 @@ def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):
     n = m // s.num_views
     r._ensure(n, (s.sh_degree + 1) ** 2)
     r.splats.copy_(dev(sp_packed))
-    C.omnigs_bin(r.cfg, n, r.splats, r.keys, r.values, r.capacity, r.ranges, r.ws)
+    C.omnigs_bin(r.cfg, n, r.splats, r.order, r.keys, r.capacity, r.ws)
     cnt = r.instance_count()
     if cnt > r.capacity:
         r._alloc_instances(cnt)
         r._ensure(n, (s.sh_degree + 1) ** 2)
         r.splats.copy_(dev(sp_packed))
-        C.omnigs_bin(r.cfg, n, r.splats, r.keys, r.values, r.capacity, r.ranges, r.ws)
-    C.omnigs_sort(r.cfg, r.capacity, r.keys, r.values, r.ranges, r.ws)
-    C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.values, r.rgb, r.T, r.ncontrib)
+        C.omnigs_bin(r.cfg, n, r.splats, r.order, r.keys, r.capacity, r.ws)
+    C.omnigs_sort(r.cfg, n, r.capacity, r.keys, r.ranges, r.ws)
+    C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.keys, r.order, r.rgb, r.T, r.ncontrib)
     torch.cuda.synchronize()
     assert r.check() is None
     return r, cnt
@@ -105,10 +105,13 @@ def test_bin_sort_bitexact(tile, V, n, W, H):
     assert cnt == len(list_ref)
     ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
     assert np.array_equal(ranges, ranges_ref)
-    vals = r.values[:cnt].cpu().numpy().view(np.uint32).astype(np.int64)
+    vals = r.sorted_splats(cnt)
     assert np.array_equal(vals, list_ref)
-    keys = r.keys[:cnt].cpu().numpy().view(np.uint32)
-    assert np.array_equal(keys, sp["depth"].view(np.uint32)[vals])
+    # the depth order behind the ranks: per view, by (t_r, splat index)
+    order = r.order.cpu().numpy().view(np.uint32).astype(np.int64).reshape(V, n)
+    for v in range(V):
+        d = sp["depth"][v * n:(v + 1) * n]
+        assert np.array_equal(order[v] - v * n, np.lexsort((np.arange(n), d)))
 
 
 def test_sort_many_ties_and_all_columns():
@@ -119,7 +122,7 @@ def test_sort_many_ties_and_all_columns():
     r, cnt = _run_splats(pack_splats(sp), _settings(W, H, V=V))
     ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, 16)
     assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_ref)
-    assert np.array_equal(r.values[:cnt].cpu().numpy().view(np.uint32), list_ref)
+    assert np.array_equal(r.sorted_splats(cnt), list_ref)
 
 
 # ------------------------------------------------------------------ S5 render forward
