@@ -12,7 +12,7 @@
 //      number of <= 9-bit passes (upsweep: per-CTA digit counts; one-CTA scan; downsweep: stable in-CTA ranking with
 //      warp match-any, staging in shared memory in digit order, and runs of equal digits written to HBM). The keys
 //      carry no payload: the splat is order[v * N + rank].
-//   4. tile_ranges: [start, end) of every tile from the sorted keys.
+//   4. tile_ranges: [start, end) of every tile by binary search in the sorted keys.
 // No pass waits on another CTA, so there are no spin loops.
 #include <algorithm>
 
@@ -237,12 +237,8 @@ lsd_upsweep_kernel(const u64* __restrict__ keys, const u64* __restrict__ count, 
             d[j] = idx < cnt ? (unsigned)(__ldg(keys + idx) >> shift) & mask : R;
         }
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            // one shared-memory add per distinct digit of the warp
-            const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
-            if (d[j] < R && lane == (unsigned)(__ffs(peers) - 1)) s_hist[warp][d[j]] += __popc(peers);
-            __syncwarp();
-        }
+        for (int j = 0; j < kSortItems; ++j)
+            if (d[j] < R) atomicAdd(&s_hist[warp][d[j]], 1u);
     }
     __syncthreads();
     for (unsigned d = threadIdx.x; d < R; d += blockDim.x) {
@@ -276,7 +272,7 @@ size_t downsweep_smem() {
 }
 
 template <bool kVals>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
 lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict__ vals_in, u64* __restrict__ keys_out,
                      unsigned* __restrict__ vals_out, const u64* __restrict__ count, u64 capacity, int shift, int dbits,
                      const unsigned* __restrict__ hist, int G) {
@@ -379,15 +375,27 @@ lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict
 
 // ------------------------------------------------------------------------------------------- 4: tile ranges
 
+// Tile t's range in the sorted keys, by two binary searches over (key >> rank_bits).
 __global__ void ranges_kernel(const u64* __restrict__ keys, const WsHeader* __restrict__ hdr, u64 capacity,
                               int rank_bits, u64 ntiles, uint32_t* __restrict__ ranges) {
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
     const u64 cnt = min(hdr->count, capacity);
-    for (u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x; s < cnt; s += (u64)gridDim.x * blockDim.x) {
-        const u64 t = __ldg(keys + s) >> rank_bits;
-        if (t >= ntiles) continue;  // cannot happen for keys written by bin_emit
-        if (s == 0 || (__ldg(keys + s - 1) >> rank_bits) != t) ranges[2 * t] = (uint32_t)s;
-        if (s + 1 == cnt || (__ldg(keys + s + 1) >> rank_bits) != t) ranges[2 * t + 1] = (uint32_t)(s + 1);
+    u64 lo = 0, hi = cnt;  // first position with tile >= t
+    while (lo < hi) {
+        const u64 mid = (lo + hi) >> 1;
+        if ((__ldg(keys + mid) >> rank_bits) < t) lo = mid + 1;
+        else hi = mid;
     }
+    const u64 first = lo;
+    hi = cnt;  // first position with tile > t
+    while (lo < hi) {
+        const u64 mid = (lo + hi) >> 1;
+        if ((__ldg(keys + mid) >> rank_bits) <= t) lo = mid + 1;
+        else hi = mid;
+    }
+    ranges[2 * t] = (uint32_t)(first < lo ? first : 0);
+    ranges[2 * t + 1] = (uint32_t)(first < lo ? lo : 0);
 }
 
 // Radix-sort geometry: `bits` key bits in an even number of passes of <= 9 bits.
@@ -495,8 +503,8 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
 cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, uint64_t* keys, uint32_t* ranges,
                         const WsLayout& L, char* ws, cudaStream_t stream) {
     const u64 ntiles = (u64)(cfg.width / cfg.tile) * (cfg.height / cfg.tile) * cfg.num_views;
-    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * ntiles, stream);
-    if (e != cudaSuccess || capacity == 0 || n == 0) return e;
+    if (capacity == 0 || n == 0) return cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * ntiles, stream);
+    cudaError_t e;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
     u64* alt = reinterpret_cast<u64*>(ws + L.alt_keys);
     unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
@@ -506,8 +514,9 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
     if (e != cudaSuccess) return e;
     {
         ProfScope prof("tile_ranges", stream);
-        ranges_kernel<<<num_sms() * 8, 256, 0, stream>>>(reinterpret_cast<const u64*>(keys), hdr, (u64)capacity,
-                                                         rank_bits_for(n), ntiles, ranges);
+        ranges_kernel<<<(unsigned)((ntiles + 255) / 256), 256, 0, stream>>>(reinterpret_cast<const u64*>(keys), hdr,
+                                                                             (u64)capacity, rank_bits_for(n), ntiles,
+                                                                             ranges);
     }
     return cudaGetLastError();
 }
