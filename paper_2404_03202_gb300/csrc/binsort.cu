@@ -249,20 +249,33 @@ lsd_upsweep_kernel(const u64* __restrict__ keys, const u64* __restrict__ count, 
     }
 }
 
-// One CTA: exclusive scan over the digit-major histogram [R * G].
-__global__ void __launch_bounds__(1024) lsd_scan_kernel(unsigned* __restrict__ hist, int total) {
+// Exclusive scan of the digit-major histogram [R][G] in two small launches: one CTA per digit scans that digit's G
+// per-CTA counts in place and writes the digit total; one CTA scans the R totals into digit starts. The downsweep
+// adds both.
+__global__ void __launch_bounds__(256) lsd_scan_digit_kernel(unsigned* __restrict__ hist, int G,
+                                                            unsigned* __restrict__ totals) {
     __shared__ unsigned scratch[32];
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per, b1 = min(b0 + per, total);
+    unsigned* h = hist + (size_t)blockIdx.x * G;
+    const int per = (G + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, G);
     unsigned local = 0;
-    for (int b = b0; b < b1; ++b) local += hist[b];
+    for (int b = b0; b < b1; ++b) local += h[b];
     unsigned tot;
     unsigned run = block_exclusive_scan<unsigned>(local, scratch, &tot);
     for (int b = b0; b < b1; ++b) {
-        const unsigned c = hist[b];
-        hist[b] = run;
+        const unsigned c = h[b];
+        h[b] = run;
         run += c;
     }
+    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kRadixMax) lsd_scan_totals_kernel(unsigned* __restrict__ totals, int R) {
+    __shared__ unsigned scratch[32];
+    const unsigned v = (int)threadIdx.x < R ? totals[threadIdx.x] : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan<unsigned>(v, scratch, &tot);
+    if ((int)threadIdx.x < R) totals[threadIdx.x] = ex;
 }
 
 template <bool kVals>
@@ -275,7 +288,7 @@ template <bool kVals>
 __global__ void __launch_bounds__(kSortThreads, 3)
 lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict__ vals_in, u64* __restrict__ keys_out,
                      unsigned* __restrict__ vals_out, const u64* __restrict__ count, u64 capacity, int shift, int dbits,
-                     const unsigned* __restrict__ hist, int G) {
+                     const unsigned* __restrict__ hist, const unsigned* __restrict__ digit_start, int G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64* s_keys = reinterpret_cast<u64*>(smem_raw);
     unsigned* s_vals = reinterpret_cast<unsigned*>(s_keys + kSortTile);
@@ -290,7 +303,7 @@ lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict
     const unsigned lt_mask = (1u << lane) - 1u;
     const u64 cnt = min(*count, capacity);
     const TileSpan span = cta_tiles(cnt, G);
-    for (unsigned d = tid; d < R; d += kSortThreads) s_gbase[d] = hist[(size_t)d * G + blockIdx.x];
+    for (unsigned d = tid; d < R; d += kSortThreads) s_gbase[d] = digit_start[d] + hist[(size_t)d * G + blockIdx.x];
     unsigned* my_hist = s_whist + warp * kHistRow;
 
     for (u64 t = span.begin; t < span.end; ++t) {
@@ -427,12 +440,13 @@ cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* co
         {
             ProfScope prof(tag_up, stream);
             lsd_upsweep_kernel<<<G, kSortThreads, 0, stream>>>(k0, count, capacity, shift, db, hist, G);
-            lsd_scan_kernel<<<1, 1024, 0, stream>>>(hist, (1 << db) * G);
+            lsd_scan_digit_kernel<<<1 << db, 256, 0, stream>>>(hist, G, hist + (size_t)kRadixMax * G);
+            lsd_scan_totals_kernel<<<1, kRadixMax, 0, stream>>>(hist + (size_t)kRadixMax * G, 1 << db);
         }
         {
             ProfScope prof(tag_down, stream);
             lsd_downsweep_kernel<kVals><<<G, kSortThreads, smem, stream>>>(k0, v0, k1, v1, count, capacity, shift, db,
-                                                                            hist, G);
+                                                                            hist, hist + (size_t)kRadixMax * G, G);
         }
         std::swap(k0, k1);
         std::swap(v0, v1);

@@ -27,7 +27,7 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     size_t off = 0;
     L.header = off;         off += align256(sizeof(WsHeader));
     L.loss_partials = off;  off += align256(sizeof(float) * L.loss_blocks);
-    L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * (size_t)num_sms() * kSortCtasPerSm);
+    L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * ((size_t)num_sms() * kSortCtasPerSm + 1));
     L.alt_keys = off;       off += align256(sizeof(unsigned long long) * (size_t)capacity);
     L.depth_keys = off;     off += align256(sizeof(unsigned long long) * total);
     L.depth_keys_alt = off; off += align256(sizeof(unsigned long long) * total);
