@@ -138,6 +138,18 @@ omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnig
 omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const float *target, float *dL_drgb,
                              float *loss, void *workspace, omnigs_stream_t stream);
 
+/* The same loss and gradient as omnigs_l1_loss without a workspace, for callers that cannot allocate device memory
+ * or hand the library any beyond their inputs and outputs (a host application that owns the CUDA allocator or has
+ * reserved all device memory, a loop with a fixed memory budget). The paper has no counterpart; this is an interface
+ * convenience. Its scratch (4096 partial sums) is a fixed array inside the library, so it allocates nothing and calls
+ * no allocating routine. Limit: V * 3 * H * W <= 268,435,456 floats; larger requests return OMNIGS_E_INVALID before
+ * anything is enqueued. The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should therefore come before any stream capture on that device. All calls on a device share the array: calls that
+ * may overlap on the GPU race and must be serialised by the caller. rgb, target, dL_drgb: 16-byte aligned device
+ * buffers [V, 3, H, W]; loss [1] device. */
+omnigs_status omnigs_l1_loss_static(const omnigs_config *cfg, const float *rgb, const float *target, float *dL_drgb,
+                                    float *loss, omnigs_stream_t stream);
+
 /* Adjoint of omnigs_render_fwd (Sec. 3.4, the blending part of Eqs. 18-20): per pixel, back to front from its
  * last contributor, recovering T by division by (1 - alpha). Writes grads [V * n] (device): dL/d(px, py, c0, c1,
  * c2, opacity, r, g, b) of every splat, summed over the pixels it reaches. The derivative of alpha is 0 where it is

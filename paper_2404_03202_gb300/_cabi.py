@@ -62,6 +62,8 @@ def load() -> ctypes.CDLL:
         lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
         lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
+        lib.omnigs_l1_loss_static.argtypes = [cfgp, P, P, P, P, P]
+        lib.omnigs_l1_loss_static.restype = st
         lib.omnigs_render_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_preprocess_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.omnigs_instance_count.argtypes = [P, ctypes.POINTER(i64), P]
@@ -144,6 +146,12 @@ def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_n
 def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):
     _check(load().omnigs_l1_loss(ctypes.byref(cfg), _ptr(rgb), _ptr(target), _ptr(dL_drgb), _ptr(loss),
                                  _ptr(workspace), _stream(stream)), "omnigs_l1_loss")
+
+
+def omnigs_l1_loss_static(cfg, rgb, target, dL_drgb, loss, stream=None):
+    """omnigs_l1_loss without a workspace (no device allocation anywhere); see include/omnigs.h for its limit."""
+    _check(load().omnigs_l1_loss_static(ctypes.byref(cfg), _ptr(rgb), _ptr(target), _ptr(dL_drgb), _ptr(loss),
+                                        _stream(stream)), "omnigs_l1_loss_static")
 
 
 def omnigs_render_bwd(cfg, n, splats, ranges, keys, order, out_T, ncontrib, dL_drgb, grads, stream=None):
