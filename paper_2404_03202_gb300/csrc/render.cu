@@ -1,19 +1,22 @@
 // Tile-based alpha blending onto the equirectangular image (Sec. 3.3, Eqs. 6-8) and its adjoint (Sec. 3.4).
 //
-// One CTA per (view, tile), one thread per pixel. The tile's sorted instance list is walked in batches of one
-// entry per thread: each thread gathers one splat (two 16-byte loads and one 4-byte load) into shared memory, with
-// the conic pre-scaled by -log2(e)/2 so that G = 2^(dx (c0' dx + c1' dy) + c2' dy^2) costs one ex2 on the SFU, and
-// with the longitude-seam shift decided once per (entry, tile): 0 or +-W for the whole tile, or a flag for the rare
-// splat whose minimal-image boundary falls inside the tile. The CTA leaves the list as soon as every pixel has
-// stopped (__syncthreads_count).
+// One CTA per (view, tile). The tile's sorted instance list is walked in batches of one entry per thread: each thread
+// gathers one splat (two 16-byte loads and one 4-byte load) into shared memory with
+//   * the conic pre-scaled by -log2(e)/2, so that G = 2^e with e = dx (c0' dx + c1' dy) + c2' dy^2 costs one ex2;
+//   * the longitude-seam shift decided once per (entry, tile): 0 or +-W for the whole tile, or a flag for the rare
+//     splat whose minimal-image boundary falls inside the tile;
+//   * the exponent threshold -log2(255 o): alpha = min(0.99, o 2^e) < 1/255 exactly when e < -log2(255 o), so a pair
+//     that cannot contribute is rejected with three FP32 operations and one compare, before the ex2, and a warp whose
+//     32 pixels all miss the splat skips it together.
+// Each thread owns PPT vertically adjacent pixels of one column: they share dx, the per-entry products and every
+// shared-memory load. The CTA leaves the list once every pixel has stopped (__syncthreads_count).
 //
 // The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
-// (1 - alpha), reduces the 9 per-pixel partial derivatives of an entry over each warp with shuffles (skipped when no
-// lane of the warp touched the entry), then over the CTA in shared memory, and adds the CTA's sum to the splat's
-// gradient with 16-byte vector atomics (red.global.add.v4.f32). Forward and adjoint evaluate alpha with the same
-// arithmetic, written identically in both kernels, so their skip / stop decisions agree. Each thread owns PPT
-// vertically adjacent pixels: they share dx and the entry loads, and the adjoint sums them before the warp
-// reduction, which halves its cost per pixel.
+// (1 - alpha) and accumulates the 9 partial derivatives of an entry over the thread's pixels. The warp then reduces
+// them with one transposed reduce-scatter (16 shuffles; lanes 0, 2, .., 16 end up with one field's total each, written
+// with one shared-memory atomic per field), the CTA sums warps in shared memory, and the CTA's sum goes to the splat's
+// gradient with 16-byte vector atomics (red.global.add.v4.f32). Forward and adjoint evaluate alpha with identical
+// arithmetic, so their skip / stop decisions agree.
 #include "common.cuh"
 
 namespace omnigs {
@@ -28,12 +31,12 @@ __device__ __forceinline__ float fast_ex2(float x) {
 }
 
 struct Staged {
-    float4 a;  // px, py, c0', c1'   (c' = conic scaled to base-2 exponent)
+    float4 a;  // px, py, c0', c1'   (c' = conic scaled to the base-2 exponent)
     float4 b;  // c2', opacity, r, g
-    float2 c;  // b, seam shift
+    float4 c;  // b, seam shift, exponent threshold -log2(255 o), unused
 };
 
-// Splat of sorted list position s: the key's low rank_bits are the splat's depth rank within its view.
+// Splat of sorted list position s: the key's low rank bits are the splat's depth rank within its view.
 __device__ __forceinline__ unsigned entry_splat(const unsigned long long* __restrict__ keys,
                                                 const uint32_t* __restrict__ view_order, uint32_t s,
                                                 unsigned long long rank_mask) {
@@ -54,12 +57,24 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     Staged s;
     s.a = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
     s.b = make_float4(-0.5f * kLog2e * b.x, b.y, b.z, b.w);
-    s.c = make_float2(blue, shift);
+    s.c = make_float4(blue, shift, -__log2f(255.f * b.y), 0.f);
     return s;
 }
 
+// Minimal-image dx of the thread's column for a staged entry.
+__device__ __forceinline__ float entry_dx(float px, float shift, float xs, float halfW, float fW) {
+    float dx = px - xs;
+    if (shift != kPerPixelWrap) {
+        dx += shift;
+    } else {
+        if (dx >= halfW) dx -= fW;
+        else if (dx < -halfW) dx += fW;
+    }
+    return dx;
+}
+
 // Pixels of a thread: column lx = t % TS, rows (t / TS) * PPT + k for k < PPT, so a warp covers a compact
-// TS x (32 / TS * PPT) block and the PPT pixels of a thread share dx and every shared-memory load of an entry.
+// TS x (32 / TS * PPT) block.
 template <int TS, int PPT>
 struct PixelMap {
     static constexpr int NT = TS * TS / PPT;  // threads per CTA
@@ -80,7 +95,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     constexpr int NT = PixelMap<TS, PPT>::NT;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
-    __shared__ float2 s_c[NT];
+    __shared__ float4 s_c[NT];
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
@@ -89,6 +104,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
+    const uint32_t* vorder = order + (size_t)v * n;
 
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT];
@@ -102,8 +118,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         if (__syncthreads_count(done) == NT) break;
         const uint32_t s = b + threadIdx.x;
         if (s < end) {
-            const Staged st = stage_entry(splats, entry_splat(keys, order + (size_t)v * n, s, rank_mask), x_first,
-                                          x_last, halfW, fW);
+            const Staged st = stage_entry(splats, entry_splat(keys, vorder, s, rank_mask), x_first, x_last, halfW, fW);
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
@@ -113,22 +128,15 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         for (int j = 0; j < nb && !done; ++j) {
             const float4 A = s_a[j];
             const float4 B = s_b[j];
-            const float2 Cc = s_c[j];
-            float dx = A.x - xs;
-            if (Cc.y != kPerPixelWrap) {
-                dx += Cc.y;
-            } else {
-                if (dx >= halfW) dx -= fW;
-                else if (dx < -halfW) dx += fW;
-            }
-            const float u = A.z * dx;
+            const float4 Cc = s_c[j];
+            const float dx = entry_dx(A.x, Cc.y, xs, halfW, fW);
+            const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (!live[k]) continue;
                 const float dy = A.y - (pm.y0 + k + 0.5f);
-                const float p2 = fmaf(dx, fmaf(A.w, dy, u), B.x * dy * dy);
-                const float alpha = fminf(kAlphaMax, B.y * fast_ex2(p2));
-                if (p2 > 0.f || alpha < kAlphaMin) continue;
+                const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
+                if (!live[k] || e < Cc.z || e > 0.f) continue;
+                const float alpha = fminf(kAlphaMax, B.y * fast_ex2(e));
                 const float Tn = T[k] * (1.f - alpha);
                 if (Tn < kTStop) {
                     live[k] = false;
@@ -159,29 +167,37 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     }
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 constexpr int kGradFields = 9;
+
+// Reduce-scatter of 16 values over the warp: on return v[0] of lanes 2f and 2f + 1 holds the warp total of value f.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], unsigned lane) {
+#pragma unroll
+    for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS * TS / PPT)
 render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
-                  const float* __restrict__ out_T,
-                  const uint32_t* __restrict__ ncontrib, const float* __restrict__ dL_drgb,
-                  float4* __restrict__ grads) {
+                  const float* __restrict__ out_T, const uint32_t* __restrict__ ncontrib,
+                  const float* __restrict__ dL_drgb, float4* __restrict__ grads) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* s_a = reinterpret_cast<float4*>(smem_raw);
     float4* s_b = s_a + NT;
-    float4* s_k = s_b + NT;                            // raw conic c0, c1, c2 and blue
-    float* s_shift = reinterpret_cast<float*>(s_k + NT);
-    unsigned* s_vg = reinterpret_cast<unsigned*>(s_shift + NT);
+    float4* s_c = s_b + NT;
+    float4* s_k = s_c + NT;                                // raw conic c0, c1, c2
+    unsigned* s_vg = reinterpret_cast<unsigned*>(s_k + NT);
     float* s_acc = reinterpret_cast<float*>(s_vg + NT);  // [NT][kGradFields]
     __shared__ unsigned s_max;
 
@@ -193,6 +209,7 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
+    const uint32_t* vorder = order + (size_t)v * n;
     const size_t HW = (size_t)H * W;
 
     uint32_t last[PPT];
@@ -222,15 +239,14 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
         const int nb = (int)(bend - bbeg);
         if ((int)threadIdx.x < nb) {
-            const unsigned vg = entry_splat(keys, order + (size_t)v * n, (uint32_t)(start + bbeg + threadIdx.x),
-                                            rank_mask);
+            const unsigned vg = entry_splat(keys, vorder, (uint32_t)(start + bbeg + threadIdx.x), rank_mask);
             const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
             const float4 raw0 = __ldg(splats + 3 * (size_t)vg);
-            const float4 raw1 = __ldg(splats + 3 * (size_t)vg + 1);
+            const float raw1 = __ldg(reinterpret_cast<const float*>(splats + 3 * (size_t)vg + 1));
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
-            s_k[threadIdx.x] = make_float4(raw0.z, raw0.w, raw1.x, st.c.x);
-            s_shift[threadIdx.x] = st.c.y;
+            s_c[threadIdx.x] = st.c;
+            s_k[threadIdx.x] = make_float4(raw0.z, raw0.w, raw1, 0.f);
             s_vg[threadIdx.x] = vg;
         }
         __syncthreads();
@@ -239,33 +255,25 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             if (__all_sync(0xffffffffu, pos >= mylast)) continue;
             const float4 A = s_a[j];
             const float4 Bv = s_b[j];
-            const float4 K = s_k[j];
-            const float shift = s_shift[j];
-            float gv[kGradFields];
+            const float4 Cc = s_c[j];
+            const float dx = entry_dx(A.x, Cc.y, xs, halfW, fW);
+            const float e0 = A.z * dx * dx, e1 = A.w * dx;
+            float gv[16];
 #pragma unroll
-            for (int f = 0; f < kGradFields; ++f) gv[f] = 0.f;
+            for (int f = 0; f < 16; ++f) gv[f] = 0.f;
             bool contrib = false;
-            float dx = A.x - xs;
-            if (shift != kPerPixelWrap) {
-                dx += shift;
-            } else {
-                if (dx >= halfW) dx -= fW;
-                else if (dx < -halfW) dx += fW;
-            }
-            const float u = A.z * dx;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (pos >= last[k]) continue;
                 const float dy = A.y - (pm.y0 + k + 0.5f);
-                const float p2 = fmaf(dx, fmaf(A.w, dy, u), Bv.x * dy * dy);
-                const float G = fast_ex2(p2);
+                const float e = fmaf(dy, fmaf(Bv.x, dy, e1), e0);
+                if (pos >= last[k] || e < Cc.z || e > 0.f) continue;
+                const float G = fast_ex2(e);
                 const float raw = Bv.y * G;
                 const float alpha = fminf(kAlphaMax, raw);
-                if (p2 > 0.f || alpha < kAlphaMin) continue;
                 contrib = true;
                 const float one_m = 1.f - alpha;
                 T[k] = __fdividef(T[k], one_m);  // transmittance in front of this entry
-                const float cr = Bv.z, cg = Bv.w, cb = K.w;
+                const float cr = Bv.z, cg = Bv.w, cb = Cc.x;
                 const float dalpha = T[k] * (g0[k] * (cr - B0[k]) + g1[k] * (cg - B1[k]) + g2[k] * (cb - B2[k]));
                 const float w = alpha * T[k];
                 gv[6] = fmaf(w, g0[k], gv[6]);
@@ -275,8 +283,9 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 B1[k] = fmaf(alpha, cg, one_m * B1[k]);
                 B2[k] = fmaf(alpha, cb, one_m * B2[k]);
                 if (raw < kAlphaMax) {
+                    const float4 K = s_k[j];
                     gv[5] = fmaf(dalpha, G, gv[5]);
-                    const float gp = dalpha * raw;  // dL/d(exponent)
+                    const float gp = dalpha * raw;  // dL/d(exponent in natural units)
                     const float gdx = gp * dx, gdy = gp * dy;
                     gv[2] = fmaf(-0.5f * dx, gdx, gv[2]);
                     gv[3] = fmaf(-dx, gdy, gv[3]);
@@ -286,12 +295,9 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int f = 0; f < kGradFields; ++f) gv[f] = warp_sum(gv[f]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int f = 0; f < kGradFields; ++f) atomicAdd(&s_acc[j * kGradFields + f], gv[f]);
-                }
+                const float tot = warp_transpose_sum16(gv, lane);
+                const unsigned f = lane >> 1;
+                if ((lane & 1u) == 0 && f < (unsigned)kGradFields) atomicAdd(&s_acc[j * kGradFields + f], tot);
             }
         }
         __syncthreads();
@@ -315,7 +321,9 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
 
 constexpr int kPPT = 2;  // pixels per thread
 
-size_t bwd_smem(int nt) { return (size_t)nt * (3 * sizeof(float4) + sizeof(float) + sizeof(unsigned) + kGradFields * sizeof(float)); }
+size_t bwd_smem(int nt) {
+    return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
+}
 
 template <int TS>
 cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
@@ -348,6 +356,12 @@ cudaError_t render_bwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order, out_T,
         nc, dL_drgb, reinterpret_cast<float4*>(grads));
     return cudaGetLastError();
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
 // mean |rgb - target| and its gradient; float4 over the [V, 3, H, W] buffers (size a multiple of 4)
