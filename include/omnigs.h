@@ -105,15 +105,17 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  *   splats  [V * n] input (device)
  *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:
  *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r).
- *   keys    [capacity] output (device): one key per instance, generated splat by splat (tiles row by row, columns in
- *           seam order): ((v * TILES + tile) << R) | r, with TILES = (W / tile) * (H / tile), tile = ty * (W / tile)
- *           + tx, r the splat's depth rank and R = max(1, ceil(log2(n))) rank bits.
+ *   keys    [capacity] output (device): one key per instance, generated view by view and splat by splat in depth
+ *           order (a splat's tiles row by row, columns in seam order): ((v * TILES + tile) << R) | r, with
+ *           TILES = (W / tile) * (H / tile), tile = ty * (W / tile) + tx, r the splat's depth rank and
+ *           R = max(1, ceil(log2(n))) rank bits. Within a tile the keys are therefore already in rank order.
  * The total instance count stays on the device (workspace); if it exceeds `capacity`, instances beyond it are dropped
  * and OMNIGS_E_CAPACITY is raised in the workspace. capacity < 2^32, the value given to omnigs_workspace_size. */
 omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
                          uint64_t *keys, int64_t capacity, void *workspace, omnigs_stream_t stream);
 
-/* Sort of the instance keys written by omnigs_bin, in place: by (view, tile), then by depth rank, i.e. the blending
+/* Stable sort of the instance keys written by omnigs_bin by their (view, tile) bits, in place, which leaves them
+ * ordered by (view, tile), then by depth rank, i.e. the blending
  * order of Sec. 3.3 (nearest first by t_r) with equal depths in splat order, the order a stable sort of (tile, t_r)
  * keys gives to instances generated splat by splat. Writes ranges [V * TILES, 2] (device): ranges[2t], ranges[2t+1] =
  * first and one-past-last sorted position of tile t (both 0 for an empty tile). n and capacity as for omnigs_bin. */

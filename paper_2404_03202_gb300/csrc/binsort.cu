@@ -3,15 +3,16 @@
 // The blending order is that of a stable sort of (view * TILES + tile, t_r) keys over instances generated splat by
 // splat. Here that order is produced with short keys and coalesced passes only:
 //   1. depth_keys + LSD sort: the V * N splats are sorted once by (view, t_r bits), stable, so ties keep splat order.
-//      order[v * N + r] is the r-th nearest splat of view v; rank[v * N + g] is the inverse. Ranks are unique, so
-//      comparing ranks equals comparing (t_r, splat index).
-//   2. bin_count / bin_scan / bin_emit: per-splat instance counts, a 64-bit exclusive scan (overflow checked against
-//      the capacity) and a warp-cooperative emission that writes, in generation order and fully coalesced, one key
-//      per instance: ((v * TILES + tile) << rank_bits) | rank.
-//   3. LSD radix sort of the instance keys over the ceil(log2(V * TILES)) + rank_bits bits in use, in an even
-//      number of <= 9-bit passes (upsweep: per-CTA digit counts; one-CTA scan; downsweep: stable in-CTA ranking with
-//      warp match-any, staging in shared memory in digit order, and runs of equal digits written to HBM). The keys
-//      carry no payload: the splat is order[v * N + rank].
+//      order[v * N + r] is the r-th nearest splat of view v (its depth rank r). Ranks are unique, so comparing ranks
+//      equals comparing (t_r, splat index).
+//   2. bin_count / bin_scan / bin_emit walk the splats in depth order (through `order`): per-splat instance counts, a
+//      64-bit exclusive scan (overflow checked against the capacity) and a warp-cooperative emission that writes,
+//      fully coalesced, one key per instance: ((v * TILES + tile) << rank_bits) | rank. The emitted stream is
+//      therefore already ordered by rank within every tile.
+//   3. A stable LSD radix sort of the instance keys over the tile bits only (ceil(log2(V * TILES)) bits above the
+//      rank, 2 passes of <= 9 bits: upsweep per-CTA digit counts; two small scans; downsweep with stable in-CTA
+//      ranking by warp match-any, staging in shared memory in digit order, runs of equal digits written to HBM). The
+//      keys carry no payload: the splat is order[v * N + rank].
 //   4. tile_ranges: [start, end) of every tile by binary search in the sorted keys.
 // No pass waits on another CTA, so there are no spin loops.
 #include <algorithm>
@@ -88,24 +89,16 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
     vals[i] = (uint32_t)i;
 }
 
-__global__ void __launch_bounds__(kBinThreads)
-rank_kernel(int64_t total, int n, const uint32_t* __restrict__ order, uint32_t* __restrict__ rank) {
-    const int64_t p = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
-    if (p >= total) return;
-    const uint32_t vg = order[p];
-    rank[vg] = (uint32_t)(p - (p / n) * n);
-}
-
 // ------------------------------------------------------------------------------------------- 2: instances
 
 __global__ void __launch_bounds__(kBinThreads)
-bin_count_kernel(int64_t total, const float4* __restrict__ splats, int tiles_x, int tiles_y, int tile,
-                 unsigned* __restrict__ block_sums) {
+bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
+                 int tiles_y, int tile, unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
-    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
     unsigned cnt = 0;
     if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)i, tiles_x, tiles_y, tile);
+        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
         if (p.radius > 0) {
             const Rect r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
             cnt = (unsigned)(r.nx * r.ny);
@@ -137,26 +130,27 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
     }
 }
 
-// The 32 splats of a warp own one contiguous output range; each lane writes every 32nd instance of it (owner found
-// by a binary search over the warp's exclusive prefix of counts), so stores are coalesced even for splats that cover
-// thousands of tiles. Instances of a splat are listed row by row, columns in seam order.
+// The 32 splats of a warp (consecutive in depth order) own one contiguous output range; each lane writes every 32nd
+// instance of it (owner found by a binary search over the warp's exclusive prefix of counts), so stores are coalesced
+// even for splats that cover thousands of tiles. Instances of a splat are listed row by row, columns in seam order.
 __global__ void __launch_bounds__(kBinThreads)
-bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, int tiles_x, int tiles_y, int tile,
-                int rank_bits, const uint32_t* __restrict__ rank, const u64* __restrict__ block_offsets,
+bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
+                int tiles_x, int tiles_y, int tile, int rank_bits, const u64* __restrict__ block_offsets,
                 u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
-    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
     const int tiles = tiles_x * tiles_y;
     unsigned cnt = 0;
     Rect r = {0, 1, 0, 0};
     u64 low = 0, tbase = 0;
     if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)i, tiles_x, tiles_y, tile);
+        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
         if (p.radius > 0) {
             r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
             cnt = (unsigned)(r.nx * r.ny);
-            low = rank[i];
-            tbase = (u64)(i / n) * (u64)tiles;
+            const int64_t v = i / n;
+            low = (u64)(i - v * n);
+            tbase = (u64)v * (u64)tiles;
         }
     }
     unsigned blk_total;
@@ -425,18 +419,19 @@ Plan plan_for(int bits) {
     return p;
 }
 
-// Sorts `count` (device) keys (and values) in (k0, v0) through (k1, v1); the result lands back in (k0, v0).
+// Stable sort of `count` (device) keys (and values) in (k0, v0) by key bits [lo_bit, lo_bit + bits), through (k1, v1);
+// the result lands back in (k0, v0).
 template <bool kVals>
-cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* count, u64 capacity, int bits, int G,
-                     unsigned* hist, cudaStream_t stream, const char* tag_up, const char* tag_down) {
+cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* count, u64 capacity, int lo_bit,
+                     int bits, int G, unsigned* hist, cudaStream_t stream, const char* tag_up, const char* tag_down) {
     const Plan P = plan_for(bits);
     const size_t smem = downsweep_smem<kVals>();
     cudaError_t e = cudaFuncSetAttribute(lsd_downsweep_kernel<kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     for (int p = 0; p < P.passes; ++p) {
-        const int shift = p * P.digit;
-        const int db = std::max(1, std::min(P.digit, bits - shift));
+        const int shift = lo_bit + p * P.digit;
+        const int db = std::max(1, std::min(P.digit, lo_bit + bits - shift));
         {
             ProfScope prof(tag_up, stream);
             lsd_upsweep_kernel<<<G, kSortThreads, 0, stream>>>(k0, count, capacity, shift, db, hist, G);
@@ -469,9 +464,9 @@ int sort_grid(u64 elems) {
 
 int rank_bits_for(int64_t n) { return std::max(1, ceil_log2((uint64_t)std::max<int64_t>(n, 1))); }
 
-int instance_key_bits(const omnigs_config& cfg, int64_t n) {
+int tile_key_bits(const omnigs_config& cfg) {
     const uint64_t tiles = (uint64_t)(cfg.width / cfg.tile) * (cfg.height / cfg.tile) * cfg.num_views;
-    return ceil_log2(tiles) + rank_bits_for(n);
+    return std::max(1, ceil_log2(tiles));
 }
 
 cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, uint32_t* order,
@@ -485,7 +480,6 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     u64* dk0 = reinterpret_cast<u64*>(ws + L.depth_keys);
     u64* dk1 = reinterpret_cast<u64*>(ws + L.depth_keys_alt);
     unsigned* dv1 = reinterpret_cast<unsigned*>(ws + L.depth_vals_alt);
-    uint32_t* rank = reinterpret_cast<uint32_t*>(ws + L.rank);
     unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
     unsigned* bsums = reinterpret_cast<unsigned*>(ws + L.block_sums);
     u64* boffs = reinterpret_cast<u64*>(ws + L.block_offsets);
@@ -494,21 +488,17 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
         ProfScope prof("depth_keys", stream);
         depth_keys_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
     }
-    e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 32 + ceil_log2(cfg.num_views),
+    e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(cfg.num_views),
                        sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
     if (e != cudaSuccess) return e;
     {
-        ProfScope prof("depth_rank", stream);
-        rank_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, order, rank);
-    }
-    {
         ProfScope prof("bin_count", stream);
-        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, tx, ty, cfg.tile, bsums);
+        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, bsums);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream);
-        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, tx, ty, cfg.tile, rank_bits_for(n), rank,
+        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, rank_bits_for(n),
                                                          boffs, reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();
@@ -523,7 +513,7 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
     u64* alt = reinterpret_cast<u64*>(ws + L.alt_keys);
     unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
     e = lsd_sort<false>(reinterpret_cast<u64*>(keys), nullptr, alt, nullptr, &hdr->count, (u64)capacity,
-                        instance_key_bits(cfg, n), sort_grid((u64)capacity), hist, stream, "sort_upsweep",
+                        rank_bits_for(n), tile_key_bits(cfg), sort_grid((u64)capacity), hist, stream, "sort_upsweep",
                         "sort_downsweep");
     if (e != cudaSuccess) return e;
     {

@@ -66,7 +66,7 @@ __device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int ti
 // Order: fixed-size regions, then those sized by the capacity, then those sized by n, so that calls which do not take
 // n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
-    size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, rank, block_sums,
+    size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
         block_offsets, total;
     int loss_blocks;
 };

@@ -32,7 +32,6 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.depth_keys = off;     off += align256(sizeof(unsigned long long) * total);
     L.depth_keys_alt = off; off += align256(sizeof(unsigned long long) * total);
     L.depth_vals_alt = off; off += align256(sizeof(uint32_t) * total);
-    L.rank = off;           off += align256(sizeof(uint32_t) * total);
     L.block_sums = off;     off += align256(sizeof(unsigned) * nb);
     L.block_offsets = off;  off += align256(sizeof(unsigned long long) * nb);
     L.total = off;

@@ -167,7 +167,7 @@ def test_profiler_collects_kernel_times():
     finally:
         C.omnigs_profiler_enable(False)
     names = {t[0] for t in times}
-    for k in ["preprocess_fwd", "depth_keys", "depth_sort", "depth_rank", "bin_count", "bin_emit", "sort_upsweep",
+    for k in ["preprocess_fwd", "depth_keys", "depth_sort", "bin_count", "bin_emit", "sort_upsweep",
               "sort_downsweep", "tile_ranges", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd"]:
         assert k in names, k
     assert all(t[2] >= 0 for t in times)
