@@ -130,64 +130,55 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
     }
 }
 
-// The 32 splats of a warp (consecutive in depth order) own one contiguous output range; each lane writes every 32nd
-// instance of it (owner found by a binary search over the warp's exclusive prefix of counts), so stores are coalesced
-// even for splats that cover thousands of tiles. Instances of a splat are listed row by row, columns in seam order.
+// The 256 splats of a CTA (consecutive in depth order) own one contiguous output range; each thread writes every 256th
+// instance of it (owner found by a binary search over the CTA's exclusive prefix of counts in shared memory), so stores
+// are coalesced and the work of the nearest, widest splats (which depth order puts side by side) is shared by the
+// whole CTA. Instances of a splat are listed row by row, columns in seam order.
 __global__ void __launch_bounds__(kBinThreads)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
                 int tiles_x, int tiles_y, int tile, int rank_bits, const u64* __restrict__ block_offsets,
                 u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
+    __shared__ unsigned s_excl[kBinThreads];
+    __shared__ int4 s_rect[kBinThreads];          // x0, nx, y0, rank
+    __shared__ unsigned s_tbase[kBinThreads];
     const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
     const int tiles = tiles_x * tiles_y;
     unsigned cnt = 0;
     Rect r = {0, 1, 0, 0};
-    u64 low = 0, tbase = 0;
+    int rank = 0;
+    unsigned tbase = 0;
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
         if (p.radius > 0) {
             r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
             cnt = (unsigned)(r.nx * r.ny);
             const int64_t v = i / n;
-            low = (u64)(i - v * n);
-            tbase = (u64)v * (u64)tiles;
+            rank = (int)(i - v * n);
+            tbase = (unsigned)v * (unsigned)tiles;
         }
     }
     unsigned blk_total;
-    const unsigned local = block_exclusive_scan<unsigned>(cnt, scratch, &blk_total);
-    const u64 off = block_offsets[blockIdx.x] + local;
-    const unsigned lane = lane_id();
-    unsigned incl = cnt;
+    const unsigned excl = block_exclusive_scan<unsigned>(cnt, scratch, &blk_total);
+    s_excl[threadIdx.x] = excl;
+    s_rect[threadIdx.x] = make_int4(r.x0, r.nx, r.y0, rank);
+    s_tbase[threadIdx.x] = tbase;
+    __syncthreads();
+    const u64 boff = block_offsets[blockIdx.x];
+    for (unsigned e = threadIdx.x; e < blk_total; e += kBinThreads) {
+        int j = 0;  // owner: the largest thread whose exclusive prefix is <= e
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += y;
-    }
-    const unsigned excl = incl - cnt;
-    const unsigned wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    const u64 woff = __shfl_sync(0xffffffffu, off - excl, 0);
-    for (unsigned base = 0; base < wtotal; base += 32) {
-        const unsigned e = base + lane;
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const unsigned ex = __shfl_sync(0xffffffffu, excl, (j + step) & 31);
-            if (j + step < 32 && ex <= e) j += step;
-        }
-        const unsigned k = e - __shfl_sync(0xffffffffu, excl, j);
-        const int x0 = __shfl_sync(0xffffffffu, r.x0, j);
-        const int nx = __shfl_sync(0xffffffffu, r.nx, j);
-        const int y0 = __shfl_sync(0xffffffffu, r.y0, j);
-        const u64 lo = __shfl_sync(0xffffffffu, low, j);
-        const u64 tb = __shfl_sync(0xffffffffu, tbase, j);
-        if (e < wtotal) {
-            const int row = (int)(k / (unsigned)nx);
-            const int col = (int)(k - (unsigned)row * (unsigned)nx);
-            int tx = (x0 + col) % tiles_x;
-            tx += tx < 0 ? tiles_x : 0;
-            const u64 idx = woff + e;
-            if (idx < capacity) keys[idx] = ((tb + (u64)((y0 + row) * tiles_x + tx)) << rank_bits) | lo;
-        }
+        for (int step = kBinThreads / 2; step >= 1; step >>= 1)
+            if (j + step < kBinThreads && s_excl[j + step] <= e) j += step;
+        const int4 rr = s_rect[j];
+        const unsigned k = e - s_excl[j];
+        const int row = (int)(k / (unsigned)rr.y);
+        const int col = (int)(k - (unsigned)row * (unsigned)rr.y);
+        int tx = (rr.x + col) % tiles_x;
+        tx += tx < 0 ? tiles_x : 0;
+        const u64 idx = boff + e;
+        if (idx < capacity)
+            keys[idx] = (((u64)s_tbase[j] + (u64)((rr.z + row) * tiles_x + tx)) << rank_bits) | (u64)rr.w;
     }
 }
 
