@@ -129,10 +129,11 @@ omnigs_status omnigs_sort(const omnigs_config *cfg, int64_t n, int64_t capacity,
  *   splats [V * n], ranges [V * TILES, 2] and keys [capacity] (from omnigs_sort), order [V * n] (from omnigs_bin):
  *   inputs (device); the splat of sorted position s of view v is order[v * n + (keys[s] & (2^R - 1))].
  *   out_rgb [V, 3, H, W], out_T [V, H, W] (final transmittance), out_ncontrib [V, H, W] (list position after the
- *   last contributor): outputs (device). out_T and out_ncontrib feed omnigs_render_bwd. */
+ *   last contributor): outputs (device). out_T and out_ncontrib feed omnigs_render_bwd.
+ *   out_count [V, H, W] (device, optional, may be NULL): number of splats blended into each pixel. */
 omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
                                 const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
-                                float *out_T, uint32_t *out_ncontrib, omnigs_stream_t stream);
+                                float *out_T, uint32_t *out_ncontrib, uint32_t *out_count, omnigs_stream_t stream);
 
 /* L1 term of the photometric loss (Eq. 17 with lambda = 0): loss = mean |rgb - target| over [V, 3, H, W];
  * dL_drgb = sign(rgb - target) / (V * 3 * H * W) (0 where equal). rgb, target: inputs; dL_drgb [V, 3, H, W] and

@@ -55,7 +55,7 @@ def _load():
         lib.orc_count_instances.restype = i64
         lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P]
         lib.orc_bin_sort.restype = i64
-        lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P]
+        lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
         lib.orc_preprocess_bwd.argtypes = [i64, i32, i32, i32, i32, f64, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib = lib
@@ -172,7 +172,8 @@ def _splat9(splats: dict) -> np.ndarray:
 
 def blend_fwd(splats: dict, ranges, lst, V: int, width: int, height: int, tile: int, bg=(0.0, 0.0, 0.0),
               eps: float = 1e-5):
-    """Eqs. 6-8 per pixel over its tile list. Returns rgb [V,3,H,W], T [V,H,W], n_contrib, near-threshold flags."""
+    """Eqs. 6-8 per pixel over its tile list. Returns rgb [V,3,H,W], T [V,H,W], n_contrib, near-threshold flags; the
+    per-pixel number of contributors of the last call is kept in blend_fwd.last_count."""
     lib = _load()
     sp = _splat9(splats)
     n = sp.shape[0] // V
@@ -181,8 +182,10 @@ def blend_fwd(splats: dict, ranges, lst, V: int, width: int, height: int, tile: 
     T = np.zeros((V, height, width))
     nc = np.zeros((V, height, width), dtype=np.int32)
     near = np.zeros((V, height, width), dtype=np.uint8)
+    count = np.zeros((V, height, width), dtype=np.int32)
     lib.orc_blend_fwd(V, n, width, height, tile, _p(bgv), _p(sp), _p(_i64(ranges)), _p(_i64(lst)), eps, _p(rgb), _p(T),
-                      _p(nc), _p(near))
+                      _p(nc), _p(near), _p(count))
+    blend_fwd.last_count = count
     return rgb, T, nc, near
 
 

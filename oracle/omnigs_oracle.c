@@ -465,10 +465,10 @@ static int64_t blend_pixel(int W, double xs, double ys, const double *splat, con
 
 /* splat: [V*n][9] = px, py, c0, c1, c2, opacity, r, g, b (conic c = Sigma~^-1 as (00, 01, 11)).
  * out_rgb [V,3,H,W], out_T [V,H,W], out_nc [V,H,W] (list position after the last contributor),
- * out_near [V,H,W] (see blend_pixel). */
+ * out_near [V,H,W] (see blend_pixel), out_count [V,H,W] (number of contributors; optional). */
 void orc_blend_fwd(int V, int64_t n, int W, int H, int T, const double *bg, const double *splat,
                    const int64_t *ranges, const int64_t *list, double eps, double *out_rgb, double *out_T,
-                   int32_t *out_nc, uint8_t *out_near)
+                   int32_t *out_nc, uint8_t *out_near, int32_t *out_count)
 {
     int64_t TX = W / T, TY = H / T, tiles = TX * TY, maxlen = 1;
     (void)n;
@@ -482,13 +482,14 @@ void orc_blend_fwd(int V, int64_t n, int W, int H, int T, const double *bg, cons
                 double Tf, acc[3];
                 int64_t nc;
                 int near;
-                blend_pixel(W, x + 0.5, y + 0.5, splat, list, ranges[2 * tile], ranges[2 * tile + 1], eps, buf, &Tf,
-                            &nc, &near, acc);
+                int64_t count = blend_pixel(W, x + 0.5, y + 0.5, splat, list, ranges[2 * tile], ranges[2 * tile + 1],
+                                            eps, buf, &Tf, &nc, &near, acc);
                 int64_t pix = ((int64_t)v * H + y) * W + x;
                 for (int ch = 0; ch < 3; ch++) out_rgb[((int64_t)v * 3 + ch) * H * W + (int64_t)y * W + x] = acc[ch] + Tf * bg[ch];
                 out_T[pix] = Tf;
                 out_nc[pix] = (int32_t)nc;
                 out_near[pix] = (uint8_t)near;
+                if (out_count) out_count[pix] = (int32_t)count;
             }
     free(buf);
 }

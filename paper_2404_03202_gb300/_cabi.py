@@ -33,12 +33,12 @@ class omnigs_kernel_time(ctypes.Structure):
 
 
 SPLAT_FLOATS = 12  # sizeof(omnigs_splat) / 4
+GRAD_FLOATS = 12   # sizeof(omnigs_splat_grad) / 4
 
 
 def rank_bits(n: int) -> int:
     """Bits of the depth rank in an instance key (max(1, ceil(log2(n))))."""
     return max(1, (max(int(n), 1) - 1).bit_length())
-GRAD_FLOATS = 12   # sizeof(omnigs_splat_grad) / 4
 
 _lib = None
 
@@ -60,7 +60,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_preprocess.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
         lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P]
         lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
-        lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
+        lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
         lib.omnigs_l1_loss_static.argtypes = [cfgp, P, P, P, P, P]
         lib.omnigs_l1_loss_static.restype = st
@@ -138,9 +138,10 @@ def omnigs_sort(cfg, n, capacity, keys, ranges, workspace, stream=None):
                               _stream(stream)), "omnigs_sort")
 
 
-def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, stream=None):
+def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, out_count=None, stream=None):
     _check(load().omnigs_render_fwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(keys), _ptr(order),
-                                    _ptr(out_rgb), _ptr(out_T), _ptr(out_ncontrib), _stream(stream)), "omnigs_render_fwd")
+                                    _ptr(out_rgb), _ptr(out_T), _ptr(out_ncontrib), _ptr(out_count), _stream(stream)),
+           "omnigs_render_fwd")
 
 
 def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):

@@ -105,7 +105,7 @@ cudaError_t launch_sort(const omnigs_config &cfg, int64_t n, int64_t capacity, u
                         const WsLayout &L, char *ws, cudaStream_t stream);
 cudaError_t launch_render_fwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
                               const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
-                              float *out_T, uint32_t *out_nc, cudaStream_t stream);
+                              float *out_T, uint32_t *out_nc, uint32_t *out_count, cudaStream_t stream);
 cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
                               const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
                               const float *out_T, const uint32_t *nc, const float *dL_drgb,

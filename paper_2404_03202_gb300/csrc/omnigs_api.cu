@@ -161,11 +161,11 @@ omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t n, int64_t capacity,
 
 omnigs_status omnigs_render_fwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
                                 const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
-                                float* out_T, uint32_t* out_ncontrib, omnigs_stream_t stream) {
+                                float* out_T, uint32_t* out_ncontrib, uint32_t* out_count, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
     if (!ranges || !out_rgb || !out_T || !out_ncontrib) return OMNIGS_E_INVALID;
     if (n > 0 && (!splats || !keys || !order || !aligned(splats, 16))) return OMNIGS_E_INVALID;
-    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib,
+    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, out_count,
                                        (cudaStream_t)stream));
 }
 

@@ -6,8 +6,9 @@
 //   * the longitude-seam shift decided once per (entry, tile): 0 or +-W for the whole tile, or a flag for the rare
 //     splat whose minimal-image boundary falls inside the tile;
 //   * the exponent threshold -log2(255 o): alpha = min(0.99, o 2^e) < 1/255 exactly when e < -log2(255 o), so a pair
-//     that cannot contribute is rejected with three FP32 operations and one compare, before the ex2, and a warp whose
-//     32 pixels all miss the splat skips it together.
+//     that cannot contribute is rejected with three FP32 operations and one compare, before the ex2;
+//   * the axis-aligned half-extents of the ellipse where alpha >= 1/255, so that a warp whose block of pixels lies
+//     outside it skips the entry with a few compares (a conservative test: no per-pixel decision changes).
 // Each thread owns PPT vertically adjacent pixels of one column: they share dx, the per-entry products and every
 // shared-memory load. The CTA leaves the list once every pixel has stopped (__syncthreads_count).
 //
@@ -32,8 +33,9 @@ __device__ __forceinline__ float fast_ex2(float x) {
 
 struct Staged {
     float4 a;  // px, py, c0', c1'   (c' = conic scaled to the base-2 exponent)
-    float4 b;  // c2', opacity, r, g
-    float4 c;  // b, seam shift, exponent threshold -log2(255 o), unused
+    float4 b;  // c2', exponent threshold -log2(255 o), half-extents hx, hy of the region where alpha >= 1/255
+    float4 c;  // seam shift, opacity, r, g
+    float4 d;  // b, raw conic c0, c1, c2 (for the adjoint)
 };
 
 // Splat of sorted list position s: the key's low rank bits are the splat's depth rank within its view.
@@ -54,11 +56,36 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     else if (lo >= halfW) shift = -fW;
     else if (hi < -halfW) shift = fW;
     else shift = kPerPixelWrap;
+    const float c0 = a.z, c1 = a.w, c2 = b.x, o = b.y;
+    const float thr = -__log2f(255.f * o);
+    // alpha >= 1/255 needs dp^T conic dp <= q = 2 ln(255 o); that ellipse lies within |dx| <= sqrt(q Sigma~_00),
+    // |dy| <= sqrt(q Sigma~_11), Sigma~ = conic^-1. The box is padded against FP32 rounding and disabled (infinite)
+    // when the conic is too close to singular for its inverse to be accurate; without the box nothing changes.
+    const float q = -2.f * 0.69314718055994531f * thr;
+    const float detc = c0 * c2 - c1 * c1;
+    float hx = __int_as_float(0x7f800000), hy = hx;
+    if (q <= 0.f) {
+        hx = hy = -1.f;  // o < 1/255: never contributes
+    } else if (detc > 1e-4f * c0 * c2) {
+        hx = sqrtf(q * c2 / detc) * 1.001f + 1e-3f;
+        hy = sqrtf(q * c0 / detc) * 1.001f + 1e-3f;
+    }
     Staged s;
-    s.a = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-    s.b = make_float4(-0.5f * kLog2e * b.x, b.y, b.z, b.w);
-    s.c = make_float4(blue, shift, -__log2f(255.f * b.y), 0.f);
+    s.a = make_float4(a.x, a.y, -0.5f * kLog2e * c0, -kLog2e * c1);
+    s.b = make_float4(-0.5f * kLog2e * c2, thr, hx, hy);
+    s.c = make_float4(shift, o, b.z, b.w);
+    s.d = make_float4(blue, c0, c1, c2);
     return s;
+}
+
+// True when the staged splat cannot reach any pixel of the warp's block (columns [x_first, x_last] of the tile,
+// pixel-centre rows [y_lo, y_hi]): a conservative test that leaves every per-pixel decision unchanged.
+__device__ __forceinline__ bool warp_misses(const float4& A, const float4& B, float shift, float x_first,
+                                            float x_last, float y_lo, float y_hi) {
+    if (shift == kPerPixelWrap) return false;
+    const float dx_hi = (A.x - x_first) + shift, dx_lo = (A.x - x_last) + shift;
+    const float dy_hi = A.y - y_lo, dy_lo = A.y - y_hi;
+    return dx_lo > B.z || dx_hi < -B.z || dy_lo > B.w || dy_hi < -B.w;
 }
 
 // Minimal-image dx of the thread's column for a staged entry.
@@ -91,11 +118,13 @@ __global__ void __launch_bounds__(TS * TS / PPT)
 render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
-                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc) {
+                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
+                  uint32_t* __restrict__ out_count) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
     __shared__ float4 s_c[NT];
+    __shared__ float s_blue[NT];
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
@@ -103,15 +132,18 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const float xs = pm.x + 0.5f;
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
+    // pixel-centre rows of this warp's block
+    const int wrow0 = tyi * TS + (int)((threadIdx.x & ~31u) / TS) * PPT;
+    const float y_lo = wrow0 + 0.5f, y_hi = wrow0 + (32 / TS) * PPT - 0.5f;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const uint32_t* vorder = order + (size_t)v * n;
 
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    uint32_t last[PPT];
+    uint32_t last[PPT], count[PPT];
     bool live[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; live[k] = true;
+        T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; count[k] = 0; live[k] = true;
     }
     int done = 0;
     for (uint32_t b = start; b < end; b += NT) {
@@ -122,32 +154,36 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
+            s_blue[threadIdx.x] = st.d.x;
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)NT, end - b);
         for (int j = 0; j < nb && !done; ++j) {
             const float4 A = s_a[j];
             const float4 B = s_b[j];
-            const float4 Cc = s_c[j];
-            const float dx = entry_dx(A.x, Cc.y, xs, halfW, fW);
+            const float shift = s_c[j].x;
+            if (warp_misses(A, B, shift, x_first, x_last, y_lo, y_hi)) continue;
+            const float dx = entry_dx(A.x, shift, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
-                if (!live[k] || e < Cc.z || e > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, B.y * fast_ex2(e));
+                if (!live[k] || e < B.y || e > 0.f) continue;
+                const float4 Cc = s_c[j];
+                const float alpha = fminf(kAlphaMax, Cc.y * fast_ex2(e));
                 const float Tn = T[k] * (1.f - alpha);
                 if (Tn < kTStop) {
                     live[k] = false;
                     continue;
                 }
                 const float w = alpha * T[k];
-                C0[k] = fmaf(w, B.z, C0[k]);
-                C1[k] = fmaf(w, B.w, C1[k]);
-                C2[k] = fmaf(w, Cc.x, C2[k]);
+                C0[k] = fmaf(w, Cc.z, C0[k]);
+                C1[k] = fmaf(w, Cc.w, C1[k]);
+                C2[k] = fmaf(w, s_blue[j], C2[k]);
                 T[k] = Tn;
                 last[k] = b - start + j + 1;
+                ++count[k];
             }
             bool any = false;
 #pragma unroll
@@ -164,6 +200,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T[k], bg2, C2[k]);
         out_T[(size_t)v * HW + pix] = T[k];
         out_nc[(size_t)v * HW + pix] = last[k];
+        if (out_count) out_count[(size_t)v * HW + pix] = count[k];
     }
 }
 
@@ -196,8 +233,8 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     float4* s_a = reinterpret_cast<float4*>(smem_raw);
     float4* s_b = s_a + NT;
     float4* s_c = s_b + NT;
-    float4* s_k = s_c + NT;                                // raw conic c0, c1, c2
-    unsigned* s_vg = reinterpret_cast<unsigned*>(s_k + NT);
+    float4* s_d = s_c + NT;                                // blue, raw conic c0, c1, c2
+    unsigned* s_vg = reinterpret_cast<unsigned*>(s_d + NT);
     float* s_acc = reinterpret_cast<float*>(s_vg + NT);  // [NT][kGradFields]
     __shared__ unsigned s_max;
 
@@ -211,6 +248,8 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
     const uint32_t* vorder = order + (size_t)v * n;
     const size_t HW = (size_t)H * W;
+    const int wrow0 = tyi * TS + (int)((threadIdx.x & ~31u) / TS) * PPT;
+    const float y_lo = wrow0 + 0.5f, y_hi = wrow0 + (32 / TS) * PPT - 0.5f;
 
     uint32_t last[PPT];
     float T[PPT], g0[PPT], g1[PPT], g2[PPT], B0[PPT], B1[PPT], B2[PPT];
@@ -234,6 +273,9 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     __syncthreads();
     const uint32_t maxlast = s_max;
     const unsigned lane = threadIdx.x & 31;
+    float gv[16];  // per-thread partial derivatives of the current entry (indices 9..15 stay 0)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) gv[q] = 0.f;
 
     for (int64_t bend = (int64_t)maxlast; bend > 0; bend -= NT) {
         const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
@@ -241,12 +283,10 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         if ((int)threadIdx.x < nb) {
             const unsigned vg = entry_splat(keys, vorder, (uint32_t)(start + bbeg + threadIdx.x), rank_mask);
             const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
-            const float4 raw0 = __ldg(splats + 3 * (size_t)vg);
-            const float raw1 = __ldg(reinterpret_cast<const float*>(splats + 3 * (size_t)vg + 1));
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
-            s_k[threadIdx.x] = make_float4(raw0.z, raw0.w, raw1, 0.f);
+            s_d[threadIdx.x] = st.d;
             s_vg[threadIdx.x] = vg;
         }
         __syncthreads();
@@ -255,25 +295,25 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             if (__all_sync(0xffffffffu, pos >= mylast)) continue;
             const float4 A = s_a[j];
             const float4 Bv = s_b[j];
-            const float4 Cc = s_c[j];
-            const float dx = entry_dx(A.x, Cc.y, xs, halfW, fW);
+            const float shift = s_c[j].x;
+            if (warp_misses(A, Bv, shift, x_first, x_last, y_lo, y_hi)) continue;
+            const float dx = entry_dx(A.x, shift, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;
-            float gv[16];
-#pragma unroll
-            for (int f = 0; f < 16; ++f) gv[f] = 0.f;
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(Bv.x, dy, e1), e0);
-                if (pos >= last[k] || e < Cc.z || e > 0.f) continue;
+                if (pos >= last[k] || e < Bv.y || e > 0.f) continue;
+                const float4 Cc = s_c[j];
+                const float4 D = s_d[j];
                 const float G = fast_ex2(e);
-                const float raw = Bv.y * G;
+                const float raw = Cc.y * G;
                 const float alpha = fminf(kAlphaMax, raw);
                 contrib = true;
                 const float one_m = 1.f - alpha;
                 T[k] = __fdividef(T[k], one_m);  // transmittance in front of this entry
-                const float cr = Bv.z, cg = Bv.w, cb = Cc.x;
+                const float cr = Cc.z, cg = Cc.w, cb = D.x;
                 const float dalpha = T[k] * (g0[k] * (cr - B0[k]) + g1[k] * (cg - B1[k]) + g2[k] * (cb - B2[k]));
                 const float w = alpha * T[k];
                 gv[6] = fmaf(w, g0[k], gv[6]);
@@ -283,21 +323,22 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 B1[k] = fmaf(alpha, cg, one_m * B1[k]);
                 B2[k] = fmaf(alpha, cb, one_m * B2[k]);
                 if (raw < kAlphaMax) {
-                    const float4 K = s_k[j];
                     gv[5] = fmaf(dalpha, G, gv[5]);
                     const float gp = dalpha * raw;  // dL/d(exponent in natural units)
                     const float gdx = gp * dx, gdy = gp * dy;
                     gv[2] = fmaf(-0.5f * dx, gdx, gv[2]);
                     gv[3] = fmaf(-dx, gdy, gv[3]);
                     gv[4] = fmaf(-0.5f * dy, gdy, gv[4]);
-                    gv[0] -= K.x * gdx + K.y * gdy;
-                    gv[1] -= K.z * gdy + K.y * gdx;
+                    gv[0] -= D.y * gdx + D.z * gdy;
+                    gv[1] -= D.w * gdy + D.z * gdx;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
                 const float tot = warp_transpose_sum16(gv, lane);
                 const unsigned f = lane >> 1;
                 if ((lane & 1u) == 0 && f < (unsigned)kGradFields) atomicAdd(&s_acc[j * kGradFields + f], tot);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) gv[q] = 0.f;
             }
         }
         __syncthreads();
@@ -325,17 +366,18 @@ size_t bwd_smem(int nt) {
     return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
+
 template <int TS>
 cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
                          const uint64_t* keys, const uint32_t* order, float* out_rgb, float* out_T, uint32_t* out_nc,
-                         cudaStream_t stream) {
+                         uint32_t* out_count, cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     ProfScope prof("render_fwd", stream);
     render_fwd_kernel<TS, kPPT><<<tiles * cfg.num_views, PixelMap<TS, kPPT>::NT, 0, stream>>>(
         cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
-        out_rgb, out_T, out_nc);
+        out_rgb, out_T, out_nc, out_count);
     return cudaGetLastError();
 }
 
@@ -399,11 +441,11 @@ __global__ void l1_finish_kernel(const float* __restrict__ partials, int nb, flo
 
 cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
                               const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
-                              float* out_T, uint32_t* out_nc, cudaStream_t stream) {
+                              float* out_T, uint32_t* out_nc, uint32_t* out_count, cudaStream_t stream) {
     switch (cfg.tile) {
-        case 8: return render_fwd_t<8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
-        case 32: return render_fwd_t<32>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
-        default: return render_fwd_t<16>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, stream);
+        case 8: return render_fwd_t<8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        case 32: return render_fwd_t<32>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        default: return render_fwd_t<16>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
     }
 }
 

@@ -62,6 +62,7 @@ class Rasterizer:
         self.rgb = _empty((V, 3, H, W), torch.float32, self.device)
         self.T = _empty((V, H, W), torch.float32, self.device)
         self.ncontrib = _empty((V, H, W), torch.int32, self.device)
+        self.count_out = None  # set to an int32 [V, H, W] tensor to receive per-pixel contributor counts
         self.dL_drgb = _empty((V, 3, H, W), torch.float32, self.device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         self.ranges = _empty((V * settings.tiles * 2,), torch.int32, self.device)
@@ -114,7 +115,7 @@ class Rasterizer:
                 C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
         C.omnigs_sort(self.cfg, n, self.capacity, self.keys, self.ranges, self.ws, stream)
         C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.keys, self.order, self.rgb, self.T,
-                            self.ncontrib, stream)
+                            self.ncontrib, self.count_out, stream)
         return self.rgb
 
     def l1_loss(self, target, stream=None):

@@ -43,7 +43,8 @@ def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):
         r.splats.copy_(dev(sp_packed))
         C.omnigs_bin(r.cfg, n, r.splats, r.order, r.keys, r.capacity, r.ws)
     C.omnigs_sort(r.cfg, n, r.capacity, r.keys, r.ranges, r.ws)
-    C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.keys, r.order, r.rgb, r.T, r.ncontrib)
+    r.count_out = torch.empty_like(r.ncontrib)
+    C.omnigs_render_fwd(r.cfg, n, r.splats, r.ranges, r.keys, r.order, r.rgb, r.T, r.ncontrib, r.count_out)
     torch.cuda.synchronize()
     assert r.check() is None
     return r, cnt
@@ -150,6 +151,7 @@ def test_render_fwd_matches_oracle(tile, V):
     assert err.max() <= 1e-5
     assert np.abs(r.T.cpu().numpy() - T)[mask].max() <= 1e-5
     assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+    assert np.array_equal(r.count_out.cpu().numpy()[mask], oracle.blend_fwd.last_count[mask])
 
 
 def test_render_fwd_opaque_stacks_stop_rule():
