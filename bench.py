@@ -14,6 +14,7 @@ region is bracketed by barriers and the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -34,14 +35,24 @@ WORKLOADS = {
     "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
 }
 
-# Algorithmic work per unit, used for the roofline (see the design doc for the derivations).
-FWD_FLOP_PER_PAIR = 22       # render_fwd: per evaluated (pixel, entry) pair
-BWD_FLOP_PER_PAIR = 62       # render_bwd: per processed (pixel, entry) pair (eval + adjoint)
+# Algorithmic work per unit, used for the roofline. A (pixel, entry) pair is "examined" when the pixel's walk of its
+# tile list reaches the entry (sum of n_contrib over pixels) and "contributes" when its alpha passes 1/255 (sum of
+# the per-pixel contributor counts). FLOPs count an FMA as 2 and ex2 as 1.
+#   examined, both passes: wrapped dx (2), dy (1), quadratic form of the conic (6), threshold compare (1)  = 10
+#   contributing, forward: ex2 (1), alpha = min(0.99, o g) (2), w = alpha T (1), C += w rgb (6),
+#                          T *= 1 - alpha (2), stop test (1)                                                = 13
+#   contributing, adjoint: alpha (3), T from T_next (2), w (1), dL/drgb (3), running colour (6), rest (3),
+#                          dL/dalpha over rgb + background (11), dL/do and dL/dexponent (2),
+#                          dL/dconic (6), dL/dmean2d (8), accumulation of the 9 fields (9)                 = 54
+FLOP_EXAMINED = 10
+FWD_FLOP_CONTRIB = 13
+BWD_FLOP_CONTRIB = 54
 SORT_BYTES_PER_KEY = 16      # sort_downsweep: one 8 B key read and written per instance and pass
-PRE_BYTES_PER_GAUSS = 236    # preprocess: 59 parameter floats read once
-PRE_BYTES_PER_SPLAT = 48     # preprocess: one 48 B splat written per (view, Gaussian)
 
-
+# DRAM traffic of render_bwd per view (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# 1-view workload; the 8-view launch processes 8 such views), with the SHA-256 of the kernel source it was taken
+# on: once render.cu changes the figure no longer applies and the bench reports traffic as null.
+RENDER_BWD_TRAFFIC = {"bytes_per_view": None, "render_cu_sha256": None}
 def build_scene(wl: dict, seed: int = 0):
     if wl["scene"] == "room":
         return synth.room_scene(wl["n"], seed)
@@ -353,19 +364,26 @@ def main():
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak_tflops = n_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    pairs = int(r.ncontrib.to(torch.int64).sum().item())
+    # examined and contributing (pixel, entry) pairs of this workload: one extra forward, outside the timed region
+    r.count_out = torch.empty((V, H, W), dtype=torch.int32, device=dev)
+    r.forward(*params, vm)
+    examined = int(r.ncontrib.to(torch.int64).sum().item())
+    contrib = int(r.count_out.to(torch.int64).sum().item())
+    r.count_out = None
     count = r.instance_count()
     per_kernel = {p[0]: {"launches": p[1], "total_ms": p[2], "avg_ms": p[2] / max(p[1], 1)} for p in prof}
     dom = max(prof, key=lambda p: p[2])[0]
     k = per_kernel[dom]
-    if dom == "render_bwd":
-        flops = pairs * BWD_FLOP_PER_PAIR
+    traffic = None
+    if dom in ("render_fwd", "render_bwd"):
+        contrib_flop = BWD_FLOP_CONTRIB if dom == "render_bwd" else FWD_FLOP_CONTRIB
+        flops = examined * FLOP_EXAMINED + contrib * contrib_flop
         roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
                 "unit": "TFLOP/s"}
-    elif dom == "render_fwd":
-        flops = pairs * FWD_FLOP_PER_PAIR
-        roof = {"bound": "alu", "achieved": flops / (k["avg_ms"] * 1e-3) / 1e12, "peak": alu_peak_tflops,
-                "unit": "TFLOP/s"}
+        if dom == "render_bwd" and RENDER_BWD_TRAFFIC["bytes_per_view"]:
+            with open(os.path.join(ROOT, "paper_2404_03202_gb300", "csrc", "render.cu"), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() == RENDER_BWD_TRAFFIC["render_cu_sha256"]:
+                    traffic = RENDER_BWD_TRAFFIC["bytes_per_view"] * V
     elif dom == "sort_downsweep":
         roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
@@ -373,7 +391,7 @@ def main():
         roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["kernel"] = dom
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") else None
-    roof["traffic"] = None
+    roof["traffic"] = traffic
     roof["peak_source"] = f"{peak_src}" + (" (ALU peak: SMs x 128 FP32 lanes x 2 x median SM clock)"
                                            if roof["bound"] == "alu" else "")
 
@@ -393,7 +411,9 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": workload_config(wl, args) | {"views_per_s": 1e3 * V * world / ms,
                                                       "graph_ms_per_step": graph_ms,
-                                                      "instances_per_step": count, "pairs_per_step": pairs},
+                                                      "instances_per_step": count,
+                                                      "examined_pairs_per_step": examined,
+                                                      "contributing_pairs_per_step": contrib},
                "gpu_launches": kernel_launches * args.steps, "kernels_per_step": per_kernel,
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)

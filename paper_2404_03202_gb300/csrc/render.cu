@@ -5,10 +5,9 @@
 //   * the conic pre-scaled by -log2(e)/2, so that G = 2^e with e = dx (c0' dx + c1' dy) + c2' dy^2 costs one ex2;
 //   * the longitude-seam shift decided once per (entry, tile): 0 or +-W for the whole tile, or a flag for the rare
 //     splat whose minimal-image boundary falls inside the tile;
-//   * the exponent threshold -log2(255 o): alpha = min(0.99, o 2^e) < 1/255 exactly when e < -log2(255 o), so a pair
-//     that cannot contribute is rejected with three FP32 operations and one compare, before the ex2;
-//   * the axis-aligned half-extents of the ellipse where alpha >= 1/255, so that a warp whose block of pixels lies
-//     outside it skips the entry with a few compares (a conservative test: no per-pixel decision changes).
+//   * the exponent threshold thr = -log2(255 o): alpha = min(0.99, o 2^e) < 1/255 exactly when e < thr, so with the
+//     exponent > 0 guard a pair passes only if thr <= e <= 0, tested as |e - thr/2| <= -thr/2 with one subtraction
+//     and one compare before the ex2.
 // Each thread owns PPT vertically adjacent pixels of one column: they share dx, the per-entry products and every
 // shared-memory load. The CTA leaves the list once every pixel has stopped (__syncthreads_count).
 //
@@ -33,7 +32,7 @@ __device__ __forceinline__ float fast_ex2(float x) {
 
 struct Staged {
     float4 a;  // px, py, c0', c1'   (c' = conic scaled to the base-2 exponent)
-    float4 b;  // c2', exponent threshold -log2(255 o), half-extents hx, hy of the region where alpha >= 1/255
+    float4 b;  // c2', m, h with the pass interval thr <= e <= 0 written |e - m| <= h (m = thr/2, h = -thr/2)
     float4 c;  // seam shift, opacity, r, g
     float4 d;  // b, raw conic c0, c1, c2 (for the adjoint)
 };
@@ -57,35 +56,13 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     else if (hi < -halfW) shift = fW;
     else shift = kPerPixelWrap;
     const float c0 = a.z, c1 = a.w, c2 = b.x, o = b.y;
-    const float thr = -__log2f(255.f * o);
-    // alpha >= 1/255 needs dp^T conic dp <= q = 2 ln(255 o); that ellipse lies within |dx| <= sqrt(q Sigma~_00),
-    // |dy| <= sqrt(q Sigma~_11), Sigma~ = conic^-1. The box is padded against FP32 rounding and disabled (infinite)
-    // when the conic is too close to singular for its inverse to be accurate; without the box nothing changes.
-    const float q = -2.f * 0.69314718055994531f * thr;
-    const float detc = c0 * c2 - c1 * c1;
-    float hx = __int_as_float(0x7f800000), hy = hx;
-    if (q <= 0.f) {
-        hx = hy = -1.f;  // o < 1/255: never contributes
-    } else if (detc > 1e-4f * c0 * c2) {
-        hx = sqrtf(q * c2 / detc) * 1.001f + 1e-3f;
-        hy = sqrtf(q * c0 / detc) * 1.001f + 1e-3f;
-    }
+    const float thr = -__log2f(255.f * o);  // may be +inf (o = 0): then nothing passes
     Staged s;
     s.a = make_float4(a.x, a.y, -0.5f * kLog2e * c0, -kLog2e * c1);
-    s.b = make_float4(-0.5f * kLog2e * c2, thr, hx, hy);
+    s.b = make_float4(-0.5f * kLog2e * c2, 0.5f * thr, -0.5f * thr, 0.f);
     s.c = make_float4(shift, o, b.z, b.w);
     s.d = make_float4(blue, c0, c1, c2);
     return s;
-}
-
-// True when the staged splat cannot reach any pixel of the warp's block (columns [x_first, x_last] of the tile,
-// pixel-centre rows [y_lo, y_hi]): a conservative test that leaves every per-pixel decision unchanged.
-__device__ __forceinline__ bool warp_misses(const float4& A, const float4& B, float shift, float x_first,
-                                            float x_last, float y_lo, float y_hi) {
-    if (shift == kPerPixelWrap) return false;
-    const float dx_hi = (A.x - x_first) + shift, dx_lo = (A.x - x_last) + shift;
-    const float dy_hi = A.y - y_lo, dy_lo = A.y - y_hi;
-    return dx_lo > B.z || dx_hi < -B.z || dy_lo > B.w || dy_hi < -B.w;
 }
 
 // Minimal-image dx of the thread's column for a staged entry.
@@ -132,9 +109,6 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const float xs = pm.x + 0.5f;
     const float halfW = 0.5f * (float)W, fW = (float)W;
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
-    // pixel-centre rows of this warp's block
-    const int wrow0 = tyi * TS + (int)((threadIdx.x & ~31u) / TS) * PPT;
-    const float y_lo = wrow0 + 0.5f, y_hi = wrow0 + (32 / TS) * PPT - 0.5f;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const uint32_t* vorder = order + (size_t)v * n;
 
@@ -162,14 +136,13 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             const float4 A = s_a[j];
             const float4 B = s_b[j];
             const float shift = s_c[j].x;
-            if (warp_misses(A, B, shift, x_first, x_last, y_lo, y_hi)) continue;
             const float dx = entry_dx(A.x, shift, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
-                if (!live[k] || e < B.y || e > 0.f) continue;
+                if (!live[k] || !(fabsf(e - B.y) <= B.z)) continue;  // alpha < 1/255, or exponent > 0
                 const float4 Cc = s_c[j];
                 const float alpha = fminf(kAlphaMax, Cc.y * fast_ex2(e));
                 const float Tn = T[k] * (1.f - alpha);
@@ -248,8 +221,6 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
     const uint32_t* vorder = order + (size_t)v * n;
     const size_t HW = (size_t)H * W;
-    const int wrow0 = tyi * TS + (int)((threadIdx.x & ~31u) / TS) * PPT;
-    const float y_lo = wrow0 + 0.5f, y_hi = wrow0 + (32 / TS) * PPT - 0.5f;
 
     uint32_t last[PPT];
     float T[PPT], g0[PPT], g1[PPT], g2[PPT], B0[PPT], B1[PPT], B2[PPT];
@@ -296,7 +267,6 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             const float4 A = s_a[j];
             const float4 Bv = s_b[j];
             const float shift = s_c[j].x;
-            if (warp_misses(A, Bv, shift, x_first, x_last, y_lo, y_hi)) continue;
             const float dx = entry_dx(A.x, shift, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;
             bool contrib = false;
@@ -304,7 +274,7 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(Bv.x, dy, e1), e0);
-                if (pos >= last[k] || e < Bv.y || e > 0.f) continue;
+                if (pos >= last[k] || !(fabsf(e - Bv.y) <= Bv.z)) continue;
                 const float4 Cc = s_c[j];
                 const float4 D = s_d[j];
                 const float G = fast_ex2(e);
