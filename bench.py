@@ -49,20 +49,62 @@ FWD_FLOP_CONTRIB = 13
 BWD_FLOP_CONTRIB = 54
 SORT_BYTES_PER_KEY = 16      # sort_downsweep: one 8 B key read and written per instance and pass
 
+
+def _sort_passes(bits: int) -> int:
+    """Passes of the LSD radix sort over `bits` key bits (digits of at most 9 bits, an even number of passes)."""
+    p = max(2, (bits + 8) // 9)
+    return p + (p % 2)
+
+
+def _ceil_log2(x: int) -> int:
+    return max(0, (int(x) - 1).bit_length())
+
+
+def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int) -> dict:
+    """Algorithmic HBM bytes per step of the memory-bound stages (each read or written once).
+
+    P = V n projected splats (48 B each), I instances (8 B keys), X = V H W pixels.
+    """
+    P, X = V * n, V * H * W
+    tiles = V * (W // tile) * (H // tile)
+    dp = _sort_passes(32 + _ceil_log2(V))
+    tp = _sort_passes(max(1, _ceil_log2(tiles)))
+    return {
+        "preprocess_fwd": n * 236 + P * 48,               # 59 parameter floats in, one splat out per view
+        "depth_keys": P * (4 + 8 + 4),                    # depth in, (view|depth) key and index out
+        "depth_sort": dp * P * (8 + 2 * 12),              # per pass: key histogram read, key+index read and written
+        "bin_count": P * (4 + 12 + 4),                    # depth order, (px, py, radius), tile count out
+        "bin_emit": P * (4 + 12 + 8) + instances * 8,     # order, (px, py, radius), offset; one key per instance
+        "sort_upsweep": tp * instances * 8,               # per pass: keys read for the digit histogram
+        "sort_downsweep": tp * instances * 16,            # per pass: keys read and written
+        "tile_ranges": tiles * 8,                         # one [start, end) pair per tile
+        "l1_loss": X * 3 * 12,                            # image and target in, dL/dC out
+        "preprocess_bwd": n * (236 + 236 + 8) + P * 48,   # parameters in, their gradients and dL/ds out, 2D grads in
+    }
+
 # DRAM traffic of render_bwd per view (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
 # 1-view workload; the 8-view launch processes 8 such views), with the SHA-256 of the kernel source it was taken
 # on: once render.cu changes the figure no longer applies and the bench reports traffic as null.
-RENDER_BWD_TRAFFIC = {"bytes_per_view": None, "render_cu_sha256": None}
+RENDER_BWD_TRAFFIC = {"bytes_per_view": 58_584_576,
+                      "render_cu_sha256": "60b5222de83bc2dc2226ee169e2d881a841063695c1ad982e8271a230580f61c"}
 def build_scene(wl: dict, seed: int = 0):
     if wl["scene"] == "room":
         return synth.room_scene(wl["n"], seed)
     return synth.shell_scene(wl["n"], seed)
 
 
-def build_poses(wl: dict, rank: int):
+def build_poses(wl: dict, rank: int, world: int = 1):
+    """This rank's poses: its slice of one seeded batch of views x world poses (weak scaling)."""
+    total = wl["views"] * world
     if wl["scene"] == "room":
-        return synth.room_viewmats(wl["views"], 1000 + rank)
-    return synth.identity_viewmats(wl["views"])
+        poses = synth.room_viewmats(total, 1000)
+    else:
+        poses = synth.identity_viewmats(total)
+    if world == 1:
+        return poses
+    from paper_2404_03202_gb300.replicas import view_range
+    a, b = view_range(total, world, rank)
+    return poses[a:b]
 
 
 def read_peaks():
@@ -219,6 +261,7 @@ def main():
 
     import paper_2404_03202_gb300 as og
     from paper_2404_03202_gb300 import _cabi as C
+    from paper_2404_03202_gb300.replicas import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,7 +276,7 @@ def main():
             dist.barrier()
 
     scene = build_scene(wl)
-    vm_np = build_poses(wl, rank)
+    vm_np = build_poses(wl, rank, world)
     V, W, H = wl["views"], wl["width"], wl["height"]
     settings = og.Settings(width=W, height=H, tile=wl["tile"], num_views=V, sh_degree=scene.sh_degree)
     params = [torch.from_numpy(a).to(dev) for a in scene.arrays()]
@@ -276,11 +319,7 @@ def main():
     prof = C.omnigs_profiler_collect(64)
     C.omnigs_profiler_enable(False)
     r.check()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
     clocks = sampler.summary()
     kernel_launches = int(sum(p[1] for p in prof) / args.steps)
 
@@ -349,11 +388,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        e_ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
         h2d = sum(h.numel() * h.element_size() for h in host_params) + host_vm.numel() * 4 + host_target.numel() * 4
         d2h = sum(h.numel() * h.element_size() for h in host_out.values()) + 4
         e2e = {"value": e_ms, "unit": "ms/iter", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
@@ -395,6 +430,23 @@ def main():
     roof["peak_source"] = f"{peak_src}" + (" (ALU peak: SMs x 128 FP32 lanes x 2 x median SM clock)"
                                            if roof["bound"] == "alu" else "")
 
+    # every stage against its own roofline (per step; a stage may span several launches)
+    stages = {}
+    sb = stage_bytes(wl["n"], V, W, H, wl["tile"], count)
+    for name, pk in per_kernel.items():
+        ms_step = pk["total_ms"] / args.steps
+        if name in sb:
+            gbs = sb[name] / (ms_step * 1e-3) / 1e9
+            stages[name] = {"ms": ms_step, "bound": "hbm", "achieved": gbs, "unit": "GB/s",
+                            "frac": gbs / peaks["hbm_gbs"]}
+        elif name in ("render_fwd", "render_bwd"):
+            cf = BWD_FLOP_CONTRIB if name == "render_bwd" else FWD_FLOP_CONTRIB
+            tf = (examined * FLOP_EXAMINED + contrib * cf) / (ms_step * 1e-3) / 1e12
+            stages[name] = {"ms": ms_step, "bound": "alu", "achieved": tf, "unit": "TFLOP/s",
+                            "frac": tf / alu_peak_tflops}
+        else:
+            stages[name] = {"ms": ms_step}
+
     # ---------------------------------------------------------------- CPU baseline (oracle), rank 0, N = 1
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -414,7 +466,7 @@ def main():
                                                       "instances_per_step": count,
                                                       "examined_pairs_per_step": examined,
                                                       "contributing_pairs_per_step": contrib},
-               "gpu_launches": kernel_launches * args.steps, "kernels_per_step": per_kernel,
+               "gpu_launches": kernel_launches * args.steps, "stages": stages,
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -49,6 +49,9 @@ typedef struct {
     int32_t sh_degree; /* 0..3; the SH array holds K = (sh_degree + 1)^2 coefficients per colour channel */
     float near_r;      /* a Gaussian is culled when its camera distance t_r <= near_r */
     float bg[3];       /* background colour added with the final transmittance */
+    int32_t pixels_per_thread; /* blend schedule: pixels of one image column each blend thread owns (2 or 4;
+                                * 4 needs tile >= 16); 0 lets the library choose. Results do not depend on it
+                                * beyond the order of floating-point additions in the gradients. */
 } omnigs_config;
 
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).
@@ -181,9 +184,10 @@ omnigs_status omnigs_instance_count(const void *workspace, int64_t *count, omnig
  * `stream`; also reports a pending CUDA error as OMNIGS_E_CUDA. */
 omnigs_status omnigs_last_error(void *workspace, omnigs_stream_t stream);
 
-/* Kernel timing. While enabled, every kernel the library launches is bracketed by CUDA events on its launching
- * stream. omnigs_profiler_collect synchronises those events, writes up to `max` per-kernel totals (launches and
- * summed milliseconds, in first-launch order) and clears the record; it returns the number of kernels. Host-side
+/* Kernel timing. While enabled, every stage the library runs (one kernel, or a few back-to-back kernels under one
+ * name) is bracketed by CUDA events on its launching stream. omnigs_profiler_collect synchronises those events,
+ * writes up to `max` per-stage totals (kernel launches and summed milliseconds, in first-launch order) and clears
+ * the record; it returns the number of stages. Host-side
  * state is global to the process and not thread-safe; use it from one thread, outside CUDA graph capture. */
 typedef struct {
     char name[48];

@@ -424,7 +424,7 @@ cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* co
         const int shift = lo_bit + p * P.digit;
         const int db = std::max(1, std::min(P.digit, lo_bit + bits - shift));
         {
-            ProfScope prof(tag_up, stream);
+            ProfScope prof(tag_up, stream, 3);
             lsd_upsweep_kernel<<<G, kSortThreads, 0, stream>>>(k0, count, capacity, shift, db, hist, G);
             lsd_scan_digit_kernel<<<1 << db, 256, 0, stream>>>(hist, G, hist + (size_t)kRadixMax * G);
             lsd_scan_totals_kernel<<<1, kRadixMax, 0, stream>>>(hist + (size_t)kRadixMax * G, 1 << db);
@@ -483,7 +483,7 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
                        sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
     if (e != cudaSuccess) return e;
     {
-        ProfScope prof("bin_count", stream);
+        ProfScope prof("bin_count", stream, 2);
         bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, bsums);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
     }

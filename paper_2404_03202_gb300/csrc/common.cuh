@@ -84,10 +84,11 @@ WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
 int rank_bits_for(int64_t n);
 
 // Kernel launches report their name and stream to the optional profiler.
+// Brackets the `kernels` launches of one named stage with CUDA events while the profiler is on.
 struct ProfScope {
     int slot;
     cudaStream_t stream;
-    ProfScope(const char *name, cudaStream_t s);
+    ProfScope(const char *name, cudaStream_t s, int kernels = 1);
     ~ProfScope();
 };
 

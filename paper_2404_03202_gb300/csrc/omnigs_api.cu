@@ -43,6 +43,7 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
 namespace {
 struct ProfRecord {
     std::string name;
+    int kernels;
     cudaEvent_t start, stop;
 };
 std::mutex g_prof_mu;
@@ -58,7 +59,7 @@ bool capturing(cudaStream_t s) {
 }
 }  // namespace
 
-ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+ProfScope::ProfScope(const char* name, cudaStream_t s, int kernels) : slot(-1), stream(s) {
     if (!g_prof_on || capturing(s)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (g_prof_used == g_prof_pool.size()) {
@@ -68,7 +69,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
         g_prof_pool.push_back({a, b});
     }
     auto ev = g_prof_pool[g_prof_used++];
-    g_prof_records.push_back({name, ev.first, ev.second});
+    g_prof_records.push_back({name, kernels, ev.first, ev.second});
     slot = (int)g_prof_records.size() - 1;
     cudaEventRecord(ev.first, s);
 }
@@ -95,6 +96,8 @@ bool valid_cfg(const omnigs_config* c) {
     if (!std::isfinite(c->near_r) || c->near_r < 0.f) return false;
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(c->bg[i])) return false;
+    if (c->pixels_per_thread != 0 && c->pixels_per_thread != 2 && c->pixels_per_thread != 4) return false;
+    if (c->pixels_per_thread == 4 && c->tile == 8) return false;
     const uint64_t tiles = (uint64_t)(c->width / c->tile) * (uint64_t)(c->height / c->tile) * (uint64_t)c->num_views;
     return tiles < (1ull << 31);
 }
@@ -253,7 +256,7 @@ int omnigs_profiler_collect(omnigs_kernel_time* out, int max) {
             std::strncpy(t.name, r.name.c_str(), sizeof(t.name) - 1);
             agg.push_back(t);
         }
-        agg[k].launches += 1;
+        agg[k].launches += r.kernels;
         agg[k].total_ms += ms;
     }
     g_prof_records.clear();

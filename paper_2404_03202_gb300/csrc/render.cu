@@ -13,9 +13,11 @@
 //
 // The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
 // (1 - alpha) and accumulates the 9 partial derivatives of an entry over the thread's pixels. The warp then reduces
-// them with one transposed reduce-scatter (16 shuffles; lanes 0, 2, .., 16 end up with one field's total each, written
-// with one shared-memory atomic per field), the CTA sums warps in shared memory, and the CTA's sum goes to the splat's
-// gradient with 16-byte vector atomics (red.global.add.v4.f32). Forward and adjoint evaluate alpha with identical
+// them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth: 14 shuffles, after which 9 lanes
+// hold one field's total each and write it with one shared-memory atomic), the CTA sums warps in shared memory, and
+// the CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
+// A thread owns PPT = 2 or 4 pixels (the blend schedule of the config): more pixels per thread share more of the
+// per-entry work and the warp reduction, fewer give more threads per tile. Forward and adjoint evaluate alpha with identical
 // arithmetic, so their skip / stop decisions agree.
 #include "common.cuh"
 
@@ -32,9 +34,9 @@ __device__ __forceinline__ float fast_ex2(float x) {
 
 struct Staged {
     float4 a;  // px, py, c0', c1'   (c' = conic scaled to the base-2 exponent)
-    float4 b;  // c2', m, h with the pass interval thr <= e <= 0 written |e - m| <= h (m = thr/2, h = -thr/2)
-    float4 c;  // seam shift, opacity, r, g
-    float4 d;  // b, raw conic c0, c1, c2 (for the adjoint)
+    float4 b;  // c2', m, h, seam shift; the pass interval thr <= e <= 0 is written |e - m| <= h (m = thr/2, h = -m)
+    float4 c;  // opacity, r, g, b
+    float4 d;  // raw conic c0, c1, c2, unused (for the adjoint)
 };
 
 // Splat of sorted list position s: the key's low rank bits are the splat's depth rank within its view.
@@ -59,9 +61,9 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     const float thr = -__log2f(255.f * o);  // may be +inf (o = 0): then nothing passes
     Staged s;
     s.a = make_float4(a.x, a.y, -0.5f * kLog2e * c0, -kLog2e * c1);
-    s.b = make_float4(-0.5f * kLog2e * c2, 0.5f * thr, -0.5f * thr, 0.f);
-    s.c = make_float4(shift, o, b.z, b.w);
-    s.d = make_float4(blue, c0, c1, c2);
+    s.b = make_float4(-0.5f * kLog2e * c2, 0.5f * thr, -0.5f * thr, shift);
+    s.c = make_float4(o, b.z, b.w, blue);
+    s.d = make_float4(c0, c1, c2, 0.f);
     return s;
 }
 
@@ -101,7 +103,6 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
     __shared__ float4 s_c[NT];
-    __shared__ float s_blue[NT];
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
@@ -128,15 +129,13 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
-            s_blue[threadIdx.x] = st.d.x;
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)NT, end - b);
         for (int j = 0; j < nb && !done; ++j) {
             const float4 A = s_a[j];
             const float4 B = s_b[j];
-            const float shift = s_c[j].x;
-            const float dx = entry_dx(A.x, shift, xs, halfW, fW);
+            const float dx = entry_dx(A.x, B.w, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -144,16 +143,16 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
                 if (!live[k] || !(fabsf(e - B.y) <= B.z)) continue;  // alpha < 1/255, or exponent > 0
                 const float4 Cc = s_c[j];
-                const float alpha = fminf(kAlphaMax, Cc.y * fast_ex2(e));
+                const float alpha = fminf(kAlphaMax, Cc.x * fast_ex2(e));
                 const float Tn = T[k] * (1.f - alpha);
                 if (Tn < kTStop) {
                     live[k] = false;
                     continue;
                 }
                 const float w = alpha * T[k];
-                C0[k] = fmaf(w, Cc.z, C0[k]);
-                C1[k] = fmaf(w, Cc.w, C1[k]);
-                C2[k] = fmaf(w, s_blue[j], C2[k]);
+                C0[k] = fmaf(w, Cc.y, C0[k]);
+                C1[k] = fmaf(w, Cc.z, C1[k]);
+                C2[k] = fmaf(w, Cc.w, C2[k]);
                 T[k] = Tn;
                 last[k] = b - start + j + 1;
                 ++count[k];
@@ -179,10 +178,13 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
 
 constexpr int kGradFields = 9;
 
-// Reduce-scatter of 16 values over the warp: on return v[0] of lanes 2f and 2f + 1 holds the warp total of value f.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], unsigned lane) {
+// Warp sums of the 9 gradient fields. Fields 0..7 go through a transposed reduce-scatter (offsets 16, 8, 4 halve
+// the values each lane carries, offsets 2 and 1 finish the sum): lane l ends with the total of field (l >> 2).
+// Field 8 is summed by a plain butterfly. On return, lanes with (l & 3) == 0 hold field l >> 2 and every lane holds
+// field 8's total in `f8`.
+__device__ __forceinline__ float warp_sum_fields(float (&v)[kGradFields], unsigned lane, float& f8) {
 #pragma unroll
-    for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+    for (int half = 4, off = 16; half >= 1; half >>= 1, off >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -191,7 +193,14 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], unsigned l
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    float t = v[0];
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    float b = v[8];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) b += __shfl_xor_sync(0xffffffffu, b, off);
+    f8 = b;
+    return t;
 }
 
 template <int TS, int PPT>
@@ -206,7 +215,7 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     float4* s_a = reinterpret_cast<float4*>(smem_raw);
     float4* s_b = s_a + NT;
     float4* s_c = s_b + NT;
-    float4* s_d = s_c + NT;                                // blue, raw conic c0, c1, c2
+    float4* s_d = s_c + NT;                                // raw conic c0, c1, c2
     unsigned* s_vg = reinterpret_cast<unsigned*>(s_d + NT);
     float* s_acc = reinterpret_cast<float*>(s_vg + NT);  // [NT][kGradFields]
     __shared__ unsigned s_max;
@@ -244,9 +253,9 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     __syncthreads();
     const uint32_t maxlast = s_max;
     const unsigned lane = threadIdx.x & 31;
-    float gv[16];  // per-thread partial derivatives of the current entry (indices 9..15 stay 0)
+    float gv[kGradFields];  // per-thread partial derivatives of the current entry
 #pragma unroll
-    for (int q = 0; q < 16; ++q) gv[q] = 0.f;
+    for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
 
     for (int64_t bend = (int64_t)maxlast; bend > 0; bend -= NT) {
         const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
@@ -266,8 +275,7 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             if (__all_sync(0xffffffffu, pos >= mylast)) continue;
             const float4 A = s_a[j];
             const float4 Bv = s_b[j];
-            const float shift = s_c[j].x;
-            const float dx = entry_dx(A.x, shift, xs, halfW, fW);
+            const float dx = entry_dx(A.x, Bv.w, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;
             bool contrib = false;
 #pragma unroll
@@ -278,12 +286,12 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 const float4 Cc = s_c[j];
                 const float4 D = s_d[j];
                 const float G = fast_ex2(e);
-                const float raw = Cc.y * G;
+                const float raw = Cc.x * G;
                 const float alpha = fminf(kAlphaMax, raw);
                 contrib = true;
                 const float one_m = 1.f - alpha;
                 T[k] = __fdividef(T[k], one_m);  // transmittance in front of this entry
-                const float cr = Cc.z, cg = Cc.w, cb = D.x;
+                const float cr = Cc.y, cg = Cc.z, cb = Cc.w;
                 const float dalpha = T[k] * (g0[k] * (cr - B0[k]) + g1[k] * (cg - B1[k]) + g2[k] * (cb - B2[k]));
                 const float w = alpha * T[k];
                 gv[6] = fmaf(w, g0[k], gv[6]);
@@ -299,16 +307,17 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                     gv[2] = fmaf(-0.5f * dx, gdx, gv[2]);
                     gv[3] = fmaf(-dx, gdy, gv[3]);
                     gv[4] = fmaf(-0.5f * dy, gdy, gv[4]);
-                    gv[0] -= D.y * gdx + D.z * gdy;
-                    gv[1] -= D.w * gdy + D.z * gdx;
+                    gv[0] -= D.x * gdx + D.y * gdy;
+                    gv[1] -= D.z * gdy + D.y * gdx;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_transpose_sum16(gv, lane);
-                const unsigned f = lane >> 1;
-                if ((lane & 1u) == 0 && f < (unsigned)kGradFields) atomicAdd(&s_acc[j * kGradFields + f], tot);
+                float tot8;
+                const float tot = warp_sum_fields(gv, lane, tot8);
+                const bool quad = (lane & 3u) == 0;
+                if (quad || lane == 1u) atomicAdd(&s_acc[j * kGradFields + (quad ? (lane >> 2) : 8u)], quad ? tot : tot8);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) gv[q] = 0.f;
+                for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
             }
         }
         __syncthreads();
@@ -330,40 +339,43 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     }
 }
 
-constexpr int kPPT = 2;  // pixels per thread
-
 size_t bwd_smem(int nt) {
     return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
+// Pixels per blend thread: the configured schedule, else 2 for 8x8 tiles and 4 for larger ones.
+int blend_ppt(const omnigs_config& cfg) {
+    if (cfg.pixels_per_thread) return cfg.pixels_per_thread;
+    return cfg.tile == 8 ? 2 : 4;
+}
 
-template <int TS>
+template <int TS, int PPT>
 cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
                          const uint64_t* keys, const uint32_t* order, float* out_rgb, float* out_T, uint32_t* out_nc,
                          uint32_t* out_count, cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     ProfScope prof("render_fwd", stream);
-    render_fwd_kernel<TS, kPPT><<<tiles * cfg.num_views, PixelMap<TS, kPPT>::NT, 0, stream>>>(
+    render_fwd_kernel<TS, PPT><<<tiles * cfg.num_views, PixelMap<TS, PPT>::NT, 0, stream>>>(
         cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
         out_rgb, out_T, out_nc, out_count);
     return cudaGetLastError();
 }
 
-template <int TS>
+template <int TS, int PPT>
 cudaError_t render_bwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
                          const uint64_t* keys, const uint32_t* order, const float* out_T, const uint32_t* nc,
                          const float* dL_drgb, omnigs_splat_grad* grads, cudaStream_t stream) {
     const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
-    constexpr int NT = PixelMap<TS, kPPT>::NT;
+    constexpr int NT = PixelMap<TS, PPT>::NT;
     const size_t smem = bwd_smem(NT);
-    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, kPPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope prof("render_bwd", stream);
-    render_bwd_kernel<TS, kPPT><<<tiles * cfg.num_views, NT, smem, stream>>>(
+    render_bwd_kernel<TS, PPT><<<tiles * cfg.num_views, NT, smem, stream>>>(
         cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order, out_T,
         nc, dL_drgb, reinterpret_cast<float4*>(grads));
@@ -399,11 +411,20 @@ l1_kernel(size_t n4, const float4* __restrict__ rgb, const float4* __restrict__ 
     }
 }
 
-__global__ void l1_finish_kernel(const float* __restrict__ partials, int nb, float inv_total, float* __restrict__ loss) {
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += partials[i];
-        *loss = (float)(s * inv_total);
+// Sum of the per-block partials in double by one CTA of kLossBlocks threads (nb <= kLossBlocks).
+__global__ void __launch_bounds__(kLossBlocks)
+l1_finish_kernel(const float* __restrict__ partials, int nb, float inv_total, float* __restrict__ loss) {
+    __shared__ double red[kLossBlocks / 32];
+    double s = (int)threadIdx.x < nb ? (double)partials[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < kLossBlocks / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *loss = (float)(s * inv_total);
     }
 }
 
@@ -412,10 +433,15 @@ __global__ void l1_finish_kernel(const float* __restrict__ partials, int nb, flo
 cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
                               const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
                               float* out_T, uint32_t* out_nc, uint32_t* out_count, cudaStream_t stream) {
+    const bool four = blend_ppt(cfg) == 4;
     switch (cfg.tile) {
-        case 8: return render_fwd_t<8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-        case 32: return render_fwd_t<32>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-        default: return render_fwd_t<16>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        case 8: return render_fwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        case 32:
+            return four ? render_fwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
+                        : render_fwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        default:
+            return four ? render_fwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
+                        : render_fwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
     }
 }
 
@@ -425,10 +451,15 @@ cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_
                               omnigs_splat_grad* grads, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(omnigs_splat_grad) * (size_t)n * cfg.num_views, stream);
     if (e != cudaSuccess) return e;
+    const bool four = blend_ppt(cfg) == 4;
     switch (cfg.tile) {
-        case 8: return render_bwd_t<8>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
-        case 32: return render_bwd_t<32>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
-        default: return render_bwd_t<16>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+        case 8: return render_bwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+        case 32:
+            return four ? render_bwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
+                        : render_bwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+        default:
+            return four ? render_bwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
+                        : render_bwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
     }
 }
 
@@ -445,7 +476,7 @@ cudaError_t launch_l1(const omnigs_config& cfg, const float* rgb, const float* t
     }
     {
         ProfScope prof("l1_finish", stream);
-        l1_finish_kernel<<<1, 32, 0, stream>>>(partials, L.loss_blocks, inv, loss);
+        l1_finish_kernel<<<1, kLossBlocks, 0, stream>>>(partials, L.loss_blocks, inv, loss);
     }
     return cudaGetLastError();
 }

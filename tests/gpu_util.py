@@ -48,3 +48,32 @@ def assert_grad_close(got, ref, name, rel=1e-4):
     el = np.abs(got - ref).max() / scale if scale > 0 else np.abs(got).max()
     assert nw <= rel and el <= rel, f"{name}: normwise {nw:.3e}, elementwise/max {el:.3e}"
     return nw, el
+
+
+def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W: int, H: int, near: float = 0.2):
+    """FP32 preprocess output against the oracle's FP64 records of the same (view, Gaussian) rows.
+
+    Culling agrees except within 1e-6 (relative) of the near distance; p within 2e-6 W (H) px, the angle carrying a
+    few ulp (longitude differences taken across the seam); conic within 1e-4 of its norm; rgb within 1e-5; opacity
+    copied exactly; radius exact unless 3 sqrt(lambda_max) lies within 1e-4 of an integer. Returns a summary."""
+    import oracle
+    ref = oracle.splats_from_records(rec)
+    near_edge = np.abs(ref["depth"] - near) < 1e-6 * near
+    alive = ref["radius"] > 0
+    assert np.array_equal((got["radius"] > 0)[~near_edge], alive[~near_edge])
+    a = alive & (got["radius"] > 0)
+    np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6)
+    dpx = (got["px"][a] - ref["px"][a] + W / 2) % W - W / 2
+    dpy = got["py"][a] - ref["py"][a]
+    assert np.abs(dpx).max(initial=0) <= 2e-6 * W and np.abs(dpy).max(initial=0) <= 2e-6 * H
+    cg = np.stack([got["c0"], got["c1"], got["c2"]], 1)[a]
+    cr = np.stack([ref["c0"], ref["c1"], ref["c2"]], 1)[a]
+    cerr = (np.abs(cg - cr).max(1) / np.abs(cr).max(1)).max(initial=0)
+    assert cerr <= 1e-4
+    rgb_err = max(np.abs(got[k][a] - ref[k][a]).max(initial=0) for k in ("r", "g", "b"))
+    assert rgb_err <= 1e-5
+    assert np.array_equal(got["opacity"][a], opacity_expected[a])
+    margin_ok = rec[:, oracle.R_RMARGIN][a] > 1e-4 * np.maximum(1.0, ref["radius"][a])
+    assert np.array_equal(got["radius"][a][margin_ok], ref["radius"][a][margin_ok])
+    return dict(alive=int(a.sum()), dpx=float(np.abs(dpx).max(initial=0)), dpy=float(np.abs(dpy).max(initial=0)),
+                conic=float(cerr), rgb=float(rgb_err))

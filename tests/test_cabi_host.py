@@ -1,6 +1,7 @@
 """CPU checks of the C ABI library: it loads, exports every function include/omnigs.h declares, answers the calls
 that need no GPU, and the host-side sort plan covers every key bit (no CUDA call is made here)."""
 import ctypes
+import importlib.util
 import os
 import re
 
@@ -47,3 +48,25 @@ def test_host_only_calls(lib):
     assert lib.omnigs_preprocess(None, 10, *([None] * 8)) == 1
     lib.omnigs_last_error.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.omnigs_last_error(None, None) == 1
+
+
+def test_config_layout_and_schedule_validation(lib):
+    """omnigs_config is 40 bytes (the header's field order); invalid blend schedules are rejected on the host."""
+    spec = importlib.util.spec_from_file_location("omnigs_cabi_layout", os.path.join(ROOT, "paper_2404_03202_gb300",
+                                                                                      "_cabi.py"))
+    text = open(spec.origin).read()
+    fields = re.findall(r'\("(\w+)", ctypes\.c_(\w+)(?: \* 3)?\)', text.split("class omnigs_config")[1].split("class ")[0])
+    assert [f for f, _ in fields] == ["width", "height", "tile", "num_views", "sh_degree", "near_r", "bg",
+                                      "pixels_per_thread"]
+
+    class Cfg(ctypes.Structure):
+        _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32),
+                    ("num_views", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_r", ctypes.c_float),
+                    ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32)]
+
+    assert ctypes.sizeof(Cfg) == 40
+    lib.omnigs_workspace_size.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_int64]
+    lib.omnigs_workspace_size.restype = ctypes.c_size_t
+    for tile, ppt in [(8, 4), (16, 3), (16, 1), (32, 8)]:
+        c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), ppt)
+        assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (tile, ppt)

@@ -24,8 +24,8 @@ import paper_2404_03202_gb300 as og  # noqa: E402
 from paper_2404_03202_gb300 import _cabi as C  # noqa: E402
 
 
-def _settings(W, H, tile=16, V=1, deg=3, bg=(0.0, 0.0, 0.0)):
-    return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=deg, bg=bg)
+def _settings(W, H, tile=16, V=1, deg=3, bg=(0.0, 0.0, 0.0), ppt=0):
+    return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=deg, bg=bg, pixels_per_thread=ppt)
 
 
 def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):
@@ -128,20 +128,20 @@ def test_sort_many_ties_and_all_columns():
 
 # ------------------------------------------------------------------ S5 render forward
 
-def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0)):
-    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V, bg=bg))
+def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V, bg=bg, ppt=ppt))
     sp64 = {k: (np.asarray(v, np.float64) if k != "radius" else v) for k, v in sp.items()}
     ranges, lst = oracle.bin_sort(sp64, V, W, H, tile)
     rgb, T, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5)
     return r, (rgb, T, nc, near), (ranges, lst, sp64)
 
 
-@pytest.mark.parametrize("tile,V", [(16, 2), (8, 1), (32, 1)])
-def test_render_fwd_matches_oracle(tile, V):
+@pytest.mark.parametrize("tile,V,ppt", [(16, 2, 4), (16, 2, 2), (8, 1, 2), (32, 1, 4), (32, 1, 2)])
+def test_render_fwd_matches_oracle(tile, V, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2500, W, H, seed=200 + tile, max_radius=24)
     bg = (0.25, 0.5, 0.75)
-    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, tile, bg)
+    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, tile, bg, ppt)
     mask = (near & 1) == 0
     frac = 1.0 - mask.mean()
     got = r.rgb.cpu().numpy()
@@ -167,12 +167,13 @@ def test_render_fwd_opaque_stacks_stop_rule():
 
 # ------------------------------------------------------------------ S7 render backward
 
-@pytest.mark.parametrize("tile,V,opac", [(16, 2, (0.05, 0.99)), (8, 1, (0.5, 1.0)), (32, 1, (0.05, 0.99))])
-def test_render_bwd_matches_oracle(tile, V, opac):
+@pytest.mark.parametrize("tile,V,opac,ppt", [(16, 2, (0.05, 0.99), 4), (16, 2, (0.05, 0.99), 2), (8, 1, (0.5, 1.0), 2),
+                                             (32, 1, (0.05, 0.99), 4), (32, 1, (0.5, 1.0), 2)])
+def test_render_bwd_matches_oracle(tile, V, opac, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2000, W, H, seed=300 + tile, max_radius=24, opacity_range=opac)
     bg = (0.1, 0.2, 0.3)
-    r, (rgb, T, nc, near), (ranges, lst, sp64) = _fwd_compare(sp, V, W, H, tile, bg)
+    r, (rgb, T, nc, near), (ranges, lst, sp64) = _fwd_compare(sp, V, W, H, tile, bg, ppt)
     g = synth.random_image_grad(V, W, H, 7)
     g[np.repeat((near != 0)[:, None], 3, axis=1)] = 0.0  # pixels near a decision threshold carry no gradient
     ref = oracle.blend_bwd(sp64, ranges, lst, g.astype(np.float64), V, W, H, tile, bg)

@@ -113,6 +113,10 @@ def test_invalid_arguments_rejected():
     assert C.omnigs_workspace_size(cfg, 10, 100) == 0
     cfg = C.make_config(256, 128, sh_degree=4)
     assert C.omnigs_workspace_size(cfg, 10, 100) == 0
+    cfg = C.make_config(256, 128, tile=8, pixels_per_thread=4)  # 16 threads per 8x8 tile: not a whole warp
+    assert C.omnigs_workspace_size(cfg, 10, 100) == 0
+    cfg = C.make_config(256, 128, pixels_per_thread=3)
+    assert C.omnigs_workspace_size(cfg, 10, 100) == 0
 
 
 def test_graph_capture_matches_eager():
