@@ -232,6 +232,48 @@ def run_reference(args, wl):
     return 0
 
 
+SERVING_SCENES = [100_000, 300_000, 600_000, 1_000_000, 2_000_000, 3_000_000]
+SERVING_RES = [((1024, 512), 0.3), ((2048, 1024), 0.5), ((4096, 2048), 0.2)]
+
+
+def serving_requests(names, count, rate, seed, t0=0.0):
+    """Poisson arrivals at `rate` per second (all at t0 when rate is None); scene uniform, resolution 0.3/0.5/0.2,
+    pose uniform within 1 m of the room centre with random yaw."""
+    from paper_2404_03202_gb300.serving import Request
+    rng = np.random.default_rng(seed)
+    poses = synth.room_viewmats(count, seed)
+    t = np.full(count, t0) if rate is None else t0 + np.cumsum(rng.exponential(1.0 / rate, count))
+    out = []
+    for i in range(count):
+        (w, h), _ = SERVING_RES[rng.choice(len(SERVING_RES), p=[p for _, p in SERVING_RES])]
+        out.append(Request(i, names[rng.integers(len(names))], poses[i], w, h, float(t[i])))
+    return out
+
+
+def serving_benchmark(dev, count: int = 96, lanes: int = 4, max_batch: int = 8) -> dict:
+    """Forward-only serving of the six resident room scenes: one request at a time (closed loop, no batching, one
+    lane) gives the capacity; Poisson traces at 0.5x, 0.9x and 1.2x of it then run with continuous batching."""
+    from paper_2404_03202_gb300 import serving
+    scenes = {f"room{n // 1000}k": synth.room_scene(n, 40 + i).arrays() for i, n in enumerate(SERVING_SCENES)}
+    names = sorted(scenes)
+    ex = serving.GpuExecutor(scenes, lanes=lanes, device=dev)
+    for nm in names:  # probes (capacity per scene and resolution) and allocator warm-up, outside the timings
+        for (w, h), _ in SERVING_RES:
+            ex.bytes_needed(nm, w, h, 1)
+    warm = serving.Scheduler(ex, lanes=lanes, max_batch=max_batch)
+    serving.run_trace(warm, serving_requests(names, 16, None, 1))
+    seq = serving.run_trace(serving.Scheduler(ex, lanes=1, max_batch=1), serving_requests(names, count // 2, None, 2))
+    out = {"scenes": SERVING_SCENES, "resolutions": [f"{w}x{h} p={p}" for (w, h), p in SERVING_RES],
+           "lanes": lanes, "max_batch": max_batch, "one_at_a_time": seq, "poisson": []}
+    cap = seq["views_per_s"]
+    for k, f in enumerate((0.5, 0.9, 1.2)):
+        res = serving.run_trace(serving.Scheduler(ex, lanes=lanes, max_batch=max_batch),
+                                serving_requests(names, count, f * cap, 10 + k))
+        out["poisson"].append({"rate_vs_capacity": f, "offered_per_s": f * cap} | res)
+    out["overflow_reruns"] = ex.overflows
+    return out
+
+
 def workload_config(wl, args):
     return {"workload": f"{args.workload}: {wl['n']} Gaussians, {wl['views']} views of {wl['width']}x{wl['height']} "
                         f"equirect, {wl['tile']}x{wl['tile']} tiles, fwd+bwd with L1 loss",
@@ -250,6 +292,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -448,6 +491,16 @@ def main():
             stages[name] = {"ms": ms_step}
 
     # ---------------------------------------------------------------- CPU baseline (oracle), rank 0, N = 1
+    # ---------------------------------------------------------------- serving loop (forward only), rank 0, N = 1
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        del r
+        torch.cuda.empty_cache()
+        try:
+            serve = serving_benchmark(dev)
+        except Exception as e:  # reported, never hidden
+            serve = {"failed": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -467,7 +520,7 @@ def main():
                                                       "examined_pairs_per_step": examined,
                                                       "contributing_pairs_per_step": contrib},
                "gpu_launches": kernel_launches * args.steps, "stages": stages,
-               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "serving": serve}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
