@@ -22,9 +22,9 @@ _SRC = os.path.join(_HERE, "omnigs_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-R_LEN = 16
+R_LEN = 18
 (R_PX, R_PY, R_DEPTH, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE, R_RADIUS, R_COV00, R_COV01, R_COV11,
- R_RMARGIN, R_FLAGS) = range(R_LEN)
+ R_RMARGIN, R_FLAGS, R_RX, R_RY) = range(R_LEN)
 SPLAT_COLS = [R_PX, R_PY, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE]
 G_LEN = 9
 
@@ -50,10 +50,10 @@ def _load():
         lib.orc_sh_basis.argtypes = [i32, P, P, P]
         lib.orc_quat_to_rot.argtypes = [P, P]
         lib.orc_preprocess.argtypes = [i64, i32, i32, i32, i32, f64, P, P, P, P, P, P, P]
-        lib.orc_rect.argtypes = [f64, f64, i32, i32, i32, i32, P]
-        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P]
+        lib.orc_rect.argtypes = [f64, f64, i32, i32, i32, i32, i32, P]
+        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P, P]
         lib.orc_count_instances.restype = i64
-        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P]
+        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P]
         lib.orc_bin_sort.restype = i64
         lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
@@ -112,11 +112,11 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
-def rect(px: float, py: float, radius: int, width: int, height: int, tile: int):
-    """Tile rectangle (x0, nx, y0, ny) of one splat."""
+def rect(px: float, py: float, rx: int, ry: int, width: int, height: int, tile: int):
+    """Tile rectangle (x0, nx, y0, ny) of the instance box (half-extents rx, ry) of one splat."""
     lib = _load()
     out = np.zeros(4, dtype=np.int64)
-    lib.orc_rect(float(px), float(py), int(radius), width, height, tile, _p(out))
+    lib.orc_rect(float(px), float(py), int(rx), int(ry), width, height, tile, _p(out))
     return tuple(int(x) for x in out)
 
 
@@ -135,17 +135,18 @@ def preprocess(scene, viewmats, width: int, height: int, near: float = 0.2) -> n
 
 
 def splats_from_records(rec: np.ndarray) -> dict:
-    """Screen-space splat fields from preprocess records (double precision)."""
+    """Screen-space splat fields from preprocess records (double precision; rx, ry and the square's radius int32)."""
     return dict(px=rec[:, R_PX], py=rec[:, R_PY], c0=rec[:, R_C0], c1=rec[:, R_C1], c2=rec[:, R_C2],
                 opacity=rec[:, R_OPAC], r=rec[:, R_RED], g=rec[:, R_GREEN], b=rec[:, R_BLUE],
-                depth=rec[:, R_DEPTH], radius=rec[:, R_RADIUS].astype(np.int32))
+                depth=rec[:, R_DEPTH], rx=rec[:, R_RX].astype(np.int32), ry=rec[:, R_RY].astype(np.int32),
+                radius=rec[:, R_RADIUS].astype(np.int32))
 
 
 def count_instances(splats: dict, V: int, width: int, height: int, tile: int) -> int:
     lib = _load()
     px, py = _f64(splats["px"]), _f64(splats["py"])
-    rad = np.ascontiguousarray(splats["radius"], dtype=np.int32)
-    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rad)))
+    rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
+    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry)))
 
 
 def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None):
@@ -153,15 +154,15 @@ def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask
     With `tile_mask` ([V*tiles] bool), only the lists of the masked tiles are built."""
     lib = _load()
     px, py, depth = _f64(splats["px"]), _f64(splats["py"]), _f64(splats["depth"])
-    rad = np.ascontiguousarray(splats["radius"], dtype=np.int32)
+    rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
     n = px.shape[0] // V
     tiles = (width // tile) * (height // tile)
     mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
     ranges = np.zeros((V * tiles, 2), dtype=np.int64)
-    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rad), _p(depth), _p(ranges), None,
-                                 None if mask is None else _p(mask)))
+    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges),
+                                 None, None if mask is None else _p(mask)))
     lst = np.zeros(max(total, 1), dtype=np.int64)
-    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rad), _p(depth), _p(ranges), _p(lst),
+    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges), _p(lst),
                      None if mask is None else _p(mask))
     return ranges, lst[:total]
 
@@ -187,6 +188,10 @@ def blend_fwd(splats: dict, ranges, lst, V: int, width: int, height: int, tile: 
                       _p(nc), _p(near), _p(count))
     blend_fwd.last_count = count
     return rgb, T, nc, near
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
 
 
 def _i64(a):

@@ -22,6 +22,12 @@
  *   - Eq. 10 prints dp_y/dt_y twice in its second row; the third entry is dp_y/dt_z (Eq. 16).
  *   - near cull t_r <= near_r; low-pass dilation Sigma~ += 0.3 I; cull if det(Sigma~) <= 0.
  *   - radius of influence r = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det)).
+ *   - instances come from the box of half-extents (rx, ry) around pixel floor(p): the square of half-side r,
+ *     narrowed per axis to the box of the region where alpha >= 1/255: with q = 2 ln(255 o), that region is the
+ *     ellipse dp^T Sigma~^-1 dp <= q, whose half-extents are sqrt(q Sigma~_00) and sqrt(q Sigma~_11);
+ *     rx = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4) + 1e-3)), ry likewise (the small widening absorbs FP32
+ *     rounding on the GPU). A Gaussian with 255 o < 1 has no instance. Outside that box alpha < 1/255 at every
+ *     pixel, so the narrowing leaves every image unchanged; it only drops instances that contribute nothing.
  *   - quaternion stored (w, x, y, z), normalised before use; Sigma = R diag(s)^2 R^T.
  *   - colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m and Y_k the real
  *     orthonormal spherical harmonics up to degree 3 (no Condon-Shortley phase).
@@ -44,10 +50,11 @@
 #define ORC_T_STOP 1e-4
 #define ORC_POLE_GUARD 1e-6
 
-/* per-(view, Gaussian) record written by orc_preprocess */
+/* per-(view, Gaussian) record written by orc_preprocess. R_RADIUS is the square's r; R_RX, R_RY the half-extents
+ * of the box the instances come from; R_RMARGIN the smallest distance of the three ceil() arguments to an integer. */
 enum {
     R_PX = 0, R_PY, R_DEPTH, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE, R_RADIUS,
-    R_COV00, R_COV01, R_COV11, R_RMARGIN, R_FLAGS, R_LEN
+    R_COV00, R_COV01, R_COV11, R_RMARGIN, R_FLAGS, R_RX, R_RY, R_LEN
 };
 /* per-(view, Gaussian) screen-space gradient, written by orc_blend_bwd and read by orc_preprocess_bwd */
 enum { G_PX = 0, G_PY, G_C0, G_C1, G_C2, G_OPAC, G_RED, G_GREEN, G_BLUE, G_LEN };
@@ -213,7 +220,7 @@ static void covariance3d(const double *q, const double *s, double *Sig, double *
 /* ------------------------------------------------------------------ per-(view, Gaussian) forward quantities */
 typedef struct {
     int culled;
-    double t[3], tr, p[2], J[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rmargin;
+    double t[3], tr, p[2], J[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rx, ry, rmargin;
     double dir[3], dist, Y[16], rgb_raw[3], rgb[3];
 } orc_fwd;
 
@@ -227,8 +234,10 @@ static void load_view(const float *viewmat, double *Wr, double *tcw, double *cam
     for (int j = 0; j < 3; j++) campos[j] = -(Wr[0 * 3 + j] * tcw[0] + Wr[1 * 3 + j] * tcw[1] + Wr[2 * 3 + j] * tcw[2]);
 }
 
+static double int_gap(double z) { return fabs(z - floor(z + 0.5)); }
+
 static void forward_one(int W, int H, int sh_degree, double near_r, const float *m_f, const float *s_f,
-                        const float *q_f, const float *sh_f, const double *Wr, const double *tcw,
+                        const float *q_f, const float *sh_f, double opacity, const double *Wr, const double *tcw,
                         const double *campos, orc_fwd *f)
 {
     int K = (sh_degree + 1) * (sh_degree + 1);
@@ -270,7 +279,14 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
     double lam = mid + sqrt(disc > 0.1 ? disc : 0.1);
     double rr = 3.0 * sqrt(lam);
     f->radius = ceil(rr);
-    f->rmargin = fabs(rr - floor(rr + 0.5));
+    /* the box of the alpha >= 1/255 ellipse, widened slightly; no instance at all when 255 o < 1 */
+    double qa = 2.0 * log(255.0 * opacity);
+    if (255.0 * opacity < 1.0) { f->culled = 1; return; }
+    if (qa < 0.0) qa = 0.0;
+    double hx = sqrt(qa * f->cov[0]) * (1.0 + 1e-4) + 1e-3, hy = sqrt(qa * f->cov[2]) * (1.0 + 1e-4) + 1e-3;
+    f->rx = ceil(hx) < f->radius ? ceil(hx) : f->radius;
+    f->ry = ceil(hy) < f->radius ? ceil(hy) : f->radius;
+    f->rmargin = fmin(int_gap(rr), fmin(int_gap(hx), int_gap(hy)));
     /* Sec. 3.1: colour from m and the SH coefficients */
     double v[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
     f->dist = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -296,7 +312,7 @@ void orc_preprocess(int64_t n, int V, int W, int H, int sh_degree, double near_r
         for (int64_t g = 0; g < n; g++) {
             orc_fwd f;
             forward_one(W, H, sh_degree, near_r, means + 3 * g, scales + 3 * g, quats + 4 * g, sh + 3 * K * g,
-                        Wr, tcw, campos, &f);
+                        opacity[g], Wr, tcw, campos, &f);
             double *o = rec + (int64_t)R_LEN * (v * n + g);
             memset(o, 0, sizeof(double) * R_LEN);
             o[R_DEPTH] = f.tr;
@@ -308,6 +324,7 @@ void orc_preprocess(int64_t n, int V, int W, int H, int sh_degree, double near_r
             o[R_RADIUS] = f.radius;
             o[R_COV00] = f.cov[0]; o[R_COV01] = f.cov[1]; o[R_COV11] = f.cov[2];
             o[R_RMARGIN] = f.rmargin;
+            o[R_RX] = f.rx; o[R_RY] = f.ry;
         }
     }
 }
@@ -320,16 +337,16 @@ static int64_t floordiv(int64_t a, int64_t b)
     return q;
 }
 
-/* Tile rectangle covered by the square of half-side `radius` around pixel floor(p). Columns start at x0 and run
+/* Tile rectangle covered by the box of half-extents (rx, ry) around pixel floor(p). Columns start at x0 and run
  * nx columns modulo the tile-column count (the longitude seam); rows y0..y0+ny-1 are clamped to the image. */
-void orc_rect(double px, double py, int radius, int W, int H, int T, int64_t *out /* x0, nx, y0, ny */)
+void orc_rect(double px, double py, int rx, int ry, int W, int H, int T, int64_t *out /* x0, nx, y0, ny */)
 {
     int64_t TX = W / T, TY = H / T;
     int64_t ix = (int64_t)floor(px), iy = (int64_t)floor(py);
-    int64_t x0 = floordiv(ix - radius, T), x1 = floordiv(ix + radius, T);
+    int64_t x0 = floordiv(ix - rx, T), x1 = floordiv(ix + rx, T);
     int64_t nx = x1 - x0 + 1;
     if (nx >= TX) { x0 = 0; nx = TX; }
-    int64_t y0 = floordiv(iy - radius, T), y1 = floordiv(iy + radius, T);
+    int64_t y0 = floordiv(iy - ry, T), y1 = floordiv(iy + ry, T);
     if (y0 < 0) y0 = 0;
     if (y1 > TY - 1) y1 = TY - 1;
     out[0] = x0; out[1] = nx; out[2] = y0; out[3] = y1 - y0 + 1;
@@ -348,13 +365,13 @@ static int inst_cmp(const void *a, const void *b)
 }
 
 int64_t orc_count_instances(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                            const int32_t *radius)
+                            const int32_t *rx, const int32_t *ry)
 {
     int64_t total = 0;
     for (int64_t i = 0; i < (int64_t)V * n; i++) {
-        if (radius[i] <= 0) continue;
+        if (rx[i] <= 0) continue;
         int64_t r[4];
-        orc_rect(px[i], py[i], radius[i], W, H, T, r);
+        orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
         total += r[1] * r[3];
     }
     return total;
@@ -366,19 +383,19 @@ int64_t orc_count_instances(int V, int64_t n, int W, int H, int T, const double 
  * (the lists of those tiles are the same as without a mask). Returns the number of listed instances; with
  * list_vg == NULL it only counts them. */
 int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                     const int32_t *radius, const double *depth, int64_t *ranges, int64_t *list_vg,
+                     const int32_t *rx, const int32_t *ry, const double *depth, int64_t *ranges, int64_t *list_vg,
                      const uint8_t *tile_mask)
 {
     int64_t TX = W / T, TY = H / T, tiles = TX * TY;
     int64_t total = 0;
     if (!tile_mask) {
-        total = orc_count_instances(V, n, W, H, T, px, py, radius);
+        total = orc_count_instances(V, n, W, H, T, px, py, rx, ry);
     } else {
         for (int v = 0; v < V; v++)
             for (int64_t g = 0; g < n; g++) {
                 int64_t i = v * n + g, r[4];
-                if (radius[i] <= 0) continue;
-                orc_rect(px[i], py[i], radius[i], W, H, T, r);
+                if (rx[i] <= 0) continue;
+                orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
                 for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
                     for (int64_t c = 0; c < r[1]; c++)
                         total += tile_mask[v * tiles + ty * TX + ((r[0] + c) % TX + TX) % TX] != 0;
@@ -390,9 +407,9 @@ int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, co
     for (int v = 0; v < V; v++)
         for (int64_t g = 0; g < n; g++) {
             int64_t i = v * n + g;
-            if (radius[i] <= 0) continue;
+            if (rx[i] <= 0) continue;
             int64_t r[4];
-            orc_rect(px[i], py[i], radius[i], W, H, T, r);
+            orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
             for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
                 for (int64_t c = 0; c < r[1]; c++) {
                     int64_t tx = ((r[0] + c) % TX + TX) % TX;
@@ -571,7 +588,7 @@ void orc_preprocess_bwd(int64_t n, int V, int W, int H, int sh_degree, double ne
             const double *gr = grad2d + (int64_t)G_LEN * (v * n + g);
             orc_fwd f;
             forward_one(W, H, sh_degree, near_r, means + 3 * g, scales + 3 * g, quats + 4 * g, sh + 3 * K * g,
-                        Wr, tcw, campos, &f);
+                        opacity[g], Wr, tcw, campos, &f);
             if (f.culled) continue;
             double dt[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
             /* opacity */

@@ -177,19 +177,21 @@ def random_viewmats(v: int, seed: int, max_offset: float = 0.3) -> np.ndarray:
 
 # ---------------------------------------------------------------- projected splats for stage-level tests
 
-SPLAT_FIELDS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth", "radius")
+SPLAT_FIELDS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth", "rx", "ry")
 
 
 def random_splats(v: int, n: int, width: int, height: int, seed: int, *, max_radius: int = 40,
                   opacity_range=(0.05, 0.99), depth_ties: float = 0.1, cull_frac: float = 0.05,
-                  seam_frac: float = 0.1, pole_frac: float = 0.05, wide_frac: float = 0.02) -> dict:
+                  seam_frac: float = 0.1, pole_frac: float = 0.05, wide_frac: float = 0.02,
+                  aniso_frac: float = 0.4) -> dict:
     """Per-(view, Gaussian) screen-space records drawn directly (not projected from 3D).
 
-    Each record is a centre (px, py) in [0, W) x [0, H), an SPD inverse covariance (c0, c1, c2) whose 3-sigma
-    ellipse fits inside the square of half-side `radius`, an opacity, an RGB colour and a depth. A fraction of the
-    records is placed on the longitude seam, near the poles, made wider than the image, or culled (radius 0), and
-    a fraction shares its depth with another record so that ties occur. Arrays are float32 (radius int32),
-    flattened over (view, Gaussian).
+    Each record is a centre (px, py) in [0, W) x [0, H), an instance box of half-extents (rx, ry), an SPD inverse
+    covariance (c0, c1, c2) whose 3-sigma ellipse fits inside that box (standard deviations along x and y at most
+    rx / 3 and ry / 3, any correlation), an opacity, an RGB colour and a depth. A fraction of the boxes is
+    anisotropic (ry drawn below rx or the other way round), and a fraction of the records is placed on the longitude
+    seam, near the poles, made wider than the image, or culled (rx = ry = 0); a fraction shares its depth with
+    another record so that ties occur. Arrays are float32 (rx, ry int32), flattened over (view, Gaussian).
     """
     rng = np.random.default_rng(seed)
     m = v * n
@@ -201,32 +203,36 @@ def random_splats(v: int, n: int, width: int, height: int, seed: int, *, max_rad
     pole = rng.uniform(size=m) < pole_frac
     py[pole] = np.where(rng.uniform(size=pole.sum()) < 0.5, rng.uniform(0, 2, size=pole.sum()),
                         height - rng.uniform(1e-3, 2, size=pole.sum()))
-    radius = rng.integers(1, max_radius + 1, size=m)
+    rx = rng.integers(1, max_radius + 1, size=m)
+    ry = rx.copy()
+    aniso = rng.uniform(size=m) < aniso_frac
+    short = rng.integers(1, max_radius + 1, size=m)
+    flip = rng.uniform(size=m) < 0.5
+    ry[aniso & ~flip] = np.minimum(rx, short)[aniso & ~flip]
+    rx[aniso & flip] = np.minimum(ry, short)[aniso & flip]
     wide = rng.uniform(size=m) < wide_frac
-    radius[wide] = rng.integers(width // 2, width + 8, size=wide.sum())
-    # principal standard deviations no larger than radius / 3, so the ellipse at 3 sigma lies inside the square
-    smax = radius / 3.0
-    s1 = smax * rng.uniform(0.3, 1.0, size=m)
-    s2 = smax * rng.uniform(0.1, 1.0, size=m)
-    s1 = np.maximum(s1, 0.3)
-    s2 = np.maximum(s2, 0.3)
-    th = rng.uniform(0, np.pi, size=m)
-    c, s = np.cos(th), np.sin(th)
-    i1, i2 = 1.0 / s1 ** 2, 1.0 / s2 ** 2
-    c0 = c * c * i1 + s * s * i2
-    c1 = c * s * (i1 - i2)
-    c2 = s * s * i1 + c * c * i2
+    rx[wide] = rng.integers(width // 2, width + 8, size=wide.sum())
+    # standard deviations along x and y no larger than a third of the half-extents (at least 0.3 px)
+    sx = np.maximum(rx / 3.0 * rng.uniform(0.3, 1.0, size=m), 0.3)
+    sy = np.maximum(ry / 3.0 * rng.uniform(0.3, 1.0, size=m), 0.3)
+    sx = np.minimum(sx, rx / 3.0)
+    sy = np.minimum(sy, ry / 3.0)
+    rho = rng.uniform(-0.9, 0.9, size=m)
+    s00, s11, s01 = sx * sx, sy * sy, rho * sx * sy
+    det = s00 * s11 - s01 * s01
+    c0, c1, c2 = s11 / det, -s01 / det, s00 / det
     opacity = rng.uniform(*opacity_range, size=m)
     rgb = rng.uniform(0.0, 1.0, size=(m, 3))
     depth = rng.uniform(0.2, 20.0, size=m)
     tie = rng.uniform(size=m) < depth_ties
     depth[tie] = depth[rng.integers(0, m, size=tie.sum())]
     cull = rng.uniform(size=m) < cull_frac
-    radius[cull] = 0
+    rx[cull] = 0
+    ry[cull] = 0
     f32 = np.float32
     return dict(px=px.astype(f32), py=py.astype(f32), c0=c0.astype(f32), c1=c1.astype(f32), c2=c2.astype(f32),
                 opacity=opacity.astype(f32), r=rgb[:, 0].astype(f32), g=rgb[:, 1].astype(f32),
-                b=rgb[:, 2].astype(f32), depth=depth.astype(f32), radius=radius.astype(np.int32))
+                b=rgb[:, 2].astype(f32), depth=depth.astype(f32), rx=rx.astype(np.int32), ry=ry.astype(np.int32))
 
 
 def random_image_grad(v: int, width: int, height: int, seed: int) -> np.ndarray:

@@ -82,6 +82,10 @@ def test_jacobian_matches_finite_differences(oracle_lib):
 
 # ------------------------------------------------------------------ covariance (Eq. 9) closed forms
 
+def _to64(sp):
+    return {k: (np.asarray(v, np.float64) if np.asarray(v).dtype.kind == "f" else v) for k, v in sp.items()}
+
+
 def _one_gaussian(mean, scale, quat, sh_dc=(0.5, 0.5, 0.5), opacity=0.5, degree=0):
     K = (degree + 1) ** 2
     sh = np.zeros((1, K, 3), np.float32)
@@ -150,6 +154,11 @@ def test_aligned_covariance_and_quaternion_order(oracle_lib):
                                    rtol=1e-6)
         lam = np.linalg.eigvalsh(cov).max()
         assert rec[oracle.R_RADIUS] == np.ceil(3 * np.sqrt(lam))
+        # instance box: the square narrowed to the box of the alpha >= 1/255 ellipse (opacity 0.5: q = 2 ln 127.5)
+        q = 2 * np.log(255 * float(sc.opacity[0]))
+        for key, var in ((oracle.R_RX, cov[0, 0]), (oracle.R_RY, cov[1, 1])):
+            expect = min(rec[oracle.R_RADIUS], np.ceil(np.sqrt(q * var) * (1 + 1e-4) + 1e-3))
+            assert rec[key] == expect
 
 
 def test_quaternion_matches_scipy(oracle_lib):
@@ -230,19 +239,19 @@ def test_near_cull(oracle_lib):
 # ------------------------------------------------------------------ binning and sort (Sec. 3.3)
 
 def _brute_force_lists(sp, V, W, H, T):
-    """For every tile, the Gaussians whose pixel square (half-side r around floor(p), columns taken modulo W,
+    """For every tile, the Gaussians whose pixel box (half-extents rx, ry around floor(p), columns taken modulo W,
     rows clipped to the image) touches one of its pixels, ordered by (t_r, index)."""
     TX, TY = W // T, H // T
     lists = [[] for _ in range(V * TX * TY)]
     n = len(sp["px"]) // V
     for i in range(V * n):
-        r = int(sp["radius"][i])
-        if r <= 0:
+        rx, ry = int(sp["rx"][i]), int(sp["ry"][i])
+        if rx <= 0:
             continue
         v = i // n
         ix, iy = int(np.floor(sp["px"][i])), int(np.floor(sp["py"][i]))
-        cols = {((c % W) // T) for c in range(ix - r, ix + r + 1)}
-        rows = {y // T for y in range(iy - r, iy + r + 1) if 0 <= y < H}
+        cols = {((c % W) // T) for c in range(ix - rx, ix + rx + 1)}
+        rows = {y // T for y in range(iy - ry, iy + ry + 1) if 0 <= y < H}
         for ty in rows:
             for tx in cols:
                 lists[v * TX * TY + ty * TX + tx].append(i)
@@ -267,13 +276,16 @@ def test_bin_sort_matches_bruteforce(oracle_lib):
 def test_rect_cases(oracle_lib):
     W, H, T = 128, 64, 16
     # plain: p = (40.5, 30.2), r = 5 -> pixels 35..45 -> tile columns 2; rows 25..35 -> tile rows 1..2
-    assert oracle.rect(40.5, 30.2, 5, W, H, T) == (2, 1, 1, 2)
+    assert oracle.rect(40.5, 30.2, 5, 5, W, H, T) == (2, 1, 1, 2)
     # across the seam: p_x = 1.2, r = 4 -> pixel columns -3..5 -> tile columns -1..0, i.e. 7 then 0
-    assert oracle.rect(1.2, 30.0, 4, W, H, T) == (-1, 2, 1, 2)
+    assert oracle.rect(1.2, 30.0, 4, 4, W, H, T) == (-1, 2, 1, 2)
     # wider than the image: every column exactly once, starting at 0
-    assert oracle.rect(60.0, 30.0, 70, W, H, T) == (0, 8, 0, 4)
+    assert oracle.rect(60.0, 30.0, 70, 70, W, H, T) == (0, 8, 0, 4)
     # pole rows clipped: pixel rows -20..20 -> tile rows 0..1; columns 40..80 -> tiles 2..5
-    assert oracle.rect(60.0, 0.3, 20, W, H, T) == (2, 4, 0, 2)
+    assert oracle.rect(60.0, 0.3, 20, 20, W, H, T) == (2, 4, 0, 2)
+    # anisotropic box: columns from rx = 20 (40..80 -> tiles 2..5), rows from ry = 2 (28..32 -> tiles 1..2)
+    assert oracle.rect(60.0, 30.0, 20, 2, W, H, T) == (2, 4, 1, 2)
+    assert oracle.rect(60.0, 30.0, 2, 20, W, H, T) == (3, 1, 0, 4)
 
 
 # ------------------------------------------------------------------ blending (Eqs. 6-8)
@@ -284,7 +296,7 @@ def _brute_force_blend(sp, V, W, H, bg):
     out = np.zeros((V, 3, H, W))
     Tout = np.zeros((V, H, W))
     for v in range(V):
-        idx = [v * n + g for g in range(n) if sp["radius"][v * n + g] > 0]
+        idx = [v * n + g for g in range(n) if sp["rx"][v * n + g] > 0]
         idx.sort(key=lambda i: (float(sp["depth"][i]), i))
         for y in range(H):
             for x in range(W):
@@ -332,8 +344,8 @@ def test_blend_matches_bruteforce_projected_scene(oracle_lib):
 def test_blend_matches_bruteforce_random_splats(oracle_lib):
     V, W, H, T = 1, 64, 32, 8
     sp = synth.random_splats(V, 80, W, H, seed=5, max_radius=12, opacity_range=(0.05, 0.35), wide_frac=0.05)
-    sp64 = {k: np.asarray(v, np.float64) if k != "radius" else v for k, v in sp.items()}
-    # random_splats bounds the 3-sigma ellipse by the radius; add the half-pixel the square test needs
+    sp64 = _to64(sp)
+    # random_splats keeps the 3-sigma ellipse inside the instance box, and alpha < 1/255 beyond 3 sigma here
     ranges, lst = oracle.bin_sort(sp64, V, W, H, T)
     rgb, Tf, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, T)
     ref, Tref = _brute_force_blend(sp64, V, W, H, (0, 0, 0))
@@ -341,12 +353,61 @@ def test_blend_matches_bruteforce_random_splats(oracle_lib):
     np.testing.assert_allclose(Tf, Tref, atol=1e-12)
 
 
+def test_instance_box_holds_every_visible_pixel(oracle_lib):
+    """Every pixel of the 3-sigma square where alpha >= 1/255 (FP64, brute force over the square) lies in the
+    narrowed box (rx, ry), and the box is no more than one pixel wider than that region needs (Sec. 3.3 tiles)."""
+    W, H = 256, 128
+    sc = synth.shell_scene(400, seed=31, log_scale_mean=-2.5)
+    sc.opacity[:] = np.random.default_rng(3).uniform(0.004, 1.0, sc.n).astype(np.float32)  # high opacities too
+    rec = oracle.preprocess(sc, synth.random_viewmats(1, 6), W, H)
+    sp = oracle.splats_from_records(rec)
+    narrower = 0
+    for i in np.nonzero(sp["rx"] > 0)[0]:
+        r = int(sp["radius"][i])
+        ix, iy = int(np.floor(sp["px"][i])), int(np.floor(sp["py"][i]))
+        xs = np.arange(ix - r, ix + r + 1) + 0.5
+        ys = np.arange(iy - r, iy + r + 1) + 0.5
+        dx, dy = sp["px"][i] - xs[None, :], sp["py"][i] - ys[:, None]
+        power = -0.5 * (sp["c0"][i] * dx * dx + sp["c2"][i] * dy * dy) - sp["c1"][i] * dx * dy
+        vis = sp["opacity"][i] * np.exp(power) >= 1.0 / 255.0
+        yy, xx = np.nonzero(vis)
+        if len(xx):
+            assert np.abs(xx - r).max() <= sp["rx"][i] and np.abs(yy - r).max() <= sp["ry"][i], i
+        narrower += int(sp["rx"][i] < r or sp["ry"][i] < r)
+    assert narrower > 100  # the narrowing is not vacuous
+
+
+def test_instance_box_leaves_images_unchanged(oracle_lib):
+    """Lists from the narrowed box and from the full 3-sigma square blend to identical images: every dropped
+    instance has alpha < 1/255 at every pixel of its tile."""
+    W, H, T = 256, 128, 16
+    sc = synth.shell_scene(1500, seed=32, log_scale_mean=-2.5)
+    sc.opacity[:] = np.random.default_rng(4).uniform(0.004, 1.0, sc.n).astype(np.float32)
+    vm = synth.random_viewmats(2, 7)
+    f = oracle.render(sc, vm, W, H, T)
+    square = dict(f["splats"], rx=f["splats"]["radius"], ry=f["splats"]["radius"])
+    ranges, lst = oracle.bin_sort(square, 2, W, H, T)
+    assert len(lst) > 1.3 * len(f["list"])  # the square lists are substantially longer
+    rgb, Tf, nc, _ = oracle.blend_fwd(square, ranges, lst, 2, W, H, T)
+    count_square = oracle.blend_fwd.last_count
+    oracle.blend_fwd(f["splats"], f["ranges"], f["list"], 2, W, H, T)
+    assert np.array_equal(rgb, f["rgb"]) and np.array_equal(Tf, f["T"])
+    assert np.array_equal(count_square, oracle.blend_fwd.last_count)
+
+
+def test_opacity_below_one_255th_has_no_instance(oracle_lib):
+    for o, culled in [(0.0035, True), (0.0040, False)]:
+        sc = _one_gaussian([0, 0, 3.0], [0.05] * 3, [1, 0, 0, 0], opacity=o)
+        rec = oracle.preprocess(sc, synth.identity_viewmats(1), 256, 128)[0]
+        assert (rec[oracle.R_RX] == 0) == culled and (rec[oracle.R_FLAGS] == 1) == culled
+
+
 def _stack(n_layers, opacity, W=32, H=16, x=5, y=7):
     """`n_layers` identical splats centred exactly on pixel (x, y), at increasing depth."""
     m = n_layers
     return dict(px=np.full(m, x + 0.5), py=np.full(m, y + 0.5), c0=np.full(m, 0.5), c1=np.zeros(m), c2=np.full(m, 0.5),
                 opacity=np.full(m, opacity), r=np.linspace(0.1, 0.9, m), g=np.full(m, 0.5), b=np.full(m, 1.0),
-                depth=np.arange(1, m + 1, dtype=np.float64), radius=np.full(m, 3, np.int32))
+                depth=np.arange(1, m + 1, dtype=np.float64), rx=np.full(m, 3, np.int32), ry=np.full(m, 3, np.int32))
 
 
 def test_termination_closed_form(oracle_lib):
@@ -391,7 +452,7 @@ def test_yaw_equals_cyclic_column_shift(oracle_lib):
 # ------------------------------------------------------------------ gradients (Eqs. 18-20)
 
 def _decisions(f):
-    return (f["n_contrib"].copy(), f["rec"][:, oracle.R_RADIUS].copy(), f["list"].copy())
+    return (f["n_contrib"].copy(), f["rec"][:, [oracle.R_RADIUS, oracle.R_RX, oracle.R_RY]].copy(), f["list"].copy())
 
 
 def _same(a, b):
@@ -406,7 +467,7 @@ def _clamping_splats(n, W, H, seed):
                 py=rng.integers(0, H, n) + 0.5 + rng.uniform(-0.05, 0.05, n),
                 c0=np.full(n, 0.01), c1=np.zeros(n), c2=np.full(n, 0.01), opacity=rng.uniform(0.992, 1.0, n),
                 r=rng.uniform(size=n), g=rng.uniform(size=n), b=rng.uniform(size=n),
-                depth=rng.uniform(1, 5, n), radius=np.full(n, 30, np.int32))
+                depth=rng.uniform(1, 5, n), rx=np.full(n, 30, np.int32), ry=np.full(n, 30, np.int32))
 
 
 @pytest.mark.parametrize("case", ["random", "clamped"])
@@ -417,7 +478,7 @@ def test_blend_bwd_matches_finite_differences(oracle_lib, case):
         sp = synth.random_splats(V, 30, W, H, seed=21, max_radius=10, wide_frac=0.0, cull_frac=0.0)
     else:
         sp = _clamping_splats(6, W, H, 21)
-    sp = {k: (np.asarray(v, np.float64) if k != "radius" else v) for k, v in sp.items()}
+    sp = _to64(sp)
     ranges, lst = oracle.bin_sort(sp, V, W, H, T)
     wgt = synth.random_image_grad(V, W, H, 4).astype(np.float64)
     bg = (0.2, 0.1, 0.4)
@@ -456,7 +517,7 @@ def test_preprocess_bwd_matches_finite_differences(oracle_lib):
     rec0 = oracle.preprocess(sc, vm, W, H)
     wts = np.random.default_rng(8).normal(size=(rec0.shape[0], 9))
     cols = oracle.SPLAT_COLS
-    alive = rec0[:, oracle.R_RADIUS] > 0
+    alive = rec0[:, oracle.R_RX] > 0
     wts[~alive] = 0.0
     grads = oracle.preprocess_bwd(sc, vm, wts, W, H)
 
