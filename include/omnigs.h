@@ -56,16 +56,19 @@ typedef struct {
 
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).
  * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H]. (c0, c1, c2): inverse of the 2x2 covariance
- * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. radius: half-side in pixels of the square whose tiles
- * receive an instance (ceil(3 sqrt(lambda_max))), 0 when the Gaussian is culled in this view. */
+ * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
+ * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
+ * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
+ * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
+ * + 1e-3)) and radius_y likewise with Sigma~_11. Outside that ellipse alpha < 1/255, so the narrowing removes only
+ * instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled. */
 typedef struct {
     float px, py;
     float c0, c1, c2;
     float opacity;
     float r, g, b;
     float depth;
-    int32_t radius;
-    uint32_t reserved; /* written as 0 */
+    int32_t radius_x, radius_y;
 } omnigs_splat;
 
 /* Gradient of the loss with respect to one omnigs_splat's differentiable fields (48 bytes, 16-byte aligned). */
@@ -91,7 +94,7 @@ size_t omnigs_workspace_size(const omnigs_config *cfg, int64_t n, int64_t capaci
 
 /* Per-(view, Gaussian) projection, Sec. 3.2-3.3: t = W m + t_cw (Eq. 1); lon, lat (Eq. 3); s (Eq. 4); p (Eq. 5);
  * J (Eqs. 10-16); Sigma~ = J W Sigma W^T J^T + 0.3 I (Eq. 9), Sigma = R(q) diag(s)^2 R(q)^T; conic = Sigma~^-1;
- * radius; colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m (Sec. 3.1).
+ * the instance box (radius_x, radius_y); colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m (Sec. 3.1).
  *   means   [n, 3]  world positions m                     scales  [n, 3]  linear scales S (> 0)
  *   quats   [n, 4]  rotations q as (w, x, y, z), any norm  opacity [n]     opacities o in [0, 1]
  *   sh      [n, K, 3] SH coefficients                     viewmats [V, 4, 4] row-major world-to-camera T_cw
@@ -101,9 +104,10 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
                                 const float *quats, const float *opacity, const float *sh, const float *viewmats,
                                 omnigs_splat *splats, omnigs_stream_t stream);
 
-/* Tile binning, Sec. 3.3 ("one instance per influence"): for every splat with radius > 0, one instance per tile
- * covered by the square of half-side `radius` around pixel floor(p). Tile columns wrap modulo W / tile (the
- * longitude seam; a square at least as wide as the image covers every column once); rows are clipped to the image.
+/* Tile binning, Sec. 3.3 ("one instance per influence"): for every splat with radius_x > 0, one instance per tile
+ * covered by the box [floor(px) - radius_x, floor(px) + radius_x] x [floor(py) - radius_y, floor(py) + radius_y].
+ * Tile columns wrap modulo W / tile (the longitude seam; a box at least as wide as the image covers every column
+ * once); rows are clipped to the image.
  * Splats whose centre lies outside [0, W] x [0, H] are ignored.
  *   splats  [V * n] input (device)
  *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:

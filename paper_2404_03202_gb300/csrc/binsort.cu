@@ -57,7 +57,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
 
 struct SplatPos {
     float px, py, depth;
-    int radius;
+    int rx, ry;  // instance box half-extents; rx = 0: no instance
 };
 
 // Splats whose centre is not a point of [0, W] x [0, H] (which the projection never produces) are treated as culled,
@@ -70,9 +70,10 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
     p.px = a.x;
     p.py = a.y;
     p.depth = c.y;
-    p.radius = __float_as_int(c.z);
+    p.rx = __float_as_int(c.z);
+    p.ry = __float_as_int(c.w);
     const bool inside = a.x >= 0.f && a.x <= (float)(tiles_x * tile) && a.y >= 0.f && a.y <= (float)(tiles_y * tile);
-    if (!inside || p.radius > kMaxRadius) p.radius = 0;
+    if (!inside || p.rx > kMaxRadius || p.ry > kMaxRadius || p.ry < 0) p.rx = 0;
     return p;
 }
 
@@ -99,8 +100,8 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
     unsigned cnt = 0;
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
-        if (p.radius > 0) {
-            const Rect r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
+        if (p.rx > 0) {
+            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile);
             cnt = (unsigned)(r.nx * r.ny);
         }
     }
@@ -150,8 +151,8 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
     unsigned tbase = 0;
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
-        if (p.radius > 0) {
-            r = splat_rect(p.px, p.py, p.radius, tiles_x, tiles_y, tile);
+        if (p.rx > 0) {
+            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile);
             cnt = (unsigned)(r.nx * r.ny);
             const int64_t v = i / n;
             rank = (int)(i - v * n);

@@ -41,18 +41,18 @@ __host__ __device__ inline int floordiv_int(int a, int b) {
     return q;
 }
 
-// Tiles covered by the square of half-side r around pixel floor(p): columns x0 .. x0 + nx - 1 modulo the column
-// count (all columns, from 0, once the square is at least as wide as the image), rows clipped to the image.
-__device__ inline Rect splat_rect(float px, float py, int r, int tiles_x, int tiles_y, int tile) {
+// Tiles covered by the box of half-extents (rx, ry) around pixel floor(p): columns x0 .. x0 + nx - 1 modulo the
+// column count (all columns, from 0, once the box is at least as wide as the image), rows clipped to the image.
+__device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_x, int tiles_y, int tile) {
     Rect R;
     int ix = (int)floorf(px), iy = (int)floorf(py);
-    int x0 = floordiv_int(ix - r, tile), x1 = floordiv_int(ix + r, tile);
+    int x0 = floordiv_int(ix - rx, tile), x1 = floordiv_int(ix + rx, tile);
     int nx = x1 - x0 + 1;
     if (nx >= tiles_x) {
         x0 = 0;
         nx = tiles_x;
     }
-    int y0 = floordiv_int(iy - r, tile), y1 = floordiv_int(iy + r, tile);
+    int y0 = floordiv_int(iy - ry, tile), y1 = floordiv_int(iy + ry, tile);
     y0 = y0 < 0 ? 0 : y0;
     y1 = y1 > tiles_y - 1 ? tiles_y - 1 : y1;
     R.x0 = x0;

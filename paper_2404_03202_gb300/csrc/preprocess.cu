@@ -241,7 +241,19 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, const float* __restr
         const float disc = fmaxf(0.1f, hd * hd + P.B * P.B);   // = mid^2 - det
         const float lam = mid + sqrtf(disc);
         const float rr = ceilf(3.f * sqrtf(lam));
-        const int radius = rr < (float)kMaxRadius ? (int)rr : kMaxRadius;
+        // the instance box: the 3-sigma square narrowed to the box of the alpha >= 1/255 ellipse
+        // dp^T conic dp <= q, q = 2 ln(255 o), whose half-extents are sqrt(q Sigma~_00) and sqrt(q Sigma~_11)
+        const float q = fmaxf(2.f * logf(255.f * o), 0.f);
+        const float hx = ceilf(fmaf(sqrtf(q * P.A), 1.0001f, 1e-3f));
+        const float hy = ceilf(fmaf(sqrtf(q * P.C), 1.0001f, 1e-3f));
+        const float lim = fminf(rr, (float)kMaxRadius);
+        const int rx = (int)fminf(hx, lim), ry = (int)fminf(hy, lim);
+        if (!(255.f * o >= 1.f)) {  // alpha < 1/255 everywhere: no instance
+            out[0] = make_float4(px, py, c0, c1);
+            out[1] = make_float4(c2, o, 0.f, 0.f);
+            out[2] = make_float4(0.f, P.tr, __int_as_float(0), __int_as_float(0));
+            continue;
+        }
 
         float d[3], Y[16];
         view_dir(w, m, d);
@@ -256,7 +268,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, const float* __restr
         }
         out[0] = make_float4(px, py, c0, c1);
         out[1] = make_float4(c2, o, rgb[0], rgb[1]);
-        out[2] = make_float4(rgb[2], P.tr, __int_as_float(radius), __uint_as_float(0u));
+        out[2] = make_float4(rgb[2], P.tr, __int_as_float(rx), __int_as_float(ry));
     }
 }
 
@@ -266,7 +278,8 @@ template <int K>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, const float* __restrict__ means,
                       const float* __restrict__ scales, const float* __restrict__ quats,
-                      const float* __restrict__ sh, const float* __restrict__ viewmats,
+                      const float* __restrict__ opacity, const float* __restrict__ sh,
+                      const float* __restrict__ viewmats,
                       const float4* __restrict__ grads, float* __restrict__ d_means, float* __restrict__ d_scales,
                       float* __restrict__ d_quats, float* __restrict__ d_opacity, float* __restrict__ d_sh,
                       float* __restrict__ d_screen) {
@@ -291,8 +304,10 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, const float* __r
         float dm[3] = {0.f, 0.f, 0.f}, dM3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float dop = 0.f, dsx = 0.f, dsy = 0.f;
         const float a = (float)W / (2.f * kPi), b = (float)H / kPi;
+        // culled in every view when alpha < 1/255 everywhere (255 o < 1): no gradient reaches it
+        const int views = 255.f * __ldg(opacity + g) >= 1.f ? V : 0;
 
-        for (int v = 0; v < V; ++v) {
+        for (int v = 0; v < views; ++v) {
             const View w = load_view(s_view, v);
             Proj P;
             float px, py;
@@ -458,7 +473,8 @@ cudaError_t preprocess_k(const omnigs_config& cfg, int64_t n, const float* means
 
 template <int K>
 cudaError_t preprocess_bwd_k(const omnigs_config& cfg, int64_t n, const float* means, const float* scales,
-                             const float* quats, const float* sh, const float* viewmats, const omnigs_splat_grad* grads,
+                             const float* quats, const float* opacity, const float* sh, const float* viewmats,
+                             const omnigs_splat_grad* grads,
                              float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_sh,
                              float* d_screen, cudaStream_t stream) {
     const size_t smem = sizeof(float) * (2 * kPreThreads * (3 * K + 1) + 16 * cfg.num_views);
@@ -468,7 +484,7 @@ cudaError_t preprocess_bwd_k(const omnigs_config& cfg, int64_t n, const float* m
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
     ProfScope prof("preprocess_bwd", stream);
     kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, means, scales,
-                                                quats, sh, viewmats, reinterpret_cast<const float4*>(grads), d_means,
+                                                quats, opacity, sh, viewmats, reinterpret_cast<const float4*>(grads), d_means,
                                                 d_scales, d_quats, d_opacity, d_sh, d_screen);
     return cudaGetLastError();
 }
@@ -491,13 +507,12 @@ cudaError_t launch_preprocess_bwd(const omnigs_config& cfg, int64_t n, const flo
                                   const float* quats, const float* opacity, const float* sh, const float* viewmats,
                                   const omnigs_splat_grad* grads, float* d_means, float* d_scales, float* d_quats,
                                   float* d_opacity, float* d_sh, float* d_screen, cudaStream_t stream) {
-    (void)opacity;
     if (n == 0) return cudaSuccess;
     switch (cfg.sh_degree) {
-        case 0: return preprocess_bwd_k<1>(cfg, n, means, scales, quats, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
-        case 1: return preprocess_bwd_k<4>(cfg, n, means, scales, quats, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
-        case 2: return preprocess_bwd_k<9>(cfg, n, means, scales, quats, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
-        default: return preprocess_bwd_k<16>(cfg, n, means, scales, quats, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
+        case 0: return preprocess_bwd_k<1>(cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
+        case 1: return preprocess_bwd_k<4>(cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
+        case 2: return preprocess_bwd_k<9>(cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
+        default: return preprocess_bwd_k<16>(cfg, n, means, scales, quats, opacity, sh, viewmats, grads, d_means, d_scales, d_quats, d_opacity, d_sh, d_screen, stream);
     }
 }
 

@@ -6,19 +6,26 @@ SPLAT_KEYS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth")
 
 
 def pack_splats(sp: dict) -> np.ndarray:
-    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (radius stored as int32 bits)."""
+    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (rx, ry stored as int32 bits)."""
     m = len(sp["px"])
     out = np.zeros((m, 12), np.float32)
     for i, k in enumerate(SPLAT_KEYS):
         out[:, i] = np.asarray(sp[k], np.float32)
-    out[:, 10] = np.asarray(sp["radius"], np.int32).view(np.float32)
+    out[:, 10] = np.asarray(sp["rx"], np.int32).view(np.float32)
+    out[:, 11] = np.asarray(sp["ry"], np.int32).view(np.float32)
     return out
 
 
 def unpack_splats(arr: np.ndarray) -> dict:
     d = {k: arr[:, i].copy() for i, k in enumerate(SPLAT_KEYS)}
-    d["radius"] = arr[:, 10].copy().view(np.int32)
+    d["rx"] = arr[:, 10].copy().view(np.int32)
+    d["ry"] = arr[:, 11].copy().view(np.int32)
     return d
+
+
+def to64(sp: dict) -> dict:
+    """Splat fields in double precision (integer fields unchanged)."""
+    return {k: (np.asarray(v, np.float64) if np.asarray(v).dtype.kind == "f" else v) for k, v in sp.items()}
 
 
 def dev(a, dtype=None):
@@ -55,13 +62,14 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
 
     Culling agrees except within 1e-6 (relative) of the near distance; p within 2e-6 W (H) px, the angle carrying a
     few ulp (longitude differences taken across the seam); conic within 1e-4 of its norm; rgb within 1e-5; opacity
-    copied exactly; radius exact unless 3 sqrt(lambda_max) lies within 1e-4 of an integer. Returns a summary."""
+    copied exactly; the instance box (rx, ry) exact unless one of its ceil() arguments lies within 1e-4 of an
+    integer. Returns a summary."""
     import oracle
     ref = oracle.splats_from_records(rec)
     near_edge = np.abs(ref["depth"] - near) < 1e-6 * near
-    alive = ref["radius"] > 0
-    assert np.array_equal((got["radius"] > 0)[~near_edge], alive[~near_edge])
-    a = alive & (got["radius"] > 0)
+    alive = ref["rx"] > 0
+    assert np.array_equal((got["rx"] > 0)[~near_edge], alive[~near_edge])
+    a = alive & (got["rx"] > 0)
     np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6)
     dpx = (got["px"][a] - ref["px"][a] + W / 2) % W - W / 2
     dpy = got["py"][a] - ref["py"][a]
@@ -74,6 +82,7 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
     assert rgb_err <= 1e-5
     assert np.array_equal(got["opacity"][a], opacity_expected[a])
     margin_ok = rec[:, oracle.R_RMARGIN][a] > 1e-4 * np.maximum(1.0, ref["radius"][a])
-    assert np.array_equal(got["radius"][a][margin_ok], ref["radius"][a][margin_ok])
+    assert np.array_equal(got["rx"][a][margin_ok], ref["rx"][a][margin_ok])
+    assert np.array_equal(got["ry"][a][margin_ok], ref["ry"][a][margin_ok])
     return dict(alive=int(a.sum()), dpx=float(np.abs(dpx).max(initial=0)), dpy=float(np.abs(dpy).max(initial=0)),
                 conic=float(cerr), rgb=float(rgb_err))

@@ -22,7 +22,8 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, check_preprocess, dev, pack_splats, scene_to_device, unpack_splats
+from tests.gpu_util import (assert_grad_close, check_preprocess, dev, pack_splats, scene_to_device, to64,
+                            unpack_splats)
 
 pytestmark = pytest.mark.gpu
 
@@ -79,11 +80,12 @@ def _tile_sample(sp, V, n, rng):
     chosen = []
     for v, y0, y1 in bands:
         mask[v, y0:y1, :] = True
-        rad, py = sp["radius"][v * n:(v + 1) * n], sp["py"][v * n:(v + 1) * n]
-        near_band = (rad > 0) & (py - rad >= y0 * TILE - 2 * TILE) & (py + rad < y1 * TILE + 2 * TILE)
+        ry, py = sp["ry"][v * n:(v + 1) * n], sp["py"][v * n:(v + 1) * n]
+        near_band = (sp["rx"][v * n:(v + 1) * n] > 0) & (py - ry >= y0 * TILE - 2 * TILE) & (py + ry < y1 * TILE + 2 * TILE)
         for g in np.nonzero(near_band)[0]:  # a loose pre-filter; the oracle's rectangle decides
             i = v * n + g
-            _, _, ry0, rny = oracle.rect(float(sp["px"][i]), float(sp["py"][i]), int(sp["radius"][i]), W, H, TILE)
+            _, _, ry0, rny = oracle.rect(float(sp["px"][i]), float(sp["py"][i]), int(sp["rx"][i]), int(sp["ry"][i]),
+                                         W, H, TILE)
             if y0 <= ry0 and ry0 + rny <= y1:
                 chosen.append(i)
     return mask.reshape(-1), np.array(sorted(set(chosen)), np.int64)
@@ -96,7 +98,7 @@ def test_tiles_sampled_full_size(name):
     # the oracle's splats, rounded to the float32 layout both sides read
     packed = pack_splats(oracle.splats_from_records(oracle.preprocess(sc, vm, W, H)))
     sp32 = unpack_splats(packed)
-    sp64 = {k: (v.astype(np.float64) if k != "radius" else v) for k, v in sp32.items()}
+    sp64 = to64(sp32)
     total = oracle.count_instances(sp64, V, W, H, TILE)
 
     r = _rasterizer(V, total)

@@ -13,7 +13,8 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, dev, normwise, pack_splats, scene_to_device, unpack_splats
+from tests.gpu_util import (assert_grad_close, check_preprocess, dev, normwise, pack_splats, scene_to_device, to64,
+                            unpack_splats)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,32 +65,9 @@ def test_preprocess_matches_oracle(deg):
     C.omnigs_preprocess(r.cfg, sc.n, *params, dev(vm), r.splats)
     got = unpack_splats(r.splats.cpu().numpy())
     rec = oracle.preprocess(sc, vm, W, H)
-    ref = oracle.splats_from_records(rec)
-    # culling agrees except within 1e-6 (relative) of the near distance
-    near_edge = np.abs(ref["depth"] - 0.2) < 1e-6 * 0.2
-    alive = ref["radius"] > 0
-    assert np.array_equal((got["radius"] > 0)[~near_edge], alive[~near_edge])
-    a = alive & (got["radius"] > 0)
-    np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6)
-    # p: atan2f / asinf carry a few ulp of the angle (< 1e-6 rad here); times W/(2 pi) and H/pi px per radian;
-    # longitude differences are taken across the seam
-    dpx = (got["px"][a] - ref["px"][a] + W / 2) % W - W / 2
-    dpy = got["py"][a] - ref["py"][a]
-    print(f"preprocess: max|dpx| {np.abs(dpx).max():.3e} max|dpy| {np.abs(dpy).max():.3e}")
-    assert np.abs(dpx).max() <= 2e-6 * W and np.abs(dpy).max() <= 2e-6 * H
-    # conic: relative to its norm; the FP32 determinant is formed without cancellation
-    cg = np.stack([got["c0"], got["c1"], got["c2"]], 1)[a]
-    cr = np.stack([ref["c0"], ref["c1"], ref["c2"]], 1)[a]
-    cerr = np.abs(cg - cr).max(1) / np.abs(cr).max(1)
-    print(f"preprocess: conic max rel {cerr.max():.3e}")
-    assert cerr.max() <= 1e-4
-    rgb_err = max(np.abs(got[k][a] - ref[k][a]).max() for k in ("r", "g", "b"))
-    print(f"preprocess: rgb max abs {rgb_err:.3e}")
-    assert rgb_err <= 1e-5
-    assert np.array_equal(got["opacity"][a], sc.opacity[np.nonzero(a)[0] % sc.n])
-    # radius = ceil(3 sqrt(lambda_max)): exact unless 3 sqrt(lambda) is within 1e-4 of an integer
-    margin_ok = rec[:, oracle.R_RMARGIN][a] > 1e-4 * np.maximum(1.0, ref["radius"][a])
-    assert np.array_equal(got["radius"][a][margin_ok], ref["radius"][a][margin_ok])
+    summary = check_preprocess(got, rec, np.tile(sc.opacity, vm.shape[0]).astype(np.float32), W, H)
+    print(f"preprocess: {summary}")
+    assert summary["alive"] > 0.5 * len(rec)
 
 
 # ------------------------------------------------------------------ S2-S4 bin, sort, ranges
@@ -130,7 +108,7 @@ def test_sort_many_ties_and_all_columns():
 
 def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
     r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V, bg=bg, ppt=ppt))
-    sp64 = {k: (np.asarray(v, np.float64) if k != "radius" else v) for k, v in sp.items()}
+    sp64 = to64(sp)
     ranges, lst = oracle.bin_sort(sp64, V, W, H, tile)
     rgb, T, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5)
     return r, (rgb, T, nc, near), (ranges, lst, sp64)
