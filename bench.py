@@ -14,6 +14,7 @@ region is bracketed by barriers and the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -29,9 +30,13 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOADS = {
-    # name: (n, views, W, H, tile, scene builder, pose builder)
+    # egocentric: 1M Gaussians in a room, 8 poses near its centre (the headline workload)
     "egocentric": dict(n=1_000_000, views=8, width=2048, height=1024, tile=16, scene="room"),
     "egocentric-1view": dict(n=1_000_000, views=1, width=2048, height=1024, tile=16, scene="room"),
+    # training: 300k Gaussians in a 0.5-20 m shell, one identity pose
+    "training": dict(n=300_000, views=1, width=2048, height=1024, tile=16, scene="shell-20"),
+    # roaming: 3M Gaussians along a 60 m corridor of 5 rooms, 16 poses on its centre line, autotuned tile/schedule
+    "roaming": dict(n=3_000_000, views=16, width=4096, height=2048, tile="auto", scene="corridor"),
     "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
 }
 
@@ -90,6 +95,10 @@ RENDER_BWD_TRAFFIC = {"bytes_per_view": 58_584_576,
 def build_scene(wl: dict, seed: int = 0):
     if wl["scene"] == "room":
         return synth.room_scene(wl["n"], seed)
+    if wl["scene"] == "corridor":
+        return synth.corridor_scene(wl["n"], seed)
+    if wl["scene"] == "shell-20":
+        return synth.shell_scene(wl["n"], seed, r_min=0.5, r_max=20.0)
     return synth.shell_scene(wl["n"], seed)
 
 
@@ -98,6 +107,8 @@ def build_poses(wl: dict, rank: int, world: int = 1):
     total = wl["views"] * world
     if wl["scene"] == "room":
         poses = synth.room_viewmats(total, 1000)
+    elif wl["scene"] == "corridor":
+        poses = synth.corridor_viewmats(total, 1000)
     else:
         poses = synth.identity_viewmats(total)
     if world == 1:
@@ -168,10 +179,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng):
+def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng, tile: int | None = None):
     """One bounded oracle sample of a step, extrapolated to the whole step (ms). Returns (ms, description)."""
     import oracle
-    W, H, T, V = wl["width"], wl["height"], wl["tile"], wl["views"]
+    W, H, V = wl["width"], wl["height"], wl["views"]
+    T = tile or (16 if wl["tile"] == "auto" else wl["tile"])
     tiles = (W // T) * (H // T)
     n = scene.n
     # Gaussian fraction for the full-list stages (bin + sort, ~n log n, taken as linear) and tile sample for blending
@@ -274,11 +286,14 @@ def serving_benchmark(dev, count: int = 96, lanes: int = 4, max_batch: int = 8) 
     return out
 
 
-def workload_config(wl, args):
+def workload_config(wl, args, settings=None):
+    tile = settings.tile if settings is not None else wl["tile"]
+    auto = " (autotuned)" if wl["tile"] == "auto" else ""
     return {"workload": f"{args.workload}: {wl['n']} Gaussians, {wl['views']} views of {wl['width']}x{wl['height']} "
-                        f"equirect, {wl['tile']}x{wl['tile']} tiles, fwd+bwd with L1 loss",
+                        f"equirect, {tile}x{tile} tiles{auto}, fwd+bwd with L1 loss",
             "gaussians": wl["n"], "views_per_step": wl["views"], "width": wl["width"], "height": wl["height"],
-            "tile": wl["tile"], "parallelism": f"replica x{args.gpus} (views per rank)",
+            "tile": tile, "pixels_per_thread": (settings.pixels_per_thread or "default") if settings else None,
+            "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)"}
 
 
@@ -321,7 +336,8 @@ def main():
     scene = build_scene(wl)
     vm_np = build_poses(wl, rank, world)
     V, W, H = wl["views"], wl["width"], wl["height"]
-    settings = og.Settings(width=W, height=H, tile=wl["tile"], num_views=V, sh_degree=scene.sh_degree)
+    auto = wl["tile"] == "auto"
+    settings = og.Settings(width=W, height=H, tile=16 if auto else wl["tile"], num_views=V, sh_degree=scene.sh_degree)
     params = [torch.from_numpy(a).to(dev) for a in scene.arrays()]
     vm = torch.from_numpy(vm_np).to(dev)
 
@@ -329,6 +345,15 @@ def main():
     pert = synth.perturbed_copy(scene, 11)
     probe = og.Rasterizer(settings, device=dev)
     target = probe.forward(*[torch.from_numpy(a).to(dev) for a in pert.arrays()], vm).clone()
+    tuning = None
+    if auto:  # tile size and blend schedule timed on this workload, before (and outside) the timed region
+        from paper_2404_03202_gb300.autotune import Autotuner
+        choice = Autotuner().tune(params, vm, settings, "train", target)
+        settings = dataclasses.replace(settings, tile=choice.tile, pixels_per_thread=choice.pixels_per_thread)
+        tuning = {"tile": choice.tile, "pixels_per_thread": choice.pixels_per_thread,
+                  "candidates_ms": {f"{t}x{t}/ppt{p}": ms for (t, p), ms in choice.table.items()}}
+        del probe
+        probe = og.Rasterizer(settings, device=dev)
     probe.forward(*params, vm)
     count = probe.count
     del probe
@@ -475,7 +500,7 @@ def main():
 
     # every stage against its own roofline (per step; a stage may span several launches)
     stages = {}
-    sb = stage_bytes(wl["n"], V, W, H, wl["tile"], count)
+    sb = stage_bytes(wl["n"], V, W, H, settings.tile, count)
     for name, pk in per_kernel.items():
         ms_step = pk["total_ms"] / args.steps
         if name in sb:
@@ -505,7 +530,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             ms_cpu, desc = oracle_step_sample(scene, vm_np, wl, synth.random_image(V, W, H, 5), 12.0,
-                                              np.random.default_rng(3))
+                                              np.random.default_rng(3), settings.tile)
             cpu = {"value": ms_cpu, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": desc}
         except Exception as e:
             cpu = {"value": None, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
@@ -514,7 +539,8 @@ def main():
         out = {"metric": "fwd+bwd ms/iter", "value": ms * 1.0, "unit": "ms/iter", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": workload_config(wl, args) | {"views_per_s": 1e3 * V * world / ms,
+               "config": workload_config(wl, args, settings) | {"views_per_s": 1e3 * V * world / ms,
+                                                      "autotune": tuning,
                                                       "graph_ms_per_step": graph_ms,
                                                       "instances_per_step": count,
                                                       "examined_pairs_per_step": examined,

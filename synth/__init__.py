@@ -101,7 +101,9 @@ def room_scene(n: int, seed: int, surface_frac: float = 0.7, sh_degree: int = 3)
 
 
 def corridor_scene(n: int, seed: int, rooms: int = 5, room_len: float = 12.0, sh_degree: int = 3) -> Scene:
-    """Roaming layout: `rooms` boxes of 8 x 3 x room_len m chained along +z (a 60 m corridor of rooms)."""
+    """Roaming layout: `rooms` boxes of 8 x 3 x room_len m chained along +z (a 60 m corridor of rooms), 70 % of
+    the means on the walls, floor and ceiling, 30 % inside; a 2 x 2.1 m doorway is cut into every wall that two
+    rooms share (the surface points there are moved inside the rooms), so poses along the centre line see through."""
     rng = np.random.default_rng(seed)
     half = np.array([4.0, 1.5, room_len / 2.0])
     n_surf = int(round(0.7 * n))
@@ -109,7 +111,13 @@ def corridor_scene(n: int, seed: int, rooms: int = 5, room_len: float = 12.0, sh
     centers = np.stack([np.zeros(rooms), np.zeros(rooms), (np.arange(rooms) + 0.5) * room_len], axis=1)
     surf = _box_surface_points(rng, n_surf, -half, half)
     inner = rng.uniform(-half, half, size=(n - n_surf, 3))
-    means = np.concatenate([surf, inner], axis=0) + centers[which]
+    local = np.concatenate([surf, inner], axis=0)
+    # doorways: |x| < 1, y from the floor (+1.5, y points down) up to 2.1 m above it, on shared z walls
+    on_wall = np.abs(np.abs(local[:, 2]) - half[2]) < 1e-9
+    shared = np.where(local[:, 2] > 0, which < rooms - 1, which > 0)
+    door = on_wall & shared & (np.abs(local[:, 0]) < 1.0) & (local[:, 1] > 1.5 - 2.1)
+    local[door] = rng.uniform(-half, half, size=(int(door.sum()), 3))
+    means = local + centers[which]
     scales, quats, opacity, sh = _attributes(rng, n, sh_degree)
     return Scene(means.astype(np.float32), scales, quats, opacity, sh, sh_degree)
 
