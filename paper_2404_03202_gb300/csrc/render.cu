@@ -92,7 +92,7 @@ struct PixelMap {
     }
 };
 
-template <int TS, int PPT>
+template <int TS, int PPT, bool kCount>
 __global__ void __launch_bounds__(TS * TS / PPT)
 render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
@@ -137,6 +137,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             const float4 B = s_b[j];
             const float dx = entry_dx(A.x, B.w, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
+            const uint32_t pos1 = b - start + j + 1;        // list position after this entry
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
@@ -154,8 +155,8 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
                 C1[k] = fmaf(w, Cc.z, C1[k]);
                 C2[k] = fmaf(w, Cc.w, C2[k]);
                 T[k] = Tn;
-                last[k] = b - start + j + 1;
-                ++count[k];
+                last[k] = pos1;
+                if (kCount) ++count[k];
             }
             bool any = false;
 #pragma unroll
@@ -172,7 +173,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
         out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T[k], bg2, C2[k]);
         out_T[(size_t)v * HW + pix] = T[k];
         out_nc[(size_t)v * HW + pix] = last[k];
-        if (out_count) out_count[(size_t)v * HW + pix] = count[k];
+        if (kCount) out_count[(size_t)v * HW + pix] = count[k];
     }
 }
 
@@ -356,7 +357,8 @@ cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
     ProfScope prof("render_fwd", stream);
-    render_fwd_kernel<TS, PPT><<<tiles * cfg.num_views, PixelMap<TS, PPT>::NT, 0, stream>>>(
+    auto kern = out_count ? render_fwd_kernel<TS, PPT, true> : render_fwd_kernel<TS, PPT, false>;
+    kern<<<tiles * cfg.num_views, PixelMap<TS, PPT>::NT, 0, stream>>>(
         cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
         out_rgb, out_T, out_nc, out_count);
