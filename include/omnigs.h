@@ -49,9 +49,9 @@ typedef struct {
     int32_t sh_degree; /* 0..3; the SH array holds K = (sh_degree + 1)^2 coefficients per colour channel */
     float near_r;      /* a Gaussian is culled when its camera distance t_r <= near_r */
     float bg[3];       /* background colour added with the final transmittance */
-    int32_t pixels_per_thread; /* blend schedule: pixels of one image column each blend thread owns (2 or 4;
-                                * 4 needs tile >= 16); 0 lets the library choose. Results do not depend on it
-                                * beyond the order of floating-point additions in the gradients. */
+    int32_t pixels_per_thread; /* blend schedule: pixels of one image column each blend thread owns (2, 4 or 8;
+                                * 4 and 8 need tile >= 16); 0 lets the library choose. Results do not depend on
+                                * it beyond the order of floating-point additions in the gradients. */
 } omnigs_config;
 
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).

@@ -1,8 +1,8 @@
 """Autotuner for the tile size and the blend schedule of a workload.
 
 The tile side (8, 16 or 32 px) trades binning and sorting work (instances grow roughly with 1 / tile^2 of the
-covered area) against blending work (a larger tile walks longer lists per pixel); the blend schedule (2 or 4 pixels
-per thread) trades per-entry sharing against threads per tile. The best choice depends on the scene, the poses and
+covered area) against blending work (a larger tile walks longer lists per pixel); the blend schedule (2, 4 or 8 pixels
+per thread) trades per-entry sharing against threads per tile (at 8 one warp covers a 16 x 16 tile). The best choice depends on the scene, the poses and
 the resolution, so the tuner times each candidate on the caller's own data, with CUDA events on the current stream,
 and keeps the fastest per workload key (Gaussian count bucket, views, resolution, SH degree, mode).
 
@@ -21,7 +21,7 @@ import torch
 from . import _cabi as C
 from .rasterizer import Rasterizer, Settings
 
-CANDIDATES = [(8, 2), (16, 2), (16, 4), (32, 2), (32, 4)]
+CANDIDATES = [(8, 2), (16, 2), (16, 4), (16, 8), (32, 2), (32, 4), (32, 8)]
 
 
 @dataclass

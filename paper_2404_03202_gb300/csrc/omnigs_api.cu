@@ -96,8 +96,9 @@ bool valid_cfg(const omnigs_config* c) {
     if (!std::isfinite(c->near_r) || c->near_r < 0.f) return false;
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(c->bg[i])) return false;
-    if (c->pixels_per_thread != 0 && c->pixels_per_thread != 2 && c->pixels_per_thread != 4) return false;
-    if (c->pixels_per_thread == 4 && c->tile == 8) return false;
+    const int ppt = c->pixels_per_thread;
+    if (ppt != 0 && ppt != 2 && ppt != 4 && ppt != 8) return false;
+    if (ppt > 2 && c->tile == 8) return false;
     const uint64_t tiles = (uint64_t)(c->width / c->tile) * (uint64_t)(c->height / c->tile) * (uint64_t)c->num_views;
     return tiles < (1ull << 31);
 }

@@ -9,15 +9,18 @@
 //     exponent > 0 guard a pair passes only if thr <= e <= 0, tested as |e - thr/2| <= -thr/2 with one subtraction
 //     and one compare before the ex2.
 // Each thread owns PPT vertically adjacent pixels of one column: they share dx, the per-entry products and every
-// shared-memory load. The CTA leaves the list once every pixel has stopped (__syncthreads_count).
+// shared-memory load. The forward's per-pixel update is branch-free (a pair that fails the test or stops the pixel
+// adds with weight 0), which costs an ex2 per examined pair but removes the divergent branch. The CTA leaves the
+// list once every pixel has stopped (__syncthreads_count).
 //
 // The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
 // (1 - alpha) and accumulates the 9 partial derivatives of an entry over the thread's pixels. The warp then reduces
 // them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth: 14 shuffles, after which 9 lanes
 // hold one field's total each and write it with one shared-memory atomic), the CTA sums warps in shared memory, and
 // the CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
-// A thread owns PPT = 2 or 4 pixels (the blend schedule of the config): more pixels per thread share more of the
-// per-entry work and the warp reduction, fewer give more threads per tile. Forward and adjoint evaluate alpha with identical
+// A thread owns PPT = 2, 4 or 8 pixels (the blend schedule of the config): more pixels per thread share more of the
+// per-entry work and the warp reduction, fewer give more threads per tile. At 8 pixels one warp covers a 16 x 16
+// tile. Forward and adjoint evaluate alpha with identical
 // arithmetic, so their skip / stop decisions agree.
 #include "common.cuh"
 
@@ -138,25 +141,24 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
             const float dx = entry_dx(A.x, B.w, xs, halfW, fW);
             const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
             const uint32_t pos1 = b - start + j + 1;        // list position after this entry
+            const float4 Cc = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
-                if (!live[k] || !(fabsf(e - B.y) <= B.z)) continue;  // alpha < 1/255, or exponent > 0
-                const float4 Cc = s_c[j];
-                const float alpha = fminf(kAlphaMax, Cc.x * fast_ex2(e));
+                const bool pass = live[k] && (fabsf(e - B.y) <= B.z);
+                const float alpha = pass ? fminf(kAlphaMax, Cc.x * fast_ex2(e)) : 0.f;
                 const float Tn = T[k] * (1.f - alpha);
-                if (Tn < kTStop) {
-                    live[k] = false;
-                    continue;
-                }
-                const float w = alpha * T[k];
+                const bool stop = pass && Tn < kTStop;
+                const bool add = pass && !stop;
+                live[k] = live[k] && !stop;
+                const float w = add ? alpha * T[k] : 0.f;
                 C0[k] = fmaf(w, Cc.y, C0[k]);
                 C1[k] = fmaf(w, Cc.z, C1[k]);
                 C2[k] = fmaf(w, Cc.w, C2[k]);
-                T[k] = Tn;
-                last[k] = pos1;
-                if (kCount) ++count[k];
+                T[k] = add ? Tn : T[k];
+                last[k] = add ? pos1 : last[k];
+                if (kCount) count[k] += add ? 1u : 0u;
             }
             bool any = false;
 #pragma unroll
@@ -344,7 +346,7 @@ size_t bwd_smem(int nt) {
     return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
-// Pixels per blend thread: the configured schedule, else 2 for 8x8 tiles and 4 for larger ones.
+// Pixels per blend thread: the configured schedule (2, 4 or 8), else 2 for 8x8 tiles and 4 for larger ones.
 int blend_ppt(const omnigs_config& cfg) {
     if (cfg.pixels_per_thread) return cfg.pixels_per_thread;
     return cfg.tile == 8 ? 2 : 4;
@@ -435,15 +437,19 @@ l1_finish_kernel(const float* __restrict__ partials, int nb, float inv_total, fl
 cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
                               const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
                               float* out_T, uint32_t* out_nc, uint32_t* out_count, cudaStream_t stream) {
-    const bool four = blend_ppt(cfg) == 4;
+    const int ppt = blend_ppt(cfg);
     switch (cfg.tile) {
         case 8: return render_fwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
         case 32:
-            return four ? render_fwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
-                        : render_fwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+            if (ppt == 8)
+                return render_fwd_t<32, 8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+            return ppt == 4 ? render_fwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
+                            : render_fwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
         default:
-            return four ? render_fwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
-                        : render_fwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+            if (ppt == 8)
+                return render_fwd_t<16, 8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+            return ppt == 4 ? render_fwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
+                            : render_fwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
     }
 }
 
@@ -453,15 +459,17 @@ cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_
                               omnigs_splat_grad* grads, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(omnigs_splat_grad) * (size_t)n * cfg.num_views, stream);
     if (e != cudaSuccess) return e;
-    const bool four = blend_ppt(cfg) == 4;
+    const int ppt = blend_ppt(cfg);
     switch (cfg.tile) {
         case 8: return render_bwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
         case 32:
-            return four ? render_bwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
-                        : render_bwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+            if (ppt == 8) return render_bwd_t<32, 8>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+            return ppt == 4 ? render_bwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
+                            : render_bwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
         default:
-            return four ? render_bwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
-                        : render_bwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+            if (ppt == 8) return render_bwd_t<16, 8>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
+            return ppt == 4 ? render_bwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream)
+                            : render_bwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
     }
 }
 

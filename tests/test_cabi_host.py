@@ -67,6 +67,6 @@ def test_config_layout_and_schedule_validation(lib):
     assert ctypes.sizeof(Cfg) == 40
     lib.omnigs_workspace_size.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_int64]
     lib.omnigs_workspace_size.restype = ctypes.c_size_t
-    for tile, ppt in [(8, 4), (16, 3), (16, 1), (32, 8)]:
+    for tile, ppt in [(8, 4), (8, 8), (16, 3), (16, 1), (32, 16)]:
         c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), ppt)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (tile, ppt)

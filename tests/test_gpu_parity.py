@@ -114,7 +114,8 @@ def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
     return r, (rgb, T, nc, near), (ranges, lst, sp64)
 
 
-@pytest.mark.parametrize("tile,V,ppt", [(16, 2, 4), (16, 2, 2), (8, 1, 2), (32, 1, 4), (32, 1, 2)])
+@pytest.mark.parametrize("tile,V,ppt", [(16, 2, 4), (16, 2, 2), (16, 2, 8), (8, 1, 2), (32, 1, 4), (32, 1, 2),
+                                        (32, 1, 8)])
 def test_render_fwd_matches_oracle(tile, V, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2500, W, H, seed=200 + tile, max_radius=24)
@@ -146,7 +147,8 @@ def test_render_fwd_opaque_stacks_stop_rule():
 # ------------------------------------------------------------------ S7 render backward
 
 @pytest.mark.parametrize("tile,V,opac,ppt", [(16, 2, (0.05, 0.99), 4), (16, 2, (0.05, 0.99), 2), (8, 1, (0.5, 1.0), 2),
-                                             (32, 1, (0.05, 0.99), 4), (32, 1, (0.5, 1.0), 2)])
+                                             (16, 2, (0.5, 1.0), 8), (32, 1, (0.05, 0.99), 4), (32, 1, (0.5, 1.0), 2),
+                                             (32, 1, (0.05, 0.99), 8)])
 def test_render_bwd_matches_oracle(tile, V, opac, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2000, W, H, seed=300 + tile, max_radius=24, opacity_range=opac)
