@@ -38,6 +38,9 @@ WORKLOADS = {
     # roaming: 3M Gaussians along a 60 m corridor of 5 rooms, 16 poses on its centre line, autotuned tile/schedule
     "roaming": dict(n=3_000_000, views=16, width=4096, height=2048, tile="auto", scene="corridor"),
     "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
+    # 360Roam-shaped: the corridor of rooms seen by 8 poses at 1536x768, the bottom 48 rows (the capture rig) left out
+    # of the loss and its gradient
+    "roam-masked": dict(n=1_000_000, views=8, width=1536, height=768, tile=16, scene="corridor", loss_rows=(0, 720)),
 }
 
 # Algorithmic work per unit, used for the roofline. A (pixel, entry) pair is "examined" when the pixel's walk of its
@@ -306,6 +309,7 @@ def workload_config(wl, args, settings=None):
                         f"equirect, {tile}x{tile} tiles{auto}, fwd+bwd with L1 loss",
             "gaussians": wl["n"], "views_per_step": wl["views"], "width": wl["width"], "height": wl["height"],
             "tile": tile, "pixels_per_thread": (settings.pixels_per_thread or "default") if settings else None,
+            "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)"}
 
@@ -313,7 +317,7 @@ def workload_config(wl, args, settings=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="egocentric", choices=sorted(WORKLOADS))
@@ -373,9 +377,11 @@ def main():
     torch.cuda.synchronize()
     r = og.Rasterizer(settings, device=dev, capacity=int(count * 1.05) + 4096, grow=False)
 
+    loss_rows = wl.get("loss_rows")
+
     def step():
         r.forward(*params, vm)
-        r.l1_loss(target)
+        r.l1_loss(target, rows=loss_rows)
         r.backward()
 
     for _ in range(args.warmup):
@@ -452,7 +458,7 @@ def main():
             dev_vm.copy_(host_vm, non_blocking=True)
             dev_target.copy_(host_target, non_blocking=True)
             r.forward(*dev_params, dev_vm)
-            r.l1_loss(dev_target)
+            r.l1_loss(dev_target, rows=loss_rows)
             grads = r.backward()
             for k in out_names:
                 host_out[k].copy_(grads[k], non_blocking=True)

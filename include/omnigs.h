@@ -148,6 +148,15 @@ omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnig
 omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const float *target, float *dL_drgb,
                              float *loss, void *workspace, omnigs_stream_t stream);
 
+/* L1 loss restricted to the image rows [row_begin, row_end), for captures whose band of rows shows the capture rig
+ * rather than the scene (Sec. 5.2: in the 360Roam captures the bottom rows, which show the robot carrying the
+ * camera, are left out of the loss and its gradient): loss = mean |rgb - target| over [V, 3, row_begin:row_end, W]; dL_drgb = sign(rgb - target) / (V * 3 *
+ * (row_end - row_begin) * W) inside those rows and 0 outside. Requires 0 <= row_begin < row_end <= H (else
+ * OMNIGS_E_INVALID). Buffers as for omnigs_l1_loss. */
+omnigs_status omnigs_l1_loss_rows(const omnigs_config *cfg, int32_t row_begin, int32_t row_end, const float *rgb,
+                                  const float *target, float *dL_drgb, float *loss, void *workspace,
+                                  omnigs_stream_t stream);
+
 /* The same loss and gradient as omnigs_l1_loss without a workspace, for callers that cannot allocate device memory
  * or hand the library any beyond their inputs and outputs (a host application that owns the CUDA allocator or has
  * reserved all device memory, a loop with a fixed memory budget). The paper has no counterpart; this is an interface

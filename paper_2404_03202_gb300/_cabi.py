@@ -62,6 +62,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
         lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
+        lib.omnigs_l1_loss_rows.argtypes = [cfgp, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
         lib.omnigs_l1_loss_static.argtypes = [cfgp, P, P, P, P, P]
         lib.omnigs_l1_loss_static.restype = st
         lib.omnigs_render_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
@@ -72,6 +73,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
         for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_l1_loss",
+                     "omnigs_l1_loss_rows",
                      "omnigs_render_bwd", "omnigs_preprocess_bwd", "omnigs_instance_count", "omnigs_last_error",
                      "omnigs_profiler_enable"):
             getattr(lib, name).restype = st
@@ -148,6 +150,12 @@ def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_n
 def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):
     _check(load().omnigs_l1_loss(ctypes.byref(cfg), _ptr(rgb), _ptr(target), _ptr(dL_drgb), _ptr(loss),
                                  _ptr(workspace), _stream(stream)), "omnigs_l1_loss")
+
+
+def omnigs_l1_loss_rows(cfg, row_begin, row_end, rgb, target, dL_drgb, loss, workspace, stream=None):
+    _check(load().omnigs_l1_loss_rows(ctypes.byref(cfg), int(row_begin), int(row_end), _ptr(rgb), _ptr(target),
+                                      _ptr(dL_drgb), _ptr(loss), _ptr(workspace), _stream(stream)),
+           "omnigs_l1_loss_rows")
 
 
 def omnigs_l1_loss_static(cfg, rgb, target, dL_drgb, loss, stream=None):

@@ -111,7 +111,7 @@ cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_
                               const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
                               const float *out_T, const uint32_t *nc, const float *dL_drgb,
                               omnigs_splat_grad *grads, cudaStream_t stream);
-cudaError_t launch_l1(const omnigs_config &cfg, const float *rgb, const float *target, float *dL_drgb, float *loss,
-                      const WsLayout &L, char *ws, cudaStream_t stream);
+cudaError_t launch_l1(const omnigs_config &cfg, int row_begin, int row_end, const float *rgb, const float *target,
+                      float *dL_drgb, float *loss, const WsLayout &L, char *ws, cudaStream_t stream);
 
 }  // namespace omnigs

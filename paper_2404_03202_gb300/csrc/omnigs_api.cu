@@ -179,7 +179,20 @@ omnigs_status omnigs_l1_loss(const omnigs_config* cfg, const float* rgb, const f
     if (!rgb || !target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
     if (!aligned(rgb, 16) || !aligned(target, 16) || !aligned(dL_drgb, 16)) return OMNIGS_E_INVALID;
     const WsLayout L = ws_layout(*cfg, 0, 0);  // the header and the loss partials sit at fixed offsets
-    return from_cuda(launch_l1(*cfg, rgb, target, dL_drgb, loss, L, (char*)workspace, (cudaStream_t)stream));
+    return from_cuda(launch_l1(*cfg, 0, cfg->height, rgb, target, dL_drgb, loss, L, (char*)workspace,
+                               (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_l1_loss_rows(const omnigs_config* cfg, int32_t row_begin, int32_t row_end, const float* rgb,
+                                  const float* target, float* dL_drgb, float* loss, void* workspace,
+                                  omnigs_stream_t stream) {
+    if (!valid_cfg(cfg)) return OMNIGS_E_INVALID;
+    if (row_begin < 0 || row_end > cfg->height || row_begin >= row_end) return OMNIGS_E_INVALID;
+    if (!rgb || !target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (!aligned(rgb, 16) || !aligned(target, 16) || !aligned(dL_drgb, 16)) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, 0, 0);
+    return from_cuda(launch_l1(*cfg, row_begin, row_end, rgb, target, dL_drgb, loss, L, (char*)workspace,
+                               (cudaStream_t)stream));
 }
 
 omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,

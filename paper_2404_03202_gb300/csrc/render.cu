@@ -392,12 +392,20 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-// mean |rgb - target| and its gradient; float4 over the [V, 3, H, W] buffers (size a multiple of 4)
+// mean |rgb - target| over the image rows [row_begin, row_end) and its gradient (0 outside those rows); float4 over
+// the [V, 3, H, W] buffers (W a multiple of 4, so a float4 never straddles two rows).
 __global__ void __launch_bounds__(kLossThreads)
 l1_kernel(size_t n4, const float4* __restrict__ rgb, const float4* __restrict__ target, float4* __restrict__ dL,
-          float inv_total, float* __restrict__ partials) {
+          float inv_total, unsigned w4, unsigned height, unsigned row_begin, unsigned row_end,
+          float* __restrict__ partials) {
     float acc = 0.f;
+    const bool all_rows = row_begin == 0 && row_end == height;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned y = all_rows ? 0u : (unsigned)((i / w4) % height);
+        if (!all_rows && (y < row_begin || y >= row_end)) {
+            dL[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         const float4 a = __ldg(rgb + i), b = __ldg(target + i);
         const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
         acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
@@ -473,16 +481,19 @@ cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_
     }
 }
 
-cudaError_t launch_l1(const omnigs_config& cfg, const float* rgb, const float* target, float* dL_drgb, float* loss,
-                      const WsLayout& L, char* ws, cudaStream_t stream) {
+cudaError_t launch_l1(const omnigs_config& cfg, int row_begin, int row_end, const float* rgb, const float* target,
+                      float* dL_drgb, float* loss, const WsLayout& L, char* ws, cudaStream_t stream) {
     const size_t total = (size_t)cfg.num_views * 3 * cfg.height * cfg.width;
-    const float inv = (float)(1.0 / (double)total);
+    const size_t counted = (size_t)cfg.num_views * 3 * (size_t)(row_end - row_begin) * cfg.width;
+    const float inv = counted ? (float)(1.0 / (double)counted) : 0.f;
     float* partials = reinterpret_cast<float*>(ws + L.loss_partials);
     {
         ProfScope prof("l1_loss", stream);
         l1_kernel<<<L.loss_blocks, kLossThreads, 0, stream>>>(total / 4, reinterpret_cast<const float4*>(rgb),
                                                               reinterpret_cast<const float4*>(target),
-                                                              reinterpret_cast<float4*>(dL_drgb), inv, partials);
+                                                              reinterpret_cast<float4*>(dL_drgb), inv,
+                                                              (unsigned)(cfg.width / 4), (unsigned)cfg.height,
+                                                              (unsigned)row_begin, (unsigned)row_end, partials);
     }
     {
         ProfScope prof("l1_finish", stream);

@@ -120,9 +120,14 @@ class Rasterizer:
                             self.ncontrib, self.count_out, stream)
         return self.rgb
 
-    def l1_loss(self, target, stream=None):
-        """mean |rgb - target| (device scalar) and its gradient in self.dL_drgb."""
-        C.omnigs_l1_loss(self.cfg, self.rgb, target, self.dL_drgb, self.loss, self.ws, stream)
+    def l1_loss(self, target, stream=None, rows=None):
+        """mean |rgb - target| (device scalar) and its gradient in self.dL_drgb; with rows = (begin, end) only those
+        image rows count (the others get a zero gradient)."""
+        if rows is None:
+            C.omnigs_l1_loss(self.cfg, self.rgb, target, self.dL_drgb, self.loss, self.ws, stream)
+        else:
+            C.omnigs_l1_loss_rows(self.cfg, rows[0], rows[1], self.rgb, target, self.dL_drgb, self.loss, self.ws,
+                                  stream)
         return self.loss
 
     # ---------------------------------------------------------------- backward

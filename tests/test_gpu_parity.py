@@ -207,3 +207,31 @@ def test_l1_loss_matches_numpy():
     assert abs(loss - np.abs(d).mean()) <= 1e-6 * np.abs(d).mean()
     exp = np.sign(d) / d.size
     assert np.array_equal(r.dL_drgb.cpu().numpy(), exp.astype(np.float32))
+
+
+@pytest.mark.parametrize("rows", [(0, 128), (0, 112), (16, 100)])
+def test_l1_loss_over_a_band_of_rows(rows):
+    """Loss restricted to image rows [begin, end) (the masked bottom band of Sec. 5.2), against float64 numpy."""
+    W, H, V = 256, 128, 2
+    rgb = synth.random_image(V, W, H, 3)
+    tgt = synth.random_image(V, W, H, 4)
+    r = og.Rasterizer(_settings(W, H, V=V))
+    r._ensure(1, 16)
+    r.rgb.copy_(dev(rgb))
+    loss = r.l1_loss(dev(tgt), rows=rows).item()
+    a, b = rows
+    d = rgb.astype(np.float64)[:, :, a:b] - tgt[:, :, a:b]
+    assert abs(loss - np.abs(d).mean()) <= 1e-6 * np.abs(d).mean()
+    exp = np.zeros_like(rgb)
+    exp[:, :, a:b] = (np.sign(d) / d.size).astype(np.float32)
+    assert np.array_equal(r.dL_drgb.cpu().numpy(), exp)
+
+
+def test_l1_loss_rows_rejects_empty_or_outside_bands():
+    r = og.Rasterizer(_settings(64, 32))
+    r._ensure(1, 16)
+    x = torch.zeros_like(r.rgb)
+    for rows in [(5, 5), (-1, 10), (0, 33), (20, 10)]:
+        with pytest.raises(og.OmnigsError) as ei:
+            r.l1_loss(x, rows=rows)
+        assert ei.value.status == C.OMNIGS_E_INVALID
