@@ -87,6 +87,8 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int) -> di
         "sort_downsweep": tp * instances * 16,            # per pass: keys read and written
         "tile_ranges": tiles * 8,                         # one [start, end) pair per tile
         "l1_loss": X * 3 * 12,                            # image and target in, dL/dC out
+        "dssim_fwd": X * 3 * (8 + 12),                    # image and target in, three sensitivity maps out
+        "dssim_bwd": X * 3 * (12 + 8 + 4),                # sensitivity maps, image and target in, dL/dC out
         "preprocess_bwd": n * (236 + 236 + 8) + P * 48,   # parameters in, their gradients and dL/ds out, 2D grads in
     }
 
@@ -311,7 +313,8 @@ def workload_config(wl, args, settings=None):
             "tile": tile, "pixels_per_thread": (settings.pixels_per_thread or "default") if settings else None,
             "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
-            "l2": "inputs larger than L2 (several GB touched per step)"}
+            "l2": "inputs larger than L2 (several GB touched per step)",
+            "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1"}
 
 
 def main():
@@ -325,6 +328,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--loss", default="l1", choices=["l1", "dssim"],
+                    help="photometric loss: L1 (lambda = 0 in Eq. 17) or L1 + D-SSIM with lambda = 0.2")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -378,10 +383,19 @@ def main():
     r = og.Rasterizer(settings, device=dev, capacity=int(count * 1.05) + 4096, grow=False)
 
     loss_rows = wl.get("loss_rows")
+    dssim_scratch = None
+    if args.loss == "dssim":
+        dssim_scratch = torch.empty(C.omnigs_dssim_scratch_size(r.cfg), dtype=torch.uint8, device=dev)
+
+    def loss_fn(tgt):
+        if dssim_scratch is not None:
+            C.omnigs_dssim_loss(r.cfg, 0.2, r.rgb, tgt, r.dL_drgb, r.loss, dssim_scratch)
+        else:
+            r.l1_loss(tgt, rows=loss_rows)
 
     def step():
         r.forward(*params, vm)
-        r.l1_loss(target, rows=loss_rows)
+        loss_fn(target)
         r.backward()
 
     for _ in range(args.warmup):
@@ -458,7 +472,7 @@ def main():
             dev_vm.copy_(host_vm, non_blocking=True)
             dev_target.copy_(host_target, non_blocking=True)
             r.forward(*dev_params, dev_vm)
-            r.l1_loss(dev_target, rows=loss_rows)
+            loss_fn(dev_target)
             grads = r.backward()
             for k in out_names:
                 host_out[k].copy_(grads[k], non_blocking=True)

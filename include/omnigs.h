@@ -157,6 +157,16 @@ omnigs_status omnigs_l1_loss_rows(const omnigs_config *cfg, int32_t row_begin, i
                                   const float *target, float *dL_drgb, float *loss, void *workspace,
                                   omnigs_stream_t stream);
 
+/* Photometric loss with its D-SSIM term, Eq. 17: L = (1 - lambda) mean|rgb - target| + lambda (1 - SSIM), SSIM the
+ * mean over [V, 3, H, W] of the per-pixel structural similarity of each colour plane with an 11 x 11 Gaussian window
+ * (sigma 1.5, normalised; zero padding at the image border), C1 = 0.01^2, C2 = 0.03^2 (the conventions of the 3DGS
+ * renderer the paper builds on; lambda = 0.2 there). Writes loss [1] and dL_drgb [V, 3, H, W] (device). lambda must
+ * lie in [0, 1]. scratch: device buffer of omnigs_dssim_scratch_size(cfg) bytes, 256-byte aligned, owned by the
+ * caller, no initialisation needed; calls sharing one scratch must not overlap on the GPU. */
+size_t omnigs_dssim_scratch_size(const omnigs_config *cfg);
+omnigs_status omnigs_dssim_loss(const omnigs_config *cfg, float lambda, const float *rgb, const float *target,
+                                float *dL_drgb, float *loss, void *scratch, omnigs_stream_t stream);
+
 /* The same loss and gradient as omnigs_l1_loss without a workspace, for callers that cannot allocate device memory
  * or hand the library any beyond their inputs and outputs (a host application that owns the CUDA allocator or has
  * reserved all device memory, a loop with a fixed memory budget). The paper has no counterpart; this is an interface

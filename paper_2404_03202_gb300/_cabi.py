@@ -64,6 +64,9 @@ def load() -> ctypes.CDLL:
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
         lib.omnigs_l1_loss_rows.argtypes = [cfgp, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
         lib.omnigs_l1_loss_static.argtypes = [cfgp, P, P, P, P, P]
+        lib.omnigs_dssim_scratch_size.argtypes = [cfgp]
+        lib.omnigs_dssim_scratch_size.restype = ctypes.c_size_t
+        lib.omnigs_dssim_loss.argtypes = [cfgp, ctypes.c_float, P, P, P, P, P, P]
         lib.omnigs_l1_loss_static.restype = st
         lib.omnigs_render_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_preprocess_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
@@ -73,7 +76,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
         for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_l1_loss",
-                     "omnigs_l1_loss_rows",
+                     "omnigs_l1_loss_rows", "omnigs_dssim_loss",
                      "omnigs_render_bwd", "omnigs_preprocess_bwd", "omnigs_instance_count", "omnigs_last_error",
                      "omnigs_profiler_enable"):
             getattr(lib, name).restype = st
@@ -156,6 +159,15 @@ def omnigs_l1_loss_rows(cfg, row_begin, row_end, rgb, target, dL_drgb, loss, wor
     _check(load().omnigs_l1_loss_rows(ctypes.byref(cfg), int(row_begin), int(row_end), _ptr(rgb), _ptr(target),
                                       _ptr(dL_drgb), _ptr(loss), _ptr(workspace), _stream(stream)),
            "omnigs_l1_loss_rows")
+
+
+def omnigs_dssim_scratch_size(cfg) -> int:
+    return int(load().omnigs_dssim_scratch_size(ctypes.byref(cfg)))
+
+
+def omnigs_dssim_loss(cfg, lam, rgb, target, dL_drgb, loss, scratch, stream=None):
+    _check(load().omnigs_dssim_loss(ctypes.byref(cfg), float(lam), _ptr(rgb), _ptr(target), _ptr(dL_drgb),
+                                    _ptr(loss), _ptr(scratch), _stream(stream)), "omnigs_dssim_loss")
 
 
 def omnigs_l1_loss_static(cfg, rgb, target, dL_drgb, loss, stream=None):

@@ -113,5 +113,8 @@ cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_
                               omnigs_splat_grad *grads, cudaStream_t stream);
 cudaError_t launch_l1(const omnigs_config &cfg, int row_begin, int row_end, const float *rgb, const float *target,
                       float *dL_drgb, float *loss, const WsLayout &L, char *ws, cudaStream_t stream);
+size_t dssim_scratch_bytes(const omnigs_config &cfg);
+cudaError_t launch_dssim(const omnigs_config &cfg, float lambda, const float *rgb, const float *target, float *dL,
+                         float *loss, char *scratch, cudaStream_t stream);
 
 }  // namespace omnigs

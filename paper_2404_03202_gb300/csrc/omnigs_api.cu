@@ -195,6 +195,18 @@ omnigs_status omnigs_l1_loss_rows(const omnigs_config* cfg, int32_t row_begin, i
                                (cudaStream_t)stream));
 }
 
+size_t omnigs_dssim_scratch_size(const omnigs_config* cfg) {
+    if (!valid_cfg(cfg)) return 0;
+    return dssim_scratch_bytes(*cfg);
+}
+
+omnigs_status omnigs_dssim_loss(const omnigs_config* cfg, float lambda, const float* rgb, const float* target,
+                                float* dL_drgb, float* loss, void* scratch, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !(lambda >= 0.f && lambda <= 1.f)) return OMNIGS_E_INVALID;
+    if (!rgb || !target || !dL_drgb || !loss || !scratch || !aligned(scratch, 256)) return OMNIGS_E_INVALID;
+    return from_cuda(launch_dssim(*cfg, lambda, rgb, target, dL_drgb, loss, (char*)scratch, (cudaStream_t)stream));
+}
+
 omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
                                 const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
                                 const float* out_T, const uint32_t* ncontrib, const float* dL_drgb,
