@@ -133,8 +133,7 @@ def densify(raw: dict, m: dict, v: dict, accum, count, max_radius, normals, cfg:
 
     for g in range(n):
         p = {k: raw[k][g] for k in raw}
-        avg = accum[g] / count[g] if count[g] > 0 else 0.0
-        hot = avg >= cfg.grad_threshold
+        hot = count[g] > 0 and accum[g] / count[g] >= cfg.grad_threshold  # never seen: never hot
         big = np.exp(p["log_scales"]).max() > cfg.percent_dense * cfg.extent
         clone, split = hot and not big, hot and big
         keep = not split and not pruned(p["logit_opacity"], p["log_scales"]) and not (
