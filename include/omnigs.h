@@ -207,6 +207,68 @@ omnigs_status omnigs_instance_count(const void *workspace, int64_t *count, omnig
  * `stream`; also reports a pending CUDA error as OMNIGS_E_CUDA. */
 omnigs_status omnigs_last_error(void *workspace, omnigs_stream_t stream);
 
+/* ---------------------------------------------------------------- reconstruction loop (Sec. 4, Algorithm 1)
+ *
+ * The optimiser keeps each Gaussian as one row of P = 11 + 3K raw floats: mean (3), log-scale (3), quaternion (4,
+ * normalised only when used), logit-opacity (1), SH coefficients (3K, laid out [K][3]). Adam moments m and v share
+ * that layout. The renderer reads the activated arrays means [n, 3], scales = exp(log-scale) [n, 3], quats [n, 4],
+ * opacity = sigmoid(logit) [n], sh [n, K, 3]. The densification thresholds live in the paper's missing supplement;
+ * the defaults a caller would pass are those of the 3DGS renderer the paper says its strategy resembles. */
+typedef struct {
+    float lr_means, lr_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest; /* per parameter group */
+    float beta1, beta2, eps;                                               /* Adam */
+} omnigs_adam_config;
+
+typedef struct {
+    float grad_threshold;    /* densify when mean |dL/ds| over the views that saw the Gaussian reaches this */
+    float percent_dense;     /* clone when the largest scale is at most percent_dense * extent, else split */
+    float extent;            /* scene extent (world units) */
+    float min_opacity;       /* prune below this opacity */
+    float max_scale_frac;    /* prune when the largest scale exceeds max_scale_frac * extent */
+    float max_screen_radius; /* prune an original whose instance half-extent exceeded this (pixels) */
+} omnigs_densify_config;
+
+/* "Advance optimizer by one step" (Algorithm 1): Adam with bias correction (step counts from 1) on the raw rows,
+ * from gradients with respect to the activated parameters (the outputs of omnigs_preprocess_bwd; the chain rule
+ * through exp and sigmoid is applied here). Updates params, m, v in place and writes the activated arrays for the
+ * next render. All pointers are device buffers; n = 0 enqueues nothing. */
+omnigs_status omnigs_adam_step(int64_t n, int32_t K, const omnigs_adam_config *cfg, int64_t step, float *params,
+                               float *m, float *v, const float *d_means, const float *d_scales, const float *d_quats,
+                               const float *d_opacity, const float *d_sh, float *means, float *scales, float *quats,
+                               float *opacity, float *sh, omnigs_stream_t stream);
+
+/* Writes the activated arrays of `params` (after a densification, before the next render). */
+omnigs_status omnigs_publish_params(int64_t n, int32_t K, const float *params, float *means, float *scales,
+                                    float *quats, float *opacity, float *sh, omnigs_stream_t stream);
+
+/* Densification statistics of one render (Sec. 4: densify by dL/ds): for every view in which Gaussian g has tile
+ * instances, accum[g] += |dL/ds| with dL/ds = dL/dp diag(W/2, H/2) (Eq. 4) from the 2D gradients of
+ * omnigs_render_bwd, count[g] += 1, and max_radius[g] = max(max_radius[g], radius_x, radius_y). accum, count,
+ * max_radius [n] are device buffers the caller zeroes after each densification. */
+omnigs_status omnigs_densify_stats(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
+                                   const omnigs_splat_grad *grads, float *accum, int32_t *count, float *max_radius,
+                                   omnigs_stream_t stream);
+
+/* Bytes of device workspace omnigs_densify needs for n Gaussians. */
+size_t omnigs_densify_workspace_size(int64_t n);
+
+/* Densify and prune (Algorithm 1). A Gaussian whose mean |dL/ds| reaches grad_threshold is cloned if its largest
+ * scale is at most percent_dense * extent and split into two otherwise. A split child has mean m + R(q) (S z), with
+ * z = normals[g][k] (standard normal draws given by the caller), scales S / 1.6 and the parent's rotation, opacity
+ * and SH; the parent is removed. Pruned: any row whose opacity is below min_opacity or whose largest scale exceeds
+ * max_scale_frac * extent, and an original whose max_radius exceeded max_screen_radius. Rows out, for each original
+ * in index order: itself if kept, its clone, its two children. Moments follow kept originals and are zero for new
+ * rows. params_out, m_out, v_out need room for 2n rows; *n_out (device, int64) receives the row count. */
+omnigs_status omnigs_densify(int64_t n, int32_t K, const omnigs_densify_config *cfg, const float *params,
+                             const float *m, const float *v, const float *accum, const int32_t *count,
+                             const float *max_radius, const float *normals, float *params_out, float *m_out,
+                             float *v_out, int64_t *n_out, void *workspace, omnigs_stream_t stream);
+
+/* "Reset large o" (Algorithm 1): logit-opacity <- min(logit-opacity, logit(value)) with its Adam moments zeroed;
+ * opacity (optional, may be NULL) receives the activated opacities. 0 < value < 1. */
+omnigs_status omnigs_reset_opacity(int64_t n, int32_t K, float value, float *params, float *m, float *v,
+                                   float *opacity, omnigs_stream_t stream);
+
 /* Kernel timing. While enabled, every stage the library runs (one kernel, or a few back-to-back kernels under one
  * name) is bracketed by CUDA events on its launching stream. omnigs_profiler_collect synchronises those events,
  * writes up to `max` per-stage totals (kernel launches and summed milliseconds, in first-launch order) and clears

@@ -28,6 +28,16 @@ class omnigs_config(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32)]
 
 
+class omnigs_adam_config(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("lr_means", "lr_scales", "lr_quats", "lr_opacity", "lr_sh_dc",
+                                              "lr_sh_rest", "beta1", "beta2", "eps")]
+
+
+class omnigs_densify_config(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("grad_threshold", "percent_dense", "extent", "min_opacity",
+                                              "max_scale_frac", "max_screen_radius")]
+
+
 class omnigs_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -72,11 +82,20 @@ def load() -> ctypes.CDLL:
         lib.omnigs_preprocess_bwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.omnigs_instance_count.argtypes = [P, ctypes.POINTER(i64), P]
         lib.omnigs_last_error.argtypes = [P, P]
+        i32 = ctypes.c_int32
+        lib.omnigs_adam_step.argtypes = [i64, i32, ctypes.POINTER(omnigs_adam_config), i64] + [P] * 13 + [P]
+        lib.omnigs_publish_params.argtypes = [i64, i32] + [P] * 6 + [P]
+        lib.omnigs_densify_stats.argtypes = [cfgp, i64, P, P, P, P, P, P]
+        lib.omnigs_densify_workspace_size.argtypes = [i64]
+        lib.omnigs_densify_workspace_size.restype = ctypes.c_size_t
+        lib.omnigs_densify.argtypes = [i64, i32, ctypes.POINTER(omnigs_densify_config)] + [P] * 12 + [P]
+        lib.omnigs_reset_opacity.argtypes = [i64, i32, ctypes.c_float, P, P, P, P, P]
         lib.omnigs_profiler_enable.argtypes = [ctypes.c_int]
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
         for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_l1_loss",
-                     "omnigs_l1_loss_rows", "omnigs_dssim_loss",
+                     "omnigs_l1_loss_rows", "omnigs_dssim_loss", "omnigs_adam_step", "omnigs_publish_params",
+                     "omnigs_densify_stats", "omnigs_densify", "omnigs_reset_opacity",
                      "omnigs_render_bwd", "omnigs_preprocess_bwd", "omnigs_instance_count", "omnigs_last_error",
                      "omnigs_profiler_enable"):
             getattr(lib, name).restype = st
@@ -209,3 +228,39 @@ def omnigs_profiler_collect(max_kernels: int = 64) -> list:
     arr = (omnigs_kernel_time * max_kernels)()
     k = load().omnigs_profiler_collect(arr, max_kernels)
     return [(arr[i].name.decode(), int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(k, max_kernels))]
+
+
+# ------------------------------------------------------------------ reconstruction loop (Algorithm 1)
+
+def omnigs_adam_step(n, K, cfg, step, params, m, v, d_means, d_scales, d_quats, d_opacity, d_sh, means, scales,
+                     quats, opacity, sh, stream=None):
+    _check(load().omnigs_adam_step(n, K, ctypes.byref(cfg), int(step), _ptr(params), _ptr(m), _ptr(v),
+                                   _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacity), _ptr(d_sh),
+                                   _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity), _ptr(sh), _stream(stream)),
+           "omnigs_adam_step")
+
+
+def omnigs_publish_params(n, K, params, means, scales, quats, opacity, sh, stream=None):
+    _check(load().omnigs_publish_params(n, K, _ptr(params), _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity),
+                                        _ptr(sh), _stream(stream)), "omnigs_publish_params")
+
+
+def omnigs_densify_stats(cfg, n, splats, grads, accum, count, max_radius, stream=None):
+    _check(load().omnigs_densify_stats(ctypes.byref(cfg), n, _ptr(splats), _ptr(grads), _ptr(accum), _ptr(count),
+                                       _ptr(max_radius), _stream(stream)), "omnigs_densify_stats")
+
+
+def omnigs_densify_workspace_size(n) -> int:
+    return int(load().omnigs_densify_workspace_size(n))
+
+
+def omnigs_densify(n, K, cfg, params, m, v, accum, count, max_radius, normals, params_out, m_out, v_out, n_out,
+                   workspace, stream=None):
+    _check(load().omnigs_densify(n, K, ctypes.byref(cfg), _ptr(params), _ptr(m), _ptr(v), _ptr(accum), _ptr(count),
+                                 _ptr(max_radius), _ptr(normals), _ptr(params_out), _ptr(m_out), _ptr(v_out),
+                                 _ptr(n_out), _ptr(workspace), _stream(stream)), "omnigs_densify")
+
+
+def omnigs_reset_opacity(n, K, value, params, m, v, opacity=None, stream=None):
+    _check(load().omnigs_reset_opacity(n, K, float(value), _ptr(params), _ptr(m), _ptr(v), _ptr(opacity),
+                                       _stream(stream)), "omnigs_reset_opacity")

@@ -113,6 +113,22 @@ cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_
                               omnigs_splat_grad *grads, cudaStream_t stream);
 cudaError_t launch_l1(const omnigs_config &cfg, int row_begin, int row_end, const float *rgb, const float *target,
                       float *dL_drgb, float *loss, const WsLayout &L, char *ws, cudaStream_t stream);
+size_t densify_workspace_bytes(int64_t n);
+cudaError_t launch_adam(int64_t n, int K, const omnigs_adam_config &cfg, int64_t step, float *params, float *m,
+                        float *v, const float *d_means, const float *d_scales, const float *d_quats,
+                        const float *d_opacity, const float *d_sh, float *means, float *scales, float *quats,
+                        float *opacity, float *sh, cudaStream_t stream);
+cudaError_t launch_publish(int64_t n, int K, const float *params, float *means, float *scales, float *quats,
+                           float *opacity, float *sh, cudaStream_t stream);
+cudaError_t launch_densify_stats(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
+                                 const omnigs_splat_grad *grads, float *accum, int *count, float *max_radius,
+                                 cudaStream_t stream);
+cudaError_t launch_densify(int64_t n, int K, const omnigs_densify_config &cfg, const float *params, const float *m,
+                           const float *v, const float *accum, const int *count, const float *max_radius,
+                           const float *normals, float *params_out, float *m_out, float *v_out, long long *n_out,
+                           char *ws, cudaStream_t stream);
+cudaError_t launch_reset_opacity(int64_t n, int K, float value, float *params, float *m, float *v, float *opacity,
+                                 cudaStream_t stream);
 size_t dssim_scratch_bytes(const omnigs_config &cfg);
 cudaError_t launch_dssim(const omnigs_config &cfg, float lambda, const float *rgb, const float *target, float *dL,
                          float *loss, char *scratch, cudaStream_t stream);

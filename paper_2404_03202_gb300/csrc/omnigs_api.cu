@@ -207,6 +207,73 @@ omnigs_status omnigs_dssim_loss(const omnigs_config* cfg, float lambda, const fl
     return from_cuda(launch_dssim(*cfg, lambda, rgb, target, dL_drgb, loss, (char*)scratch, (cudaStream_t)stream));
 }
 
+namespace {
+bool valid_rows(int64_t n, int32_t K) {
+    return n >= 0 && n < (1ll << 31) && (K == 1 || K == 4 || K == 9 || K == 16);
+}
+}  // namespace
+
+omnigs_status omnigs_adam_step(int64_t n, int32_t K, const omnigs_adam_config* cfg, int64_t step, float* params,
+                               float* m, float* v, const float* d_means, const float* d_scales, const float* d_quats,
+                               const float* d_opacity, const float* d_sh, float* means, float* scales, float* quats,
+                               float* opacity, float* sh, omnigs_stream_t stream) {
+    if (!cfg || !valid_rows(n, K) || step < 1) return OMNIGS_E_INVALID;
+    if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
+        return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!params || !m || !v || !d_means || !d_scales || !d_quats || !d_opacity || !d_sh || !means || !scales ||
+        !quats || !opacity || !sh)
+        return OMNIGS_E_INVALID;
+    return from_cuda(launch_adam(n, K, *cfg, step, params, m, v, d_means, d_scales, d_quats, d_opacity, d_sh, means,
+                                 scales, quats, opacity, sh, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_publish_params(int64_t n, int32_t K, const float* params, float* means, float* scales,
+                                    float* quats, float* opacity, float* sh, omnigs_stream_t stream) {
+    if (!valid_rows(n, K)) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!params || !means || !scales || !quats || !opacity || !sh) return OMNIGS_E_INVALID;
+    return from_cuda(launch_publish(n, K, params, means, scales, quats, opacity, sh, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_densify_stats(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
+                                   const omnigs_splat_grad* grads, float* accum, int32_t* count, float* max_radius,
+                                   omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!splats || !grads || !accum || !count || !max_radius || !aligned(splats, 16) || !aligned(grads, 16))
+        return OMNIGS_E_INVALID;
+    return from_cuda(launch_densify_stats(*cfg, n, splats, grads, accum, count, max_radius, (cudaStream_t)stream));
+}
+
+size_t omnigs_densify_workspace_size(int64_t n) {
+    if (n < 0 || n >= (1ll << 31)) return 0;
+    return densify_workspace_bytes(n);
+}
+
+omnigs_status omnigs_densify(int64_t n, int32_t K, const omnigs_densify_config* cfg, const float* params,
+                             const float* m, const float* v, const float* accum, const int32_t* count,
+                             const float* max_radius, const float* normals, float* params_out, float* m_out,
+                             float* v_out, int64_t* n_out, void* workspace, omnigs_stream_t stream) {
+    if (!cfg || !valid_rows(n, K) || !n_out) return OMNIGS_E_INVALID;
+    if (!(cfg->extent > 0.f)) return OMNIGS_E_INVALID;
+    if (n == 0) return from_cuda(cudaMemsetAsync(n_out, 0, sizeof(int64_t), (cudaStream_t)stream));
+    if (!params || !m || !v || !accum || !count || !max_radius || !normals || !params_out || !m_out || !v_out ||
+        !workspace || !aligned(workspace, 256))
+        return OMNIGS_E_INVALID;
+    return from_cuda(launch_densify(n, K, *cfg, params, m, v, accum, count, max_radius, normals, params_out, m_out,
+                                    v_out, reinterpret_cast<long long*>(n_out), (char*)workspace,
+                                    (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_reset_opacity(int64_t n, int32_t K, float value, float* params, float* m, float* v,
+                                   float* opacity, omnigs_stream_t stream) {
+    if (!valid_rows(n, K) || !(value > 0.f && value < 1.f)) return OMNIGS_E_INVALID;
+    if (n == 0) return OMNIGS_OK;
+    if (!params || !m || !v) return OMNIGS_E_INVALID;
+    return from_cuda(launch_reset_opacity(n, K, value, params, m, v, opacity, (cudaStream_t)stream));
+}
+
 omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
                                 const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
                                 const float* out_T, const uint32_t* ncontrib, const float* dL_drgb,
