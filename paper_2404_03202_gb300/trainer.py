@@ -7,7 +7,7 @@ one step. Every step runs in the CUDA library; this module owns the buffers and 
 The optimiser state is one row of P = 11 + 3K raw floats per Gaussian (mean, log-scale, quaternion, logit-opacity,
 SH), with Adam moments of the same layout; the renderer reads the activated arrays the Adam step publishes. As in the
 3DGS loop the paper follows, an iteration that densifies does not also take an optimiser step (the rows it would
-update have just been rebuilt).
+update have just been rebuilt), and the prune by screen-space size only starts after the first opacity reset.
 """
 from __future__ import annotations
 
@@ -51,11 +51,11 @@ class TrainConfig:
         a.beta1, a.beta2, a.eps = self.beta1, self.beta2, self.eps
         return a
 
-    def densify(self, extent: float) -> C.omnigs_densify_config:
+    def densify(self, extent: float, screen_limit: bool = True) -> C.omnigs_densify_config:
         d = C.omnigs_densify_config()
         d.grad_threshold, d.percent_dense, d.extent = self.grad_threshold, self.percent_dense, extent
-        d.min_opacity, d.max_scale_frac, d.max_screen_radius = (self.min_opacity, self.max_scale_frac,
-                                                                self.max_screen_radius)
+        d.min_opacity, d.max_scale_frac = self.min_opacity, self.max_scale_frac
+        d.max_screen_radius = self.max_screen_radius if screen_limit else float("inf")
         return d
 
 
@@ -137,8 +137,10 @@ class Trainer:
         mo, vo = torch.empty_like(po), torch.empty_like(po)
         n_out = torch.zeros(1, dtype=torch.int64, device=mdl.params.device)
         ws = torch.empty(max(C.omnigs_densify_workspace_size(n), 256), dtype=torch.uint8, device=mdl.params.device)
-        C.omnigs_densify(n, mdl.K, self.cfg.densify(self.extent), mdl.params, mdl.m, mdl.v, mdl.accum, mdl.count,
-                         mdl.max_radius, normals, po, mo, vo, n_out, ws)
+        # as in the 3DGS loop, the screen-size prune starts after the first opacity reset
+        screen_limit = self.iteration > self.cfg.opacity_reset_interval
+        C.omnigs_densify(n, mdl.K, self.cfg.densify(self.extent, screen_limit), mdl.params, mdl.m, mdl.v, mdl.accum,
+                         mdl.count, mdl.max_radius, normals, po, mo, vo, n_out, ws)
         k = int(n_out.item())
         mdl._set_rows(po[:k].clone(), mo[:k].clone(), vo[:k].clone())
         return k
