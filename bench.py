@@ -304,6 +304,43 @@ def serving_benchmark(dev, count: int = 96, lanes: int = 4, max_batch: int = 8) 
     return out
 
 
+def train_loop_benchmark(dev, scene, vm, settings, target, iters: int = 20) -> dict:
+    """Algorithm 1 on the device for the same views: Trainer iterations (render, Eq. 17 with D-SSIM, adjoint,
+    densification statistics, Adam), then one densify-and-prune pass timed on its own."""
+    import torch
+    from paper_2404_03202_gb300 import _cabi as C
+    from paper_2404_03202_gb300.trainer import GaussianModel, TrainConfig, Trainer
+    cfg = TrainConfig(densify_from=10 ** 9, opacity_reset_interval=10 ** 9)
+    tr = Trainer(GaussianModel.from_scene(scene, device=dev), settings, cfg, extent=5.0)
+    for _ in range(3):
+        tr.step(vm, target)
+    torch.cuda.synchronize()
+    C.omnigs_profiler_enable(True)
+    C.omnigs_profiler_collect()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        tr.step(vm, target)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = {p[0]: p[2] / iters for p in C.omnigs_profiler_collect(64)}
+    mdl = tr.model
+    seen = mdl.count > 0
+    tr.cfg.grad_threshold = float(torch.quantile((mdl.accum[seen] / mdl.count[seen]).float(), 0.9).item())
+    n0 = mdl.n
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record()
+    n1 = tr.densify_and_prune()
+    d1.record()
+    torch.cuda.synchronize()
+    C.omnigs_profiler_enable(False)
+    return {"ms_per_iteration": e0.elapsed_time(e1) / iters, "iterations": iters, "loss": "L1 + D-SSIM, lambda 0.2",
+            "adam_step_ms": prof.get("adam_step"), "densify_stats_ms": prof.get("densify_stats"),
+            "dssim_ms": (prof.get("dssim_fwd") or 0) + (prof.get("dssim_bwd") or 0),
+            "densify_and_prune_ms": d0.elapsed_time(d1), "densify_threshold": "90th percentile of mean |dL/ds|",
+            "gaussians_before": n0, "gaussians_after": n1}
+
+
 def workload_config(wl, args, settings=None):
     tile = settings.tile if settings is not None else wl["tile"]
     auto = " (autotuned)" if wl["tile"] == "auto" else ""
@@ -328,6 +365,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-train-loop", action="store_true")
     ap.add_argument("--loss", default="l1", choices=["l1", "dssim"],
                     help="photometric loss: L1 (lambda = 0 in Eq. 17) or L1 + D-SSIM with lambda = 0.2")
     args = ap.parse_args()
@@ -550,6 +588,14 @@ def main():
             stages[name] = {"ms": ms_step}
 
     # ---------------------------------------------------------------- CPU baseline (oracle), rank 0, N = 1
+    # ---------------------------------------------------------------- Algorithm 1 iterations (Adam, densification)
+    train_loop = None
+    if rank == 0 and world == 1 and not args.no_train_loop:
+        try:
+            train_loop = train_loop_benchmark(dev, scene, vm, settings, target)
+        except Exception as e:  # reported, never hidden
+            train_loop = {"failed": f"{type(e).__name__}: {e}"}
+
     # ---------------------------------------------------------------- serving loop (forward only), rank 0, N = 1
     serve = None
     if rank == 0 and world == 1 and not args.no_serving:
@@ -580,7 +626,8 @@ def main():
                                                       "examined_pairs_per_step": examined,
                                                       "contributing_pairs_per_step": contrib},
                "gpu_launches": kernel_launches * args.steps, "stages": stages,
-               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "serving": serve}
+               "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "serving": serve,
+               "train_loop": train_loop}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
