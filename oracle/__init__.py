@@ -57,6 +57,7 @@ def _load():
         lib.orc_bin_sort.restype = i64
         lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
+        lib.orc_set_camera.argtypes = [i32, f64, f64, f64, f64]
         lib.orc_preprocess_bwd.argtypes = [i64, i32, i32, i32, i32, f64, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -65,6 +66,19 @@ def _load():
 def _p(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def pinhole(fx: float, fy: float, cx: float, cy: float) -> dict:
+    """A pinhole camera (Eq. 2) for the `camera` argument of the stage functions (None = equirectangular)."""
+    return dict(fx=float(fx), fy=float(fy), cx=float(cx), cy=float(cy))
+
+
+def _camera(camera):
+    lib = _load()
+    if camera is None:
+        lib.orc_set_camera(0, 0.0, 0.0, 0.0, 0.0)
+    else:
+        lib.orc_set_camera(1, camera["fx"], camera["fy"], camera["cx"], camera["cy"])
 
 
 def _f32(a):
@@ -112,9 +126,10 @@ def quat_to_rot(q) -> np.ndarray:
     return R.reshape(3, 3)
 
 
-def rect(px: float, py: float, rx: int, ry: int, width: int, height: int, tile: int):
+def rect(px: float, py: float, rx: int, ry: int, width: int, height: int, tile: int, camera=None):
     """Tile rectangle (x0, nx, y0, ny) of the instance box (half-extents rx, ry) of one splat."""
     lib = _load()
+    _camera(camera)
     out = np.zeros(4, dtype=np.int64)
     lib.orc_rect(float(px), float(py), int(rx), int(ry), width, height, tile, _p(out))
     return tuple(int(x) for x in out)
@@ -122,9 +137,10 @@ def rect(px: float, py: float, rx: int, ry: int, width: int, height: int, tile: 
 
 # ------------------------------------------------------------------ stages
 
-def preprocess(scene, viewmats, width: int, height: int, near: float = 0.2) -> np.ndarray:
+def preprocess(scene, viewmats, width: int, height: int, near: float = 0.2, camera=None) -> np.ndarray:
     """Per-(view, Gaussian) records [V * N, 16] (field order: see R_* constants)."""
     lib = _load()
+    _camera(camera)
     means, scales, quats, opacity, sh = (_f32(a) for a in scene.arrays())
     vm = _f32(viewmats).reshape(-1, 16)
     V, n = vm.shape[0], means.shape[0]
@@ -142,17 +158,19 @@ def splats_from_records(rec: np.ndarray) -> dict:
                 radius=rec[:, R_RADIUS].astype(np.int32))
 
 
-def count_instances(splats: dict, V: int, width: int, height: int, tile: int) -> int:
+def count_instances(splats: dict, V: int, width: int, height: int, tile: int, camera=None) -> int:
     lib = _load()
+    _camera(camera)
     px, py = _f64(splats["px"]), _f64(splats["py"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
     return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry)))
 
 
-def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None):
+def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None, camera=None):
     """Instances sorted by (view, tile, t_r, Gaussian): returns ranges [V*tiles, 2] and the list of (v*N + g).
     With `tile_mask` ([V*tiles] bool), only the lists of the masked tiles are built."""
     lib = _load()
+    _camera(camera)
     px, py, depth = _f64(splats["px"]), _f64(splats["py"]), _f64(splats["depth"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
     n = px.shape[0] // V
@@ -172,10 +190,11 @@ def _splat9(splats: dict) -> np.ndarray:
 
 
 def blend_fwd(splats: dict, ranges, lst, V: int, width: int, height: int, tile: int, bg=(0.0, 0.0, 0.0),
-              eps: float = 1e-5):
+              eps: float = 1e-5, camera=None):
     """Eqs. 6-8 per pixel over its tile list. Returns rgb [V,3,H,W], T [V,H,W], n_contrib, near-threshold flags; the
     per-pixel number of contributors of the last call is kept in blend_fwd.last_count."""
     lib = _load()
+    _camera(camera)
     sp = _splat9(splats)
     n = sp.shape[0] // V
     bgv = _f64(bg)
@@ -198,9 +217,11 @@ def _i64(a):
     return np.ascontiguousarray(a, dtype=np.int64)
 
 
-def blend_bwd(splats: dict, ranges, lst, dL_drgb, V: int, width: int, height: int, tile: int, bg=(0.0, 0.0, 0.0)):
+def blend_bwd(splats: dict, ranges, lst, dL_drgb, V: int, width: int, height: int, tile: int, bg=(0.0, 0.0, 0.0),
+              camera=None):
     """Exact adjoint of blend_fwd: per-(view, Gaussian) [V*N, 9] = dL/d(px, py, c0, c1, c2, opacity, r, g, b)."""
     lib = _load()
+    _camera(camera)
     sp = _splat9(splats)
     n = sp.shape[0] // V
     bgv = _f64(bg)
@@ -210,9 +231,10 @@ def blend_bwd(splats: dict, ranges, lst, dL_drgb, V: int, width: int, height: in
     return out
 
 
-def preprocess_bwd(scene, viewmats, grad2d, width: int, height: int, near: float = 0.2) -> dict:
+def preprocess_bwd(scene, viewmats, grad2d, width: int, height: int, near: float = 0.2, camera=None) -> dict:
     """Chain rule from screen-space gradients back to means, scales, quats, opacity and SH (Eqs. 18-20)."""
     lib = _load()
+    _camera(camera)
     means, scales, quats, opacity, sh = (_f32(a) for a in scene.arrays())
     vm = _f32(viewmats).reshape(-1, 16)
     V, n = vm.shape[0], means.shape[0]
@@ -229,23 +251,23 @@ def preprocess_bwd(scene, viewmats, grad2d, width: int, height: int, near: float
 # ------------------------------------------------------------------ the whole path
 
 def render(scene, viewmats, width: int, height: int, tile: int = 16, bg=(0.0, 0.0, 0.0), near: float = 0.2,
-           eps: float = 1e-5) -> dict:
+           eps: float = 1e-5, camera=None) -> dict:
     """Forward render of every view: projection, binning, sort by t_r, blending."""
     V = np.asarray(viewmats).reshape(-1, 16).shape[0]
-    rec = preprocess(scene, viewmats, width, height, near)
+    rec = preprocess(scene, viewmats, width, height, near, camera)
     sp = splats_from_records(rec)
-    ranges, lst = bin_sort(sp, V, width, height, tile)
-    rgb, T, nc, nearf = blend_fwd(sp, ranges, lst, V, width, height, tile, bg, eps)
+    ranges, lst = bin_sort(sp, V, width, height, tile, camera=camera)
+    rgb, T, nc, nearf = blend_fwd(sp, ranges, lst, V, width, height, tile, bg, eps, camera)
     return dict(rec=rec, splats=sp, ranges=ranges, list=lst, rgb=rgb, T=T, n_contrib=nc, near=nearf)
 
 
 def render_grad(scene, viewmats, dL_drgb, width: int, height: int, tile: int = 16, bg=(0.0, 0.0, 0.0),
-                near: float = 0.2, fwd: dict | None = None) -> dict:
+                near: float = 0.2, fwd: dict | None = None, camera=None) -> dict:
     """Gradients of sum(dL_drgb * render(...)) with respect to every Gaussian parameter."""
     V = np.asarray(viewmats).reshape(-1, 16).shape[0]
     if fwd is None:
-        fwd = render(scene, viewmats, width, height, tile, bg, near)
-    g2 = blend_bwd(fwd["splats"], fwd["ranges"], fwd["list"], dL_drgb, V, width, height, tile, bg)
-    out = preprocess_bwd(scene, viewmats, g2, width, height, near)
+        fwd = render(scene, viewmats, width, height, tile, bg, near, camera=camera)
+    g2 = blend_bwd(fwd["splats"], fwd["ranges"], fwd["list"], dL_drgb, V, width, height, tile, bg, camera)
+    out = preprocess_bwd(scene, viewmats, g2, width, height, near, camera)
     out["grad2d"] = g2
     return out

@@ -37,6 +37,12 @@
  *     T (1 - alpha) < 1e-4; background bg added with the final T.
  *   - the gradient is the exact derivative of the above (zero where alpha is clamped at 0.99 or a colour at 0).
  *   - pole guard: rho = sqrt(t_x^2 + t_z^2) is replaced by max(rho, 1e-6 t_r) inside J.
+ *
+ * Pinhole camera (Eq. 2, the perspective model of 3DGS the paper contrasts with; selected by orc_set_camera):
+ *   p = (f_x t_x / t_z + c_x, f_y t_y / t_z + c_y); the depth that orders Gaussians is t_z; near cull t_z <= near_r;
+ *   J = [[f_x / t_z, 0, -f_x u / t_z], [0, f_y / t_z, -f_y w / t_z]] with u = clamp(t_x / t_z, +-1.3 W / (2 f_x))
+ *   and w = clamp(t_y / t_z, +-1.3 H / (2 f_y)) (the 3DGS guard that keeps J bounded off screen), while dp/dt, the
+ *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped.
  */
 #include <math.h>
 #include <stdint.h>
@@ -61,6 +67,15 @@ enum { G_PX = 0, G_PY, G_C0, G_C1, G_C2, G_OPAC, G_RED, G_GREEN, G_BLUE, G_LEN }
 
 int orc_record_len(void) { return R_LEN; }
 int orc_grad_len(void) { return G_LEN; }
+
+/* ------------------------------------------------------------------ camera model */
+typedef struct { int model; double fx, fy, cx, cy; } orc_cam;  /* model 0: equirectangular, 1: pinhole */
+static orc_cam g_cam = {0, 0.0, 0.0, 0.0, 0.0};
+
+void orc_set_camera(int model, double fx, double fy, double cx, double cy)
+{
+    g_cam.model = model; g_cam.fx = fx; g_cam.fy = fy; g_cam.cx = cx; g_cam.cy = cy;
+}
 
 /* ------------------------------------------------------------------ Eqs. 3-5: t -> (lon, lat) -> s -> p */
 void orc_project(const double *t, int W, int H, double *lonlat, double *s, double *p)
@@ -129,6 +144,24 @@ static void jacobian_grad(const double *t, int W, int H, double dJ[2][3][3])
         dJ[1][2][k] = -b * ((t[1] * ez + t[2] * ey) / (tr2 * rho) - 2.0 * t[2] * t[1] * dtr[k] / (tr3 * rho)
                             - t[2] * t[1] * drho[k] / (tr2 * rho2));
     }
+}
+
+/* dJ/dt of the pinhole Jacobian (Eq. 2) with its clamped ratios: a clamped ratio is a constant. */
+static void pinhole_jacobian_grad(const double *t, int W, int H, double dJ[2][3][3])
+{
+    double tz = t[2], fx = g_cam.fx, fy = g_cam.fy;
+    double limx = 1.3 * W / (2.0 * fx), limy = 1.3 * H / (2.0 * fy);
+    double u = t[0] / tz, w = t[1] / tz;
+    int cu = u < -limx || u > limx, cw = w < -limy || w > limy;
+    double uc = u < -limx ? -limx : (u > limx ? limx : u), wc = w < -limy ? -limy : (w > limy ? limy : w);
+    memset(dJ, 0, sizeof(double) * 18);
+    dJ[0][0][2] = -fx / (tz * tz);
+    dJ[1][1][2] = -fy / (tz * tz);
+    /* J02 = -fx u / tz: unclamped u = tx / tz gives -fx tx / tz^2 */
+    if (cu) dJ[0][2][2] = fx * uc / (tz * tz);
+    else { dJ[0][2][0] = -fx / (tz * tz); dJ[0][2][2] = 2.0 * fx * t[0] / (tz * tz * tz); }
+    if (cw) dJ[1][2][2] = fy * wc / (tz * tz);
+    else { dJ[1][2][1] = -fy / (tz * tz); dJ[1][2][2] = 2.0 * fy * t[1] / (tz * tz * tz); }
 }
 
 /* ------------------------------------------------------------------ Sec. 3.1: colour from SH (real basis) */
@@ -220,7 +253,7 @@ static void covariance3d(const double *q, const double *s, double *Sig, double *
 /* ------------------------------------------------------------------ per-(view, Gaussian) forward quantities */
 typedef struct {
     int culled;
-    double t[3], tr, p[2], J[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rx, ry, rmargin;
+    double t[3], tr, p[2], J[6], Jp[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rx, ry, rmargin;
     double dir[3], dist, Y[16], rgb_raw[3], rgb[3];
 } orc_fwd;
 
@@ -247,12 +280,30 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
     memcpy(f->Wr, Wr, sizeof(double) * 9);
     /* Eq. 1 */
     for (int i = 0; i < 3; i++) f->t[i] = Wr[i * 3 + 0] * m[0] + Wr[i * 3 + 1] * m[1] + Wr[i * 3 + 2] * m[2] + tcw[i];
-    f->tr = sqrt(f->t[0] * f->t[0] + f->t[1] * f->t[1] + f->t[2] * f->t[2]);
-    if (f->tr <= near_r) { f->culled = 1; return; }
-    /* Eqs. 3-5 and 10-16 */
-    double lonlat[2], sv[2];
-    orc_project(f->t, W, H, lonlat, sv, f->p);
-    orc_jacobian(f->t, W, H, f->J);
+    if (g_cam.model == 1) {
+        /* Eq. 2 and its Jacobian; the depth that orders Gaussians is t_z */
+        double tz = f->t[2];
+        f->tr = tz;
+        if (tz <= near_r) { f->culled = 1; return; }
+        f->p[0] = g_cam.fx * f->t[0] / tz + g_cam.cx;
+        f->p[1] = g_cam.fy * f->t[1] / tz + g_cam.cy;
+        double limx = 1.3 * W / (2.0 * g_cam.fx), limy = 1.3 * H / (2.0 * g_cam.fy);
+        double u = f->t[0] / tz, w = f->t[1] / tz;
+        u = u < -limx ? -limx : (u > limx ? limx : u);
+        w = w < -limy ? -limy : (w > limy ? limy : w);
+        f->J[0] = g_cam.fx / tz; f->J[1] = 0.0; f->J[2] = -g_cam.fx * u / tz;
+        f->J[3] = 0.0; f->J[4] = g_cam.fy / tz; f->J[5] = -g_cam.fy * w / tz;
+        f->Jp[0] = g_cam.fx / tz; f->Jp[1] = 0.0; f->Jp[2] = -g_cam.fx * f->t[0] / (tz * tz);
+        f->Jp[3] = 0.0; f->Jp[4] = g_cam.fy / tz; f->Jp[5] = -g_cam.fy * f->t[1] / (tz * tz);
+    } else {
+        f->tr = sqrt(f->t[0] * f->t[0] + f->t[1] * f->t[1] + f->t[2] * f->t[2]);
+        if (f->tr <= near_r) { f->culled = 1; return; }
+        /* Eqs. 3-5 and 10-16 */
+        double lonlat[2], sv[2];
+        orc_project(f->t, W, H, lonlat, sv, f->p);
+        orc_jacobian(f->t, W, H, f->J);
+        memcpy(f->Jp, f->J, sizeof(f->J));
+    }
     /* Eq. 9: Sigma~ = (J W) Sigma (J W)^T, 2x2 block, plus the low-pass dilation */
     covariance3d(q, s, f->Sig, f->R);
     for (int r = 0; r < 2; r++)
@@ -344,7 +395,12 @@ void orc_rect(double px, double py, int rx, int ry, int W, int H, int T, int64_t
     int64_t TX = W / T, TY = H / T;
     int64_t ix = (int64_t)floor(px), iy = (int64_t)floor(py);
     int64_t x0 = floordiv(ix - rx, T), x1 = floordiv(ix + rx, T);
+    if (g_cam.model == 1) { /* pinhole: columns clipped like rows */
+        if (x0 < 0) x0 = 0;
+        if (x1 > TX - 1) x1 = TX - 1;
+    }
     int64_t nx = x1 - x0 + 1;
+    if (nx < 0) nx = 0;
     if (nx >= TX) { x0 = 0; nx = TX; }
     int64_t y0 = floordiv(iy - ry, T), y1 = floordiv(iy + ry, T);
     if (y0 < 0) y0 = 0;
@@ -451,8 +507,10 @@ static int64_t blend_pixel(int W, double xs, double ys, const double *splat, con
     for (int64_t j = lo; j < hi; j++) {
         const double *sp = splat + 9 * list[j];
         double dx = sp[0] - xs, dy = sp[1] - ys;
-        if (dx >= 0.5 * W) dx -= W;
-        else if (dx < -0.5 * W) dx += W;
+        if (g_cam.model == 0) { /* minimal image across the longitude seam */
+            if (dx >= 0.5 * W) dx -= W;
+            else if (dx < -0.5 * W) dx += W;
+        }
         double q0 = 0.5 * sp[2] * dx * dx, q2 = 0.5 * sp[4] * dy * dy, q1 = sp[3] * dx * dy;
         double power = -q0 - q2 - q1;
         double mag = fabs(q0) + fabs(q1) + fabs(q2);
@@ -593,8 +651,8 @@ void orc_preprocess_bwd(int64_t n, int V, int W, int H, int sh_degree, double ne
             double dt[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
             /* opacity */
             d_opacity[g] += gr[G_OPAC];
-            /* p(t): dp/dt = J */
-            for (int k = 0; k < 3; k++) dt[k] += gr[G_PX] * f.J[k] + gr[G_PY] * f.J[3 + k];
+            /* p(t): dp/dt (the Jacobian itself for the equirectangular camera, Eqs. 11-16) */
+            for (int k = 0; k < 3; k++) dt[k] += gr[G_PX] * f.Jp[k] + gr[G_PY] * f.Jp[3 + k];
             d_screen[2 * g + 0] += gr[G_PX] * W / 2.0;
             d_screen[2 * g + 1] += gr[G_PY] * H / 2.0;
             /* conic = inverse of (a, b; b, c) */
@@ -630,7 +688,8 @@ void orc_preprocess_bwd(int64_t n, int V, int W, int H, int sh_degree, double ne
                     dJ[r * 3 + k] = acc;
                 }
             double dJdt[2][3][3];
-            jacobian_grad(f.t, W, H, dJdt);
+            if (g_cam.model == 1) pinhole_jacobian_grad(f.t, W, H, dJdt);
+            else jacobian_grad(f.t, W, H, dJdt);
             for (int r = 0; r < 2; r++)
                 for (int cc = 0; cc < 3; cc++)
                     for (int k = 0; k < 3; k++) dt[k] += dJ[r * 3 + cc] * dJdt[r][cc][k];
