@@ -42,7 +42,8 @@
  *   p = (f_x t_x / t_z + c_x, f_y t_y / t_z + c_y); the depth that orders Gaussians is t_z; near cull t_z <= near_r;
  *   J = [[f_x / t_z, 0, -f_x u / t_z], [0, f_y / t_z, -f_y w / t_z]] with u = clamp(t_x / t_z, +-1.3 W / (2 f_x))
  *   and w = clamp(t_y / t_z, +-1.3 H / (2 f_y)) (the 3DGS guard that keeps J bounded off screen), while dp/dt, the
- *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped.
+ *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped; centres beyond
+ *   2^23 px are culled (a bound on integer tile arithmetic).
  */
 #include <math.h>
 #include <stdint.h>
@@ -287,6 +288,8 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
         if (tz <= near_r) { f->culled = 1; return; }
         f->p[0] = g_cam.fx * f->t[0] / tz + g_cam.cx;
         f->p[1] = g_cam.fy * f->t[1] / tz + g_cam.cy;
+        /* a bound on the tile arithmetic of any implementation: centres beyond 2^23 px are culled */
+        if (!(fabs(f->p[0]) < 8388608.0 && fabs(f->p[1]) < 8388608.0)) { f->culled = 1; return; }
         double limx = 1.3 * W / (2.0 * g_cam.fx), limy = 1.3 * H / (2.0 * g_cam.fy);
         double u = f->t[0] / tz, w = f->t[1] / tz;
         u = u < -limx ? -limx : (u > limx ? limx : u);
