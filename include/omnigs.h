@@ -52,10 +52,19 @@ typedef struct {
     int32_t pixels_per_thread; /* blend schedule: pixels of one image column each blend thread owns (2, 4 or 8;
                                 * 4 and 8 need tile >= 16); 0 lets the library choose. Results do not depend on
                                 * it beyond the order of floating-point additions in the gradients. */
+    int32_t camera;            /* OMNIGS_CAMERA_EQUIRECT (0): Eqs. 3-5, the paper's camera. OMNIGS_CAMERA_PINHOLE (1):
+                                * Eq. 2, the perspective model of 3DGS: p = (fx tx / tz + cx, fy ty / tz + cy);
+                                * Gaussians are ordered by t_z and culled when t_z <= near_r or |p| >= 2^23; J holds
+                                * t_x / t_z and t_y / t_z within 1.3 half-fields of view (W / (2 fx), H / (2 fy));
+                                * tile columns are clipped like rows and dx is not wrapped. */
+    float fx, fy, cx, cy;      /* pinhole intrinsics in pixels (fx, fy > 0); ignored for the equirectangular camera */
 } omnigs_config;
 
+#define OMNIGS_CAMERA_EQUIRECT 0
+#define OMNIGS_CAMERA_PINHOLE 1
+
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).
- * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H]. (c0, c1, c2): inverse of the 2x2 covariance
+ * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the image). (c0, c1, c2): inverse of the 2x2 covariance
  * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
  * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
  * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the

@@ -63,7 +63,7 @@ struct SplatPos {
 // Splats whose centre is not a point of [0, W] x [0, H] (which the projection never produces) are treated as culled,
 // so malformed input cannot produce a tile index outside the image.
 __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size_t i, int tiles_x, int tiles_y,
-                                             int tile) {
+                                             int tile, bool wrap) {
     const float4 a = __ldg(sp + 3 * i);
     const float4 c = __ldg(sp + 3 * i + 2);
     SplatPos p;
@@ -72,7 +72,10 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
     p.depth = c.y;
     p.rx = __float_as_int(c.z);
     p.ry = __float_as_int(c.w);
-    const bool inside = a.x >= 0.f && a.x <= (float)(tiles_x * tile) && a.y >= 0.f && a.y <= (float)(tiles_y * tile);
+    // the equirectangular projection lands in [0, W] x [0, H]; a pinhole centre may lie off the image (|p| < 2^23)
+    const bool inside = wrap ? (a.x >= 0.f && a.x <= (float)(tiles_x * tile) && a.y >= 0.f &&
+                                a.y <= (float)(tiles_y * tile))
+                             : (fabsf(a.x) < 8388608.f && fabsf(a.y) < 8388608.f);
     if (!inside || p.rx > kMaxRadius || p.ry > kMaxRadius || p.ry < 0) p.rx = 0;
     return p;
 }
@@ -94,14 +97,14 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
 
 __global__ void __launch_bounds__(kBinThreads)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
-                 int tiles_y, int tile, unsigned* __restrict__ block_sums) {
+                 int tiles_y, int tile, int wrap, unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
     const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
     unsigned cnt = 0;
     if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
+        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
-            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile);
+            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
             cnt = (unsigned)(r.nx * r.ny);
         }
     }
@@ -137,7 +140,7 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
 // whole CTA. Instances of a splat are listed row by row, columns in seam order.
 __global__ void __launch_bounds__(kBinThreads)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
-                int tiles_x, int tiles_y, int tile, int rank_bits, const u64* __restrict__ block_offsets,
+                int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, const u64* __restrict__ block_offsets,
                 u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ unsigned s_excl[kBinThreads];
@@ -150,9 +153,9 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
     int rank = 0;
     unsigned tbase = 0;
     if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile);
+        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
-            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile);
+            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
             cnt = (unsigned)(r.nx * r.ny);
             const int64_t v = i / n;
             rank = (int)(i - v * n);
@@ -465,6 +468,7 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
                        uint64_t* keys, int64_t capacity, const WsLayout& L, char* ws, cudaStream_t stream) {
     const int64_t total = n * cfg.num_views;
     const int tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile;
+    const int wrap = cfg.camera == OMNIGS_CAMERA_EQUIRECT;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
     cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
     if (e != cudaSuccess || total == 0) return e;
@@ -485,12 +489,13 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     if (e != cudaSuccess) return e;
     {
         ProfScope prof("bin_count", stream, 2);
-        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, bsums);
+        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, bsums);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream);
-        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, rank_bits_for(n),
+        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, wrap,
+                                                         rank_bits_for(n),
                                                          boffs, reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();

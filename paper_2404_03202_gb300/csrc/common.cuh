@@ -42,12 +42,17 @@ __host__ __device__ inline int floordiv_int(int a, int b) {
 }
 
 // Tiles covered by the box of half-extents (rx, ry) around pixel floor(p): columns x0 .. x0 + nx - 1 modulo the
-// column count (all columns, from 0, once the box is at least as wide as the image), rows clipped to the image.
-__device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_x, int tiles_y, int tile) {
+// column count (all columns, from 0, once the box is at least as wide as the image) when `wrap` (the equirectangular
+// longitude seam), clipped to the image like the rows otherwise (pinhole camera).
+__device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_x, int tiles_y, int tile, bool wrap) {
     Rect R;
     int ix = (int)floorf(px), iy = (int)floorf(py);
     int x0 = floordiv_int(ix - rx, tile), x1 = floordiv_int(ix + rx, tile);
-    int nx = x1 - x0 + 1;
+    if (!wrap) {
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 > tiles_x - 1 ? tiles_x - 1 : x1;
+    }
+    int nx = x1 >= x0 ? x1 - x0 + 1 : 0;
     if (nx >= tiles_x) {
         x0 = 0;
         nx = tiles_x;

@@ -99,6 +99,11 @@ bool valid_cfg(const omnigs_config* c) {
     const int ppt = c->pixels_per_thread;
     if (ppt != 0 && ppt != 2 && ppt != 4 && ppt != 8) return false;
     if (ppt > 2 && c->tile == 8) return false;
+    if (c->camera != OMNIGS_CAMERA_EQUIRECT && c->camera != OMNIGS_CAMERA_PINHOLE) return false;
+    if (c->camera == OMNIGS_CAMERA_PINHOLE &&
+        !(std::isfinite(c->fx) && std::isfinite(c->fy) && c->fx > 0.f && c->fy > 0.f && std::isfinite(c->cx) &&
+          std::isfinite(c->cy)))
+        return false;
     const uint64_t tiles = (uint64_t)(c->width / c->tile) * (uint64_t)(c->height / c->tile) * (uint64_t)c->num_views;
     return tiles < (1ull << 31);
 }

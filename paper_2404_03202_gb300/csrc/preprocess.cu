@@ -94,21 +94,54 @@ __device__ __forceinline__ View load_view(const float* s_view, int v) {
     return w;
 }
 
+// Camera model of the config: the equirectangular camera (Eqs. 3-5) or the pinhole of Eq. 2 with the 3DGS bound on
+// the ratios t_x / t_z and t_y / t_z inside J (limx, limy = 1.3 half-fields of view).
+struct Cam {
+    int pinhole;
+    float fx, fy, cx, cy, limx, limy;
+};
+
+constexpr float kMaxCoord = 8388608.f;  // 2^23: pinhole Gaussians projected beyond this are culled
+
+Cam make_cam(const omnigs_config& cfg) {
+    Cam c{};
+    c.pinhole = cfg.camera == OMNIGS_CAMERA_PINHOLE;
+    if (c.pinhole) {
+        c.fx = cfg.fx; c.fy = cfg.fy; c.cx = cfg.cx; c.cy = cfg.cy;
+        c.limx = 1.3f * (float)cfg.width / (2.f * cfg.fx);
+        c.limy = 1.3f * (float)cfg.height / (2.f * cfg.fy);
+    }
+    return c;
+}
+
 // Quantities of one (view, Gaussian) pair shared by the forward pass and its adjoint.
 struct Proj {
-    float t[3], tr, rho, rg;
-    float J[6];       // dp/dt, 2 x 3 (J[1] = 0)
+    float t[3], tr, rho, rg;  // tr: the depth that orders Gaussians (t_r, or t_z for the pinhole camera)
+    float J[6];       // the covariance Jacobian, 2 x 3 (J[1] = 0); dp/dt itself for the equirectangular camera
     float M[6];       // J W
     float Tm[6];      // M R diag(s)
     float A, B, C;    // Sigma~ entries 00, 01, 11 (with dilation)
     float det;
 };
 
-// Eqs. 1, 3-5 (position) and 9-16 (covariance). Returns false when culled (near plane or det <= 0).
-__device__ __forceinline__ bool project(const View& w, const float m[3], const float M3[9], int W, int H,
-                                        float near_r, Proj& P, float& px, float& py) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) P.t[i] = fmaf(w.Wr[3 * i], m[0], fmaf(w.Wr[3 * i + 1], m[1], fmaf(w.Wr[3 * i + 2], m[2], w.t[i])));
+// Eq. 2 (pinhole) position and Jacobian; returns false when culled.
+__device__ __forceinline__ bool project_pinhole(const Cam& cam, float near_r, Proj& P, float& px, float& py) {
+    const float tx = P.t[0], ty = P.t[1], tz = P.t[2];
+    P.tr = tz;
+    P.rho = P.rg = 0.f;
+    if (!(tz > near_r)) return false;
+    const float iz = 1.f / tz;
+    px = fmaf(cam.fx, tx * iz, cam.cx);
+    py = fmaf(cam.fy, ty * iz, cam.cy);
+    if (!(fabsf(px) < kMaxCoord && fabsf(py) < kMaxCoord)) return false;
+    const float u = fminf(fmaxf(tx * iz, -cam.limx), cam.limx), v = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
+    P.J[0] = cam.fx * iz; P.J[1] = 0.f; P.J[2] = -cam.fx * u * iz;
+    P.J[3] = 0.f; P.J[4] = cam.fy * iz; P.J[5] = -cam.fy * v * iz;
+    return true;
+}
+
+// Eqs. 3-5 and 10-16; returns false when culled.
+__device__ __forceinline__ bool project_equirect(int W, int H, float near_r, Proj& P, float& px, float& py) {
     const float tx = P.t[0], ty = P.t[1], tz = P.t[2];
     P.tr = sqrtf(tx * tx + ty * ty + tz * tz);
     if (!(P.tr > near_r)) return false;
@@ -129,6 +162,11 @@ __device__ __forceinline__ bool project(const View& w, const float m[3], const f
     P.J[3] = -b * tx * ty / (tr2 * rg);
     P.J[4] = b * rg / tr2;
     P.J[5] = -b * tz * ty / (tr2 * rg);
+    return true;
+}
+
+// Eq. 9: Sigma~ = (J W M3)(J W M3)^T + 0.3 I with its determinant as a sum of non-negative terms.
+__device__ __forceinline__ bool covariance(const View& w, const float M3[9], Proj& P) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         P.M[j] = P.J[0] * w.Wr[j] + P.J[2] * w.Wr[6 + j];
@@ -151,6 +189,20 @@ __device__ __forceinline__ bool project(const View& w, const float m[3], const f
     P.C = n1 + kDilation;
     P.det = (cx * cx + cy * cy + cz * cz) + kDilation * (n0 + n1) + kDilation * kDilation;
     return P.det > 0.f;
+}
+
+// Eqs. 1, 3-5 (position) and 9-16 (covariance), or Eq. 2 for the pinhole camera. Returns false when culled (near
+// plane or det <= 0).
+__device__ __forceinline__ bool project(const View& w, const Cam& cam, const float m[3], const float M3[9], int W,
+                                        int H, float near_r, Proj& P, float& px, float& py) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P.t[i] = fmaf(w.Wr[3 * i], m[0], fmaf(w.Wr[3 * i + 1], m[1], fmaf(w.Wr[3 * i + 2], m[2], w.t[i])));
+    if (cam.pinhole) {
+        if (!project_pinhole(cam, near_r, P, px, py)) return false;
+    } else if (!project_equirect(W, H, near_r, P, px, py)) {
+        return false;
+    }
+    return covariance(w, M3, P);
 }
 
 // R(q) for the unit quaternion (w, x, y, z); M3 = R diag(s).
@@ -202,7 +254,7 @@ __device__ __forceinline__ void stage_sh(float* s_sh, const float* __restrict__ 
 
 template <int K>
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_kernel(int n, int V, int W, int H, float near_r, const float* __restrict__ means,
+preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                   const float* __restrict__ scales, const float* __restrict__ quats, const float* __restrict__ opacity,
                   const float* __restrict__ sh, const float* __restrict__ viewmats, float4* __restrict__ splats) {
     constexpr int STRIDE = 3 * K + 1;
@@ -228,7 +280,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, const float* __restr
         Proj P;
         float px, py;
         float4* out = splats + 3 * ((size_t)v * n + g);
-        if (!project(w, m, M3, W, H, near_r, P, px, py)) {
+        if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[2] = make_float4(0.f, P.tr, __int_as_float(0), __uint_as_float(0u));
@@ -276,7 +328,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, const float* __restr
 
 template <int K>
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, const float* __restrict__ means,
+preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                       const float* __restrict__ scales, const float* __restrict__ quats,
                       const float* __restrict__ opacity, const float* __restrict__ sh,
                       const float* __restrict__ viewmats,
@@ -311,7 +363,7 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, const float* __r
             const View w = load_view(s_view, v);
             Proj P;
             float px, py;
-            if (!project(w, m, M3, W, H, near_r, P, px, py)) continue;
+            if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) continue;
             const float4 g0v = __ldg(grads + 3 * ((size_t)v * n + g));
             const float4 g1v = __ldg(grads + 3 * ((size_t)v * n + g) + 1);
             const float4 g2v = __ldg(grads + 3 * ((size_t)v * n + g) + 2);
@@ -352,20 +404,40 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, const float* __r
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
                     dJ[3 * r + k] = dM[3 * r] * w.Wr[3 * k] + dM[3 * r + 1] * w.Wr[3 * k + 1] + dM[3 * r + 2] * w.Wr[3 * k + 2];
-            // dJ/dt (quotient rule on Eqs. 11-16; rho replaced by the guarded rg)
-            const float tx = P.t[0], ty = P.t[1], tz = P.t[2], tr = P.tr, rg = P.rg;
-            float drg[3];
-            if (P.rho >= kPoleGuard * tr) {
-                drg[0] = tx / rg; drg[1] = 0.f; drg[2] = tz / rg;
-            } else {
-                drg[0] = kPoleGuard * tx / tr; drg[1] = kPoleGuard * ty / tr; drg[2] = kPoleGuard * tz / tr;
-            }
-            const float tr2 = tr * tr, tr4 = tr2 * tr2, rg2 = rg * rg, rg3 = rg2 * rg;
             float dt[3];
-            // p(t): dp/dt = J (Eqs. 11-16 are exactly dp/ds * ds/dt)
+            if (cam.pinhole) {
+                // dp/dt of Eq. 2 (unclamped), then dJ/dt: a ratio held at its bound is a constant
+                const float tx = P.t[0], ty = P.t[1], tz = P.t[2], iz = 1.f / tz, iz2 = iz * iz;
+                dt[0] = gpx * cam.fx * iz;
+                dt[1] = gpy * cam.fy * iz;
+                dt[2] = -(gpx * cam.fx * tx + gpy * cam.fy * ty) * iz2;
+                const float u = tx * iz, v = ty * iz;
+                dt[2] -= (dJ[0] * cam.fx + dJ[4] * cam.fy) * iz2;
+                if (u < -cam.limx || u > cam.limx) {
+                    dt[2] += dJ[2] * cam.fx * fminf(fmaxf(u, -cam.limx), cam.limx) * iz2;
+                } else {
+                    dt[0] -= dJ[2] * cam.fx * iz2;
+                    dt[2] += dJ[2] * 2.f * cam.fx * tx * iz2 * iz;
+                }
+                if (v < -cam.limy || v > cam.limy) {
+                    dt[2] += dJ[5] * cam.fy * fminf(fmaxf(v, -cam.limy), cam.limy) * iz2;
+                } else {
+                    dt[1] -= dJ[5] * cam.fy * iz2;
+                    dt[2] += dJ[5] * 2.f * cam.fy * ty * iz2 * iz;
+                }
+            } else {
+                // dJ/dt (quotient rule on Eqs. 11-16; rho replaced by the guarded rg)
+                const float tx = P.t[0], ty = P.t[1], tz = P.t[2], tr = P.tr, rg = P.rg;
+                float drg[3];
+                if (P.rho >= kPoleGuard * tr) {
+                    drg[0] = tx / rg; drg[1] = 0.f; drg[2] = tz / rg;
+                } else {
+                    drg[0] = kPoleGuard * tx / tr; drg[1] = kPoleGuard * ty / tr; drg[2] = kPoleGuard * tz / tr;
+                }
+                const float tr2 = tr * tr, tr4 = tr2 * tr2, rg2 = rg * rg, rg3 = rg2 * rg;
+                // p(t): dp/dt = J (Eqs. 11-16 are exactly dp/ds * ds/dt)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) dt[k] = gpx * P.J[k] + gpy * P.J[3 + k];
-            {
+                for (int k = 0; k < 3; ++k) dt[k] = gpx * P.J[k] + gpy * P.J[3 + k];
                 const float e00 = dJ[0], e02 = dJ[2], e10 = dJ[3], e11 = dJ[4], e12 = dJ[5];
                 // J00 = a tz / rg^2
                 const float k00 = -2.f * a * tz / rg3;
@@ -466,8 +538,9 @@ cudaError_t preprocess_k(const omnigs_config& cfg, int64_t n, const float* means
     if (e != cudaSuccess) return e;
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
     ProfScope prof("preprocess_fwd", stream);
-    kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, means, scales,
-                                                quats, opacity, sh, viewmats, reinterpret_cast<float4*>(splats));
+    kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, make_cam(cfg),
+                                                means, scales, quats, opacity, sh, viewmats,
+                                                reinterpret_cast<float4*>(splats));
     return cudaGetLastError();
 }
 
@@ -483,9 +556,10 @@ cudaError_t preprocess_bwd_k(const omnigs_config& cfg, int64_t n, const float* m
     if (e != cudaSuccess) return e;
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
     ProfScope prof("preprocess_bwd", stream);
-    kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, means, scales,
-                                                quats, opacity, sh, viewmats, reinterpret_cast<const float4*>(grads), d_means,
-                                                d_scales, d_quats, d_opacity, d_sh, d_screen);
+    kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, make_cam(cfg),
+                                                means, scales, quats, opacity, sh, viewmats,
+                                                reinterpret_cast<const float4*>(grads), d_means, d_scales, d_quats,
+                                                d_opacity, d_sh, d_screen);
     return cudaGetLastError();
 }
 

@@ -97,7 +97,8 @@ struct PixelMap {
 
 template <int TS, int PPT, bool kCount>
 __global__ void __launch_bounds__(TS * TS / PPT)
-render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
+render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0,
+                  float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
                   float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
@@ -111,7 +112,7 @@ render_fwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
     const PixelMap<TS, PPT> pm(txi, tyi);
     const float xs = pm.x + 0.5f;
-    const float halfW = 0.5f * (float)W, fW = (float)W;
+    const float fW = (float)W;  // halfW: W / 2, or +inf for the pinhole camera (no seam)
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const uint32_t* vorder = order + (size_t)v * n;
@@ -208,7 +209,8 @@ __device__ __forceinline__ float warp_sum_fields(float (&v)[kGradFields], unsign
 
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS * TS / PPT)
-render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0, float bg1,
+render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0,
+                  float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
                   const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
                   const float* __restrict__ out_T, const uint32_t* __restrict__ ncontrib,
@@ -228,7 +230,7 @@ render_bwd_kernel(int W, int H, int tiles_x, int tiles, int n, unsigned long lon
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
     const PixelMap<TS, PPT> pm(txi, tyi);
     const float xs = pm.x + 0.5f;
-    const float halfW = 0.5f * (float)W, fW = (float)W;
+    const float fW = (float)W;  // halfW: W / 2, or +inf for the pinhole camera (no seam)
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
     const uint32_t start = ranges[2 * tile_id], len = ranges[2 * tile_id + 1] - start;
     const uint32_t* vorder = order + (size_t)v * n;
@@ -346,6 +348,11 @@ size_t bwd_smem(int nt) {
     return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
+// Half the image width for the minimal-image dx across the longitude seam; +inf turns the wrap off (pinhole camera).
+float seam_half_width(const omnigs_config& cfg) {
+    return cfg.camera == OMNIGS_CAMERA_EQUIRECT ? 0.5f * (float)cfg.width : INFINITY;
+}
+
 // Pixels per blend thread: the configured schedule (2, 4 or 8), else 2 for 8x8 tiles and 4 for larger ones.
 int blend_ppt(const omnigs_config& cfg) {
     if (cfg.pixels_per_thread) return cfg.pixels_per_thread;
@@ -361,7 +368,7 @@ cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat
     ProfScope prof("render_fwd", stream);
     auto kern = out_count ? render_fwd_kernel<TS, PPT, true> : render_fwd_kernel<TS, PPT, false>;
     kern<<<tiles * cfg.num_views, PixelMap<TS, PPT>::NT, 0, stream>>>(
-        cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
+        cfg.width, cfg.height, seam_half_width(cfg), tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
         out_rgb, out_T, out_nc, out_count);
     return cudaGetLastError();
@@ -380,7 +387,7 @@ cudaError_t render_bwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat
     if (e != cudaSuccess) return e;
     ProfScope prof("render_bwd", stream);
     render_bwd_kernel<TS, PPT><<<tiles * cfg.num_views, NT, smem, stream>>>(
-        cfg.width, cfg.height, tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
+        cfg.width, cfg.height, seam_half_width(cfg), tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
         reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order, out_T,
         nc, dL_drgb, reinterpret_cast<float4*>(grads));
     return cudaGetLastError();

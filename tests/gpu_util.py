@@ -70,7 +70,7 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
     alive = ref["rx"] > 0
     assert np.array_equal((got["rx"] > 0)[~near_edge], alive[~near_edge])
     a = alive & (got["rx"] > 0)
-    np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6)
+    np.testing.assert_allclose(got["depth"], ref["depth"], rtol=2e-6, atol=1e-6)
     dpx = (got["px"][a] - ref["px"][a] + W / 2) % W - W / 2
     dpy = got["py"][a] - ref["py"][a]
     assert np.abs(dpx).max(initial=0) <= 2e-6 * W and np.abs(dpy).max(initial=0) <= 2e-6 * H

@@ -57,16 +57,20 @@ def test_config_layout_and_schedule_validation(lib):
     text = open(spec.origin).read()
     fields = re.findall(r'\("(\w+)", ctypes\.c_(\w+)(?: \* 3)?\)', text.split("class omnigs_config")[1].split("class ")[0])
     assert [f for f, _ in fields] == ["width", "height", "tile", "num_views", "sh_degree", "near_r", "bg",
-                                      "pixels_per_thread"]
+                                      "pixels_per_thread", "camera", "fx", "fy", "cx", "cy"]
 
     class Cfg(ctypes.Structure):
         _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32),
                     ("num_views", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_r", ctypes.c_float),
-                    ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32)]
+                    ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("camera", ctypes.c_int32),
+                    ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
 
-    assert ctypes.sizeof(Cfg) == 40
+    assert ctypes.sizeof(Cfg) == 60
     lib.omnigs_workspace_size.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_int64]
     lib.omnigs_workspace_size.restype = ctypes.c_size_t
     for tile, ppt in [(8, 4), (8, 8), (16, 3), (16, 1), (32, 16)]:
         c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), ppt)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (tile, ppt)
+    for cam, fx, fy in [(2, 100.0, 100.0), (1, 0.0, 100.0), (1, 100.0, -1.0), (1, float("nan"), 100.0)]:
+        c = Cfg(256, 128, 16, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0, cam, fx, fy, 128.0, 64.0)
+        assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (cam, fx, fy)
