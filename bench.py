@@ -38,6 +38,9 @@ WORKLOADS = {
     # roaming: 3M Gaussians along a 60 m corridor of 5 rooms, 16 poses on its centre line, autotuned tile/schedule
     "roaming": dict(n=3_000_000, views=16, width=4096, height=2048, tile="auto", scene="corridor"),
     "shell-small": dict(n=10_000, views=1, width=512, height=256, tile=16, scene="shell"),
+    # the perspective split of the egocentric capture: 6 cube faces (90-degree pinhole, Eq. 2) for each of 8 poses
+    "egocentric-cubemap": dict(n=1_000_000, views=48, width=512, height=512, tile=16, scene="room",
+                               pinhole=(256.0, 256.0, 256.0, 256.0), faces=6),
     # 360Roam-shaped: the corridor of rooms seen by 8 poses at 1536x768, the bottom 48 rows (the capture rig) left out
     # of the loss and its gradient
     "roam-masked": dict(n=1_000_000, views=8, width=1536, height=768, tile=16, scene="corridor", loss_rows=(0, 720)),
@@ -123,6 +126,9 @@ def build_scene(wl: dict, seed: int = 0):
 def build_poses(wl: dict, rank: int, world: int = 1):
     """This rank's poses: its slice of one seeded batch of views x world poses (weak scaling)."""
     total = wl["views"] * world
+    if wl.get("faces"):
+        return synth.cube_face_viewmats(build_poses(dict(wl, views=wl["views"] // wl["faces"], faces=None), rank,
+                                                    world))
     if wl["scene"] == "room":
         poses = synth.room_viewmats(total, 1000)
     elif wl["scene"] == "corridor":
@@ -200,6 +206,7 @@ class ClockSampler:
 def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng, tile: int | None = None):
     """One bounded oracle sample of a step, extrapolated to the whole step (ms). Returns (ms, description)."""
     import oracle
+    cam = oracle.pinhole(*wl["pinhole"]) if wl.get("pinhole") else None
     W, H, V = wl["width"], wl["height"], wl["views"]
     T = tile or (16 if wl["tile"] == "auto" else wl["tile"])
     tiles = (W // T) * (H // T)
@@ -211,24 +218,24 @@ def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng, 
     idx = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False)) if frac < 1.0 else np.arange(n)
     sub = scene.subset(idx)
     t0 = time.perf_counter()
-    rec = oracle.preprocess(scene, viewmats[v:v + 1], W, H)
+    rec = oracle.preprocess(scene, viewmats[v:v + 1], W, H, camera=cam)
     t_pre = time.perf_counter() - t0
     sp = oracle.splats_from_records(rec)
     t0 = time.perf_counter()
-    rec_s = oracle.preprocess(sub, viewmats[v:v + 1], W, H)
-    oracle.bin_sort(oracle.splats_from_records(rec_s), 1, W, H, T)
+    rec_s = oracle.preprocess(sub, viewmats[v:v + 1], W, H, camera=cam)
+    oracle.bin_sort(oracle.splats_from_records(rec_s), 1, W, H, T, camera=cam)
     t_sort = (time.perf_counter() - t0) / frac
     mask = np.zeros(tiles, bool)
     mask[rng.choice(tiles, k_tiles, replace=False)] = True
     t0 = time.perf_counter()
-    rg, lst = oracle.bin_sort(sp, 1, W, H, T, tile_mask=mask)
-    rgb, Tf, nc, _ = oracle.blend_fwd(sp, rg, lst, 1, W, H, T)
+    rg, lst = oracle.bin_sort(sp, 1, W, H, T, tile_mask=mask, camera=cam)
+    rgb, Tf, nc, _ = oracle.blend_fwd(sp, rg, lst, 1, W, H, T, camera=cam)
     d = rgb - target[v:v + 1]
     g = (np.sign(d) / (V * d.size)).astype(np.float64)
-    g2 = oracle.blend_bwd(sp, rg, lst, g, 1, W, H, T)
+    g2 = oracle.blend_bwd(sp, rg, lst, g, 1, W, H, T, camera=cam)
     t_blend = (time.perf_counter() - t0) * tiles / k_tiles
     t0 = time.perf_counter()
-    oracle.preprocess_bwd(scene, viewmats[v:v + 1], g2, W, H)
+    oracle.preprocess_bwd(scene, viewmats[v:v + 1], g2, W, H, camera=cam)
     t_pbwd = time.perf_counter() - t0
     ms = 1e3 * V * (t_pre + t_sort + t_blend + t_pbwd)
     desc = (f"1 of {V} views: preprocess + preprocess_bwd of all {n} Gaussians, bin + sort of a {frac:.0%} Gaussian "
@@ -356,7 +363,8 @@ def workload_config(wl, args, settings=None):
             "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)",
-            "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1"}
+            "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1",
+            "camera": f"pinhole fx, fy, cx, cy = {wl['pinhole']}" if wl.get("pinhole") else "equirectangular"}
 
 
 def main():
@@ -402,7 +410,8 @@ def main():
     vm_np = build_poses(wl, rank, world)
     V, W, H = wl["views"], wl["width"], wl["height"]
     auto = wl["tile"] == "auto"
-    settings = og.Settings(width=W, height=H, tile=16 if auto else wl["tile"], num_views=V, sh_degree=scene.sh_degree)
+    settings = og.Settings(width=W, height=H, tile=16 if auto else wl["tile"], num_views=V, sh_degree=scene.sh_degree,
+                           pinhole=wl.get("pinhole"))
     params = [torch.from_numpy(a).to(dev) for a in scene.arrays()]
     vm = torch.from_numpy(vm_np).to(dev)
 

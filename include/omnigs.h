@@ -216,6 +216,16 @@ omnigs_status omnigs_instance_count(const void *workspace, int64_t *count, omnig
  * `stream`; also reports a pending CUDA error as OMNIGS_E_CUDA. */
 omnigs_status omnigs_last_error(void *workspace, omnigs_stream_t stream);
 
+/* Perspective crops of equirectangular images (Sec. 5.4 compares rendered equirectangular views with perspective
+ * renders after cropping them into perspective images). Output pixel (x, y) of view v looks along the camera-frame
+ * direction d = R_v^T ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1) (a pinhole of Eq. 2 rotated by R_v); its longitude
+ * and latitude (Eq. 3) place it on the equirectangular image (Eqs. 4-5), which is sampled bilinearly between pixel
+ * centres, columns wrapping across the seam and rows clamped at the poles.
+ *   equirect [V, 3, eq_height, eq_width], rotations [V, 3, 3] (row-major), out [V, 3, height, width]: device. */
+omnigs_status omnigs_equirect_crop(int32_t V, int32_t eq_width, int32_t eq_height, const float *equirect,
+                                   const float *rotations, int32_t width, int32_t height, float fx, float fy, float cx,
+                                   float cy, float *out, omnigs_stream_t stream);
+
 /* ---------------------------------------------------------------- reconstruction loop (Sec. 4, Algorithm 1)
  *
  * The optimiser keeps each Gaussian as one row of P = 11 + 3K raw floats: mean (3), log-scale (3), quaternion (4,

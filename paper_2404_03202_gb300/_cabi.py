@@ -93,12 +93,14 @@ def load() -> ctypes.CDLL:
         lib.omnigs_densify_workspace_size.restype = ctypes.c_size_t
         lib.omnigs_densify.argtypes = [i64, i32, ctypes.POINTER(omnigs_densify_config)] + [P] * 12 + [P]
         lib.omnigs_reset_opacity.argtypes = [i64, i32, ctypes.c_float, P, P, P, P, P]
+        f32 = ctypes.c_float
+        lib.omnigs_equirect_crop.argtypes = [i32, i32, i32, P, P, i32, i32, f32, f32, f32, f32, P, P]
         lib.omnigs_profiler_enable.argtypes = [ctypes.c_int]
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
         for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_l1_loss",
                      "omnigs_l1_loss_rows", "omnigs_dssim_loss", "omnigs_adam_step", "omnigs_publish_params",
-                     "omnigs_densify_stats", "omnigs_densify", "omnigs_reset_opacity",
+                     "omnigs_densify_stats", "omnigs_densify", "omnigs_reset_opacity", "omnigs_equirect_crop",
                      "omnigs_render_bwd", "omnigs_preprocess_bwd", "omnigs_instance_count", "omnigs_last_error",
                      "omnigs_profiler_enable"):
             getattr(lib, name).restype = st
@@ -271,3 +273,9 @@ def omnigs_densify(n, K, cfg, params, m, v, accum, count, max_radius, normals, p
 def omnigs_reset_opacity(n, K, value, params, m, v, opacity=None, stream=None):
     _check(load().omnigs_reset_opacity(n, K, float(value), _ptr(params), _ptr(m), _ptr(v), _ptr(opacity),
                                        _stream(stream)), "omnigs_reset_opacity")
+
+
+def omnigs_equirect_crop(V, eq_width, eq_height, equirect, rotations, width, height, fx, fy, cx, cy, out, stream=None):
+    _check(load().omnigs_equirect_crop(V, eq_width, eq_height, _ptr(equirect), _ptr(rotations), width, height,
+                                       float(fx), float(fy), float(cx), float(cy), _ptr(out), _stream(stream)),
+           "omnigs_equirect_crop")

@@ -134,6 +134,8 @@ cudaError_t launch_densify(int64_t n, int K, const omnigs_densify_config &cfg, c
                            char *ws, cudaStream_t stream);
 cudaError_t launch_reset_opacity(int64_t n, int K, float value, float *params, float *m, float *v, float *opacity,
                                  cudaStream_t stream);
+cudaError_t launch_crop(int V, int We, int He, const float *eq, const float *rot, int W, int H, float fx, float fy,
+                        float cx, float cy, float *out, cudaStream_t stream);
 size_t dssim_scratch_bytes(const omnigs_config &cfg);
 cudaError_t launch_dssim(const omnigs_config &cfg, float lambda, const float *rgb, const float *target, float *dL,
                          float *loss, char *scratch, cudaStream_t stream);

@@ -279,6 +279,20 @@ omnigs_status omnigs_reset_opacity(int64_t n, int32_t K, float value, float* par
     return from_cuda(launch_reset_opacity(n, K, value, params, m, v, opacity, (cudaStream_t)stream));
 }
 
+omnigs_status omnigs_equirect_crop(int32_t V, int32_t eq_width, int32_t eq_height, const float* equirect,
+                                   const float* rotations, int32_t width, int32_t height, float fx, float fy, float cx,
+                                   float cy, float* out, omnigs_stream_t stream) {
+    if (V < 0 || eq_width <= 0 || eq_height <= 0 || width <= 0 || height <= 0) return OMNIGS_E_INVALID;
+    if (eq_width > (1 << 20) || eq_height > (1 << 20) || width > (1 << 20) || height > (1 << 20) || V > 65535)
+        return OMNIGS_E_INVALID;
+    if (!(std::isfinite(fx) && std::isfinite(fy) && fx > 0.f && fy > 0.f && std::isfinite(cx) && std::isfinite(cy)))
+        return OMNIGS_E_INVALID;
+    if (V == 0) return OMNIGS_OK;
+    if (!equirect || !rotations || !out) return OMNIGS_E_INVALID;
+    return from_cuda(launch_crop(V, eq_width, eq_height, equirect, rotations, width, height, fx, fy, cx, cy, out,
+                                 (cudaStream_t)stream));
+}
+
 omnigs_status omnigs_render_bwd(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
                                 const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
                                 const float* out_T, const uint32_t* ncontrib, const float* dL_drgb,

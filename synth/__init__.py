@@ -183,6 +183,25 @@ def random_viewmats(v: int, seed: int, max_offset: float = 0.3) -> np.ndarray:
     return out.astype(np.float32)
 
 
+def cube_face_viewmats(viewmats: np.ndarray) -> np.ndarray:
+    """Six 90-degree pinhole views per pose (the faces of a cube map: looking along +z, +x, -z, -x, -y, +y of each
+    camera), pose-major: the perspective split of an equirectangular capture."""
+    faces = []
+    for yaw in (0.0, 0.5 * np.pi, np.pi, 1.5 * np.pi):
+        faces.append(_rot_y(yaw))
+    c, s = np.cos(0.5 * np.pi), np.sin(0.5 * np.pi)
+    faces.append(np.array([[1, 0, 0], [0, c, -s], [0, s, c]]))   # looking up (-y, y points down)
+    faces.append(np.array([[1, 0, 0], [0, c, s], [0, -s, c]]))   # looking down
+    out = []
+    for vm in np.asarray(viewmats, np.float64):
+        for F in faces:
+            m = np.eye(4)
+            m[:3, :3] = F @ vm[:3, :3]
+            m[:3, 3] = F @ vm[:3, 3]
+            out.append(m)
+    return np.array(out, np.float32)
+
+
 # ---------------------------------------------------------------- projected splats for stage-level tests
 
 SPLAT_FIELDS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth", "rx", "ry")
