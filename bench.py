@@ -356,8 +356,10 @@ def train_loop_benchmark(dev, scene, vm, settings, target, iters: int = 20) -> d
 def workload_config(wl, args, settings=None):
     tile = settings.tile if settings is not None else wl["tile"]
     auto = " (autotuned)" if wl["tile"] == "auto" else ""
+    cam = "pinhole" if wl.get("pinhole") else "equirect"
+    loss = "L1 + D-SSIM" if getattr(args, "loss", "l1") == "dssim" else "L1"
     return {"workload": f"{args.workload}: {wl['n']} Gaussians, {wl['views']} views of {wl['width']}x{wl['height']} "
-                        f"equirect, {tile}x{tile} tiles{auto}, fwd+bwd with L1 loss",
+                        f"{cam}, {tile}x{tile} tiles{auto}, fwd+bwd with {loss} loss",
             "gaussians": wl["n"], "views_per_step": wl["views"], "width": wl["width"], "height": wl["height"],
             "tile": tile, "pixels_per_thread": (settings.pixels_per_thread or "default") if settings else None,
             "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
