@@ -22,9 +22,9 @@ _SRC = os.path.join(_HERE, "omnigs_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-R_LEN = 18
+R_LEN = 19
 (R_PX, R_PY, R_DEPTH, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE, R_RADIUS, R_COV00, R_COV01, R_COV11,
- R_RMARGIN, R_FLAGS, R_RX, R_RY) = range(R_LEN)
+ R_RMARGIN, R_FLAGS, R_RX, R_RY, R_Q) = range(R_LEN)
 SPLAT_COLS = [R_PX, R_PY, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE]
 G_LEN = 9
 
@@ -33,7 +33,8 @@ def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (gcc), in place."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -51,9 +52,10 @@ def _load():
         lib.orc_quat_to_rot.argtypes = [P, P]
         lib.orc_preprocess.argtypes = [i64, i32, i32, i32, i32, f64, P, P, P, P, P, P, P]
         lib.orc_rect.argtypes = [f64, f64, i32, i32, i32, i32, i32, P]
-        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P, P]
+        lib.orc_row_columns.argtypes = [f64, f64, f64, f64, f64, f64, i64, i64, i64, i64, i32, P]
+        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P]
         lib.orc_count_instances.restype = i64
-        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P]
+        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_bin_sort.restype = i64
         lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
@@ -138,7 +140,7 @@ def rect(px: float, py: float, rx: int, ry: int, width: int, height: int, tile: 
 # ------------------------------------------------------------------ stages
 
 def preprocess(scene, viewmats, width: int, height: int, near: float = 0.2, camera=None) -> np.ndarray:
-    """Per-(view, Gaussian) records [V * N, 16] (field order: see R_* constants)."""
+    """Per-(view, Gaussian) records [V * N, R_LEN] (field order: see R_* constants)."""
     lib = _load()
     _camera(camera)
     means, scales, quats, opacity, sh = (_f32(a) for a in scene.arrays())
@@ -155,7 +157,31 @@ def splats_from_records(rec: np.ndarray) -> dict:
     return dict(px=rec[:, R_PX], py=rec[:, R_PY], c0=rec[:, R_C0], c1=rec[:, R_C1], c2=rec[:, R_C2],
                 opacity=rec[:, R_OPAC], r=rec[:, R_RED], g=rec[:, R_GREEN], b=rec[:, R_BLUE],
                 depth=rec[:, R_DEPTH], rx=rec[:, R_RX].astype(np.int32), ry=rec[:, R_RY].astype(np.int32),
-                radius=rec[:, R_RADIUS].astype(np.int32))
+                radius=rec[:, R_RADIUS].astype(np.int32), q=rec[:, R_Q])
+
+
+def splat_q(splats: dict) -> np.ndarray:
+    """q = 2 ln(255 o) of each splat (the alpha >= 1/255 level of its ellipse): the stored value when the dict has
+    one (preprocess records), else computed from the opacity (hand-made splats)."""
+    if "q" in splats:
+        return _f64(splats["q"])
+    o = _f64(splats["opacity"])
+    with np.errstate(divide="ignore"):
+        return np.maximum(2.0 * np.log(255.0 * o), 0.0)
+
+
+def row_columns(px, py, c0, c1, c2, q, x0: int, nx: int, tiles_x: int, ty: int, tile: int):
+    """Unwrapped tile columns (first, last) of tile row ty that a splat with box columns x0 .. x0 + nx - 1 keeps
+    (first > last: none)."""
+    lib = _load()
+    out = np.zeros(2, dtype=np.int64)
+    lib.orc_row_columns(float(px), float(py), float(c0), float(c1), float(c2), float(q), int(x0), int(nx),
+                        int(tiles_x), int(ty), int(tile), _p(out))
+    return int(out[0]), int(out[1])
+
+
+def _conic_q(splats: dict):
+    return _f64(splats["c0"]), _f64(splats["c1"]), _f64(splats["c2"]), splat_q(splats)
 
 
 def count_instances(splats: dict, V: int, width: int, height: int, tile: int, camera=None) -> int:
@@ -163,7 +189,9 @@ def count_instances(splats: dict, V: int, width: int, height: int, tile: int, ca
     _camera(camera)
     px, py = _f64(splats["px"]), _f64(splats["py"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
-    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry)))
+    c0, c1, c2, q = _conic_q(splats)
+    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry),
+                                       _p(c0), _p(c1), _p(c2), _p(q)))
 
 
 def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None, camera=None):
@@ -173,15 +201,17 @@ def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask
     _camera(camera)
     px, py, depth = _f64(splats["px"]), _f64(splats["py"]), _f64(splats["depth"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
+    c0, c1, c2, q = _conic_q(splats)
     n = px.shape[0] // V
     tiles = (width // tile) * (height // tile)
     mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
     ranges = np.zeros((V * tiles, 2), dtype=np.int64)
-    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges),
-                                 None, None if mask is None else _p(mask)))
+    conic = (_p(c0), _p(c1), _p(c2), _p(q))
+    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), *conic, _p(depth),
+                                 _p(ranges), None, None if mask is None else _p(mask)))
     lst = np.zeros(max(total, 1), dtype=np.int64)
-    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges), _p(lst),
-                     None if mask is None else _p(mask))
+    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), *conic, _p(depth), _p(ranges),
+                     _p(lst), None if mask is None else _p(mask))
     return ranges, lst[:total]
 
 

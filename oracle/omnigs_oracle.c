@@ -28,6 +28,11 @@
  *     rx = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4) + 1e-3)), ry likewise (the small widening absorbs FP32
  *     rounding on the GPU). A Gaussian with 255 o < 1 has no instance. Outside that box alpha < 1/255 at every
  *     pixel, so the narrowing leaves every image unchanged; it only drops instances that contribute nothing.
+ *     rx and ry are held at 65535 (images are at most 65536 px wide).
+ *   - within the box, a tile row keeps only the columns whose pixel centres the (widened) alpha >= 1/255 ellipse can
+ *     reach: the ellipse's x-extent over the row's band of pixel-centre y values, widened by one pixel
+ *     (row_columns below). The decision takes FP32 operations in a fixed order, so that an FP32 implementation
+ *     making the same operations lists the same tiles; q = 2 ln(255 o) is stored with the splat (R_Q).
  *   - quaternion stored (w, x, y, z), normalised before use; Sigma = R diag(s)^2 R^T.
  *   - colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m and Y_k the real
  *     orthonormal spherical harmonics up to degree 3 (no Condon-Shortley phase).
@@ -61,7 +66,7 @@
  * of the box the instances come from; R_RMARGIN the smallest distance of the three ceil() arguments to an integer. */
 enum {
     R_PX = 0, R_PY, R_DEPTH, R_C0, R_C1, R_C2, R_OPAC, R_RED, R_GREEN, R_BLUE, R_RADIUS,
-    R_COV00, R_COV01, R_COV11, R_RMARGIN, R_FLAGS, R_RX, R_RY, R_LEN
+    R_COV00, R_COV01, R_COV11, R_RMARGIN, R_FLAGS, R_RX, R_RY, R_Q, R_LEN
 };
 /* per-(view, Gaussian) screen-space gradient, written by orc_blend_bwd and read by orc_preprocess_bwd */
 enum { G_PX = 0, G_PY, G_C0, G_C1, G_C2, G_OPAC, G_RED, G_GREEN, G_BLUE, G_LEN };
@@ -254,7 +259,7 @@ static void covariance3d(const double *q, const double *s, double *Sig, double *
 /* ------------------------------------------------------------------ per-(view, Gaussian) forward quantities */
 typedef struct {
     int culled;
-    double t[3], tr, p[2], J[6], Jp[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rx, ry, rmargin;
+    double t[3], tr, p[2], J[6], Jp[6], Wr[9], M[6], Sig[9], R[9], cov[3], det, conic[3], radius, rx, ry, rmargin, q;
     double dir[3], dist, Y[16], rgb_raw[3], rgb[3];
 } orc_fwd;
 
@@ -340,6 +345,9 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
     double hx = sqrt(qa * f->cov[0]) * (1.0 + 1e-4) + 1e-3, hy = sqrt(qa * f->cov[2]) * (1.0 + 1e-4) + 1e-3;
     f->rx = ceil(hx) < f->radius ? ceil(hx) : f->radius;
     f->ry = ceil(hy) < f->radius ? ceil(hy) : f->radius;
+    if (f->rx > 65535.0) f->rx = 65535.0;
+    if (f->ry > 65535.0) f->ry = 65535.0;
+    f->q = qa;
     f->rmargin = fmin(int_gap(rr), fmin(int_gap(hx), int_gap(hy)));
     /* Sec. 3.1: colour from m and the SH coefficients */
     double v[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
@@ -378,7 +386,7 @@ void orc_preprocess(int64_t n, int V, int W, int H, int sh_degree, double near_r
             o[R_RADIUS] = f.radius;
             o[R_COV00] = f.cov[0]; o[R_COV01] = f.cov[1]; o[R_COV11] = f.cov[2];
             o[R_RMARGIN] = f.rmargin;
-            o[R_RX] = f.rx; o[R_RY] = f.ry;
+            o[R_RX] = f.rx; o[R_RY] = f.ry; o[R_Q] = f.q;
         }
     }
 }
@@ -423,61 +431,153 @@ static int inst_cmp(const void *a, const void *b)
     return 0;
 }
 
+/* Columns [*cl, *cr] (unwrapped tile columns, within the box's x0 .. x0 + nx - 1) of tile row ty that the alpha >=
+ * 1/255 ellipse dp^T conic dp <= q of a splat can reach, widened: q is raised by 0.1 % + 1e-3, the x-extent by one
+ * pixel. Over the row's band of pixel-centre offsets v in [ty T + 1/2 - py, ty T + T - 1/2 - py], the ellipse spans
+ * u in [x-(v_L), x+(v_R)] with x-+(v) = (-c1 v -+ sqrt(c0 q - det v^2)) / c0, det = c0 c2 - c1^2, and v_L, v_R the
+ * offsets of its leftmost and rightmost points (+-c1 sqrt(q / (det c2))) clamped to the band. Every step is one FP32
+ * operation (single rounding, no contraction). Rows of a box that spans every column, and splats whose det is not
+ * well above zero, keep the whole row. *cl > *cr means no column. */
+static void row_columns(float px, float py, float c0, float c1, float c2, float q, int64_t x0, int64_t nx,
+                        int64_t TX, int64_t ty, int T, int64_t *cl, int64_t *cr)
+{
+    *cl = x0;
+    *cr = x0 + nx - 1;
+    if (nx >= TX) return;
+    float c0c2 = c0 * c2, c1c1 = c1 * c1;
+    float det = c0c2 - c1c1;
+    float guard = 1e-3f * c0c2;
+    if (!(det > guard) || !(c0 > 0.0f) || !(c2 > 0.0f)) return;
+    float qw = q * 1.001f;
+    qw = qw + 1e-3f;
+    float tyT = (float)(ty * T);
+    float yl = tyT + 0.5f;
+    yl = yl - py;
+    float yh = tyT + (float)T;
+    yh = yh - 0.5f;
+    yh = yh - py;
+    float e2 = qw * c0;
+    e2 = e2 / det;
+    float ey = sqrtf(e2);
+    float ney = -ey;
+    float lo = yl > ney ? yl : ney;
+    float hi = yh < ey ? yh : ey;
+    if (lo > hi) { *cl = 1; *cr = 0; return; }
+    float d2 = det * c2;
+    float r2 = qw / d2;
+    float yL = sqrtf(r2);
+    yL = c1 * yL;
+    float nyL = -yL;
+    float vL = yL < lo ? lo : (yL > hi ? hi : yL);
+    float vR = nyL < lo ? lo : (nyL > hi ? hi : nyL);
+    float c0q = c0 * qw;
+    float sL = vL * vL;
+    sL = det * sL;
+    sL = c0q - sL;
+    sL = sL > 0.0f ? sL : 0.0f;
+    float sR = vR * vR;
+    sR = det * sR;
+    sR = c0q - sR;
+    sR = sR > 0.0f ? sR : 0.0f;
+    float xl = c1 * vL;
+    xl = -xl;
+    xl = xl - sqrtf(sL);
+    xl = xl / c0;
+    float xr = c1 * vR;
+    xr = -xr;
+    xr = xr + sqrtf(sR);
+    xr = xr / c0;
+    float ul = px + xl;
+    ul = ul - 1.0f;
+    float ur = px + xr;
+    ur = ur + 1.0f;
+    /* tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur */
+    float fT = (float)T;
+    float a = ul + 0.5f;
+    a = a - fT;
+    a = a / fT;
+    a = ceilf(a);
+    float b = ur - 0.5f;
+    b = b / fT;
+    b = floorf(b);
+    float fx0 = (float)x0, fx1 = (float)(x0 + nx - 1);
+    a = a > fx0 ? a : fx0;
+    b = b < fx1 ? b : fx1;
+    *cl = (int64_t)a;
+    *cr = (int64_t)b;
+}
+
+void orc_row_columns(double px, double py, double c0, double c1, double c2, double q, int64_t x0, int64_t nx,
+                     int64_t TX, int64_t ty, int T, int64_t *out)
+{
+    row_columns((float)px, (float)py, (float)c0, (float)c1, (float)c2, (float)q, x0, nx, TX, ty, T, out, out + 1);
+}
+
+/* Instances of one splat: tile rows of its box, each with the columns row_columns keeps. */
+static int64_t splat_instances(double px, double py, int rx, int ry, double c0, double c1, double c2, double q, int W,
+                               int H, int T, int64_t *tiles_out /* NULL: count only */)
+{
+    int64_t TX = W / T, r[4], k = 0;
+    orc_rect(px, py, rx, ry, W, H, T, r);
+    for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++) {
+        int64_t cl, cr;
+        row_columns((float)px, (float)py, (float)c0, (float)c1, (float)c2, (float)q, r[0], r[1], TX, ty, T, &cl, &cr);
+        for (int64_t c = cl; c <= cr; c++) {
+            if (tiles_out) tiles_out[k] = ty * TX + ((c % TX) + TX) % TX;
+            k++;
+        }
+    }
+    return k;
+}
+
 int64_t orc_count_instances(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                            const int32_t *rx, const int32_t *ry)
+                            const int32_t *rx, const int32_t *ry, const double *c0, const double *c1,
+                            const double *c2, const double *q)
 {
     int64_t total = 0;
     for (int64_t i = 0; i < (int64_t)V * n; i++) {
         if (rx[i] <= 0) continue;
-        int64_t r[4];
-        orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
-        total += r[1] * r[3];
+        total += splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, NULL);
     }
     return total;
 }
 
-/* One instance per (Gaussian, covered tile); order by (view, tile), then t_r, then Gaussian index (the order a
- * stable sort by (tile, t_r) gives when instances are generated Gaussian by Gaussian). ranges: [V*TX*TY][2].
+/* One instance per (Gaussian, kept tile); order by (view, tile), then t_r, then Gaussian index (the order a stable
+ * sort by (tile, t_r) gives when instances are generated Gaussian by Gaussian). ranges: [V*TX*TY][2].
  * tile_mask (optional, [V*TX*TY]): when given, only instances of tiles whose mask byte is non-zero are listed
  * (the lists of those tiles are the same as without a mask). Returns the number of listed instances; with
  * list_vg == NULL it only counts them. */
 int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                     const int32_t *rx, const int32_t *ry, const double *depth, int64_t *ranges, int64_t *list_vg,
+                     const int32_t *rx, const int32_t *ry, const double *c0, const double *c1, const double *c2,
+                     const double *q, const double *depth, int64_t *ranges, int64_t *list_vg,
                      const uint8_t *tile_mask)
 {
     int64_t TX = W / T, TY = H / T, tiles = TX * TY;
+    int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(tiles > 0 ? tiles : 1));
     int64_t total = 0;
-    if (!tile_mask) {
-        total = orc_count_instances(V, n, W, H, T, px, py, rx, ry);
-    } else {
-        for (int v = 0; v < V; v++)
-            for (int64_t g = 0; g < n; g++) {
-                int64_t i = v * n + g, r[4];
-                if (rx[i] <= 0) continue;
-                orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
-                for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
-                    for (int64_t c = 0; c < r[1]; c++)
-                        total += tile_mask[v * tiles + ty * TX + ((r[0] + c) % TX + TX) % TX] != 0;
-            }
-    }
-    if (!list_vg) return total; /* count only */
+    for (int v = 0; v < V; v++)
+        for (int64_t g = 0; g < n; g++) {
+            int64_t i = v * n + g;
+            if (rx[i] <= 0) continue;
+            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, buf);
+            for (int64_t k = 0; k < m; k++) total += !tile_mask || tile_mask[v * tiles + buf[k]];
+        }
+    if (!list_vg) { free(buf); return total; } /* count only */
     orc_inst *inst = (orc_inst *)malloc(sizeof(orc_inst) * (total > 0 ? total : 1));
     int64_t k = 0;
     for (int v = 0; v < V; v++)
         for (int64_t g = 0; g < n; g++) {
             int64_t i = v * n + g;
             if (rx[i] <= 0) continue;
-            int64_t r[4];
-            orc_rect(px[i], py[i], rx[i], ry[i], W, H, T, r);
-            for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
-                for (int64_t c = 0; c < r[1]; c++) {
-                    int64_t tx = ((r[0] + c) % TX + TX) % TX;
-                    if (tile_mask && !tile_mask[v * tiles + ty * TX + tx]) continue;
-                    inst[k].tile = v * tiles + ty * TX + tx;
-                    inst[k].depth = depth[i];
-                    inst[k].vg = i;
-                    k++;
-                }
+            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, buf);
+            for (int64_t e = 0; e < m; e++) {
+                int64_t t = v * tiles + buf[e];
+                if (tile_mask && !tile_mask[t]) continue;
+                inst[k].tile = t;
+                inst[k].depth = depth[i];
+                inst[k].vg = i;
+                k++;
+            }
         }
     qsort(inst, (size_t)total, sizeof(orc_inst), inst_cmp);
     for (int64_t t = 0; t < (int64_t)V * tiles; t++) { ranges[2 * t] = 0; ranges[2 * t + 1] = 0; }
@@ -488,6 +588,7 @@ int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, co
         if (j == total - 1 || inst[j + 1].tile != t) ranges[2 * t + 1] = j + 1;
     }
     free(inst);
+    free(buf);
     return total;
 }
 
