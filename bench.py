@@ -84,8 +84,8 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int) -> di
         "preprocess_fwd": n * 236 + P * 48,               # 59 parameter floats in, one splat out per view
         "depth_keys": P * (4 + 8 + 4),                    # depth in, (view|depth) key and index out
         "depth_sort": dp * P * (8 + 2 * 12),              # per pass: key histogram read, key+index read and written
-        "bin_count": P * (4 + 16 + 4),                    # depth order, (px, py, rx, ry), tile count out
-        "bin_emit": P * (4 + 16 + 8) + instances * 8,     # order, (px, py, rx, ry), offset; one key per instance
+        "bin_count": P * (4 + 36 + 4),                    # depth order, (p, conic, depth, radii, q), tile count out
+        "bin_emit": P * (4 + 36 + 8) + instances * 8,     # order, (p, conic, depth, radii, q), offset; one key each
         "sort_upsweep": tp * instances * 8,               # per pass: keys read for the digit histogram
         "sort_downsweep": tp * instances * 16,            # per pass: keys read and written
         "tile_ranges": tiles * 8,                         # one [start, end) pair per tile

@@ -69,15 +69,17 @@ typedef struct {
  * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
  * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
  * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
- * + 1e-3)) and radius_y likewise with Sigma~_11. Outside that ellipse alpha < 1/255, so the narrowing removes only
- * instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled. */
+ * + 1e-3)) and radius_y likewise with Sigma~_11, both held at 65535. Outside that ellipse alpha < 1/255, so the
+ * narrowing removes only instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled. q = 2 ln(255 o)
+ * (0 when culled) is the level of that ellipse, dp^T conic dp <= q, which omnigs_bin uses to cull tiles row by row. */
 typedef struct {
     float px, py;
     float c0, c1, c2;
     float opacity;
     float r, g, b;
     float depth;
-    int32_t radius_x, radius_y;
+    uint16_t radius_x, radius_y;
+    float q;
 } omnigs_splat;
 
 /* Gradient of the loss with respect to one omnigs_splat's differentiable fields (48 bytes, 16-byte aligned). */
@@ -114,9 +116,14 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
                                 omnigs_splat *splats, omnigs_stream_t stream);
 
 /* Tile binning, Sec. 3.3 ("one instance per influence"): for every splat with radius_x > 0, one instance per tile
- * covered by the box [floor(px) - radius_x, floor(px) + radius_x] x [floor(py) - radius_y, floor(py) + radius_y].
- * Tile columns wrap modulo W / tile (the longitude seam; a box at least as wide as the image covers every column
- * once); rows are clipped to the image.
+ * covered by the box [floor(px) - radius_x, floor(px) + radius_x] x [floor(py) - radius_y, floor(py) + radius_y]
+ * that the splat's alpha >= 1/255 ellipse can reach. Tile columns wrap modulo W / tile (the longitude seam; a box at
+ * least as wide as the image covers every column once); rows are clipped to the image. Within a tile row of a box
+ * narrower than the image, only the columns whose pixel centres lie within one pixel of the ellipse
+ * dp^T conic dp <= q (1.001) + 1e-3, over the row's band of pixel-centre y values, are kept; the column bounds come
+ * from a fixed sequence of correctly rounded FP32 operations, so that they are reproducible bit for bit. A dropped
+ * tile has alpha < 1/255 at each of its pixels: no image changes. Splats with c0 c2 - c1^2 <= 1e-3 c0 c2 keep whole
+ * rows.
  * Splats whose centre lies outside [0, W] x [0, H] are ignored.
  *   splats  [V * n] input (device)
  *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:

@@ -57,6 +57,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
 
 struct SplatPos {
     float px, py, depth;
+    float c0, c1, c2, q;
     int rx, ry;  // instance box half-extents; rx = 0: no instance
 };
 
@@ -65,19 +66,100 @@ struct SplatPos {
 __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size_t i, int tiles_x, int tiles_y,
                                              int tile, bool wrap) {
     const float4 a = __ldg(sp + 3 * i);
+    const float c2 = __ldg(reinterpret_cast<const float*>(sp + 3 * i + 1));
     const float4 c = __ldg(sp + 3 * i + 2);
     SplatPos p;
     p.px = a.x;
     p.py = a.y;
+    p.c0 = a.z;
+    p.c1 = a.w;
+    p.c2 = c2;
     p.depth = c.y;
-    p.rx = __float_as_int(c.z);
-    p.ry = __float_as_int(c.w);
+    const unsigned radii = __float_as_uint(c.z);
+    p.rx = (int)(radii & 0xffffu);
+    p.ry = (int)(radii >> 16);
+    p.q = c.w;
     // the equirectangular projection lands in [0, W] x [0, H]; a pinhole centre may lie off the image (|p| < 2^23)
     const bool inside = wrap ? (a.x >= 0.f && a.x <= (float)(tiles_x * tile) && a.y >= 0.f &&
                                 a.y <= (float)(tiles_y * tile))
                              : (fabsf(a.x) < 8388608.f && fabsf(a.y) < 8388608.f);
-    if (!inside || p.rx > kMaxRadius || p.ry > kMaxRadius || p.ry < 0) p.rx = 0;
+    if (!inside) p.rx = 0;
     return p;
+}
+
+// Column culling within the tile rows of a box. The alpha >= 1/255 ellipse dp^T conic dp <= q, with q raised to
+// q (1.001) + 1e-3, spans, over a band of pixel-centre offsets v = y + 1/2 - py in [v_lo, v_hi], the offsets
+// u in [x-(v_L), x+(v_R)], x-+(v) = (-c1 v -+ sqrt(c0 q - det v^2)) / c0 with det = c0 c2 - c1^2, where v_L and v_R
+// (the v of the ellipse's leftmost and rightmost points, +-c1 sqrt(q / (det c2))) are clamped to the band
+// intersected with the ellipse's own rows |v| <= sqrt(q c0 / det). A tile column is kept when its pixel centres come
+// within one pixel of that span. Each step is a single correctly rounded FP32 operation (no contraction), so that the
+// same decision can be reproduced exactly elsewhere. The row-invariant part is computed once per splat.
+struct RowCull {
+    float px, py, c0, c1;  // centre and the conic entries the rows use
+    float det, ey, yL, c0q;  // det <= 0: no culling (whole rows)
+};
+
+__device__ __forceinline__ RowCull row_cull_setup(const SplatPos& p, int nx, int tiles_x) {
+    RowCull rc;
+    rc.px = p.px;
+    rc.py = p.py;
+    rc.c0 = p.c0;
+    rc.c1 = p.c1;
+    rc.det = -1.f;
+    rc.ey = rc.yL = rc.c0q = 0.f;
+    if (nx >= tiles_x) return rc;
+    const float c0c2 = __fmul_rn(p.c0, p.c2), c1c1 = __fmul_rn(p.c1, p.c1);
+    const float det = __fsub_rn(c0c2, c1c1);
+    const float guard = __fmul_rn(1e-3f, c0c2);
+    if (!(det > guard) || !(p.c0 > 0.f) || !(p.c2 > 0.f)) return rc;
+    const float qw = __fadd_rn(__fmul_rn(p.q, 1.001f), 1e-3f);
+    rc.det = det;
+    rc.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(qw, p.c0), det));
+    rc.yL = __fmul_rn(p.c1, __fsqrt_rn(__fdiv_rn(qw, __fmul_rn(det, p.c2))));
+    rc.c0q = __fmul_rn(p.c0, qw);
+    return rc;
+}
+
+// Unwrapped tile columns (first, last) of tile row ty kept by a box with columns x0 .. x0 + nx - 1; first > last: none.
+__device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int ty, int tile) {
+    if (!(rc.det > 0.f)) return make_int2(x0, x0 + nx - 1);
+    const float tyT = (float)(ty * tile), fT = (float)tile;
+    const float yl = __fsub_rn(__fadd_rn(tyT, 0.5f), rc.py);
+    const float yh = __fsub_rn(__fsub_rn(__fadd_rn(tyT, fT), 0.5f), rc.py);
+    const float ney = -rc.ey;
+    const float lo = yl > ney ? yl : ney;
+    const float hi = yh < rc.ey ? yh : rc.ey;
+    if (lo > hi) return make_int2(1, 0);
+    const float nyL = -rc.yL;
+    const float vL = rc.yL < lo ? lo : (rc.yL > hi ? hi : rc.yL);
+    const float vR = nyL < lo ? lo : (nyL > hi ? hi : nyL);
+    float sL = __fsub_rn(rc.c0q, __fmul_rn(rc.det, __fmul_rn(vL, vL)));
+    sL = sL > 0.f ? sL : 0.f;
+    float sR = __fsub_rn(rc.c0q, __fmul_rn(rc.det, __fmul_rn(vR, vR)));
+    sR = sR > 0.f ? sR : 0.f;
+    const float xl = __fdiv_rn(__fsub_rn(-__fmul_rn(rc.c1, vL), __fsqrt_rn(sL)), rc.c0);
+    const float xr = __fdiv_rn(__fadd_rn(-__fmul_rn(rc.c1, vR), __fsqrt_rn(sR)), rc.c0);
+    const float ul = __fsub_rn(__fadd_rn(rc.px, xl), 1.f);
+    const float ur = __fadd_rn(__fadd_rn(rc.px, xr), 1.f);
+    // tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur
+    float a = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(ul, 0.5f), fT), fT));
+    float b = floorf(__fdiv_rn(__fsub_rn(ur, 0.5f), fT));
+    const float fx0 = (float)x0, fx1 = (float)(x0 + nx - 1);
+    a = a > fx0 ? a : fx0;
+    b = b < fx1 ? b : fx1;
+    return make_int2((int)a, (int)b);
+}
+
+// Instances of one splat: the kept columns of every row of its box.
+__device__ __forceinline__ unsigned splat_instances(const SplatPos& p, const Rect& r, int tiles_x, int tile) {
+    const RowCull rc = row_cull_setup(p, r.nx, tiles_x);
+    if (!(rc.det > 0.f)) return (unsigned)(r.nx * r.ny);
+    unsigned cnt = 0;
+    for (int ty = r.y0; ty < r.y0 + r.ny; ++ty) {
+        const int2 c = row_cols(rc, r.x0, r.nx, ty, tile);
+        cnt += c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+    }
+    return cnt;
 }
 
 // ------------------------------------------------------------------------------------------- 1: splat depth order
@@ -105,7 +187,7 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
             const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
-            cnt = (unsigned)(r.nx * r.ny);
+            cnt = splat_instances(p, r, tiles_x, tile);
         }
     }
     unsigned tot;
@@ -134,55 +216,101 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
     }
 }
 
-// The 256 splats of a CTA (consecutive in depth order) own one contiguous output range; each thread writes every 256th
-// instance of it (owner found by a binary search over the CTA's exclusive prefix of counts in shared memory), so stores
-// are coalesced and the work of the nearest, widest splats (which depth order puts side by side) is shared by the
-// whole CTA. Instances of a splat are listed row by row, columns in seam order.
+// The 256 splats of a CTA (consecutive in depth order) own one contiguous output range. Their box rows ("row items",
+// in splat order) are taken in chunks of kRowChunk: each thread finds the kept columns of kRowChunk / 256 consecutive
+// row items (owner splat by binary search over the CTA's prefix of row counts), a CTA scan turns the column counts
+// into output offsets, and each thread then writes every 256th instance of the chunk (owner row item by binary
+// search), so stores are coalesced and the work of the nearest, widest splats (which depth order puts side by side)
+// is shared by the whole CTA. Instances of a splat are listed row by row, columns in seam order.
+constexpr int kRowChunk = 1024;
+constexpr int kRowsPerThread = kRowChunk / kBinThreads;
+
 __global__ void __launch_bounds__(kBinThreads)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
                 int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, const u64* __restrict__ block_offsets,
                 u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
-    __shared__ unsigned s_excl[kBinThreads];
+    __shared__ unsigned s_rexcl[kBinThreads];     // prefix of box-row counts over the CTA's splats
     __shared__ int4 s_rect[kBinThreads];          // x0, nx, y0, rank
     __shared__ unsigned s_tbase[kBinThreads];
+    __shared__ float4 s_rc0[kBinThreads];         // RowCull: px, py, c0, c1
+    __shared__ float4 s_rc1[kBinThreads];         //          det, ey, yL, c0q
+    __shared__ unsigned s_iexcl[kRowChunk];       // prefix of kept-column counts over the chunk's row items
+    __shared__ int4 s_item[kRowChunk];            // first kept column (unwrapped), tile row, owner splat
     const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
     const int tiles = tiles_x * tiles_y;
-    unsigned cnt = 0;
+    unsigned rows = 0;
     Rect r = {0, 1, 0, 0};
     int rank = 0;
     unsigned tbase = 0;
+    RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f};
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
             r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
-            cnt = (unsigned)(r.nx * r.ny);
+            rows = r.nx > 0 ? (unsigned)r.ny : 0u;
+            rc = row_cull_setup(p, r.nx, tiles_x);
             const int64_t v = i / n;
             rank = (int)(i - v * n);
             tbase = (unsigned)v * (unsigned)tiles;
         }
     }
-    unsigned blk_total;
-    const unsigned excl = block_exclusive_scan<unsigned>(cnt, scratch, &blk_total);
-    s_excl[threadIdx.x] = excl;
+    unsigned rows_total;
+    const unsigned rexcl = block_exclusive_scan<unsigned>(rows, scratch, &rows_total);
+    s_rexcl[threadIdx.x] = rexcl;
     s_rect[threadIdx.x] = make_int4(r.x0, r.nx, r.y0, rank);
     s_tbase[threadIdx.x] = tbase;
+    s_rc0[threadIdx.x] = make_float4(rc.px, rc.py, rc.c0, rc.c1);
+    s_rc1[threadIdx.x] = make_float4(rc.det, rc.ey, rc.yL, rc.c0q);
     __syncthreads();
-    const u64 boff = block_offsets[blockIdx.x];
-    for (unsigned e = threadIdx.x; e < blk_total; e += kBinThreads) {
-        int j = 0;  // owner: the largest thread whose exclusive prefix is <= e
+    u64 out = block_offsets[blockIdx.x];
+    for (unsigned r0 = 0; r0 < rows_total; r0 += kRowChunk) {
+        unsigned cnt[kRowsPerThread], local = 0;
 #pragma unroll
-        for (int step = kBinThreads / 2; step >= 1; step >>= 1)
-            if (j + step < kBinThreads && s_excl[j + step] <= e) j += step;
-        const int4 rr = s_rect[j];
-        const unsigned k = e - s_excl[j];
-        const int row = (int)(k / (unsigned)rr.y);
-        const int col = (int)(k - (unsigned)row * (unsigned)rr.y);
-        int tx = (rr.x + col) % tiles_x;
-        tx += tx < 0 ? tiles_x : 0;
-        const u64 idx = boff + e;
-        if (idx < capacity)
-            keys[idx] = (((u64)s_tbase[j] + (u64)((rr.z + row) * tiles_x + tx)) << rank_bits) | (u64)rr.w;
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const unsigned ri = r0 + threadIdx.x * kRowsPerThread + k;
+            cnt[k] = 0;
+            int4 item = make_int4(0, 0, 0, 0);
+            if (ri < rows_total) {
+                int j = 0;  // owner: the largest splat whose row prefix is <= ri
+#pragma unroll
+                for (int step = kBinThreads / 2; step >= 1; step >>= 1)
+                    if (j + step < kBinThreads && s_rexcl[j + step] <= ri) j += step;
+                const int4 rr = s_rect[j];
+                const float4 a0 = s_rc0[j], a1 = s_rc1[j];
+                const RowCull rq = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const int ty = rr.z + (int)(ri - s_rexcl[j]);
+                const int2 c = row_cols(rq, rr.x, rr.y, ty, tile);
+                cnt[k] = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                item = make_int4(c.x, ty, j, 0);
+            }
+            s_item[threadIdx.x * kRowsPerThread + k] = item;
+            local += cnt[k];
+        }
+        unsigned chunk_total;
+        unsigned run = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const unsigned ri = r0 + threadIdx.x * kRowsPerThread + k;
+            s_iexcl[threadIdx.x * kRowsPerThread + k] = ri < rows_total ? run : 0xffffffffu;
+            run += cnt[k];
+        }
+        __syncthreads();
+        for (unsigned e = threadIdx.x; e < chunk_total; e += kBinThreads) {
+            int m = 0;  // owner: the largest row item whose prefix is <= e
+#pragma unroll
+            for (int step = kRowChunk / 2; step >= 1; step >>= 1)
+                if (m + step < kRowChunk && s_iexcl[m + step] <= e) m += step;
+            const int4 it = s_item[m];
+            const int4 rr = s_rect[it.z];
+            int tx = (it.x + (int)(e - s_iexcl[m])) % tiles_x;
+            tx += tx < 0 ? tiles_x : 0;
+            const u64 idx = out + e;
+            if (idx < capacity)
+                keys[idx] = (((u64)s_tbase[it.z] + (u64)(it.y * tiles_x + tx)) << rank_bits) | (u64)rr.w;
+        }
+        out += chunk_total;
+        __syncthreads();
     }
 }
 

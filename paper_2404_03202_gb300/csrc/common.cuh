@@ -17,7 +17,7 @@ constexpr float kAlphaMax = 0.99f;       // alpha clamp
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;          // stop once accumulated alpha would reach 0.9999
 constexpr float kPoleGuard = 1e-6f;      // rho is kept >= 1e-6 t_r inside J
-constexpr int kMaxRadius = 1 << 24;      // radii beyond W + H change nothing; kept finite for integer maths
+constexpr int kMaxRadius = 65535;        // instance-box half-extents are stored in 16 bits
 
 constexpr uint32_t kErrCapacity = 1u;
 

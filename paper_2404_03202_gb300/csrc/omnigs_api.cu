@@ -10,6 +10,8 @@
 
 #include "common.cuh"
 
+static_assert(sizeof(omnigs_splat) == 48, "omnigs_splat is three float4");
+
 namespace omnigs {
 
 int num_sms() {

@@ -283,7 +283,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[2] = make_float4(0.f, P.tr, __int_as_float(0), __uint_as_float(0u));
+            out[2] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
             continue;
         }
         const float inv = 1.f / P.det;
@@ -303,7 +303,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         if (!(255.f * o >= 1.f)) {  // alpha < 1/255 everywhere: no instance
             out[0] = make_float4(px, py, c0, c1);
             out[1] = make_float4(c2, o, 0.f, 0.f);
-            out[2] = make_float4(0.f, P.tr, __int_as_float(0), __int_as_float(0));
+            out[2] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
             continue;
         }
 
@@ -320,7 +320,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         }
         out[0] = make_float4(px, py, c0, c1);
         out[1] = make_float4(c2, o, rgb[0], rgb[1]);
-        out[2] = make_float4(rgb[2], P.tr, __int_as_float(rx), __int_as_float(ry));
+        out[2] = make_float4(rgb[2], P.tr, __uint_as_float((unsigned)rx | ((unsigned)ry << 16)), q);
     }
 }
 

@@ -96,7 +96,8 @@ densify_stats_kernel(int64_t n, int V, float half_w, float half_h, const float4*
     for (int v = 0; v < V; ++v) {
         const size_t i = (size_t)v * n + g;
         const float4 c = __ldg(splats + 3 * i + 2);
-        const int rx = __float_as_int(c.z), ry = __float_as_int(c.w);
+        const unsigned radii = __float_as_uint(c.z);
+        const int rx = (int)(radii & 0xffffu), ry = (int)(radii >> 16);
         if (rx <= 0) continue;
         const float4 gr = __ldg(grads + 3 * i);
         a += hypotf(gr.x * half_w, gr.y * half_h);

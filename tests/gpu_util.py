@@ -6,20 +6,26 @@ SPLAT_KEYS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth")
 
 
 def pack_splats(sp: dict) -> np.ndarray:
-    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (rx, ry stored as int32 bits)."""
+    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (rx | ry << 16 stored as uint32 bits, then
+    q = 2 ln(255 o), the dict's own when it has one)."""
+    import oracle
     m = len(sp["px"])
     out = np.zeros((m, 12), np.float32)
     for i, k in enumerate(SPLAT_KEYS):
         out[:, i] = np.asarray(sp[k], np.float32)
-    out[:, 10] = np.asarray(sp["rx"], np.int32).view(np.float32)
-    out[:, 11] = np.asarray(sp["ry"], np.int32).view(np.float32)
+    rx, ry = np.asarray(sp["rx"], np.int64), np.asarray(sp["ry"], np.int64)
+    assert rx.min(initial=0) >= 0 and rx.max(initial=0) <= 65535 and ry.min(initial=0) >= 0 and ry.max(initial=0) <= 65535
+    out[:, 10] = (rx | (ry << 16)).astype(np.uint32).view(np.float32)
+    out[:, 11] = oracle.splat_q(sp).astype(np.float32)
     return out
 
 
 def unpack_splats(arr: np.ndarray) -> dict:
     d = {k: arr[:, i].copy() for i, k in enumerate(SPLAT_KEYS)}
-    d["rx"] = arr[:, 10].copy().view(np.int32)
-    d["ry"] = arr[:, 11].copy().view(np.int32)
+    radii = arr[:, 10].copy().view(np.uint32)
+    d["rx"] = (radii & 0xFFFF).astype(np.int32)
+    d["ry"] = (radii >> 16).astype(np.int32)
+    d["q"] = arr[:, 11].copy()
     return d
 
 
@@ -62,8 +68,8 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
 
     Culling agrees except within 1e-6 (relative) of the near distance; p within 2e-6 W (H) px, the angle carrying a
     few ulp (longitude differences taken across the seam); conic within 1e-4 of its norm; rgb within 1e-5; opacity
-    copied exactly; the instance box (rx, ry) exact unless one of its ceil() arguments lies within 1e-4 of an
-    integer. Returns a summary."""
+    copied exactly; q = 2 ln(255 o) within 1e-5; the instance box (rx, ry) exact unless one of its ceil() arguments
+    lies within 1e-4 of an integer. Returns a summary."""
     import oracle
     ref = oracle.splats_from_records(rec)
     near_edge = np.abs(ref["depth"] - near) < 1e-6 * near
@@ -81,6 +87,7 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
     rgb_err = max(np.abs(got[k][a] - ref[k][a]).max(initial=0) for k in ("r", "g", "b"))
     assert rgb_err <= 1e-5
     assert np.array_equal(got["opacity"][a], opacity_expected[a])
+    np.testing.assert_allclose(got["q"][a], ref["q"][a], rtol=1e-5, atol=1e-5)
     margin_ok = rec[:, oracle.R_RMARGIN][a] > 1e-4 * np.maximum(1.0, ref["radius"][a])
     assert np.array_equal(got["rx"][a][margin_ok], ref["rx"][a][margin_ok])
     assert np.array_equal(got["ry"][a][margin_ok], ref["ry"][a][margin_ok])

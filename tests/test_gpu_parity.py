@@ -106,6 +106,44 @@ def test_sort_many_ties_and_all_columns():
 
 # ------------------------------------------------------------------ S5 render forward
 
+def _row_cull_splats(V, n, W, H, seed):
+    """Large, strongly sheared ellipses (correlations up to and past the 1 - 1e-3 determinant guard), opacities down
+    to just above 1/255 (q near 0), centres on pixel centres and tile corners; the nearest (first in depth order) are
+    the largest, so that one CTA's splats span many more than 1024 tile rows."""
+    rng = np.random.default_rng(seed)
+    m = V * n
+    sx, sy = rng.uniform(0.4, 50.0, m), rng.uniform(0.4, 50.0, m)
+    rho = rng.choice([0.0, 0.5, -0.9, 0.99, 0.9994, -0.9996, 0.99999, rng.uniform(-1, 1)], m)
+    s00, s11, s01 = sx * sx, sy * sy, rho * sx * sy
+    det = s00 * s11 - s01 * s01
+    o = rng.choice([1.0 / 255 + 1e-6, 0.01, 0.3, 0.99], m)
+    q = np.maximum(2 * np.log(255 * o), 0.0)
+    px = rng.uniform(0, W, m)
+    py = rng.uniform(0, H, m)
+    k = rng.uniform(size=m)
+    px[k < 0.2] = np.floor(px[k < 0.2]) + 0.5
+    px[(k >= 0.2) & (k < 0.3)] = 16.0 * rng.integers(0, W // 16, ((k >= 0.2) & (k < 0.3)).sum())
+    py[k >= 0.8] = 16.0 * rng.integers(0, H // 16, (k >= 0.8).sum())
+    rx = np.minimum(np.ceil(np.sqrt(q * s00) * (1 + 1e-4) + 1e-3), 3000).astype(np.int32)
+    ry = np.minimum(np.ceil(np.sqrt(q * s11) * (1 + 1e-4) + 1e-3), 3000).astype(np.int32)
+    return dict(px=px.astype(np.float32), py=py.astype(np.float32), c0=(s11 / det).astype(np.float32),
+                c1=(-s01 / det).astype(np.float32), c2=(s00 / det).astype(np.float32), opacity=o.astype(np.float32),
+                r=np.full(m, 0.5, np.float32), g=np.full(m, 0.5, np.float32), b=np.full(m, 0.5, np.float32),
+                depth=(1.0 / (sx * sy)).astype(np.float32), rx=rx, ry=ry, q=q.astype(np.float32))
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_bin_sort_row_culling_edges(tile):
+    """Tile lists under the per-row column culling, bit-exact, on splats that stress its decision procedure."""
+    W, H, V, n = 512, 256, 2, 3000
+    sp = _row_cull_splats(V, n, W, H, 40 + tile)
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V), capacity=1 << 20)
+    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
+    assert cnt == len(list_ref)
+    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64), ranges_ref)
+    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+
+
 def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
     r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V, bg=bg, ppt=ppt))
     sp64 = to64(sp)

@@ -345,6 +345,8 @@ def test_row_columns_hand_computed(oracle_lib):
     # the box bounds the columns; a box over every column keeps the row whole
     assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.0, 1 / 16, 9.0, 6, 1, 16, 3, 16) == (6, 6)
     assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.0, 1 / 16, 9.0, 0, 16, 16, 0, 16) == (0, 15)
+    # a conic whose determinant is within 1e-3 of c0 c2 from zero (a needle) keeps whole rows, even far away
+    assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.99999 / 16, 1 / 16, 9.0, 0, 15, 16, 0, 16) == (0, 14)
     # a sheared ellipse reaches further left above its centre when c1 < 0 ... and further right when c1 > 0
     lo = oracle.row_columns(108.4, 50.0, 1 / 16, -0.04, 1 / 16, 9.0, 0, 15, 16, 2, 16)
     hi = oracle.row_columns(108.4, 50.0, 1 / 16, 0.04, 1 / 16, 9.0, 0, 15, 16, 2, 16)
