@@ -434,10 +434,11 @@ static int inst_cmp(const void *a, const void *b)
 /* Columns [*cl, *cr] (unwrapped tile columns, within the box's x0 .. x0 + nx - 1) of tile row ty that the alpha >=
  * 1/255 ellipse dp^T conic dp <= q of a splat can reach, widened: q is raised by 0.1 % + 1e-3, the x-extent by one
  * pixel. Over the row's band of pixel-centre offsets v in [ty T + 1/2 - py, ty T + T - 1/2 - py], the ellipse spans
- * u in [x-(v_L), x+(v_R)] with x-+(v) = (-c1 v -+ sqrt(c0 q - det v^2)) / c0, det = c0 c2 - c1^2, and v_L, v_R the
- * offsets of its leftmost and rightmost points (+-c1 sqrt(q / (det c2))) clamped to the band. Every step is one FP32
- * operation (single rounding, no contraction). Rows of a box that spans every column, and splats whose det is not
- * well above zero, keep the whole row. *cl > *cr means no column. */
+ * u in [x-(v_L), x+(v_R)] with x-+(v) = -s v -+ sqrt(w2 - k v^2), where s = c1 / c0, w2 = q / c0 and
+ * k = det / c0^2 (det = c0 c2 - c1^2), and v_L, v_R the offsets of its leftmost and rightmost points
+ * (+-c1 sqrt(q / (det c2))) clamped to the band and to the ellipse's rows |v| <= sqrt(q c0 / det). Every step is one
+ * FP32 operation (single rounding, no contraction); the quotients by c0 are taken once per splat. Rows of a box that
+ * spans every column, and splats whose det is not well above zero, keep the whole row. *cl > *cr means no column. */
 static void row_columns(float px, float py, float c0, float c1, float c2, float q, int64_t x0, int64_t nx,
                         int64_t TX, int64_t ty, int T, int64_t *cl, int64_t *cr)
 {
@@ -450,43 +451,46 @@ static void row_columns(float px, float py, float c0, float c1, float c2, float 
     if (!(det > guard) || !(c0 > 0.0f) || !(c2 > 0.0f)) return;
     float qw = q * 1.001f;
     qw = qw + 1e-3f;
+    /* per splat */
+    float e2 = qw * c0;
+    e2 = e2 / det;
+    float ey = sqrtf(e2);
+    float d2 = det * c2;
+    float r2 = qw / d2;
+    float yL = sqrtf(r2);
+    yL = c1 * yL;
+    float s = c1 / c0;
+    float w2 = qw / c0;
+    float k = det / c0;
+    k = k / c0;
+    /* per row */
     float tyT = (float)(ty * T);
     float yl = tyT + 0.5f;
     yl = yl - py;
     float yh = tyT + (float)T;
     yh = yh - 0.5f;
     yh = yh - py;
-    float e2 = qw * c0;
-    e2 = e2 / det;
-    float ey = sqrtf(e2);
     float ney = -ey;
     float lo = yl > ney ? yl : ney;
     float hi = yh < ey ? yh : ey;
     if (lo > hi) { *cl = 1; *cr = 0; return; }
-    float d2 = det * c2;
-    float r2 = qw / d2;
-    float yL = sqrtf(r2);
-    yL = c1 * yL;
     float nyL = -yL;
     float vL = yL < lo ? lo : (yL > hi ? hi : yL);
     float vR = nyL < lo ? lo : (nyL > hi ? hi : nyL);
-    float c0q = c0 * qw;
-    float sL = vL * vL;
-    sL = det * sL;
-    sL = c0q - sL;
-    sL = sL > 0.0f ? sL : 0.0f;
-    float sR = vR * vR;
-    sR = det * sR;
-    sR = c0q - sR;
-    sR = sR > 0.0f ? sR : 0.0f;
-    float xl = c1 * vL;
+    float hL = vL * vL;
+    hL = k * hL;
+    hL = w2 - hL;
+    hL = hL > 0.0f ? hL : 0.0f;
+    float hR = vR * vR;
+    hR = k * hR;
+    hR = w2 - hR;
+    hR = hR > 0.0f ? hR : 0.0f;
+    float xl = s * vL;
     xl = -xl;
-    xl = xl - sqrtf(sL);
-    xl = xl / c0;
-    float xr = c1 * vR;
+    xl = xl - sqrtf(hL);
+    float xr = s * vR;
     xr = -xr;
-    xr = xr + sqrtf(sR);
-    xr = xr / c0;
+    xr = xr + sqrtf(hR);
     float ul = px + xl;
     ul = ul - 1.0f;
     float ur = px + xr;
