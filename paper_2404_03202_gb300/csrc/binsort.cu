@@ -65,15 +65,14 @@ struct SplatPos {
 // so malformed input cannot produce a tile index outside the image.
 __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size_t i, int tiles_x, int tiles_y,
                                              int tile, bool wrap) {
-    const float4 a = __ldg(sp + 3 * i);
-    const float c2 = __ldg(reinterpret_cast<const float*>(sp + 3 * i + 1));
-    const float4 c = __ldg(sp + 3 * i + 2);
+    const float4 a = __ldg(sp + 3 * i);      // px, py, c0, c1
+    const float4 c = __ldg(sp + 3 * i + 1);  // c2, depth, radii, q
     SplatPos p;
     p.px = a.x;
     p.py = a.y;
     p.c0 = a.z;
     p.c1 = a.w;
-    p.c2 = c2;
+    p.c2 = c.x;
     p.depth = c.y;
     const unsigned radii = __float_as_uint(c.z);
     p.rx = (int)(radii & 0xffffu);
@@ -89,40 +88,36 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
 
 // Column culling within the tile rows of a box. The alpha >= 1/255 ellipse dp^T conic dp <= q, with q raised to
 // q (1.001) + 1e-3, spans, over a band of pixel-centre offsets v = y + 1/2 - py in [v_lo, v_hi], the offsets
-// u in [x-(v_L), x+(v_R)], x-+(v) = (-c1 v -+ sqrt(c0 q - det v^2)) / c0 with det = c0 c2 - c1^2, where v_L and v_R
-// (the v of the ellipse's leftmost and rightmost points, +-c1 sqrt(q / (det c2))) are clamped to the band
-// intersected with the ellipse's own rows |v| <= sqrt(q c0 / det). A tile column is kept when its pixel centres come
-// within one pixel of that span. Each step is a single correctly rounded FP32 operation (no contraction), so that the
-// same decision can be reproduced exactly elsewhere. The row-invariant part is computed once per splat.
+// u in [x-(v_L), x+(v_R)], x-+(v) = -s v -+ sqrt(w2 - k v^2) with s = c1 / c0, w2 = q / c0, k = det / c0^2 and
+// det = c0 c2 - c1^2, where v_L and v_R (the v of the ellipse's leftmost and rightmost points, +-c1 sqrt(q / (det c2)))
+// are clamped to the band intersected with the ellipse's own rows |v| <= sqrt(q c0 / det). A tile column is kept when
+// its pixel centres come within one pixel of that span. Each step is a single correctly rounded FP32 operation (no
+// contraction), so that the same decision can be reproduced exactly elsewhere. The row-invariant part is computed
+// once per splat.
 struct RowCull {
-    float px, py, c0, c1;  // centre and the conic entries the rows use
-    float det, ey, yL, c0q;  // det <= 0: no culling (whole rows)
+    float px, py, s, yL;  // centre, shear c1 / c0, leftmost-point offset
+    float ey, w2, k;      // ey < 0: no culling (whole rows)
 };
 
 __device__ __forceinline__ RowCull row_cull_setup(const SplatPos& p, int nx, int tiles_x) {
-    RowCull rc;
-    rc.px = p.px;
-    rc.py = p.py;
-    rc.c0 = p.c0;
-    rc.c1 = p.c1;
-    rc.det = -1.f;
-    rc.ey = rc.yL = rc.c0q = 0.f;
+    RowCull rc = {p.px, p.py, 0.f, 0.f, -1.f, 0.f, 0.f};
     if (nx >= tiles_x) return rc;
     const float c0c2 = __fmul_rn(p.c0, p.c2), c1c1 = __fmul_rn(p.c1, p.c1);
     const float det = __fsub_rn(c0c2, c1c1);
     const float guard = __fmul_rn(1e-3f, c0c2);
     if (!(det > guard) || !(p.c0 > 0.f) || !(p.c2 > 0.f)) return rc;
     const float qw = __fadd_rn(__fmul_rn(p.q, 1.001f), 1e-3f);
-    rc.det = det;
     rc.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(qw, p.c0), det));
     rc.yL = __fmul_rn(p.c1, __fsqrt_rn(__fdiv_rn(qw, __fmul_rn(det, p.c2))));
-    rc.c0q = __fmul_rn(p.c0, qw);
+    rc.s = __fdiv_rn(p.c1, p.c0);
+    rc.w2 = __fdiv_rn(qw, p.c0);
+    rc.k = __fdiv_rn(__fdiv_rn(det, p.c0), p.c0);
     return rc;
 }
 
 // Unwrapped tile columns (first, last) of tile row ty kept by a box with columns x0 .. x0 + nx - 1; first > last: none.
 __device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int ty, int tile) {
-    if (!(rc.det > 0.f)) return make_int2(x0, x0 + nx - 1);
+    if (!(rc.ey >= 0.f)) return make_int2(x0, x0 + nx - 1);
     const float tyT = (float)(ty * tile), fT = (float)tile;
     const float yl = __fsub_rn(__fadd_rn(tyT, 0.5f), rc.py);
     const float yh = __fsub_rn(__fsub_rn(__fadd_rn(tyT, fT), 0.5f), rc.py);
@@ -133,27 +128,41 @@ __device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int 
     const float nyL = -rc.yL;
     const float vL = rc.yL < lo ? lo : (rc.yL > hi ? hi : rc.yL);
     const float vR = nyL < lo ? lo : (nyL > hi ? hi : nyL);
-    float sL = __fsub_rn(rc.c0q, __fmul_rn(rc.det, __fmul_rn(vL, vL)));
-    sL = sL > 0.f ? sL : 0.f;
-    float sR = __fsub_rn(rc.c0q, __fmul_rn(rc.det, __fmul_rn(vR, vR)));
-    sR = sR > 0.f ? sR : 0.f;
-    const float xl = __fdiv_rn(__fsub_rn(-__fmul_rn(rc.c1, vL), __fsqrt_rn(sL)), rc.c0);
-    const float xr = __fdiv_rn(__fadd_rn(-__fmul_rn(rc.c1, vR), __fsqrt_rn(sR)), rc.c0);
+    float hL = __fsub_rn(rc.w2, __fmul_rn(rc.k, __fmul_rn(vL, vL)));
+    hL = hL > 0.f ? hL : 0.f;
+    float hR = __fsub_rn(rc.w2, __fmul_rn(rc.k, __fmul_rn(vR, vR)));
+    hR = hR > 0.f ? hR : 0.f;
+    const float xl = __fsub_rn(-__fmul_rn(rc.s, vL), __fsqrt_rn(hL));
+    const float xr = __fadd_rn(-__fmul_rn(rc.s, vR), __fsqrt_rn(hR));
     const float ul = __fsub_rn(__fadd_rn(rc.px, xl), 1.f);
     const float ur = __fadd_rn(__fadd_rn(rc.px, xr), 1.f);
-    // tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur
-    float a = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(ul, 0.5f), fT), fT));
-    float b = floorf(__fdiv_rn(__fsub_rn(ur, 0.5f), fT));
+    // tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur; T is a power of two, so the
+    // product with 1 / T equals the correctly rounded quotient by T
+    const float inv_T = 1.f / fT;
+    float a = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(ul, 0.5f), fT), inv_T));
+    float b = floorf(__fmul_rn(__fsub_rn(ur, 0.5f), inv_T));
     const float fx0 = (float)x0, fx1 = (float)(x0 + nx - 1);
     a = a > fx0 ? a : fx0;
     b = b < fx1 ? b : fx1;
     return make_int2((int)a, (int)b);
 }
 
+// The CTAs of the binning passes are dispatched view-interleaved, so that the first blocks of every view, which hold
+// its nearest and widest splats and most of its instances, start first instead of forming a tail: dispatch index b
+// runs the (b / V)-th block of view b mod V, view v owning the blocks from the one holding its first splat
+// (floor(v n / 256)) up to the next view's. -1: no block (the grid is V times the largest view's block count).
+__device__ __forceinline__ int64_t logical_block(int V, int64_t n, unsigned nb) {
+    const unsigned b = blockIdx.x;
+    const int64_t v = b % (unsigned)V, j = b / (unsigned)V;
+    const int64_t first = v * n / kBinThreads;
+    const int64_t next = v + 1 < V ? (v + 1) * n / kBinThreads : (int64_t)nb;
+    return first + j < next ? first + j : -1;
+}
+
 // Instances of one splat: the kept columns of every row of its box.
 __device__ __forceinline__ unsigned splat_instances(const SplatPos& p, const Rect& r, int tiles_x, int tile) {
     const RowCull rc = row_cull_setup(p, r.nx, tiles_x);
-    if (!(rc.det > 0.f)) return (unsigned)(r.nx * r.ny);
+    if (!(rc.ey >= 0.f)) return (unsigned)(r.nx * r.ny);
     unsigned cnt = 0;
     for (int ty = r.y0; ty < r.y0 + r.ny; ++ty) {
         const int2 c = row_cols(rc, r.x0, r.nx, ty, tile);
@@ -170,29 +179,31 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
     const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
     if (i == 0) *count = (u64)total;
     if (i >= total) return;
-    const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 2) + 1);
+    const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 1) + 1);
     keys[i] = ((u64)(i / n) << 32) | (u64)__float_as_uint(d);
     vals[i] = (uint32_t)i;
 }
 
 // ------------------------------------------------------------------------------------------- 2: instances
 
-__global__ void __launch_bounds__(kBinThreads)
+__global__ void __launch_bounds__(kBinThreads, 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
-                 int tiles_y, int tile, int wrap, unsigned* __restrict__ block_sums) {
+                 int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
-    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
+    const int64_t blk = logical_block(V, n, nb);
+    if (blk < 0) return;
+    const int64_t i = blk * kBinThreads + threadIdx.x;  // position in (view, depth) order
     unsigned cnt = 0;
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
-            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
+            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
             cnt = splat_instances(p, r, tiles_x, tile);
         }
     }
     unsigned tot;
     block_exclusive_scan<unsigned>(cnt, scratch, &tot);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+    if (threadIdx.x == 0) block_sums[blk] = tot;
 }
 
 // One CTA: exclusive scan of the per-CTA sums in 64 bits; total to the header, overflow flagged.
@@ -218,36 +229,42 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
 
 // The 256 splats of a CTA (consecutive in depth order) own one contiguous output range. Their box rows ("row items",
 // in splat order) are taken in chunks of kRowChunk: each thread finds the kept columns of kRowChunk / 256 consecutive
-// row items (owner splat by binary search over the CTA's prefix of row counts), a CTA scan turns the column counts
-// into output offsets, and each thread then writes every 256th instance of the chunk (owner row item by binary
-// search), so stores are coalesced and the work of the nearest, widest splats (which depth order puts side by side)
-// is shared by the whole CTA. Instances of a splat are listed row by row, columns in seam order.
-constexpr int kRowChunk = 1024;
+// row items, and a CTA scan turns the column counts into output offsets. The chunk's instances are then produced in
+// rounds of kEmitSlots: each thread fills kEmitSlots / 256 consecutive slots of a shared-memory buffer, walking the
+// row items from the owner of its first slot (one binary search per thread and round), and the CTA copies the buffer
+// out with coalesced stores. The nearest, widest splats, which depth order puts side by side in the first CTAs of a
+// view, thus have their many instances written by the whole CTA at full store width. Instances of a splat are listed
+// row by row, columns in seam order.
+constexpr int kRowChunk = 512;
 constexpr int kRowsPerThread = kRowChunk / kBinThreads;
+constexpr int kEmitSlots = 1024;
+constexpr int kSlotsPerThread = kEmitSlots / kBinThreads;
 
-__global__ void __launch_bounds__(kBinThreads)
+__global__ void __launch_bounds__(kBinThreads, 8)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
-                int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, const u64* __restrict__ block_offsets,
-                u64* __restrict__ keys, u64 capacity) {
+                int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb,
+                const u64* __restrict__ block_offsets, u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ unsigned s_rexcl[kBinThreads];     // prefix of box-row counts over the CTA's splats
     __shared__ int4 s_rect[kBinThreads];          // x0, nx, y0, rank
-    __shared__ unsigned s_tbase[kBinThreads];
-    __shared__ float4 s_rc0[kBinThreads];         // RowCull: px, py, c0, c1
-    __shared__ float4 s_rc1[kBinThreads];         //          det, ey, yL, c0q
-    __shared__ unsigned s_iexcl[kRowChunk];       // prefix of kept-column counts over the chunk's row items
-    __shared__ int4 s_item[kRowChunk];            // first kept column (unwrapped), tile row, owner splat
-    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;  // position in (view, depth) order
+    __shared__ float4 s_rc0[kBinThreads];         // RowCull: px, py, s, yL
+    __shared__ float4 s_rc1[kBinThreads];         //          ey, w2, k; the view's first tile key (bits)
+    __shared__ unsigned s_iexcl[kRowChunk + 1];   // prefix of kept-column counts over the chunk's row items
+    __shared__ int2 s_item[kRowChunk];            // first kept column (unwrapped), tile row << 8 | owner splat
+    __shared__ u64 s_keys[kEmitSlots];
+    const int64_t blk = logical_block(V, n, nb);
+    if (blk < 0) return;
+    const int64_t i = blk * kBinThreads + threadIdx.x;  // position in (view, depth) order
     const int tiles = tiles_x * tiles_y;
     unsigned rows = 0;
     Rect r = {0, 1, 0, 0};
     int rank = 0;
     unsigned tbase = 0;
-    RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f};
+    RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
     if (i < total) {
         const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
         if (p.rx > 0) {
-            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, tile, wrap);
+            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
             rows = r.nx > 0 ? (unsigned)r.ny : 0u;
             rc = row_cull_setup(p, r.nx, tiles_x);
             const int64_t v = i / n;
@@ -259,30 +276,34 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
     const unsigned rexcl = block_exclusive_scan<unsigned>(rows, scratch, &rows_total);
     s_rexcl[threadIdx.x] = rexcl;
     s_rect[threadIdx.x] = make_int4(r.x0, r.nx, r.y0, rank);
-    s_tbase[threadIdx.x] = tbase;
-    s_rc0[threadIdx.x] = make_float4(rc.px, rc.py, rc.c0, rc.c1);
-    s_rc1[threadIdx.x] = make_float4(rc.det, rc.ey, rc.yL, rc.c0q);
+    s_rc0[threadIdx.x] = make_float4(rc.px, rc.py, rc.s, rc.yL);
+    s_rc1[threadIdx.x] = make_float4(rc.ey, rc.w2, rc.k, __uint_as_float(tbase));
     __syncthreads();
-    u64 out = block_offsets[blockIdx.x];
+    u64 out = block_offsets[blk];
     for (unsigned r0 = 0; r0 < rows_total; r0 += kRowChunk) {
+        // kept columns of this thread's row items r0 + tid * kRowsPerThread + k
+        const unsigned ri0 = r0 + threadIdx.x * kRowsPerThread;
         unsigned cnt[kRowsPerThread], local = 0;
+        int j = 0;  // owner of ri0: the largest splat whose row prefix is <= ri0
+        if (ri0 < rows_total) {
+#pragma unroll
+            for (int step = kBinThreads / 2; step >= 1; step >>= 1)
+                if (j + step < kBinThreads && s_rexcl[j + step] <= ri0) j += step;
+        }
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            const unsigned ri = r0 + threadIdx.x * kRowsPerThread + k;
+            const unsigned ri = ri0 + k;
             cnt[k] = 0;
-            int4 item = make_int4(0, 0, 0, 0);
+            int2 item = make_int2(0, 0);
             if (ri < rows_total) {
-                int j = 0;  // owner: the largest splat whose row prefix is <= ri
-#pragma unroll
-                for (int step = kBinThreads / 2; step >= 1; step >>= 1)
-                    if (j + step < kBinThreads && s_rexcl[j + step] <= ri) j += step;
+                while (j + 1 < kBinThreads && s_rexcl[j + 1] <= ri) ++j;
                 const int4 rr = s_rect[j];
                 const float4 a0 = s_rc0[j], a1 = s_rc1[j];
-                const RowCull rq = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const RowCull rq = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
                 const int ty = rr.z + (int)(ri - s_rexcl[j]);
                 const int2 c = row_cols(rq, rr.x, rr.y, ty, tile);
                 cnt[k] = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
-                item = make_int4(c.x, ty, j, 0);
+                item = make_int2(c.x, (ty << 8) | j);
             }
             s_item[threadIdx.x * kRowsPerThread + k] = item;
             local += cnt[k];
@@ -291,26 +312,46 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         unsigned run = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            const unsigned ri = r0 + threadIdx.x * kRowsPerThread + k;
+            const unsigned ri = ri0 + k;
             s_iexcl[threadIdx.x * kRowsPerThread + k] = ri < rows_total ? run : 0xffffffffu;
             run += cnt[k];
         }
+        if (threadIdx.x == 0) s_iexcl[kRowChunk] = 0xffffffffu;
         __syncthreads();
-        for (unsigned e = threadIdx.x; e < chunk_total; e += kBinThreads) {
-            int m = 0;  // owner: the largest row item whose prefix is <= e
+        for (unsigned base = 0; base < chunk_total; base += kEmitSlots) {
+            const unsigned slot0 = base + threadIdx.x * kSlotsPerThread;
+            if (slot0 < chunk_total) {
+                int m = 0;  // owner of slot0: the largest row item whose prefix is <= slot0
 #pragma unroll
-            for (int step = kRowChunk / 2; step >= 1; step >>= 1)
-                if (m + step < kRowChunk && s_iexcl[m + step] <= e) m += step;
-            const int4 it = s_item[m];
-            const int4 rr = s_rect[it.z];
-            int tx = (it.x + (int)(e - s_iexcl[m])) % tiles_x;
-            tx += tx < 0 ? tiles_x : 0;
-            const u64 idx = out + e;
-            if (idx < capacity)
-                keys[idx] = (((u64)s_tbase[it.z] + (u64)(it.y * tiles_x + tx)) << rank_bits) | (u64)rr.w;
+                for (int step = kRowChunk / 2; step >= 1; step >>= 1)
+                    if (m + step < kRowChunk && s_iexcl[m + step] <= slot0) m += step;
+                unsigned cur = s_iexcl[m], next = s_iexcl[m + 1];
+                int2 it = s_item[m];
+                const unsigned slot1 = min(slot0 + kSlotsPerThread, chunk_total);
+                for (unsigned e = slot0; e < slot1; ++e) {
+                    while (e >= next) {  // zero-count items share their prefix with the next item
+                        ++m;
+                        cur = next;
+                        next = s_iexcl[m + 1];
+                        it = s_item[m];
+                    }
+                    const int js = it.y & 0xff, ty = it.y >> 8;
+                    // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
+                    int tx = it.x + (int)(e - cur);
+                    tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
+                    const unsigned tb = __float_as_uint(s_rc1[js].w);
+                    s_keys[e - base] = (((u64)tb + (u64)(ty * tiles_x + tx)) << rank_bits) | (u64)s_rect[js].w;
+                }
+            }
+            __syncthreads();
+            const unsigned cnt_round = min((unsigned)kEmitSlots, chunk_total - base);
+            for (unsigned e = threadIdx.x; e < cnt_round; e += kBinThreads) {
+                const u64 idx = out + base + e;
+                if (idx < capacity) keys[idx] = s_keys[e];
+            }
+            __syncthreads();
         }
         out += chunk_total;
-        __syncthreads();
     }
 }
 
@@ -615,16 +656,24 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(cfg.num_views),
                        sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
     if (e != cudaSuccess) return e;
+    const int V = cfg.num_views;
+    unsigned per_view = 0;  // the largest number of blocks a view owns
+    for (int v = 0; v < V; ++v) {
+        const int64_t first = (int64_t)v * n / kBinThreads;
+        const int64_t next = v + 1 < V ? (int64_t)(v + 1) * n / kBinThreads : (int64_t)nb;
+        per_view = std::max(per_view, (unsigned)(next - first));
+    }
+    const unsigned grid = per_view * (unsigned)V;
     {
         ProfScope prof("bin_count", stream, 2);
-        bin_count_kernel<<<nb, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, bsums);
+        bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb, bsums);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream);
-        bin_emit_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, wrap,
-                                                         rank_bits_for(n),
-                                                         boffs, reinterpret_cast<u64*>(keys), (u64)capacity);
+        bin_emit_kernel<<<grid, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, wrap,
+                                                           rank_bits_for(n), V, nb, boffs,
+                                                           reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();
 }

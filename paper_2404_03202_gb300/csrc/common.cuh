@@ -35,19 +35,15 @@ struct Rect {
     int x0, nx, y0, ny;
 };
 
-__host__ __device__ inline int floordiv_int(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
-
 // Tiles covered by the box of half-extents (rx, ry) around pixel floor(p): columns x0 .. x0 + nx - 1 modulo the
 // column count (all columns, from 0, once the box is at least as wide as the image) when `wrap` (the equirectangular
 // longitude seam), clipped to the image like the rows otherwise (pinhole camera).
-__device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_x, int tiles_y, int tile, bool wrap) {
+// tile_shift = log2(tile) (tiles are powers of two): an arithmetic right shift is the floor quotient.
+__device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_x, int tiles_y, int tile_shift,
+                                  bool wrap) {
     Rect R;
     int ix = (int)floorf(px), iy = (int)floorf(py);
-    int x0 = floordiv_int(ix - rx, tile), x1 = floordiv_int(ix + rx, tile);
+    int x0 = (ix - rx) >> tile_shift, x1 = (ix + rx) >> tile_shift;
     if (!wrap) {
         x0 = x0 < 0 ? 0 : x0;
         x1 = x1 > tiles_x - 1 ? tiles_x - 1 : x1;
@@ -57,7 +53,7 @@ __device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_
         x0 = 0;
         nx = tiles_x;
     }
-    int y0 = floordiv_int(iy - ry, tile), y1 = floordiv_int(iy + ry, tile);
+    int y0 = (iy - ry) >> tile_shift, y1 = (iy + ry) >> tile_shift;
     y0 = y0 < 0 ? 0 : y0;
     y1 = y1 > tiles_y - 1 ? tiles_y - 1 : y1;
     R.x0 = x0;

@@ -92,7 +92,7 @@ bool valid_cfg(const omnigs_config* c) {
     if (!c) return false;
     if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
     if (c->width <= 0 || c->height <= 0 || c->width % c->tile || c->height % c->tile) return false;
-    if (c->width > (1 << 20) || c->height > (1 << 20)) return false;
+    if (c->width > 65536 || c->height > 65536) return false;  // instance-box half-extents are 16-bit
     if (c->num_views < 1 || c->num_views > 4096) return false;
     if (c->sh_degree < 0 || c->sh_degree > 3) return false;
     if (!std::isfinite(c->near_r) || c->near_r < 0.f) return false;

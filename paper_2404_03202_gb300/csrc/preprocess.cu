@@ -282,8 +282,8 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         float4* out = splats + 3 * ((size_t)v * n + g);
         if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[2] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
+            out[1] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
+            out[2] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
         const float inv = 1.f / P.det;
@@ -302,8 +302,8 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         const int rx = (int)fminf(hx, lim), ry = (int)fminf(hy, lim);
         if (!(255.f * o >= 1.f)) {  // alpha < 1/255 everywhere: no instance
             out[0] = make_float4(px, py, c0, c1);
-            out[1] = make_float4(c2, o, 0.f, 0.f);
-            out[2] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
+            out[1] = make_float4(c2, P.tr, __uint_as_float(0u), 0.f);
+            out[2] = make_float4(o, 0.f, 0.f, 0.f);
             continue;
         }
 
@@ -319,8 +319,8 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
             rgb[ch] = fmaxf(acc + 0.5f, 0.f);
         }
         out[0] = make_float4(px, py, c0, c1);
-        out[1] = make_float4(c2, o, rgb[0], rgb[1]);
-        out[2] = make_float4(rgb[2], P.tr, __uint_as_float((unsigned)rx | ((unsigned)ry << 16)), q);
+        out[1] = make_float4(c2, P.tr, __uint_as_float((unsigned)rx | ((unsigned)ry << 16)), q);
+        out[2] = make_float4(o, rgb[0], rgb[1], rgb[2]);
     }
 }
 

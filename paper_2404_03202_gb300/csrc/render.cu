@@ -51,21 +51,21 @@ __device__ __forceinline__ unsigned entry_splat(const unsigned long long* __rest
 
 __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats, unsigned vg, float x_first,
                                               float x_last, float halfW, float fW) {
-    const float4 a = __ldg(splats + 3 * (size_t)vg);
-    const float4 b = __ldg(splats + 3 * (size_t)vg + 1);
-    const float blue = __ldg(reinterpret_cast<const float*>(splats + 3 * (size_t)vg + 2));
+    const float4 a = __ldg(splats + 3 * (size_t)vg);                                   // px, py, c0, c1
+    const float c2 = __ldg(reinterpret_cast<const float*>(splats + 3 * (size_t)vg + 1));
+    const float4 col = __ldg(splats + 3 * (size_t)vg + 2);                             // opacity, r, g, b
     const float hi = a.x - x_first, lo = a.x - x_last;  // extreme dx over the tile's pixel columns
     float shift;
     if (lo >= -halfW && hi < halfW) shift = 0.f;
     else if (lo >= halfW) shift = -fW;
     else if (hi < -halfW) shift = fW;
     else shift = kPerPixelWrap;
-    const float c0 = a.z, c1 = a.w, c2 = b.x, o = b.y;
+    const float c0 = a.z, c1 = a.w, o = col.x;
     const float thr = -__log2f(255.f * o);  // may be +inf (o = 0): then nothing passes
     Staged s;
     s.a = make_float4(a.x, a.y, -0.5f * kLog2e * c0, -kLog2e * c1);
     s.b = make_float4(-0.5f * kLog2e * c2, 0.5f * thr, -0.5f * thr, shift);
-    s.c = make_float4(o, b.z, b.w, blue);
+    s.c = col;
     s.d = make_float4(c0, c1, c2, 0.f);
     return s;
 }

@@ -95,7 +95,7 @@ densify_stats_kernel(int64_t n, int V, float half_w, float half_h, const float4*
     int k = count[g];
     for (int v = 0; v < V; ++v) {
         const size_t i = (size_t)v * n + g;
-        const float4 c = __ldg(splats + 3 * i + 2);
+        const float4 c = __ldg(splats + 3 * i + 1);  // c2, depth, radii, q
         const unsigned radii = __float_as_uint(c.z);
         const int rx = (int)(radii & 0xffffu), ry = (int)(radii >> 16);
         if (rx <= 0) continue;
