@@ -150,25 +150,13 @@ __device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int 
 // The CTAs of the binning passes are dispatched view-interleaved, so that the first blocks of every view, which hold
 // its nearest and widest splats and most of its instances, start first instead of forming a tail: dispatch index b
 // runs the (b / V)-th block of view b mod V, view v owning the blocks from the one holding its first splat
-// (floor(v n / 256)) up to the next view's. -1: no block (the grid is V times the largest view's block count).
+// (floor(v n / kBinSplats)) up to the next view's. -1: no block (the grid is V times the largest view's block count).
 __device__ __forceinline__ int64_t logical_block(int V, int64_t n, unsigned nb) {
     const unsigned b = blockIdx.x;
     const int64_t v = b % (unsigned)V, j = b / (unsigned)V;
-    const int64_t first = v * n / kBinThreads;
-    const int64_t next = v + 1 < V ? (v + 1) * n / kBinThreads : (int64_t)nb;
+    const int64_t first = v * n / kBinSplats;
+    const int64_t next = v + 1 < V ? (v + 1) * n / kBinSplats : (int64_t)nb;
     return first + j < next ? first + j : -1;
-}
-
-// Instances of one splat: the kept columns of every row of its box.
-__device__ __forceinline__ unsigned splat_instances(const SplatPos& p, const Rect& r, int tiles_x, int tile) {
-    const RowCull rc = row_cull_setup(p, r.nx, tiles_x);
-    if (!(rc.ey >= 0.f)) return (unsigned)(r.nx * r.ny);
-    unsigned cnt = 0;
-    for (int ty = r.y0; ty < r.y0 + r.ny; ++ty) {
-        const int2 c = row_cols(rc, r.x0, r.nx, ty, tile);
-        cnt += c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
-    }
-    return cnt;
 }
 
 // ------------------------------------------------------------------------------------------- 1: splat depth order
@@ -186,19 +174,108 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
 
 // ------------------------------------------------------------------------------------------- 2: instances
 
+// Both instance passes give each CTA kBinSplats consecutive splats of the (view, depth) order (kSplatsPerThread
+// consecutive ones per thread, their loads in flight together) and work on their box rows ("row items", in splat
+// order), so that the rows of the nearest, widest splats, which depth order puts side by side, are spread over the
+// whole CTA: every thread takes kRowsPerThread consecutive row items at a time (owner splat by one binary search over
+// the CTA's prefix of row counts, then a forward walk).
+constexpr int kRowChunk = 512;
+constexpr int kRowsPerThread = kRowChunk / kBinThreads;
+
+struct CtaRows {
+    unsigned rexcl[kBinSplats];  // prefix of box-row counts over the CTA's splats
+    int4 rect[kBinSplats];       // x0, nx, y0, depth rank
+    float4 rc0[kBinSplats];      // RowCull: px, py, s, yL
+    float4 rc1[kBinSplats];      //          ey, w2, k; the view's first tile key (bits)
+};
+
+// Loads splats i0 + kSplatsPerThread * tid + u (positions in (view, depth) order) and fills S; returns the CTA's
+// row-item count.
+__device__ __forceinline__ unsigned stage_rows(CtaRows& S, unsigned* scratch, const float4* __restrict__ splats,
+                                               const uint32_t* __restrict__ order, int64_t i0, int64_t total, int64_t n,
+                                               int tiles_x, int tiles_y, int tile, int wrap) {
+    const int s0 = threadIdx.x * kSplatsPerThread;
+    unsigned rows[kSplatsPerThread], local = 0;
+    uint32_t idx[kSplatsPerThread];
+#pragma unroll
+    for (int u = 0; u < kSplatsPerThread; ++u) {
+        const int64_t i = i0 + s0 + u;
+        idx[u] = i < total ? __ldg(order + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kSplatsPerThread; ++u) {
+        const int64_t i = i0 + s0 + u;
+        rows[u] = 0;
+        Rect r = {0, 1, 0, 0};
+        int rank = 0;
+        unsigned tbase = 0;
+        RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
+        if (i < total) {
+            const SplatPos p = load_pos(splats, (size_t)idx[u], tiles_x, tiles_y, tile, wrap);
+            if (p.rx > 0) {
+                r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
+                rows[u] = r.nx > 0 ? (unsigned)r.ny : 0u;
+                rc = row_cull_setup(p, r.nx, tiles_x);
+                const int64_t v = i / n;
+                rank = (int)(i - v * n);
+                tbase = (unsigned)v * (unsigned)(tiles_x * tiles_y);
+            }
+        }
+        S.rect[s0 + u] = make_int4(r.x0, r.nx, r.y0, rank);
+        S.rc0[s0 + u] = make_float4(rc.px, rc.py, rc.s, rc.yL);
+        S.rc1[s0 + u] = make_float4(rc.ey, rc.w2, rc.k, __uint_as_float(tbase));
+        local += rows[u];
+    }
+    unsigned rows_total;
+    unsigned run = block_exclusive_scan<unsigned>(local, scratch, &rows_total);
+#pragma unroll
+    for (int u = 0; u < kSplatsPerThread; ++u) {
+        S.rexcl[s0 + u] = run;
+        run += rows[u];
+    }
+    __syncthreads();
+    return rows_total;
+}
+
+// The splat owning row item ri: the largest j whose row prefix is <= ri (ri < the CTA's row-item count).
+__device__ __forceinline__ int row_owner(const CtaRows& S, unsigned ri) {
+    int j = 0;
+#pragma unroll
+    for (int step = kBinSplats / 2; step >= 1; step >>= 1)
+        if (j + step < kBinSplats && S.rexcl[j + step] <= ri) j += step;
+    return j;
+}
+
+// Kept columns of row item ri, whose owner is j or a later splat (j is advanced to it); tile row in *ty.
+__device__ __forceinline__ int2 row_item_cols(const CtaRows& S, unsigned ri, int& j, int tile, int* ty) {
+    while (j + 1 < kBinSplats && S.rexcl[j + 1] <= ri) ++j;
+    const int4 rr = S.rect[j];
+    const float4 a0 = S.rc0[j], a1 = S.rc1[j];
+    const RowCull rq = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
+    *ty = rr.z + (int)(ri - S.rexcl[j]);
+    return row_cols(rq, rr.x, rr.y, *ty, tile);
+}
+
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
                  int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
+    __shared__ CtaRows S;
     const int64_t blk = logical_block(V, n, nb);
     if (blk < 0) return;
-    const int64_t i = blk * kBinThreads + threadIdx.x;  // position in (view, depth) order
+    const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
+                                           tile, wrap);
     unsigned cnt = 0;
-    if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
-        if (p.rx > 0) {
-            const Rect r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
-            cnt = splat_instances(p, r, tiles_x, tile);
+    for (unsigned ri0 = threadIdx.x * kRowsPerThread; ri0 < rows_total; ri0 += kRowChunk) {
+        int j = row_owner(S, ri0);
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const unsigned ri = ri0 + k;
+            if (ri < rows_total) {
+                int ty;
+                const int2 c = row_item_cols(S, ri, j, tile, &ty);
+                cnt += c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+            }
         }
     }
     unsigned tot;
@@ -227,129 +304,75 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
     }
 }
 
-// The 256 splats of a CTA (consecutive in depth order) own one contiguous output range. Their box rows ("row items",
-// in splat order) are taken in chunks of kRowChunk: each thread finds the kept columns of kRowChunk / 256 consecutive
-// row items, and a CTA scan turns the column counts into output offsets. The chunk's instances are then produced in
-// rounds of kEmitSlots: each thread fills kEmitSlots / 256 consecutive slots of a shared-memory buffer, walking the
-// row items from the owner of its first slot (one binary search per thread and round), and the CTA copies the buffer
-// out with coalesced stores. The nearest, widest splats, which depth order puts side by side in the first CTAs of a
-// view, thus have their many instances written by the whole CTA at full store width. Instances of a splat are listed
-// row by row, columns in seam order.
-constexpr int kRowChunk = 512;
-constexpr int kRowsPerThread = kRowChunk / kBinThreads;
-constexpr int kEmitSlots = 1024;
-constexpr int kSlotsPerThread = kEmitSlots / kBinThreads;
+// The splats of a CTA (consecutive in depth order) own one contiguous output range. Their row items are taken
+// kRowsPerThread consecutive ones per thread at a time; a CTA scan of the kept-column counts gives every row item its
+// output offset. A thread writes the instances of its short row items itself (kDirect columns or fewer); the warp
+// writes the longer ones together, 32 consecutive columns per store, so that the rows of the nearest, widest splats
+// are written at full store width. Instances of a splat are listed row by row, columns in seam order.
+constexpr unsigned kDirect = 4;
 
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
                 int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb,
                 const u64* __restrict__ block_offsets, u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
-    __shared__ unsigned s_rexcl[kBinThreads];     // prefix of box-row counts over the CTA's splats
-    __shared__ int4 s_rect[kBinThreads];          // x0, nx, y0, rank
-    __shared__ float4 s_rc0[kBinThreads];         // RowCull: px, py, s, yL
-    __shared__ float4 s_rc1[kBinThreads];         //          ey, w2, k; the view's first tile key (bits)
-    __shared__ unsigned s_iexcl[kRowChunk + 1];   // prefix of kept-column counts over the chunk's row items
-    __shared__ int2 s_item[kRowChunk];            // first kept column (unwrapped), tile row << 8 | owner splat
-    __shared__ u64 s_keys[kEmitSlots];
+    __shared__ CtaRows S;
     const int64_t blk = logical_block(V, n, nb);
     if (blk < 0) return;
-    const int64_t i = blk * kBinThreads + threadIdx.x;  // position in (view, depth) order
-    const int tiles = tiles_x * tiles_y;
-    unsigned rows = 0;
-    Rect r = {0, 1, 0, 0};
-    int rank = 0;
-    unsigned tbase = 0;
-    RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
-    if (i < total) {
-        const SplatPos p = load_pos(splats, (size_t)order[i], tiles_x, tiles_y, tile, wrap);
-        if (p.rx > 0) {
-            r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
-            rows = r.nx > 0 ? (unsigned)r.ny : 0u;
-            rc = row_cull_setup(p, r.nx, tiles_x);
-            const int64_t v = i / n;
-            rank = (int)(i - v * n);
-            tbase = (unsigned)v * (unsigned)tiles;
-        }
-    }
-    unsigned rows_total;
-    const unsigned rexcl = block_exclusive_scan<unsigned>(rows, scratch, &rows_total);
-    s_rexcl[threadIdx.x] = rexcl;
-    s_rect[threadIdx.x] = make_int4(r.x0, r.nx, r.y0, rank);
-    s_rc0[threadIdx.x] = make_float4(rc.px, rc.py, rc.s, rc.yL);
-    s_rc1[threadIdx.x] = make_float4(rc.ey, rc.w2, rc.k, __uint_as_float(tbase));
-    __syncthreads();
+    const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
+                                           tile, wrap);
+    const unsigned lane = lane_id();
     u64 out = block_offsets[blk];
     for (unsigned r0 = 0; r0 < rows_total; r0 += kRowChunk) {
-        // kept columns of this thread's row items r0 + tid * kRowsPerThread + k
         const unsigned ri0 = r0 + threadIdx.x * kRowsPerThread;
         unsigned cnt[kRowsPerThread], local = 0;
-        int j = 0;  // owner of ri0: the largest splat whose row prefix is <= ri0
-        if (ri0 < rows_total) {
-#pragma unroll
-            for (int step = kBinThreads / 2; step >= 1; step >>= 1)
-                if (j + step < kBinThreads && s_rexcl[j + step] <= ri0) j += step;
-        }
+        u64 key0[kRowsPerThread];  // key of the item's first column, before the column wrap
+        int cl[kRowsPerThread];
+        int j = ri0 < rows_total ? row_owner(S, ri0) : 0;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
             const unsigned ri = ri0 + k;
             cnt[k] = 0;
-            int2 item = make_int2(0, 0);
+            cl[k] = 0;
+            key0[k] = 0;
             if (ri < rows_total) {
-                while (j + 1 < kBinThreads && s_rexcl[j + 1] <= ri) ++j;
-                const int4 rr = s_rect[j];
-                const float4 a0 = s_rc0[j], a1 = s_rc1[j];
-                const RowCull rq = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
-                const int ty = rr.z + (int)(ri - s_rexcl[j]);
-                const int2 c = row_cols(rq, rr.x, rr.y, ty, tile);
+                int ty;
+                const int2 c = row_item_cols(S, ri, j, tile, &ty);
                 cnt[k] = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
-                item = make_int2(c.x, (ty << 8) | j);
+                cl[k] = c.x;
+                const unsigned tb = __float_as_uint(S.rc1[j].w) + (unsigned)(ty * tiles_x);
+                key0[k] = ((u64)tb << rank_bits) | (u64)S.rect[j].w;
             }
-            s_item[threadIdx.x * kRowsPerThread + k] = item;
             local += cnt[k];
         }
         unsigned chunk_total;
-        unsigned run = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+        const u64 base = out + block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+        u64 off = base;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            const unsigned ri = ri0 + k;
-            s_iexcl[threadIdx.x * kRowsPerThread + k] = ri < rows_total ? run : 0xffffffffu;
-            run += cnt[k];
-        }
-        if (threadIdx.x == 0) s_iexcl[kRowChunk] = 0xffffffffu;
-        __syncthreads();
-        for (unsigned base = 0; base < chunk_total; base += kEmitSlots) {
-            const unsigned slot0 = base + threadIdx.x * kSlotsPerThread;
-            if (slot0 < chunk_total) {
-                int m = 0;  // owner of slot0: the largest row item whose prefix is <= slot0
-#pragma unroll
-                for (int step = kRowChunk / 2; step >= 1; step >>= 1)
-                    if (m + step < kRowChunk && s_iexcl[m + step] <= slot0) m += step;
-                unsigned cur = s_iexcl[m], next = s_iexcl[m + 1];
-                int2 it = s_item[m];
-                const unsigned slot1 = min(slot0 + kSlotsPerThread, chunk_total);
-                for (unsigned e = slot0; e < slot1; ++e) {
-                    while (e >= next) {  // zero-count items share their prefix with the next item
-                        ++m;
-                        cur = next;
-                        next = s_iexcl[m + 1];
-                        it = s_item[m];
-                    }
-                    const int js = it.y & 0xff, ty = it.y >> 8;
-                    // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
-                    int tx = it.x + (int)(e - cur);
+            // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
+            if (cnt[k] <= kDirect) {
+                for (unsigned c = 0; c < cnt[k]; ++c) {
+                    int tx = cl[k] + (int)c;
                     tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-                    const unsigned tb = __float_as_uint(s_rc1[js].w);
-                    s_keys[e - base] = (((u64)tb + (u64)(ty * tiles_x + tx)) << rank_bits) | (u64)s_rect[js].w;
+                    if (off + c < capacity) keys[off + c] = key0[k] + ((u64)tx << rank_bits);
                 }
             }
-            __syncthreads();
-            const unsigned cnt_round = min((unsigned)kEmitSlots, chunk_total - base);
-            for (unsigned e = threadIdx.x; e < cnt_round; e += kBinThreads) {
-                const u64 idx = out + base + e;
-                if (idx < capacity) keys[idx] = s_keys[e];
+            unsigned long_items = __ballot_sync(0xffffffffu, cnt[k] > kDirect);
+            while (long_items) {
+                const int src = __ffs(long_items) - 1;
+                long_items &= long_items - 1;
+                const unsigned m = __shfl_sync(0xffffffffu, cnt[k], src);
+                const int c0 = __shfl_sync(0xffffffffu, cl[k], src);
+                const u64 k0 = __shfl_sync(0xffffffffu, key0[k], src);
+                const u64 o = __shfl_sync(0xffffffffu, off, src);
+                for (unsigned c = lane; c < m; c += 32) {
+                    int tx = c0 + (int)c;
+                    tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
+                    if (o + c < capacity) keys[o + c] = k0 + ((u64)tx << rank_bits);
+                }
             }
-            __syncthreads();
+            off += cnt[k];
         }
         out += chunk_total;
     }
@@ -648,10 +671,11 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
     unsigned* bsums = reinterpret_cast<unsigned*>(ws + L.block_sums);
     u64* boffs = reinterpret_cast<u64*>(ws + L.block_offsets);
-    const unsigned nb = (unsigned)((total + kBinThreads - 1) / kBinThreads);
+    const unsigned nb = (unsigned)((total + kBinSplats - 1) / kBinSplats);  // blocks of the instance passes
     {
         ProfScope prof("depth_keys", stream);
-        depth_keys_kernel<<<nb, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
+        const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
+        depth_keys_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
     }
     e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(cfg.num_views),
                        sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
@@ -659,8 +683,8 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     const int V = cfg.num_views;
     unsigned per_view = 0;  // the largest number of blocks a view owns
     for (int v = 0; v < V; ++v) {
-        const int64_t first = (int64_t)v * n / kBinThreads;
-        const int64_t next = v + 1 < V ? (int64_t)(v + 1) * n / kBinThreads : (int64_t)nb;
+        const int64_t first = (int64_t)v * n / kBinSplats;
+        const int64_t next = v + 1 < V ? (int64_t)(v + 1) * n / kBinSplats : (int64_t)nb;
         per_view = std::max(per_view, (unsigned)(next - first));
     }
     const unsigned grid = per_view * (unsigned)V;

@@ -75,6 +75,8 @@ struct WsLayout {
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kBinThreads = 256;
+constexpr int kSplatsPerThread = 1;  // splats per thread in the instance passes
+constexpr int kBinSplats = kBinThreads * kSplatsPerThread;
 constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
 constexpr int kSortCtasPerSm = 6;    // radix-sort grid: up to this many CTAs per SM
 constexpr int kLossThreads = 256;
