@@ -42,8 +42,8 @@ typedef enum {
 
 /* Image and camera set-up shared by all calls of one frame. */
 typedef struct {
-    int32_t width;     /* W, equirectangular width in pixels; a multiple of `tile` */
-    int32_t height;    /* H, height in pixels; a multiple of `tile` (W = 2H is the usual equirect shape) */
+    int32_t width;     /* W, equirectangular width in pixels; a multiple of `tile`, at most 65536 */
+    int32_t height;    /* H, height in pixels; a multiple of `tile`, at most 65536 (W = 2H is the usual shape) */
     int32_t tile;      /* square tile side in pixels: 8, 16 or 32 */
     int32_t num_views; /* V >= 1 camera poses rendered in one call */
     int32_t sh_degree; /* 0..3; the SH array holds K = (sh_degree + 1)^2 coefficients per colour channel */
@@ -63,7 +63,8 @@ typedef struct {
 #define OMNIGS_CAMERA_EQUIRECT 0
 #define OMNIGS_CAMERA_PINHOLE 1
 
-/* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned).
+/* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned). The fields binning reads
+ * (position, conic, depth, box, q) fill the first 32 bytes, the colour fields the last 16.
  * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the image). (c0, c1, c2): inverse of the 2x2 covariance
  * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
  * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
@@ -75,11 +76,11 @@ typedef struct {
 typedef struct {
     float px, py;
     float c0, c1, c2;
-    float opacity;
-    float r, g, b;
     float depth;
     uint16_t radius_x, radius_y;
     float q;
+    float opacity;
+    float r, g, b;
 } omnigs_splat;
 
 /* Gradient of the loss with respect to one omnigs_splat's differentiable fields (48 bytes, 16-byte aligned). */

@@ -2,30 +2,34 @@
 import numpy as np
 import torch
 
-SPLAT_KEYS = ("px", "py", "c0", "c1", "c2", "opacity", "r", "g", "b", "depth")
+SPLAT_KEYS = ("px", "py", "c0", "c1", "c2", "depth")  # columns 0-5; 6: rx | ry << 16; 7: q; 8-11: COLOUR_KEYS
+COLOUR_KEYS = ("opacity", "r", "g", "b")
 
 
 def pack_splats(sp: dict) -> np.ndarray:
-    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (rx | ry << 16 stored as uint32 bits, then
-    q = 2 ln(255 o), the dict's own when it has one)."""
+    """Generator splat fields -> the [m, 12] float32 layout of omnigs_splat (px, py, c0, c1, c2, depth, rx | ry << 16
+    stored as uint32 bits, q = 2 ln(255 o) (the dict's own when it has one), opacity, r, g, b)."""
     import oracle
     m = len(sp["px"])
     out = np.zeros((m, 12), np.float32)
     for i, k in enumerate(SPLAT_KEYS):
         out[:, i] = np.asarray(sp[k], np.float32)
+    for i, k in enumerate(COLOUR_KEYS):
+        out[:, 8 + i] = np.asarray(sp[k], np.float32)
     rx, ry = np.asarray(sp["rx"], np.int64), np.asarray(sp["ry"], np.int64)
     assert rx.min(initial=0) >= 0 and rx.max(initial=0) <= 65535 and ry.min(initial=0) >= 0 and ry.max(initial=0) <= 65535
-    out[:, 10] = (rx | (ry << 16)).astype(np.uint32).view(np.float32)
-    out[:, 11] = oracle.splat_q(sp).astype(np.float32)
+    out[:, 6] = (rx | (ry << 16)).astype(np.uint32).view(np.float32)
+    out[:, 7] = oracle.splat_q(sp).astype(np.float32)
     return out
 
 
 def unpack_splats(arr: np.ndarray) -> dict:
     d = {k: arr[:, i].copy() for i, k in enumerate(SPLAT_KEYS)}
-    radii = arr[:, 10].copy().view(np.uint32)
+    d.update({k: arr[:, 8 + i].copy() for i, k in enumerate(COLOUR_KEYS)})
+    radii = arr[:, 6].copy().view(np.uint32)
     d["rx"] = (radii & 0xFFFF).astype(np.int32)
     d["ry"] = (radii >> 16).astype(np.int32)
-    d["q"] = arr[:, 11].copy()
+    d["q"] = arr[:, 7].copy()
     return d
 
 

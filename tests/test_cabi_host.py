@@ -51,7 +51,8 @@ def test_host_only_calls(lib):
 
 
 def test_config_layout_and_schedule_validation(lib):
-    """omnigs_config is 40 bytes (the header's field order); invalid blend schedules are rejected on the host."""
+    """omnigs_config is 60 bytes (the header's field order); invalid blend schedules, cameras and image sizes beyond
+    65536 pixels (instance-box half-extents are 16-bit) are rejected on the host."""
     spec = importlib.util.spec_from_file_location("omnigs_cabi_layout", os.path.join(ROOT, "paper_2404_03202_gb300",
                                                                                       "_cabi.py"))
     text = open(spec.origin).read()
@@ -71,6 +72,9 @@ def test_config_layout_and_schedule_validation(lib):
     for tile, ppt in [(8, 4), (8, 8), (16, 3), (16, 1), (32, 16)]:
         c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), ppt)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (tile, ppt)
+    for w, h in [(65536 + 16, 128), (256, 65536 + 16), (250, 128)]:
+        c = Cfg(w, h, 16, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0)
+        assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (w, h)
     for cam, fx, fy in [(2, 100.0, 100.0), (1, 0.0, 100.0), (1, 100.0, -1.0), (1, float("nan"), 100.0)]:
         c = Cfg(256, 128, 16, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0, cam, fx, fy, 128.0, 64.0)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (cam, fx, fy)
