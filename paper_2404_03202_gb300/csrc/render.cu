@@ -258,7 +258,14 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     __syncthreads();
     const uint32_t maxlast = s_max;
     const unsigned lane = threadIdx.x & 31;
-    float gv[kGradFields];  // per-thread partial derivatives of the current entry
+    // Per-thread sums over the thread's pixels for the current entry. With gp = dL/d(exponent) per pixel, the
+    // exponent's derivatives give dL/dc0 = -1/2 sum gp dx^2, dL/dc1 = -sum gp dx dy, dL/dc2 = -1/2 sum gp dy^2,
+    // dL/dpx = -(c0 sum gp dx + c1 sum gp dy), dL/dpy = -(c1 sum gp dx + c2 sum gp dy). A thread's pixels share dx,
+    // so only sum gp, sum gp dy and sum gp dy^2 are accumulated per pixel; the warp reduces the moments
+    // (sum gp dx, sum gp dx^2, sum gp dy, sum gp dx dy, sum gp dy^2, then dL/do and dL/dc) and the conic is applied
+    // once per entry when the CTA's sums are flushed.
+    float gv[kGradFields];
+    float sg = 0.f, sgy = 0.f, sgyy = 0.f;
 #pragma unroll
     for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
 
@@ -289,40 +296,43 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                 const float e = fmaf(dy, fmaf(Bv.x, dy, e1), e0);
                 if (pos >= last[k] || !(fabsf(e - Bv.y) <= Bv.z)) continue;
                 const float4 Cc = s_c[j];
-                const float4 D = s_d[j];
                 const float G = fast_ex2(e);
                 const float raw = Cc.x * G;
                 const float alpha = fminf(kAlphaMax, raw);
                 contrib = true;
-                const float one_m = 1.f - alpha;
-                T[k] = __fdividef(T[k], one_m);  // transmittance in front of this entry
-                const float cr = Cc.y, cg = Cc.z, cb = Cc.w;
-                const float dalpha = T[k] * (g0[k] * (cr - B0[k]) + g1[k] * (cg - B1[k]) + g2[k] * (cb - B2[k]));
+                T[k] = __fdividef(T[k], 1.f - alpha);  // transmittance in front of this entry
+                // colour minus the colour behind, per unit of transmittance; the latter then moves to this entry
+                const float d0 = Cc.y - B0[k], d1 = Cc.z - B1[k], d2 = Cc.w - B2[k];
+                const float dalpha = T[k] * fmaf(g0[k], d0, fmaf(g1[k], d1, g2[k] * d2));
                 const float w = alpha * T[k];
                 gv[6] = fmaf(w, g0[k], gv[6]);
                 gv[7] = fmaf(w, g1[k], gv[7]);
                 gv[8] = fmaf(w, g2[k], gv[8]);
-                B0[k] = fmaf(alpha, cr, one_m * B0[k]);
-                B1[k] = fmaf(alpha, cg, one_m * B1[k]);
-                B2[k] = fmaf(alpha, cb, one_m * B2[k]);
+                B0[k] = fmaf(alpha, d0, B0[k]);
+                B1[k] = fmaf(alpha, d1, B1[k]);
+                B2[k] = fmaf(alpha, d2, B2[k]);
                 if (raw < kAlphaMax) {
                     gv[5] = fmaf(dalpha, G, gv[5]);
                     const float gp = dalpha * raw;  // dL/d(exponent in natural units)
-                    const float gdx = gp * dx, gdy = gp * dy;
-                    gv[2] = fmaf(-0.5f * dx, gdx, gv[2]);
-                    gv[3] = fmaf(-dx, gdy, gv[3]);
-                    gv[4] = fmaf(-0.5f * dy, gdy, gv[4]);
-                    gv[0] -= D.x * gdx + D.y * gdy;
-                    gv[1] -= D.z * gdy + D.y * gdx;
+                    const float gdy = gp * dy;
+                    sg += gp;
+                    sgy += gdy;
+                    sgyy = fmaf(gdy, dy, sgyy);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
+                gv[0] = dx * sg;        // sum gp dx
+                gv[1] = dx * gv[0];     // sum gp dx^2
+                gv[2] = sgy;            // sum gp dy
+                gv[3] = dx * sgy;       // sum gp dx dy
+                gv[4] = sgyy;           // sum gp dy^2
                 float tot8;
                 const float tot = warp_sum_fields(gv, lane, tot8);
                 const bool quad = (lane & 3u) == 0;
                 if (quad || lane == 1u) atomicAdd(&s_acc[j * kGradFields + (quad ? (lane >> 2) : 8u)], quad ? tot : tot8);
 #pragma unroll
                 for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
+                sg = sgy = sgyy = 0.f;
             }
         }
         __syncthreads();
@@ -332,9 +342,13 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
 #pragma unroll
             for (int f = 0; f < kGradFields; ++f) any |= (acc[f] != 0.f);
             if (any) {
+                // the CTA's moments -> dL/d(px, py, c0, c1, c2)
+                const float4 D = s_d[threadIdx.x];
+                const float gpx = -fmaf(D.x, acc[0], D.y * acc[2]);
+                const float gpy = -fmaf(D.y, acc[0], D.z * acc[2]);
                 float4* gdst = grads + 3 * (size_t)s_vg[threadIdx.x];
-                atomicAdd(gdst, make_float4(acc[0], acc[1], acc[2], acc[3]));
-                atomicAdd(gdst + 1, make_float4(acc[4], acc[5], acc[6], acc[7]));
+                atomicAdd(gdst, make_float4(gpx, gpy, -0.5f * acc[1], -acc[3]));
+                atomicAdd(gdst + 1, make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]));
                 atomicAdd(reinterpret_cast<float*>(gdst + 2), acc[8]);
             }
 #pragma unroll
