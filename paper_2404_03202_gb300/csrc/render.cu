@@ -148,16 +148,16 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                 const float dy = A.y - (pm.y0 + k + 0.5f);
                 const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
                 const bool pass = live[k] && (fabsf(e - B.y) <= B.z);
-                const float alpha = pass ? fminf(kAlphaMax, Cc.x * fast_ex2(e)) : 0.f;
-                const float Tn = T[k] * (1.f - alpha);
-                const bool stop = pass && Tn < kTStop;
+                const float alpha = fminf(kAlphaMax, Cc.x * fast_ex2(e));
+                const bool stop = pass && fmaf(-T[k], alpha, T[k]) < kTStop;
                 const bool add = pass && !stop;
                 live[k] = live[k] && !stop;
-                const float w = add ? alpha * T[k] : 0.f;
+                const float a_add = add ? alpha : 0.f;  // the alpha applied: 0 when skipped or stopped
+                const float w = a_add * T[k];
                 C0[k] = fmaf(w, Cc.y, C0[k]);
                 C1[k] = fmaf(w, Cc.z, C1[k]);
                 C2[k] = fmaf(w, Cc.w, C2[k]);
-                T[k] = add ? Tn : T[k];
+                T[k] = fmaf(-T[k], a_add, T[k]);        // T (1 - alpha), or T unchanged
                 last[k] = add ? pos1 : last[k];
                 if (kCount) count[k] += add ? 1u : 0u;
             }
