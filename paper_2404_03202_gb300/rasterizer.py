@@ -139,15 +139,24 @@ class Rasterizer:
                             g, self.grads2d, stream)
         return self.grads2d
 
-    def backward(self, dL_drgb=None, stream=None):
-        """Gradients of the loss with respect to means, scales, quats, opacity, sh, and dL/ds (screen space)."""
+    GRAD_NAMES = ("means", "scales", "quats", "opacity", "sh", "screen")
+
+    def backward(self, dL_drgb=None, stream=None, out=None):
+        """Gradients of the loss with respect to means, scales, quats, opacity, sh, and dL/ds (screen space).
+        They go to this Rasterizer's buffers, or to the device tensors of `out` (a dict with the keys of
+        GRAD_NAMES, shaped like those buffers)."""
         self.backward_2d(dL_drgb, stream)
         means, scales, quats, opacity, sh, viewmats = self._params
+        g = dict(means=self.d_means, scales=self.d_scales, quats=self.d_quats, opacity=self.d_opacity, sh=self.d_sh,
+                 screen=self.d_screen)
+        if out is not None:
+            for k in self.GRAD_NAMES:
+                if tuple(out[k].shape) != tuple(g[k].shape) or out[k].dtype != torch.float32 or not out[k].is_cuda:
+                    raise ValueError(f"out[{k!r}] must be a float32 device tensor of shape {tuple(g[k].shape)}")
+            g = {k: out[k] for k in self.GRAD_NAMES}
         C.omnigs_preprocess_bwd(self.cfg, self.n, means, scales, quats, opacity, sh, viewmats, self.grads2d,
-                                self.d_means, self.d_scales, self.d_quats, self.d_opacity, self.d_sh, self.d_screen,
-                                stream)
-        return dict(means=self.d_means, scales=self.d_scales, quats=self.d_quats, opacity=self.d_opacity,
-                    sh=self.d_sh, screen=self.d_screen)
+                                g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], g["screen"], stream)
+        return g
 
     def check(self, stream=None) -> None:
         """Raise if a device-side error (capacity overflow) was recorded since the last check (synchronises)."""
