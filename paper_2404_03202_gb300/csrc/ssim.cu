@@ -2,7 +2,9 @@
 //
 // SSIM per colour plane with an 11 x 11 Gaussian window (sigma 1.5, normalised), "same"-size filtering with zero
 // padding, C1 = 0.01^2, C2 = 0.03^2 (the 3DGS conventions the paper defers to). The window is separable, so each
-// filtered moment is a horizontal then a vertical 11-tap pass over a shared-memory tile with a 5-pixel halo.
+// filtered moment is a horizontal then a vertical 11-tap pass over a shared-memory tile with a 5-pixel halo. Both
+// passes are register-blocked: a thread filters 4 adjacent outputs from one run of 14 inputs (read as 16-byte
+// vectors in the horizontal pass), so each output costs a few shared-memory loads instead of 11 per moment.
 //
 // Precision: the moments are formed of the shifted images x' = x - 1/2 and y' = y - 1/2 (padding -1/2, which is what
 // zero padding of x means after the shift). Variances and the covariance are shift-invariant, and mid-grey images
@@ -23,8 +25,11 @@ namespace omnigs {
 namespace {
 
 constexpr int kSsimR = 5;                    // window radius (11 taps)
-constexpr int kSsimTW = 32, kSsimTH = 16;    // output tile
+constexpr int kSsimTW = 32, kSsimTH = 32;    // output tile
 constexpr int kSsimInW = kSsimTW + 2 * kSsimR, kSsimInH = kSsimTH + 2 * kSsimR;
+constexpr int kSsimStride = 44;              // staged row stride (16-byte aligned rows, >= kSsimInW + 2)
+constexpr int kSsimRun = 4;                  // adjacent outputs per thread and pass
+constexpr int kSsimSpan = kSsimRun + 2 * kSsimR;  // inputs one run reads (14)
 constexpr int kSsimThreads = 256;
 constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 constexpr float kShift = 0.5f;
@@ -58,65 +63,93 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
     return s;
 }
 
-// Grid: (ceil(W / 32), ceil(H / 16), V * 3). partials: [2][blocks] (SSIM sum, |x - y| sum).
+// Horizontal pass over one staged plane: 16 inputs from row r starting at column c0 (a multiple of 4), as four
+// 16-byte loads.
+__device__ __forceinline__ void load_run16(const float* row, int c0, float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 f = *reinterpret_cast<const float4*>(row + c0 + 4 * q);
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+}
+
+// Grid: (ceil(W / 32), ceil(H / 32), V * 3). partials: [2][blocks] (SSIM sum, |x - y| sum).
 __global__ void __launch_bounds__(kSsimThreads)
 dssim_fwd_kernel(int W, int H, SsimTaps taps, const float* __restrict__ x, const float* __restrict__ y,
                  float* __restrict__ m1, float* __restrict__ m2, float* __restrict__ m3, float* __restrict__ partials) {
-    __shared__ float sx[kSsimInH][kSsimInW], sy[kSsimInH][kSsimInW];
-    __shared__ float hx[kSsimInH][kSsimTW], hy[kSsimInH][kSsimTW], hxx[kSsimInH][kSsimTW], hyy[kSsimInH][kSsimTW],
-        hxy[kSsimInH][kSsimTW];
+    __shared__ __align__(16) float sx[kSsimInH][kSsimStride], sy[kSsimInH][kSsimStride];
+    __shared__ float hm[5][kSsimInH][kSsimTW];  // horizontal moments: x', y', x'^2, y'^2, x'y'
     __shared__ float red[kSsimThreads / 32];
     const size_t plane = (size_t)blockIdx.z * H * W;
     const int ox = blockIdx.x * kSsimTW, oy = blockIdx.y * kSsimTH;
-    for (int i = threadIdx.x; i < kSsimInH * kSsimInW; i += kSsimThreads) {
-        const int r = i / kSsimInW, c = i - r * kSsimInW;
+    for (int i = threadIdx.x; i < kSsimInH * kSsimStride; i += kSsimThreads) {
+        const int r = i / kSsimStride, c = i - r * kSsimStride;
         const int gy = oy + r - kSsimR, gx = ox + c - kSsimR;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const bool in = c < kSsimInW && gx >= 0 && gx < W && gy >= 0 && gy < H;
         sx[r][c] = (in ? __ldg(x + plane + (size_t)gy * W + gx) : 0.f) - kShift;
         sy[r][c] = (in ? __ldg(y + plane + (size_t)gy * W + gx) : 0.f) - kShift;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimInH * kSsimTW; i += kSsimThreads) {
-        const int r = i / kSsimTW, c = i - r * kSsimTW;
-        float ax = 0.f, ay = 0.f, axx = 0.f, ayy = 0.f, axy = 0.f;
+    // horizontal: run (r, 4 s .. 4 s + 3) of the 32 output columns, for every staged row
+    for (int i = threadIdx.x; i < kSsimInH * (kSsimTW / kSsimRun); i += kSsimThreads) {
+        const int r = i / (kSsimTW / kSsimRun), c0 = (i - r * (kSsimTW / kSsimRun)) * kSsimRun;
+        float a[16], b[16];
+        load_run16(sx[r], c0, a);
+        load_run16(sy[r], c0, b);
 #pragma unroll
-        for (int t = 0; t <= 2 * kSsimR; ++t) {
-            const float g = taps.g[t], a = sx[r][c + t], b = sy[r][c + t];
-            ax = fmaf(g, a, ax);
-            ay = fmaf(g, b, ay);
-            axx = fmaf(g, a * a, axx);
-            ayy = fmaf(g, b * b, ayy);
-            axy = fmaf(g, a * b, axy);
+        for (int o = 0; o < kSsimRun; ++o) {
+            float ax = 0.f, ay = 0.f, axx = 0.f, ayy = 0.f, axy = 0.f;
+#pragma unroll
+            for (int t = 0; t <= 2 * kSsimR; ++t) {
+                const float g = taps.g[t], u = a[o + t], w = b[o + t];
+                const float gu = g * u, gw = g * w;
+                ax += gu;
+                ay += gw;
+                axx = fmaf(gu, u, axx);
+                ayy = fmaf(gw, w, ayy);
+                axy = fmaf(gu, w, axy);
+            }
+            hm[0][r][c0 + o] = ax; hm[1][r][c0 + o] = ay; hm[2][r][c0 + o] = axx; hm[3][r][c0 + o] = ayy;
+            hm[4][r][c0 + o] = axy;
         }
-        hx[r][c] = ax; hy[r][c] = ay; hxx[r][c] = axx; hyy[r][c] = ayy; hxy[r][c] = axy;
     }
     __syncthreads();
+    // vertical: rows 4 q .. 4 q + 3 of output column c
     float s_sum = 0.f, l1_sum = 0.f;
-    for (int i = threadIdx.x; i < kSsimTH * kSsimTW; i += kSsimThreads) {
-        const int r = i / kSsimTW, c = i - r * kSsimTW;
-        const int gy = oy + r, gx = ox + c;
-        if (gx >= W || gy >= H) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    for (int i = threadIdx.x; i < kSsimTW * (kSsimTH / kSsimRun); i += kSsimThreads) {
+        const int c = i % kSsimTW, r0 = (i / kSsimTW) * kSsimRun;
+        float mom[5][kSsimRun];
 #pragma unroll
-        for (int t = 0; t <= 2 * kSsimR; ++t) {
-            const float g = taps.g[t];
-            mx = fmaf(g, hx[r + t][c], mx);
-            my = fmaf(g, hy[r + t][c], my);
-            exx = fmaf(g, hxx[r + t][c], exx);
-            eyy = fmaf(g, hyy[r + t][c], eyy);
-            exy = fmaf(g, hxy[r + t][c], exy);
+        for (int k = 0; k < 5; ++k) {
+            float v[kSsimSpan];
+#pragma unroll
+            for (int t = 0; t < kSsimSpan; ++t) v[t] = hm[k][r0 + t][c];
+#pragma unroll
+            for (int o = 0; o < kSsimRun; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t <= 2 * kSsimR; ++t) acc = fmaf(taps.g[t], v[o + t], acc);
+                mom[k][o] = acc;
+            }
         }
-        const float vx = fmaf(-mx, mx, exx), vy = fmaf(-my, my, eyy), cxy = fmaf(-mx, my, exy);
-        const float Mx = mx + kShift, My = my + kShift;  // the means of the unshifted images
-        const float a1 = fmaf(2.f * Mx, My, kSsimC1), a2 = fmaf(2.f, cxy, kSsimC2);
-        const float b1 = fmaf(Mx, Mx, fmaf(My, My, kSsimC1)), b2 = vx + vy + kSsimC2;
-        const float S = (a1 * a2) / (b1 * b2);
-        const size_t pix = plane + (size_t)gy * W + gx;
-        m1[pix] = S * (2.f * My / a1 - 2.f * Mx / b1 - 2.f * my / a2 + 2.f * mx / b2);
-        m2[pix] = -S / b2;
-        m3[pix] = 2.f * S / a2;
-        s_sum += S;
-        l1_sum += fabsf(sx[r + kSsimR][c + kSsimR] - sy[r + kSsimR][c + kSsimR]);
+        const int gx = ox + c;
+#pragma unroll
+        for (int o = 0; o < kSsimRun; ++o) {
+            const int gy = oy + r0 + o;
+            if (gx >= W || gy >= H) continue;
+            const float mx = mom[0][o], my = mom[1][o];
+            const float vx = fmaf(-mx, mx, mom[2][o]), vy = fmaf(-my, my, mom[3][o]), cxy = fmaf(-mx, my, mom[4][o]);
+            const float Mx = mx + kShift, My = my + kShift;  // the means of the unshifted images
+            const float a1 = fmaf(2.f * Mx, My, kSsimC1), a2 = fmaf(2.f, cxy, kSsimC2);
+            const float b1 = fmaf(Mx, Mx, fmaf(My, My, kSsimC1)), b2 = vx + vy + kSsimC2;
+            const float S = (a1 * a2) / (b1 * b2);
+            const size_t pix = plane + (size_t)gy * W + gx;
+            m1[pix] = S * (2.f * My / a1 - 2.f * Mx / b1 - 2.f * my / a2 + 2.f * mx / b2);
+            m2[pix] = -S / b2;
+            m3[pix] = 2.f * S / a2;
+            s_sum += S;
+            l1_sum += fabsf(sx[r0 + o + kSsimR][c + kSsimR] - sy[r0 + o + kSsimR][c + kSsimR]);
+        }
     }
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
@@ -133,51 +166,64 @@ __global__ void __launch_bounds__(kSsimThreads)
 dssim_bwd_kernel(int W, int H, SsimTaps taps, float lambda, float inv_n, const float* __restrict__ x,
                  const float* __restrict__ y, const float* __restrict__ m1, const float* __restrict__ m2,
                  const float* __restrict__ m3, float* __restrict__ dL) {
-    __shared__ float s1[kSsimInH][kSsimInW], s2[kSsimInH][kSsimInW], s3[kSsimInH][kSsimInW];
-    __shared__ float h1[kSsimInH][kSsimTW], h2[kSsimInH][kSsimTW], h3[kSsimInH][kSsimTW];
+    __shared__ __align__(16) float sm[3][kSsimInH][kSsimStride];
+    __shared__ float hm[3][kSsimInH][kSsimTW];
     const size_t plane = (size_t)blockIdx.z * H * W;
     const int ox = blockIdx.x * kSsimTW, oy = blockIdx.y * kSsimTH;
-    for (int i = threadIdx.x; i < kSsimInH * kSsimInW; i += kSsimThreads) {
-        const int r = i / kSsimInW, c = i - r * kSsimInW;
+    for (int i = threadIdx.x; i < kSsimInH * kSsimStride; i += kSsimThreads) {
+        const int r = i / kSsimStride, c = i - r * kSsimStride;
         const int gy = oy + r - kSsimR, gx = ox + c - kSsimR;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const bool in = c < kSsimInW && gx >= 0 && gx < W && gy >= 0 && gy < H;
         const size_t p = plane + (size_t)gy * W + gx;
-        s1[r][c] = in ? __ldg(m1 + p) : 0.f;
-        s2[r][c] = in ? __ldg(m2 + p) : 0.f;
-        s3[r][c] = in ? __ldg(m3 + p) : 0.f;
+        sm[0][r][c] = in ? __ldg(m1 + p) : 0.f;
+        sm[1][r][c] = in ? __ldg(m2 + p) : 0.f;
+        sm[2][r][c] = in ? __ldg(m3 + p) : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimInH * kSsimTW; i += kSsimThreads) {
-        const int r = i / kSsimTW, c = i - r * kSsimTW;
-        float a = 0.f, b = 0.f, d = 0.f;
+    for (int i = threadIdx.x; i < kSsimInH * (kSsimTW / kSsimRun); i += kSsimThreads) {
+        const int r = i / (kSsimTW / kSsimRun), c0 = (i - r * (kSsimTW / kSsimRun)) * kSsimRun;
 #pragma unroll
-        for (int t = 0; t <= 2 * kSsimR; ++t) {
-            const float g = taps.g[t];
-            a = fmaf(g, s1[r][c + t], a);
-            b = fmaf(g, s2[r][c + t], b);
-            d = fmaf(g, s3[r][c + t], d);
+        for (int k = 0; k < 3; ++k) {
+            float a[16];
+            load_run16(sm[k][r], c0, a);
+#pragma unroll
+            for (int o = 0; o < kSsimRun; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t <= 2 * kSsimR; ++t) acc = fmaf(taps.g[t], a[o + t], acc);
+                hm[k][r][c0 + o] = acc;
+            }
         }
-        h1[r][c] = a; h2[r][c] = b; h3[r][c] = d;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSsimTH * kSsimTW; i += kSsimThreads) {
-        const int r = i / kSsimTW, c = i - r * kSsimTW;
-        const int gy = oy + r, gx = ox + c;
-        if (gx >= W || gy >= H) continue;
-        float a = 0.f, b = 0.f, d = 0.f;
+    for (int i = threadIdx.x; i < kSsimTW * (kSsimTH / kSsimRun); i += kSsimThreads) {
+        const int c = i % kSsimTW, r0 = (i / kSsimTW) * kSsimRun;
+        float f[3][kSsimRun];
 #pragma unroll
-        for (int t = 0; t <= 2 * kSsimR; ++t) {
-            const float g = taps.g[t];
-            a = fmaf(g, h1[r + t][c], a);
-            b = fmaf(g, h2[r + t][c], b);
-            d = fmaf(g, h3[r + t][c], d);
+        for (int k = 0; k < 3; ++k) {
+            float v[kSsimSpan];
+#pragma unroll
+            for (int t = 0; t < kSsimSpan; ++t) v[t] = hm[k][r0 + t][c];
+#pragma unroll
+            for (int o = 0; o < kSsimRun; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t <= 2 * kSsimR; ++t) acc = fmaf(taps.g[t], v[o + t], acc);
+                f[k][o] = acc;
+            }
         }
-        const size_t pix = plane + (size_t)gy * W + gx;
-        const float xv = __ldg(x + pix), yv = __ldg(y + pix);
-        const float diff = xv - yv;
-        const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float dssim = a + 2.f * (xv - kShift) * b + (yv - kShift) * d;
-        dL[pix] = inv_n * ((1.f - lambda) * sg - lambda * dssim);
+        const int gx = ox + c;
+#pragma unroll
+        for (int o = 0; o < kSsimRun; ++o) {
+            const int gy = oy + r0 + o;
+            if (gx >= W || gy >= H) continue;
+            const size_t pix = plane + (size_t)gy * W + gx;
+            const float xv = __ldg(x + pix), yv = __ldg(y + pix);
+            const float diff = xv - yv;
+            const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+            const float dssim = f[0][o] + 2.f * (xv - kShift) * f[1][o] + (yv - kShift) * f[2][o];
+            dL[pix] = inv_n * ((1.f - lambda) * sg - lambda * dssim);
+        }
     }
 }
 
