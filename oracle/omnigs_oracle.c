@@ -48,7 +48,9 @@
  *   J = [[f_x / t_z, 0, -f_x u / t_z], [0, f_y / t_z, -f_y w / t_z]] with u = clamp(t_x / t_z, +-1.3 W / (2 f_x))
  *   and w = clamp(t_y / t_z, +-1.3 H / (2 f_y)) (the 3DGS guard that keeps J bounded off screen), while dp/dt, the
  *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped; centres beyond
- *   2^23 px are culled (a bound on integer tile arithmetic).
+ *   2^23 px are culled (a bound on integer tile arithmetic), and so is a Gaussian whose instance box
+ *   [floor(p_x) - r_x, floor(p_x) + r_x] x [floor(p_y) - r_y, floor(p_y) + r_y] misses the image [0, W) x [0, H)
+ *   (the frustum cull of 3DGS: such a Gaussian has no tile, hence no instance, either way).
  */
 #include <math.h>
 #include <stdint.h>
@@ -347,6 +349,13 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
     f->ry = ceil(hy) < f->radius ? ceil(hy) : f->radius;
     if (f->rx > 65535.0) f->rx = 65535.0;
     if (f->ry > 65535.0) f->ry = 65535.0;
+    if (g_cam.model == 1) { /* pinhole: a box that misses the image has no tile */
+        double ix = floor(f->p[0]), iy = floor(f->p[1]);
+        if (ix + f->rx < 0.0 || ix - f->rx >= (double)W || iy + f->ry < 0.0 || iy - f->ry >= (double)H) {
+            f->culled = 1;
+            return;
+        }
+    }
     f->q = qa;
     f->rmargin = fmin(int_gap(rr), fmin(int_gap(hx), int_gap(hy)));
     /* Sec. 3.1: colour from m and the SH coefficients */

@@ -27,7 +27,7 @@ def test_projection_and_depth(oracle_lib):
 
 def test_near_plane_is_on_t_z(oracle_lib):
     for Z, culled in [(0.19, True), (0.21, False), (-1.0, True)]:
-        rec = oracle.preprocess(_one([5.0, 0.0, Z], [0.01] * 3), synth.identity_viewmats(1), W, H, camera=CAM)[0]
+        rec = oracle.preprocess(_one([0.05, 0.0, Z], [0.01] * 3), synth.identity_viewmats(1), W, H, camera=CAM)[0]
         assert (rec[oracle.R_RX] == 0) == culled
 
 
@@ -47,7 +47,8 @@ def test_off_screen_jacobian_is_clamped(oracle_lib):
     lim = 1.3 * W / (2 * 90.0)
 
     def cov(k):
-        rec = oracle.preprocess(_one([k * lim * 2.0, 0.0, 2.0], [0.05, 0.02, 0.03]), synth.identity_viewmats(1), W, H,
+        # broad enough that the box still reaches the image from beyond the clamp
+        rec = oracle.preprocess(_one([k * lim * 2.0, 0.0, 2.0], [0.6, 0.2, 0.3]), synth.identity_viewmats(1), W, H,
                                 camera=CAM)[0]
         return rec[oracle.R_PX], rec[[oracle.R_COV00, oracle.R_COV01, oracle.R_COV11]]
 
@@ -56,6 +57,25 @@ def test_off_screen_jacobian_is_clamped(oracle_lib):
     np.testing.assert_allclose(c1, c2, rtol=1e-12)
     (_, c3), (_, c4) = cov(0.95), cov(0.98)
     assert np.abs(c3 - c4).max() > 1e-6 * np.abs(c3).max()
+
+
+def test_box_off_the_image_is_culled(oracle_lib):
+    """A Gaussian whose instance box [floor(p) -+ r] misses the image is culled (it has no tile either way). A tiny
+    Gaussian has r_x = r_y = 2 (the 0.3 px^2 dilation sets its footprint), so p_x = -2.5 (box -5..-1) is culled and
+    p_x = -1.5 (box -4..0) is kept; likewise p_x = W + 2.3 (box W..W+4) against W + 1.5, and the same for rows."""
+    Z = 2.0
+
+    def rec(px, py):
+        X, Y = (px - 64.0) * Z / 90.0, (py - 40.0) * Z / 80.0
+        return oracle.preprocess(_one([X, Y, Z], [0.002] * 3), synth.identity_viewmats(1), W, H, camera=CAM)[0]
+
+    centre = rec(40.3, 30.6)
+    assert centre[oracle.R_RX] == 2 and centre[oracle.R_RY] == 2
+    for px, py, culled in [(-2.5, 30.5, True), (-1.5, 30.5, False), (W + 2.3, 30.5, True), (W + 1.5, 30.5, False),
+                           (40.5, -2.5, True), (40.5, -1.5, False), (40.5, H + 2.3, True), (40.5, H + 1.5, False)]:
+        r = rec(px, py)
+        assert abs(r[oracle.R_PX] - px) < 1e-3 or culled  # the centre lands where intended
+        assert (r[oracle.R_RX] == 0) == culled, (px, py)
 
 
 def test_columns_are_clipped_not_wrapped(oracle_lib):
@@ -79,7 +99,7 @@ def test_no_wrap_across_the_image_edge(oracle_lib):
 
 
 def test_blend_matches_bruteforce_without_seam(oracle_lib):
-    sc = synth.shell_scene(60, seed=3, log_scale_mean=-2.5)
+    sc = synth.shell_scene(300, seed=3, log_scale_mean=-2.5)
     sc.opacity[:] = np.minimum(sc.opacity, 0.34)
     vm = synth.random_viewmats(1, 4)
     f = oracle.render(sc, vm, W, H, 16, camera=CAM)
