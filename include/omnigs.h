@@ -128,7 +128,9 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  * Splats whose centre lies outside [0, W] x [0, H] are ignored.
  *   splats  [V * n] input (device)
  *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:
- *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r).
+ *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r). With the
+ *           equirectangular camera every splat is ranked; with the pinhole camera only those with instances are
+ *           (a view sees a fraction of the scene), and the entries past a view's ranked splats are unspecified.
  *   keys    [capacity] output (device): one key per instance, generated view by view and splat by splat in depth
  *           order (a splat's tiles row by row, columns in seam order): ((v * TILES + tile) << R) | r, with
  *           TILES = (W / tile) * (H / tile), tile = ty * (W / tile) + tx, r the splat's depth rank and

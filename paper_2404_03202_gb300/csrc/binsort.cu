@@ -172,6 +172,113 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
     vals[i] = (uint32_t)i;
 }
 
+// Pinhole views see a fraction of the scene, so their splats without instances (radius_x = 0: culled, or a box off
+// the image) are left out of the depth sort: vis_count / vis_scan / depth_keys_compact write the keys of the others
+// densely (view-major; view v's from vis_start[v]), and order_scatter puts the sorted splats back at
+// order[v * n + rank]. A block covers kVisSlots slots of one view (4 strided slots per thread), so vis_start[v] is a
+// block offset. vis_count reads only the radius word of each splat and leaves one ballot word per warp and slot
+// group for the compaction, which keeps the slots in index order (the depth sort breaks ties by it).
+constexpr int kVisWords = kVisSlots / 32;
+
+__device__ __forceinline__ bool has_radius(const float4* __restrict__ splats, size_t i) {
+    return (__ldg(reinterpret_cast<const unsigned*>(splats + 3 * i + 1) + 2) & 0xffffu) != 0u;
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+vis_count_kernel(int64_t n, int nbv, const float4* __restrict__ splats, unsigned* __restrict__ sums,
+                 unsigned* __restrict__ masks) {
+    __shared__ unsigned s_cnt[kBinThreads / 32];
+    const int v = blockIdx.x / nbv, j = blockIdx.x - v * nbv;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    bool vis[kVisPerThread];
+#pragma unroll
+    for (int u = 0; u < kVisPerThread; ++u) {
+        const int64_t g = (int64_t)j * kVisSlots + u * kBinThreads + threadIdx.x;
+        vis[u] = g < n && has_radius(splats, (size_t)(v * n + g));
+    }
+    unsigned c = 0;
+#pragma unroll
+    for (int u = 0; u < kVisPerThread; ++u) {
+        const unsigned m = __ballot_sync(0xffffffffu, vis[u]);
+        if (lane == 0) masks[(size_t)blockIdx.x * kVisWords + u * (kBinThreads / 32) + warp] = m;
+        c += __popc(m);
+    }
+    if (lane == 0) s_cnt[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < kBinThreads / 32; ++w) t += s_cnt[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// One CTA: exclusive scan of the per-block counts in place; vis_start[v] (v <= V) and the splat count.
+__global__ void __launch_bounds__(1024)
+vis_scan_kernel(int nblocks, int nbv, int V, unsigned* __restrict__ sums, unsigned* __restrict__ vis_start,
+                u64* __restrict__ count) {
+    __shared__ unsigned scratch[32];
+    const int per = (nblocks + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblocks);
+    unsigned local = 0;
+    for (int b = b0; b < b1; ++b) local += sums[b];
+    unsigned tot;
+    unsigned run = block_exclusive_scan<unsigned>(local, scratch, &tot);
+    for (int b = b0; b < b1; ++b) {
+        const unsigned c = sums[b];
+        sums[b] = run;
+        if (b % nbv == 0) vis_start[b / nbv] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        vis_start[V] = tot;
+        *count = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+depth_keys_compact_kernel(int64_t n, int nbv, const float4* __restrict__ splats, const unsigned* __restrict__ offsets,
+                          const unsigned* __restrict__ masks, u64* __restrict__ keys, uint32_t* __restrict__ vals) {
+    __shared__ unsigned s_word[kVisWords], s_before[kVisWords];
+    const int v = blockIdx.x / nbv, j = blockIdx.x - v * nbv;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    static_assert(kVisWords == 32, "one warp scans the block's ballot words");
+    if (warp == 0) {
+        const unsigned m = __ldg(masks + (size_t)blockIdx.x * kVisWords + lane);
+        unsigned x = __popc(m);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        s_word[lane] = m;
+        s_before[lane] = x - __popc(m);
+    }
+    __syncthreads();
+    const unsigned base = offsets[blockIdx.x];
+#pragma unroll
+    for (int u = 0; u < kVisPerThread; ++u) {
+        const int w = u * (kBinThreads / 32) + (int)warp;
+        const unsigned m = s_word[w];
+        if (!((m >> lane) & 1u)) continue;
+        const int64_t g = (int64_t)j * kVisSlots + u * kBinThreads + threadIdx.x;
+        const size_t i = (size_t)(v * n + g);
+        const unsigned c = base + s_before[w] + __popc(m & ((1u << lane) - 1u));
+        const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 1) + 1);
+        keys[c] = ((u64)v << 32) | (u64)__float_as_uint(d);
+        vals[c] = (uint32_t)i;
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+order_scatter_kernel(int64_t n, const u64* __restrict__ keys, const uint32_t* __restrict__ vals,
+                     const unsigned* __restrict__ vis_start, const u64* __restrict__ count,
+                     uint32_t* __restrict__ order) {
+    const u64 i = (u64)blockIdx.x * kBinThreads + threadIdx.x;
+    if (i >= *count) return;
+    const unsigned v = (unsigned)(keys[i] >> 32);
+    order[(u64)v * n + (i - vis_start[v])] = vals[i];
+}
+
 // ------------------------------------------------------------------------------------------- 2: instances
 
 // Both instance passes give each CTA kBinSplats consecutive splats of the (view, depth) order (kSplatsPerThread
@@ -193,14 +300,18 @@ struct CtaRows {
 // row-item count.
 __device__ __forceinline__ unsigned stage_rows(CtaRows& S, unsigned* scratch, const float4* __restrict__ splats,
                                                const uint32_t* __restrict__ order, int64_t i0, int64_t total, int64_t n,
-                                               int tiles_x, int tiles_y, int tile, int wrap) {
+                                               int tiles_x, int tiles_y, int tile, int wrap,
+                                               const unsigned* __restrict__ vis_start) {
     const int s0 = threadIdx.x * kSplatsPerThread;
     unsigned rows[kSplatsPerThread], local = 0;
     uint32_t idx[kSplatsPerThread];
+    bool ranked[kSplatsPerThread];  // positions beyond a compacted view's splat count hold no splat
 #pragma unroll
     for (int u = 0; u < kSplatsPerThread; ++u) {
         const int64_t i = i0 + s0 + u;
-        idx[u] = i < total ? __ldg(order + i) : 0u;
+        ranked[u] = i < total && (vis_start == nullptr ||
+                                  i - (i / n) * n < (int64_t)(vis_start[i / n + 1] - vis_start[i / n]));
+        idx[u] = ranked[u] ? __ldg(order + i) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kSplatsPerThread; ++u) {
@@ -210,7 +321,7 @@ __device__ __forceinline__ unsigned stage_rows(CtaRows& S, unsigned* scratch, co
         int rank = 0;
         unsigned tbase = 0;
         RowCull rc = {0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
-        if (i < total) {
+        if (ranked[u]) {
             const SplatPos p = load_pos(splats, (size_t)idx[u], tiles_x, tiles_y, tile, wrap);
             if (p.rx > 0) {
                 r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
@@ -256,15 +367,27 @@ __device__ __forceinline__ int2 row_item_cols(const CtaRows& S, unsigned ri, int
     return row_cols(rq, rr.x, rr.y, *ty, tile);
 }
 
+// A block inside one view that starts past the view's ranked splats has nothing to do.
+__device__ __forceinline__ bool block_unranked(int64_t blk, int64_t n, const unsigned* __restrict__ vis_start) {
+    if (vis_start == nullptr) return false;
+    const int64_t i0 = blk * kBinSplats, v = i0 / n;
+    return i0 + kBinSplats <= (v + 1) * n && i0 - v * n >= (int64_t)(vis_start[v + 1] - vis_start[v]);
+}
+
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
-                 int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, unsigned* __restrict__ block_sums) {
+                 int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, const unsigned* __restrict__ vis_start,
+                 unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
     const int64_t blk = logical_block(V, n, nb);
     if (blk < 0) return;
+    if (block_unranked(blk, n, vis_start)) {
+        if (threadIdx.x == 0) block_sums[blk] = 0;
+        return;
+    }
     const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
-                                           tile, wrap);
+                                           tile, wrap, vis_start);
     unsigned cnt = 0;
     for (unsigned ri0 = threadIdx.x * kRowsPerThread; ri0 < rows_total; ri0 += kRowChunk) {
         int j = row_owner(S, ri0);
@@ -314,13 +437,14 @@ constexpr unsigned kDirect = 4;
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
                 int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb,
-                const u64* __restrict__ block_offsets, u64* __restrict__ keys, u64 capacity) {
+                const unsigned* __restrict__ vis_start, const u64* __restrict__ block_offsets,
+                u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
     const int64_t blk = logical_block(V, n, nb);
-    if (blk < 0) return;
+    if (blk < 0 || block_unranked(blk, n, vis_start)) return;
     const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
-                                           tile, wrap);
+                                           tile, wrap, vis_start);
     const unsigned lane = lane_id();
     u64 out = block_offsets[blk];
     for (unsigned r0 = 0; r0 < rows_total; r0 += kRowChunk) {
@@ -674,15 +798,39 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     unsigned* bsums = reinterpret_cast<unsigned*>(ws + L.block_sums);
     u64* boffs = reinterpret_cast<u64*>(ws + L.block_offsets);
     const unsigned nb = (unsigned)((total + kBinSplats - 1) / kBinSplats);  // blocks of the instance passes
-    {
-        ProfScope prof("depth_keys", stream);
-        const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
-        depth_keys_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
-    }
-    e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(cfg.num_views),
-                       sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
-    if (e != cudaSuccess) return e;
     const int V = cfg.num_views;
+    const unsigned* vis_start = nullptr;  // set when the depth sort ranks only the splats with instances
+    if (wrap) {
+        {
+            ProfScope prof("depth_keys", stream);
+            const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
+            depth_keys_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, sp, dk0, order, &hdr->splat_count);
+        }
+        e = lsd_sort<true>(dk0, order, dk1, dv1, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(V),
+                           sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
+        if (e != cudaSuccess) return e;
+    } else {
+        const int nbv = (int)((n + kVisSlots - 1) / kVisSlots);
+        unsigned* vsums = reinterpret_cast<unsigned*>(ws + L.vis_sums);
+        unsigned* vstart = reinterpret_cast<unsigned*>(ws + L.vis_start);
+        unsigned* vmask = reinterpret_cast<unsigned*>(ws + L.vis_mask);
+        {
+            ProfScope prof("depth_keys", stream, 3);
+            vis_count_kernel<<<V * nbv, kBinThreads, 0, stream>>>(n, nbv, sp, vsums, vmask);
+            vis_scan_kernel<<<1, 1024, 0, stream>>>(V * nbv, nbv, V, vsums, vstart, &hdr->splat_count);
+            depth_keys_compact_kernel<<<V * nbv, kBinThreads, 0, stream>>>(n, nbv, sp, vsums, vmask, dk0, dv1);
+        }
+        // the sorted keys and splats land back in (dk0, dv1); order is the other value buffer meanwhile
+        e = lsd_sort<true>(dk0, dv1, dk1, order, &hdr->splat_count, (u64)total, 0, 32 + ceil_log2(V),
+                           sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope prof("depth_keys", stream);
+            const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
+            order_scatter_kernel<<<g, kBinThreads, 0, stream>>>(n, dk0, dv1, vstart, &hdr->splat_count, order);
+        }
+        vis_start = vstart;
+    }
     unsigned per_view = 0;  // the largest number of blocks a view owns
     for (int v = 0; v < V; ++v) {
         const int64_t first = (int64_t)v * n / kBinSplats;
@@ -692,13 +840,14 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     const unsigned grid = per_view * (unsigned)V;
     {
         ProfScope prof("bin_count", stream, 2);
-        bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb, bsums);
+        bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb,
+                                                           vis_start, bsums);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream);
         bin_emit_kernel<<<grid, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, wrap,
-                                                           rank_bits_for(n), V, nb, boffs,
+                                                           rank_bits_for(n), V, nb, vis_start, boffs,
                                                            reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();

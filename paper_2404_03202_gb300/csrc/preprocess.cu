@@ -252,6 +252,30 @@ __device__ __forceinline__ void stage_sh(float* s_sh, const float* __restrict__ 
     }
 }
 
+// The instance box (rx, ry): the 3-sigma square of half-side ceil(3 sqrt(lambda_max)) narrowed to the box of the
+// alpha >= 1/255 ellipse dp^T conic dp <= q, q = 2 ln(255 o), whose half-extents are sqrt(q Sigma~_00) and
+// sqrt(q Sigma~_11) (slightly widened), held at kMaxRadius. Returns q.
+__device__ __forceinline__ float instance_box(const Proj& P, float o, int& rx, int& ry) {
+    const float mid = 0.5f * (P.A + P.C);
+    const float hd = 0.5f * (P.A - P.C);
+    const float disc = fmaxf(0.1f, hd * hd + P.B * P.B);   // = mid^2 - det
+    const float lam = mid + sqrtf(disc);
+    const float rr = ceilf(3.f * sqrtf(lam));
+    const float q = fmaxf(2.f * logf(255.f * o), 0.f);
+    const float hx = ceilf(fmaf(sqrtf(q * P.A), 1.0001f, 1e-3f));
+    const float hy = ceilf(fmaf(sqrtf(q * P.C), 1.0001f, 1e-3f));
+    const float lim = fminf(rr, (float)kMaxRadius);
+    rx = (int)fminf(hx, lim);
+    ry = (int)fminf(hy, lim);
+    return q;
+}
+
+// The pinhole's frustum cull: a box [floor(p) -+ r] that misses the image has no tile (|p| < 2^23 here).
+__device__ __forceinline__ bool box_off_image(float px, float py, int rx, int ry, int W, int H) {
+    const int ix = (int)floorf(px), iy = (int)floorf(py);
+    return ix + rx < 0 || ix - rx >= W || iy + ry < 0 || iy - ry >= H;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
@@ -288,19 +312,10 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         }
         const float inv = 1.f / P.det;
         const float c0 = P.C * inv, c1 = -P.B * inv, c2 = P.A * inv;
-        const float mid = 0.5f * (P.A + P.C);
-        const float hd = 0.5f * (P.A - P.C);
-        const float disc = fmaxf(0.1f, hd * hd + P.B * P.B);   // = mid^2 - det
-        const float lam = mid + sqrtf(disc);
-        const float rr = ceilf(3.f * sqrtf(lam));
-        // the instance box: the 3-sigma square narrowed to the box of the alpha >= 1/255 ellipse
-        // dp^T conic dp <= q, q = 2 ln(255 o), whose half-extents are sqrt(q Sigma~_00) and sqrt(q Sigma~_11)
-        const float q = fmaxf(2.f * logf(255.f * o), 0.f);
-        const float hx = ceilf(fmaf(sqrtf(q * P.A), 1.0001f, 1e-3f));
-        const float hy = ceilf(fmaf(sqrtf(q * P.C), 1.0001f, 1e-3f));
-        const float lim = fminf(rr, (float)kMaxRadius);
-        const int rx = (int)fminf(hx, lim), ry = (int)fminf(hy, lim);
-        if (!(255.f * o >= 1.f)) {  // alpha < 1/255 everywhere: no instance
+        int rx, ry;
+        const float q = instance_box(P, o, rx, ry);
+        const bool off = cam.pinhole && box_off_image(px, py, rx, ry, W, H);
+        if (!(255.f * o >= 1.f) || off) {  // alpha < 1/255 everywhere, or no tile: no instance
             out[0] = make_float4(px, py, c0, c1);
             out[1] = make_float4(c2, P.tr, __uint_as_float(0u), 0.f);
             out[2] = make_float4(o, 0.f, 0.f, 0.f);
@@ -326,7 +341,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
 
 // ---------------------------------------------------------------------------------------------------- adjoint
 
-template <int K>
+template <int K, bool kPin>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                       const float* __restrict__ scales, const float* __restrict__ quats,
@@ -336,6 +351,7 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
                       float* __restrict__ d_quats, float* __restrict__ d_opacity, float* __restrict__ d_sh,
                       float* __restrict__ d_screen) {
     constexpr int KK = 3 * K, STRIDE = KK + 1;
+    cam.pinhole = kPin;  // the camera model as a compile-time constant
     extern __shared__ float smem[];
     float* s_sh = smem;
     float* s_dsh = smem + kPreThreads * STRIDE;
@@ -364,6 +380,11 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
             Proj P;
             float px, py;
             if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) continue;
+            if (kPin) {  // culled in the forward when its box misses the image: no gradient
+                int rx, ry;
+                instance_box(P, __ldg(opacity + g), rx, ry);
+                if (box_off_image(px, py, rx, ry, W, H)) continue;
+            }
             const float4 g0v = __ldg(grads + 3 * ((size_t)v * n + g));
             const float4 g1v = __ldg(grads + 3 * ((size_t)v * n + g) + 1);
             const float4 g2v = __ldg(grads + 3 * ((size_t)v * n + g) + 2);
@@ -405,7 +426,7 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
                 for (int k = 0; k < 3; ++k)
                     dJ[3 * r + k] = dM[3 * r] * w.Wr[3 * k] + dM[3 * r + 1] * w.Wr[3 * k + 1] + dM[3 * r + 2] * w.Wr[3 * k + 2];
             float dt[3];
-            if (cam.pinhole) {
+            if (kPin) {
                 // dp/dt of Eq. 2 (unclamped), then dJ/dt: a ratio held at its bound is a constant
                 const float tx = P.t[0], ty = P.t[1], tz = P.t[2], iz = 1.f / tz, iz2 = iz * iz;
                 dt[0] = gpx * cam.fx * iz;
@@ -551,7 +572,7 @@ cudaError_t preprocess_bwd_k(const omnigs_config& cfg, int64_t n, const float* m
                              float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_sh,
                              float* d_screen, cudaStream_t stream) {
     const size_t smem = sizeof(float) * (2 * kPreThreads * (3 * K + 1) + 16 * cfg.num_views);
-    auto kern = preprocess_bwd_kernel<K>;
+    auto kern = cfg.camera == OMNIGS_CAMERA_PINHOLE ? preprocess_bwd_kernel<K, true> : preprocess_bwd_kernel<K, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);

@@ -41,6 +41,7 @@ def _front_scene(n, seed):
 
 def test_preprocess_matches_oracle():
     sc = _front_scene(8000, 1)
+    sc.scales[1::2] *= 8.0  # broad Gaussians: some centred far off the image still reach it
     vm = np.concatenate([synth.identity_viewmats(1), synth.random_viewmats(1, 2, max_offset=0.1)])
     r = og.Rasterizer(_settings(V=2))
     r._ensure(sc.n, 16)
@@ -55,7 +56,8 @@ def test_preprocess_matches_oracle():
     gp = np.stack([got["px"] - INTR[2], got["py"] - INTR[3]], 1)[far]
     rp = np.stack([dx, dy], 1)[far]
     assert far.sum() > 100 and (np.abs(gp - rp).max(1) / np.abs(rp).max(1)).max() <= 2e-6
-    summary = check_preprocess({k: v[on] for k, v in got.items()}, rec[on], np.tile(sc.opacity, 2)[on], W, H)
+    summary = check_preprocess({k: v[on] for k, v in got.items()}, rec[on], np.tile(sc.opacity, 2)[on], W, H,
+                               pinhole=True)
     print("pinhole preprocess:", summary)
     assert summary["alive"] > 2000
 
