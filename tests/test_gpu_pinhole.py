@@ -159,3 +159,32 @@ def test_end_to_end_against_oracle():
     ref = oracle.render_grad(sc, vm, g.astype(np.float64), W, H, 16, fwd=f, camera=CAM)
     for name in ["means", "scales", "quats", "opacity", "sh"]:
         assert normwise(grads[name].cpu().numpy(), ref[name]) <= 1e-2, name
+
+
+def test_views_that_see_nothing_or_everything():
+    """Three pinhole views of front-facing Gaussians: the first looks at them, the second away from them (every splat
+    culled: no instance, background only), the third at them again. The depth sort ranks only what each view sees,
+    so the views must not disturb one another: lists bit-exact and images against the oracle."""
+    sc = _front_scene(3000, 41)
+    back = synth.identity_viewmats(1)
+    back[0, :3, :3] = np.diag([-1.0, 1.0, -1.0])  # yaw by pi: everything behind the camera
+    vm = np.concatenate([synth.identity_viewmats(1), back, synth.random_viewmats(1, 42, max_offset=0.05)])
+    vm[2, :3, :3] = np.eye(3)
+    bg = (0.1, 0.2, 0.3)
+    r = og.Rasterizer(_settings(V=3, bg=bg))
+    img = r.forward(*scene_to_device(sc), dev(vm)).cpu().numpy()
+    f = oracle.render(sc, vm, W, H, 16, bg=bg, eps=1e-3, camera=CAM)
+    assert (f["splats"]["rx"].reshape(3, -1)[1] == 0).all() and (f["splats"]["rx"].reshape(3, -1)[0] > 0).sum() > 500
+    assert np.array_equal(img[1], np.broadcast_to(np.array(bg, np.float32)[:, None, None], img[1].shape))
+    cnt = r.instance_count()
+    ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    tiles = (W // 16) * (H // 16)
+    assert (ranges[tiles:2 * tiles] == 0).all()
+    # lists on the GPU's own splats, against the oracle's binning of the same float32 splats
+    sp = unpack_splats(r.splats.cpu().numpy())
+    ranges_ref, list_ref = oracle.bin_sort(sp, 3, W, H, 16, camera=CAM)
+    assert cnt == len(list_ref) and np.array_equal(ranges, ranges_ref)
+    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+    mask = (f["near"] & 1) == 0
+    err = np.abs(img - f["rgb"]).max(axis=1)[mask]
+    assert np.quantile(err, 0.999) <= 1e-4 and err.max() <= 2e-6 * W * 4
