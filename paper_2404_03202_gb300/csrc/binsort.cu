@@ -151,8 +151,7 @@ __device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int 
 // its nearest and widest splats and most of its instances, start first instead of forming a tail: dispatch index b
 // runs the (b / V)-th block of view b mod V, view v owning the blocks from the one holding its first splat
 // (floor(v n / kBinSplats)) up to the next view's. -1: no block (the grid is V times the largest view's block count).
-__device__ __forceinline__ int64_t logical_block(int V, int64_t n, unsigned nb) {
-    const unsigned b = blockIdx.x;
+__device__ __forceinline__ int64_t logical_block(int V, int64_t n, unsigned nb, unsigned b) {
     const int64_t v = b % (unsigned)V, j = b / (unsigned)V;
     const int64_t first = v * n / kBinSplats;
     const int64_t next = v + 1 < V ? (v + 1) * n / kBinSplats : (int64_t)nb;
@@ -380,7 +379,7 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
                  unsigned* __restrict__ block_sums) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
-    const int64_t blk = logical_block(V, n, nb);
+    const int64_t blk = logical_block(V, n, nb, blockIdx.x);
     if (blk < 0) return;
     if (block_unranked(blk, n, vis_start)) {
         if (threadIdx.x == 0) block_sums[blk] = 0;
@@ -406,23 +405,40 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
     if (threadIdx.x == 0) block_sums[blk] = tot;
 }
 
-// One CTA: exclusive scan of the per-CTA sums in 64 bits; total to the header, overflow flagged.
+// One CTA: exclusive scan of the per-CTA sums in 64 bits; total to the header, overflow flagged. With piece > 0, a
+// block with more than `piece` instances gets ceil(sum / piece) - 1 extra bin_emit CTAs ("pieces"): piece_start[b]
+// is the first of block b's extra pieces, piece_block[e] the block of extra piece e (at most max_pieces of them).
 __global__ void __launch_bounds__(1024)
 bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __restrict__ block_offsets,
-                WsHeader* __restrict__ hdr, u64 capacity) {
+                unsigned piece, unsigned* __restrict__ piece_start, unsigned* __restrict__ piece_block,
+                unsigned max_pieces, WsHeader* __restrict__ hdr, u64 capacity) {
     __shared__ u64 scratch[32];
+    __shared__ unsigned scratch32[32];
     const int per = (nblocks + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblocks);
     u64 local = 0;
-    for (int b = b0; b < b1; ++b) local += block_sums[b];
+    unsigned extra = 0;
+    for (int b = b0; b < b1; ++b) {
+        local += block_sums[b];
+        if (piece) extra += (block_sums[b] + piece - 1) / piece - (block_sums[b] > 0 ? 1u : 0u);
+    }
     u64 tot;
     u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
+    unsigned extra_tot;
+    unsigned erun = block_exclusive_scan<unsigned>(extra, scratch32, &extra_tot);
     for (int b = b0; b < b1; ++b) {
         block_offsets[b] = run;
         run += block_sums[b];
+        if (!piece) continue;
+        const unsigned eb = (block_sums[b] + piece - 1) / piece - (block_sums[b] > 0 ? 1u : 0u);
+        piece_start[b] = erun;
+        for (unsigned k = 0; k < eb; ++k)
+            if (erun + k < max_pieces) piece_block[erun + k] = (unsigned)b;
+        erun += eb;
     }
     if (threadIdx.x == 0) {
         hdr->count = tot;
+        hdr->extra_pieces = min(extra_tot, max_pieces);
         if (tot > capacity) hdr->error |= kErrCapacity;
     }
 }
@@ -434,20 +450,39 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
 // are written at full store width. Instances of a splat are listed row by row, columns in seam order.
 constexpr unsigned kDirect = 4;
 
+template <bool kSplit>
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
-                int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb,
-                const unsigned* __restrict__ vis_start, const u64* __restrict__ block_offsets,
+                int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb, unsigned piece,
+                unsigned max_pieces,
+                const unsigned* __restrict__ vis_start, const unsigned* __restrict__ block_sums,
+                const u64* __restrict__ block_offsets, const unsigned* __restrict__ piece_start,
+                const unsigned* __restrict__ piece_block, const WsHeader* __restrict__ hdr,
                 u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
-    const int64_t blk = logical_block(V, n, nb);
-    if (blk < 0 || block_unranked(blk, n, vis_start)) return;
+    // The first max_pieces CTAs take the extra pieces of the blocks with more than `piece` instances (the
+    // nearest, widest splats, which would otherwise leave one CTA writing hundreds of thousands of keys while the
+    // others idle); they start first. The rest take piece 0 of every block, view-interleaved.
+    int64_t blk;
+    u64 lo = 0;  // output slots [lo, lo + piece) of the block are this CTA's (all of them for a light block)
+    if (kSplit && blockIdx.x < max_pieces) {
+        const unsigned e = blockIdx.x;
+        if (e >= hdr->extra_pieces) return;
+        blk = piece_block[e];
+        lo = (u64)(1 + e - piece_start[blk]) * piece;
+    } else {
+        blk = logical_block(V, n, nb, blockIdx.x - max_pieces);
+        if (blk < 0 || block_unranked(blk, n, vis_start)) return;
+    }
+    const u64 hi = kSplit && block_sums[blk] > piece ? lo + piece : ~0ull;
     const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
                                            tile, wrap, vis_start);
     const unsigned lane = lane_id();
-    u64 out = block_offsets[blk];
-    for (unsigned r0 = 0; r0 < rows_total; r0 += kRowChunk) {
+    const u64 first = block_offsets[blk];
+    const u64 plo = first + lo, phi = kSplit && hi != ~0ull ? first + hi : ~0ull;  // this CTA's output positions
+    u64 out = first;
+    for (unsigned r0 = 0; r0 < rows_total && (!kSplit || out < phi); r0 += kRowChunk) {
         const unsigned ri0 = r0 + threadIdx.x * kRowsPerThread;
         unsigned cnt[kRowsPerThread], local = 0;
         u64 key0[kRowsPerThread];  // key of the item's first column, before the column wrap
@@ -471,6 +506,10 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         }
         unsigned chunk_total;
         const u64 base = out + block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+        if (kSplit && out + chunk_total <= plo) {  // the chunk lies before this CTA's piece
+            out += chunk_total;
+            continue;
+        }
         u64 off = base;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
@@ -479,7 +518,9 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 for (unsigned c = 0; c < cnt[k]; ++c) {
                     int tx = cl[k] + (int)c;
                     tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-                    if (off + c < capacity) keys[off + c] = key0[k] + ((u64)tx << rank_bits);
+                    const u64 at = off + c;
+                    if ((!kSplit || (at >= plo && at < phi)) && at < capacity)
+                        keys[at] = key0[k] + ((u64)tx << rank_bits);
                 }
             }
             unsigned long_items = __ballot_sync(0xffffffffu, cnt[k] > kDirect);
@@ -493,7 +534,8 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 for (unsigned c = lane; c < m; c += 32) {
                     int tx = c0 + (int)c;
                     tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-                    if (o + c < capacity) keys[o + c] = k0 + ((u64)tx << rank_bits);
+                    const u64 at = o + c;
+                    if ((!kSplit || (at >= plo && at < phi)) && at < capacity) keys[at] = k0 + ((u64)tx << rank_bits);
                 }
             }
             off += cnt[k];
@@ -838,17 +880,26 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
         per_view = std::max(per_view, (unsigned)(next - first));
     }
     const unsigned grid = per_view * (unsigned)V;
+    unsigned* pstart = reinterpret_cast<unsigned*>(ws + L.piece_start);
+    unsigned* pblock = reinterpret_cast<unsigned*>(ws + L.piece_block);
+    // Splitting heavy blocks pays when few views share the launch; with more, the view-interleaved dispatch already
+    // overlaps their heavy first blocks, and the pieces' repeated row work would cost more than it saves.
+    const unsigned piece = V <= 2 ? (unsigned)kEmitPiece : 0u;
+    const unsigned max_pieces = piece ? (unsigned)((u64)capacity / piece + 1) : 0u;
     {
         ProfScope prof("bin_count", stream, 2);
         bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb,
                                                            vis_start, bsums);
-        bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, hdr, (u64)capacity);
+        bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, piece, pstart, pblock, max_pieces, hdr,
+                                                (u64)capacity);
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream);
-        bin_emit_kernel<<<grid, kBinThreads, 0, stream>>>(total, (int)n, sp, order, tx, ty, cfg.tile, wrap,
-                                                           rank_bits_for(n), V, nb, vis_start, boffs,
-                                                           reinterpret_cast<u64*>(keys), (u64)capacity);
+        auto emit = piece ? bin_emit_kernel<true> : bin_emit_kernel<false>;
+        emit<<<grid + max_pieces, kBinThreads, 0, stream>>>(
+            total, (int)n, sp, order, tx, ty, cfg.tile, wrap, rank_bits_for(n), V, nb, piece, max_pieces, vis_start,
+            bsums, boffs,
+            pstart, pblock, hdr, reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();
 }

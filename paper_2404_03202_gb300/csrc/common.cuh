@@ -26,7 +26,7 @@ struct WsHeader {
     unsigned long long count;        // total instances of the last bin (may exceed capacity)
     unsigned long long splat_count;  // V * n of the last bin
     unsigned int error;              // sticky device-side error bits
-    unsigned int pad0;
+    unsigned int extra_pieces;       // bin_emit CTAs beyond one per block (blocks with many instances)
     float loss;
     unsigned int pad1;
 };
@@ -68,7 +68,7 @@ __device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_
 // n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
     size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
-        block_offsets, vis_sums, vis_start, vis_mask, total;
+        block_offsets, piece_start, piece_block, vis_sums, vis_start, vis_mask, total;
     int loss_blocks;
 };
 
@@ -77,6 +77,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr int kBinThreads = 256;
 constexpr int kSplatsPerThread = 1;  // splats per thread in the instance passes
 constexpr int kBinSplats = kBinThreads * kSplatsPerThread;
+constexpr int kEmitPiece = 16384;  // instances one bin_emit CTA writes at most (a block with more is split)
 constexpr int kVisPerThread = 4;                      // slots per thread of the visibility pass (pinhole views)
 constexpr int kVisSlots = kBinThreads * kVisPerThread;
 constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
