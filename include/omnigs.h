@@ -71,7 +71,8 @@ typedef struct {
  * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
  * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
  * + 1e-3)) and radius_y likewise with Sigma~_11, both held at 65535. Outside that ellipse alpha < 1/255, so the
- * narrowing removes only instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled. q = 2 ln(255 o)
+ * narrowing removes only instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled, and with the
+ * pinhole camera so is one whose box misses the image (it has no tile either way). q = 2 ln(255 o)
  * (0 when culled) is the level of that ellipse, dp^T conic dp <= q, which omnigs_bin uses to cull tiles row by row. */
 typedef struct {
     float px, py;
@@ -125,7 +126,8 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  * from a fixed sequence of correctly rounded FP32 operations, so that they are reproducible bit for bit. A dropped
  * tile has alpha < 1/255 at each of its pixels: no image changes. Splats with c0 c2 - c1^2 <= 1e-3 c0 c2 keep whole
  * rows.
- * Splats whose centre lies outside [0, W] x [0, H] are ignored.
+ * Splats whose centre lies outside [0, W] x [0, H] (equirectangular camera) or beyond 2^23 px (pinhole camera) are
+ * ignored.
  *   splats  [V * n] input (device)
  *   order   [V * n] output (device): the splats of each view by increasing depth t_r, equal depths by splat index:
  *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r). With the
