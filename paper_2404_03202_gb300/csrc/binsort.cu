@@ -366,6 +366,14 @@ __device__ __forceinline__ int2 row_item_cols(const CtaRows& S, unsigned ri, int
     return row_cols(rq, rr.x, rr.y, *ty, tile);
 }
 
+// bin_count stores every row item it evaluates (in the tile-sort's spare key buffer, which is free until the sort),
+// so that bin_emit reads them instead of re-gathering the splats and re-deriving the rows: first kept column
+// (unwrapped, 16 bits), kept-column count, tile row and owner splat (position in the block) in one 64-bit word.
+// A block whose rows do not fit (the buffer holds `capacity` items) is recomputed by bin_emit.
+__device__ __forceinline__ u64 pack_row(int cl, unsigned cnt, int ty, int j) {
+    return (u64)(unsigned short)cl | ((u64)cnt << 16) | ((u64)(unsigned)ty << 32) | ((u64)(unsigned)j << 48);
+}
+
 // A block inside one view that starts past the view's ranked splats has nothing to do.
 __device__ __forceinline__ bool block_unranked(int64_t blk, int64_t n, const unsigned* __restrict__ vis_start) {
     if (vis_start == nullptr) return false;
@@ -376,17 +384,30 @@ __device__ __forceinline__ bool block_unranked(int64_t blk, int64_t n, const uns
 __global__ void __launch_bounds__(kBinThreads, 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
                  int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, const unsigned* __restrict__ vis_start,
-                 unsigned* __restrict__ block_sums) {
+                 unsigned* __restrict__ block_sums, u64* __restrict__ rows, u64 row_cap, unsigned* __restrict__ row_base,
+                 unsigned* __restrict__ row_count, WsHeader* __restrict__ hdr) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
+    __shared__ unsigned s_rbase;
     const int64_t blk = logical_block(V, n, nb, blockIdx.x);
     if (blk < 0) return;
     if (block_unranked(blk, n, vis_start)) {
-        if (threadIdx.x == 0) block_sums[blk] = 0;
+        if (threadIdx.x == 0) {
+            block_sums[blk] = 0;
+            row_count[blk] = 0;
+        }
         return;
     }
     const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
                                            tile, wrap, vis_start);
+    if (threadIdx.x == 0) {
+        const u64 b = atomicAdd(&hdr->rows_used, (u64)rows_total);
+        s_rbase = b + rows_total <= row_cap ? (unsigned)b : 0xffffffffu;
+        row_base[blk] = s_rbase;
+        row_count[blk] = rows_total;
+    }
+    __syncthreads();
+    const unsigned rbase = s_rbase;
     unsigned cnt = 0;
     for (unsigned ri0 = threadIdx.x * kRowsPerThread; ri0 < rows_total; ri0 += kRowChunk) {
         int j = row_owner(S, ri0);
@@ -396,7 +417,9 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
             if (ri < rows_total) {
                 int ty;
                 const int2 c = row_item_cols(S, ri, j, tile, &ty);
-                cnt += c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                const unsigned m = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                cnt += m;
+                if (rbase != 0xffffffffu) rows[(u64)rbase + ri] = pack_row(c.x, m, ty, j);
             }
         }
     }
@@ -458,7 +481,8 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const unsigned* __restrict__ vis_start, const unsigned* __restrict__ block_sums,
                 const u64* __restrict__ block_offsets, const unsigned* __restrict__ piece_start,
                 const unsigned* __restrict__ piece_block, const WsHeader* __restrict__ hdr,
-                u64* __restrict__ keys, u64 capacity) {
+                const u64* __restrict__ rows, const unsigned* __restrict__ row_base,
+                const unsigned* __restrict__ row_count, u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
     // The first max_pieces CTAs take the extra pieces of the blocks with more than `piece` instances (the
@@ -476,8 +500,13 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         if (blk < 0 || block_unranked(blk, n, vis_start)) return;
     }
     const u64 hi = kSplit && block_sums[blk] > piece ? lo + piece : ~0ull;
-    const unsigned rows_total = stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x, tiles_y,
-                                           tile, wrap, vis_start);
+    const unsigned rbase = row_base[blk];
+    const bool stored = rbase != 0xffffffffu;  // block-uniform: rows from bin_count, or derived again here
+    const unsigned rows_total = stored ? row_count[blk]
+                                       : stage_rows(S, scratch, splats, order, blk * kBinSplats, total, n, tiles_x,
+                                                    tiles_y, tile, wrap, vis_start);
+    // depth rank and view of the block's splat j: the block's 256 positions span at most two views
+    const int64_t p0 = blk * kBinSplats, v0 = p0 / n, next_view = (v0 + 1) * n - p0;
     const unsigned lane = lane_id();
     const u64 first = block_offsets[blk];
     const u64 plo = first + lo, phi = kSplit && hi != ~0ull ? first + hi : ~0ull;  // this CTA's output positions
@@ -487,7 +516,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         unsigned cnt[kRowsPerThread], local = 0;
         u64 key0[kRowsPerThread];  // key of the item's first column, before the column wrap
         int cl[kRowsPerThread];
-        int j = ri0 < rows_total ? row_owner(S, ri0) : 0;
+        int j = !stored && ri0 < rows_total ? row_owner(S, ri0) : 0;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
             const unsigned ri = ri0 + k;
@@ -496,11 +525,21 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             key0[k] = 0;
             if (ri < rows_total) {
                 int ty;
-                const int2 c = row_item_cols(S, ri, j, tile, &ty);
-                cnt[k] = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
-                cl[k] = c.x;
-                const unsigned tb = __float_as_uint(S.rc1[j].w) + (unsigned)(ty * tiles_x);
-                key0[k] = ((u64)tb << rank_bits) | (u64)S.rect[j].w;
+                if (stored) {
+                    const u64 w = __ldg(rows + (u64)rbase + ri);
+                    cl[k] = (int)(short)(unsigned short)(w & 0xffffu);
+                    cnt[k] = (unsigned)(w >> 16) & 0xffffu;
+                    ty = (int)((w >> 32) & 0xffffu);
+                    j = (int)(w >> 48);
+                } else {
+                    const int2 c = row_item_cols(S, ri, j, tile, &ty);
+                    cnt[k] = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                    cl[k] = c.x;
+                }
+                const int64_t v = j < next_view ? v0 : v0 + 1;
+                const unsigned rank = (unsigned)(p0 + j - v * n);
+                const unsigned tb = (unsigned)v * (unsigned)(tiles_x * tiles_y) + (unsigned)(ty * tiles_x);
+                key0[k] = ((u64)tb << rank_bits) | (u64)rank;
             }
             local += cnt[k];
         }
@@ -881,6 +920,9 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     }
     const unsigned grid = per_view * (unsigned)V;
     unsigned* pstart = reinterpret_cast<unsigned*>(ws + L.piece_start);
+    u64* rows = reinterpret_cast<u64*>(ws + L.alt_keys);  // free until the tile sort
+    unsigned* rbase = reinterpret_cast<unsigned*>(ws + L.row_base);
+    unsigned* rcount = reinterpret_cast<unsigned*>(ws + L.row_count);
     unsigned* pblock = reinterpret_cast<unsigned*>(ws + L.piece_block);
     // Splitting heavy blocks pays when few views share the launch; with more, the view-interleaved dispatch already
     // overlaps their heavy first blocks, and the pieces' repeated row work would cost more than it saves.
@@ -889,7 +931,8 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     {
         ProfScope prof("bin_count", stream, 2);
         bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb,
-                                                           vis_start, bsums);
+                                                           vis_start, bsums, rows, (u64)capacity, rbase, rcount,
+                                                           hdr);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, piece, pstart, pblock, max_pieces, hdr,
                                                 (u64)capacity);
     }
@@ -898,8 +941,7 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
         auto emit = piece ? bin_emit_kernel<true> : bin_emit_kernel<false>;
         emit<<<grid + max_pieces, kBinThreads, 0, stream>>>(
             total, (int)n, sp, order, tx, ty, cfg.tile, wrap, rank_bits_for(n), V, nb, piece, max_pieces, vis_start,
-            bsums, boffs,
-            pstart, pblock, hdr, reinterpret_cast<u64*>(keys), (u64)capacity);
+            bsums, boffs, pstart, pblock, hdr, rows, rbase, rcount, reinterpret_cast<u64*>(keys), (u64)capacity);
     }
     return cudaGetLastError();
 }

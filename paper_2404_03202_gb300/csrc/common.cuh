@@ -29,6 +29,7 @@ struct WsHeader {
     unsigned int extra_pieces;       // bin_emit CTAs beyond one per block (blocks with many instances)
     float loss;
     unsigned int pad1;
+    unsigned long long rows_used;    // row items bin_count has stored for bin_emit
 };
 
 struct Rect {
@@ -68,7 +69,7 @@ __device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_
 // n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
     size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
-        block_offsets, piece_start, piece_block, vis_sums, vis_start, vis_mask, total;
+        block_offsets, piece_start, piece_block, row_base, row_count, vis_sums, vis_start, vis_mask, total;
     int loss_blocks;
 };
 

@@ -37,6 +37,8 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.block_sums = off;     off += align256(sizeof(unsigned) * nb);
     L.block_offsets = off;  off += align256(sizeof(unsigned long long) * nb);
     L.piece_start = off;    off += align256(sizeof(unsigned) * nb);
+    L.row_base = off;       off += align256(sizeof(unsigned) * nb);
+    L.row_count = off;      off += align256(sizeof(unsigned) * nb);
     L.piece_block = off;    off += align256(sizeof(unsigned) * ((size_t)capacity / kEmitPiece + 1));
     // visibility blocks per view, their counts and one ballot word per 32 slots
     const size_t nbv = std::max<size_t>(1, ((size_t)n + kVisSlots - 1) / kVisSlots);
