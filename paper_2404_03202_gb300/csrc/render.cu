@@ -14,10 +14,12 @@
 // list once every pixel has stopped (__syncthreads_count).
 //
 // The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
-// (1 - alpha) and accumulates the 9 partial derivatives of an entry over the thread's pixels. The warp then reduces
-// them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth: 14 shuffles, after which 9 lanes
-// hold one field's total each and write it with one shared-memory atomic), the CTA sums warps in shared memory, and
-// the CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
+// (1 - alpha) and accumulates 9 sums per entry over the thread's pixels: dL/do, dL/d(r, g, b) and the exponent
+// moments sum gp, sum gp dy, sum gp dy^2 (gp = dL/d exponent; the pixels share dx, so the moments in dx follow per
+// thread). The warp then reduces them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth:
+// 14 shuffles, after which 9 lanes hold one field's total each and write it with one shared-memory atomic), the CTA
+// sums warps in shared memory, the conic turns the moments into dL/d(px, py, c0, c1, c2) once per entry, and the
+// CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
 // A thread owns PPT = 2, 4 or 8 pixels (the blend schedule of the config): more pixels per thread share more of the
 // per-entry work and the warp reduction, fewer give more threads per tile. At 8 pixels one warp covers a 16 x 16
 // tile. Forward and adjoint evaluate alpha with identical
