@@ -706,17 +706,22 @@ lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict
             k[j] = ok ? __ldg(keys_in + idx) : ~0ull;
             if (kVals) val[j] = ok ? __ldg(vals_in + idx) : 0u;
         }
-        // rank within the warp: the lanes holding the same digit (match_any) take consecutive slots after the
-        // warp's running count of that digit, which their leader advances with one shared-memory atomic
+        // rank within the warp: the lanes holding the same digit (found by one ballot per digit bit, the padding
+        // digit R included) take consecutive slots after the warp's running count of that digit; every lane reads
+        // the count, and the lowest lane of each digit advances it (the digits' counters are distinct addresses)
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const u64 idx = base + (u64)j * 32;
             const unsigned d = idx < cnt ? (unsigned)(k[j] >> shift) & mask : R;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const unsigned leader = (unsigned)(__ffs(peers) - 1);
-            unsigned before = 0;
-            if (lane == leader) before = atomicAdd(&my_hist[d], (unsigned)__popc(peers));
-            before = __shfl_sync(0xffffffffu, before, leader);
+            unsigned peers = 0xffffffffu;
+            for (int b = 0; b <= dbits; ++b) {
+                const unsigned bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bal : ~bal;
+            }
+            const unsigned before = my_hist[d];
+            __syncwarp();
+            if ((peers & lt_mask) == 0) my_hist[d] = before + __popc(peers);
+            __syncwarp();
             rk[j] = before + __popc(peers & lt_mask);
         }
         __syncthreads();

@@ -82,7 +82,7 @@ constexpr int kEmitPiece = 16384;  // instances one bin_emit CTA writes at most 
 constexpr int kVisPerThread = 4;                      // slots per thread of the visibility pass (pinhole views)
 constexpr int kVisSlots = kBinThreads * kVisPerThread;
 constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
-constexpr int kSortCtasPerSm = 6;    // radix-sort grid: up to this many CTAs per SM
+constexpr int kSortCtasPerSm = 12;   // radix-sort grid: up to this many CTAs per SM
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocks = 1024;
 
