@@ -376,141 +376,162 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
         // culled in every view when alpha < 1/255 everywhere (255 o < 1): no gradient reaches it
         const int views = 255.f * __ldg(opacity + g) >= 1.f ? V : 0;
 
-        for (int v = 0; v < views; ++v) {
-            const View w = load_view(s_view, v);
-            Proj P;
-            float px, py;
-            if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) continue;
-            if (kPin) {  // culled in the forward when its box misses the image: no gradient
-                int rx, ry;
-                instance_box(P, __ldg(opacity + g), rx, ry);
-                if (box_off_image(px, py, rx, ry, W, H)) continue;
+        // Every term of a view's contribution is a product with one of its nine splat-gradient fields, so a view
+        // that passed this splat no gradient (culled, occluded, or reaching no pixel) adds exactly nothing. The
+        // views with some gradient are collected 32 at a time (their loads all in flight), and only those are
+        // walked: most splats are hidden in most views.
+        for (int v0 = 0; v0 < views; v0 += 32) {
+            const int vn = min(32, views - v0);
+            unsigned live = 0;
+#pragma unroll 8
+            for (int i = 0; i < vn; ++i) {
+                const float4* gp = grads + 3 * ((size_t)(v0 + i) * n + g);
+                const float4 a0 = __ldg(gp), a1 = __ldg(gp + 1);
+                const float a2 = __ldg(reinterpret_cast<const float*>(gp + 2));
+                const bool some = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f || a1.x != 0.f ||
+                                  a1.y != 0.f || a1.z != 0.f || a1.w != 0.f || a2 != 0.f;
+                live |= some ? 1u << i : 0u;
             }
-            const float4 g0v = __ldg(grads + 3 * ((size_t)v * n + g));
-            const float4 g1v = __ldg(grads + 3 * ((size_t)v * n + g) + 1);
-            const float4 g2v = __ldg(grads + 3 * ((size_t)v * n + g) + 2);
-            const float gpx = g0v.x, gpy = g0v.y, gc0 = g0v.z, gc1 = g0v.w, gc2 = g1v.x;
-            dop += g1v.y;
-            const float grgb[3] = {g1v.z, g1v.w, g2v.x};
-            dsx += gpx * 0.5f * (float)W;
-            dsy += gpy * 0.5f * (float)H;
+            while (live) {
+                const int v = v0 + __ffs(live) - 1;
+                live &= live - 1;
+                const float4 g0v = __ldg(grads + 3 * ((size_t)v * n + g));
+                const float4 g1v = __ldg(grads + 3 * ((size_t)v * n + g) + 1);
+                const float4 g2v = __ldg(grads + 3 * ((size_t)v * n + g) + 2);
+                const View w = load_view(s_view, v);
+                Proj P;
+                float px, py;
+                if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) continue;
+                if (kPin) {  // culled in the forward when its box misses the image: no gradient
+                    int rx, ry;
+                    instance_box(P, __ldg(opacity + g), rx, ry);
+                    if (box_off_image(px, py, rx, ry, W, H)) continue;
+                }
+                const float gpx = g0v.x, gpy = g0v.y, gc0 = g0v.z, gc1 = g0v.w, gc2 = g1v.x;
+                dop += g1v.y;
+                const float grgb[3] = {g1v.z, g1v.w, g2v.x};
+                dsx += gpx * 0.5f * (float)W;
+                dsy += gpy * 0.5f * (float)H;
 
-            // conic -> Sigma~: dSigma~ = -conic dconic conic (symmetric parametrisation of the off-diagonal)
-            const float inv = 1.f / P.det;
-            const float c0 = P.C * inv, c1 = -P.B * inv, c2 = P.A * inv;
-            const float dA = -(gc0 * c0 * c0 + gc1 * c0 * c1 + gc2 * c1 * c1);
-            const float dB = -(2.f * gc0 * c0 * c1 + gc1 * (c0 * c2 + c1 * c1) + 2.f * gc2 * c1 * c2);
-            const float dC = -(gc0 * c1 * c1 + gc1 * c1 * c2 + gc2 * c2 * c2);
-            // Sigma~ = Tm Tm^T + 0.3 I: dTm0 = 2 dA Tm0 + dB Tm1, dTm1 = dB Tm0 + 2 dC Tm1
-            float dTm[6];
+                // conic -> Sigma~: dSigma~ = -conic dconic conic (symmetric parametrisation of the off-diagonal)
+                const float inv = 1.f / P.det;
+                const float c0 = P.C * inv, c1 = -P.B * inv, c2 = P.A * inv;
+                const float dA = -(gc0 * c0 * c0 + gc1 * c0 * c1 + gc2 * c1 * c1);
+                const float dB = -(2.f * gc0 * c0 * c1 + gc1 * (c0 * c2 + c1 * c1) + 2.f * gc2 * c1 * c2);
+                const float dC = -(gc0 * c1 * c1 + gc1 * c1 * c2 + gc2 * c2 * c2);
+                // Sigma~ = Tm Tm^T + 0.3 I: dTm0 = 2 dA Tm0 + dB Tm1, dTm1 = dB Tm0 + 2 dC Tm1
+                float dTm[6];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                dTm[j] = 2.f * dA * P.Tm[j] + dB * P.Tm[3 + j];
-                dTm[3 + j] = dB * P.Tm[j] + 2.f * dC * P.Tm[3 + j];
-            }
-            // Tm = M M3: dM = dTm M3^T, dM3 += M^T dTm
-            float dM[6];
+                for (int j = 0; j < 3; ++j) {
+                    dTm[j] = 2.f * dA * P.Tm[j] + dB * P.Tm[3 + j];
+                    dTm[3 + j] = dB * P.Tm[j] + 2.f * dC * P.Tm[3 + j];
+                }
+                // Tm = M M3: dM = dTm M3^T, dM3 += M^T dTm
+                float dM[6];
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        dM[3 * r + k] =
+                            dTm[3 * r] * M3[3 * k] + dTm[3 * r + 1] * M3[3 * k + 1] + dTm[3 * r + 2] * M3[3 * k + 2];
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    dM[3 * r + k] = dTm[3 * r] * M3[3 * k] + dTm[3 * r + 1] * M3[3 * k + 1] + dTm[3 * r + 2] * M3[3 * k + 2];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+                    for (int j = 0; j < 3; ++j) dM3[3 * k + j] += P.M[k] * dTm[j] + P.M[3 + k] * dTm[3 + j];
+                // M = J W: dJ = dM W^T
+                float dJ[6];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) dM3[3 * k + j] += P.M[k] * dTm[j] + P.M[3 + k] * dTm[3 + j];
-            // M = J W: dJ = dM W^T
-            float dJ[6];
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    dJ[3 * r + k] = dM[3 * r] * w.Wr[3 * k] + dM[3 * r + 1] * w.Wr[3 * k + 1] + dM[3 * r + 2] * w.Wr[3 * k + 2];
-            float dt[3];
-            if (kPin) {
-                // dp/dt of Eq. 2 (unclamped), then dJ/dt: a ratio held at its bound is a constant
-                const float tx = P.t[0], ty = P.t[1], tz = P.t[2], iz = 1.f / tz, iz2 = iz * iz;
-                dt[0] = gpx * cam.fx * iz;
-                dt[1] = gpy * cam.fy * iz;
-                dt[2] = -(gpx * cam.fx * tx + gpy * cam.fy * ty) * iz2;
-                const float u = tx * iz, v = ty * iz;
-                dt[2] -= (dJ[0] * cam.fx + dJ[4] * cam.fy) * iz2;
-                if (u < -cam.limx || u > cam.limx) {
-                    dt[2] += dJ[2] * cam.fx * fminf(fmaxf(u, -cam.limx), cam.limx) * iz2;
+                    for (int k = 0; k < 3; ++k)
+                        dJ[3 * r + k] =
+                            dM[3 * r] * w.Wr[3 * k] + dM[3 * r + 1] * w.Wr[3 * k + 1] + dM[3 * r + 2] * w.Wr[3 * k + 2];
+                float dt[3];
+                if (kPin) {
+                    // dp/dt of Eq. 2 (unclamped), then dJ/dt: a ratio held at its bound is a constant
+                    const float tx = P.t[0], ty = P.t[1], tz = P.t[2], iz = 1.f / tz, iz2 = iz * iz;
+                    dt[0] = gpx * cam.fx * iz;
+                    dt[1] = gpy * cam.fy * iz;
+                    dt[2] = -(gpx * cam.fx * tx + gpy * cam.fy * ty) * iz2;
+                    const float u = tx * iz, v = ty * iz;
+                    dt[2] -= (dJ[0] * cam.fx + dJ[4] * cam.fy) * iz2;
+                    if (u < -cam.limx || u > cam.limx) {
+                        dt[2] += dJ[2] * cam.fx * fminf(fmaxf(u, -cam.limx), cam.limx) * iz2;
+                    } else {
+                        dt[0] -= dJ[2] * cam.fx * iz2;
+                        dt[2] += dJ[2] * 2.f * cam.fx * tx * iz2 * iz;
+                    }
+                    if (v < -cam.limy || v > cam.limy) {
+                        dt[2] += dJ[5] * cam.fy * fminf(fmaxf(v, -cam.limy), cam.limy) * iz2;
+                    } else {
+                        dt[1] -= dJ[5] * cam.fy * iz2;
+                        dt[2] += dJ[5] * 2.f * cam.fy * ty * iz2 * iz;
+                    }
                 } else {
-                    dt[0] -= dJ[2] * cam.fx * iz2;
-                    dt[2] += dJ[2] * 2.f * cam.fx * tx * iz2 * iz;
-                }
-                if (v < -cam.limy || v > cam.limy) {
-                    dt[2] += dJ[5] * cam.fy * fminf(fmaxf(v, -cam.limy), cam.limy) * iz2;
-                } else {
-                    dt[1] -= dJ[5] * cam.fy * iz2;
-                    dt[2] += dJ[5] * 2.f * cam.fy * ty * iz2 * iz;
-                }
-            } else {
-                // dJ/dt (quotient rule on Eqs. 11-16; rho replaced by the guarded rg)
-                const float tx = P.t[0], ty = P.t[1], tz = P.t[2], tr = P.tr, rg = P.rg;
-                float drg[3];
-                if (P.rho >= kPoleGuard * tr) {
-                    drg[0] = tx / rg; drg[1] = 0.f; drg[2] = tz / rg;
-                } else {
-                    drg[0] = kPoleGuard * tx / tr; drg[1] = kPoleGuard * ty / tr; drg[2] = kPoleGuard * tz / tr;
-                }
-                const float tr2 = tr * tr, tr4 = tr2 * tr2, rg2 = rg * rg, rg3 = rg2 * rg;
-                // p(t): dp/dt = J (Eqs. 11-16 are exactly dp/ds * ds/dt)
+                    // dJ/dt (quotient rule on Eqs. 11-16; rho replaced by the guarded rg)
+                    const float tx = P.t[0], ty = P.t[1], tz = P.t[2], tr = P.tr, rg = P.rg;
+                    float drg[3];
+                    if (P.rho >= kPoleGuard * tr) {
+                        drg[0] = tx / rg; drg[1] = 0.f; drg[2] = tz / rg;
+                    } else {
+                        drg[0] = kPoleGuard * tx / tr; drg[1] = kPoleGuard * ty / tr; drg[2] = kPoleGuard * tz / tr;
+                    }
+                    const float tr2 = tr * tr, tr4 = tr2 * tr2, rg2 = rg * rg, rg3 = rg2 * rg;
+                    // p(t): dp/dt = J (Eqs. 11-16 are exactly dp/ds * ds/dt)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) dt[k] = gpx * P.J[k] + gpy * P.J[3 + k];
-                const float e00 = dJ[0], e02 = dJ[2], e10 = dJ[3], e11 = dJ[4], e12 = dJ[5];
-                // J00 = a tz / rg^2
-                const float k00 = -2.f * a * tz / rg3;
-                // J02 = -a tx / rg^2
-                const float k02 = 2.f * a * tx / rg3;
-                // J10 = -b tx ty / (tr^2 rg), J12 = -b tz ty / (tr^2 rg)
-                const float q1 = b / (tr2 * rg);
-                const float q1t = 2.f * b / (tr4 * rg);     // derivative of 1/tr^2 part: + 2 b tx ty t / (tr^4 rg)
-                const float q1r = b / (tr2 * rg2);          // derivative of 1/rg part:  + b tx ty drg / (tr^2 rg^2)
-                // J11 = b rg / tr^2
-                const float k11r = b / tr2, k11t = -2.f * b * rg / tr4;
+                    for (int k = 0; k < 3; ++k) dt[k] = gpx * P.J[k] + gpy * P.J[3 + k];
+                    const float e00 = dJ[0], e02 = dJ[2], e10 = dJ[3], e11 = dJ[4], e12 = dJ[5];
+                    // J00 = a tz / rg^2
+                    const float k00 = -2.f * a * tz / rg3;
+                    // J02 = -a tx / rg^2
+                    const float k02 = 2.f * a * tx / rg3;
+                    // J10 = -b tx ty / (tr^2 rg), J12 = -b tz ty / (tr^2 rg)
+                    const float q1 = b / (tr2 * rg);
+                    const float q1t = 2.f * b / (tr4 * rg);     // derivative of 1/tr^2 part: + 2 b tx ty t / (tr^4 rg)
+                    const float q1r = b / (tr2 * rg2);          // derivative of 1/rg part:  + b tx ty drg / (tr^2 rg^2)
+                    // J11 = b rg / tr^2
+                    const float k11r = b / tr2, k11t = -2.f * b * rg / tr4;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float ex = (k == 0) ? 1.f : 0.f, ey = (k == 1) ? 1.f : 0.f, ez = (k == 2) ? 1.f : 0.f;
-                    float acc = e00 * (a * ez / rg2 + k00 * drg[k]);
-                    acc += e02 * (-a * ex / rg2 + k02 * drg[k]);
-                    acc += e10 * (-q1 * (ty * ex + tx * ey) + q1t * tx * ty * P.t[k] + q1r * tx * ty * drg[k]);
-                    acc += e11 * (k11r * drg[k] + k11t * P.t[k]);
-                    acc += e12 * (-q1 * (ty * ez + tz * ey) + q1t * tz * ty * P.t[k] + q1r * tz * ty * drg[k]);
-                    dt[k] += acc;
+                    for (int k = 0; k < 3; ++k) {
+                        const float ex = (k == 0) ? 1.f : 0.f, ey = (k == 1) ? 1.f : 0.f, ez = (k == 2) ? 1.f : 0.f;
+                        float acc = e00 * (a * ez / rg2 + k00 * drg[k]);
+                        acc += e02 * (-a * ex / rg2 + k02 * drg[k]);
+                        acc += e10 * (-q1 * (ty * ex + tx * ey) + q1t * tx * ty * P.t[k] + q1r * tx * ty * drg[k]);
+                        acc += e11 * (k11r * drg[k] + k11t * P.t[k]);
+                        acc += e12 * (-q1 * (ty * ez + tz * ey) + q1t * tz * ty * P.t[k] + q1r * tz * ty * drg[k]);
+                        dt[k] += acc;
+                    }
                 }
-            }
-            // t = W m + t_cw
+                // t = W m + t_cw
 #pragma unroll
-            for (int j = 0; j < 3; ++j) dm[j] += w.Wr[j] * dt[0] + w.Wr[3 + j] * dt[1] + w.Wr[6 + j] * dt[2];
+                for (int j = 0; j < 3; ++j) dm[j] += w.Wr[j] * dt[0] + w.Wr[3 + j] * dt[1] + w.Wr[6 + j] * dt[2];
 
-            // colour: c = max(sum_k Y_k(d) sh_k + 0.5, 0), d = (m - c_cam) / |m - c_cam|
-            float d[3], Y[16];
-            const float dist = view_dir(w, m, d);
-            sh_eval<K>(d[0], d[1], d[2], Y);
-            float wk[16];
-            float gm[3];
+                // colour: c = max(sum_k Y_k(d) sh_k + 0.5, 0), d = (m - c_cam) / |m - c_cam|
+                float d[3], Y[16];
+                const float dist = view_dir(w, m, d);
+                sh_eval<K>(d[0], d[1], d[2], Y);
+                float wk[16];
+                float gm[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.f;
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.f;
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc = fmaf(Y[k], shc[3 * k + ch], acc);
-                gm[ch] = (acc + 0.5f > 0.f) ? grgb[ch] : 0.f;
+                    for (int k = 0; k < K; ++k) acc = fmaf(Y[k], shc[3 * k + ch], acc);
+                    gm[ch] = (acc + 0.5f > 0.f) ? grgb[ch] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    wk[k] = shc[3 * k] * gm[0] + shc[3 * k + 1] * gm[1] + shc[3 * k + 2] * gm[2];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) dshc[3 * k + ch] += Y[k] * gm[ch];
+                }
+                const float3 gd = sh_grad_dot<K>(d[0], d[1], d[2], wk);
+                const float dd = gd.x * d[0] + gd.y * d[1] + gd.z * d[2];
+                const float idist = 1.f / dist;
+                dm[0] += (gd.x - d[0] * dd) * idist;
+                dm[1] += (gd.y - d[1] * dd) * idist;
+                dm[2] += (gd.z - d[2] * dd) * idist;
             }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                wk[k] = shc[3 * k] * gm[0] + shc[3 * k + 1] * gm[1] + shc[3 * k + 2] * gm[2];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) dshc[3 * k + ch] += Y[k] * gm[ch];
-            }
-            const float3 gd = sh_grad_dot<K>(d[0], d[1], d[2], wk);
-            const float dd = gd.x * d[0] + gd.y * d[1] + gd.z * d[2];
-            const float idist = 1.f / dist;
-            dm[0] += (gd.x - d[0] * dd) * idist;
-            dm[1] += (gd.y - d[1] * dd) * idist;
-            dm[2] += (gd.z - d[2] * dd) * idist;
         }
 
         // M3 = R diag(s): ds_j = sum_i dM3_ij R_ij, dR_ij = dM3_ij s_j
