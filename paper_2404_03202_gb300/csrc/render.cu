@@ -37,6 +37,23 @@ __device__ __forceinline__ float fast_ex2(float x) {
     return y;
 }
 
+// The forward's update works on pairs of a thread's vertically adjacent pixels with packed FP32 (f32x2) adds,
+// multiplies and FMAs, one instruction per pair. Opacity and colour are staged negated so that every packed step
+// rounds exactly like the scalar form it replaces: T' = fma(T, -alpha, T), -alpha = max(-0.99, (-o) G) and
+// C' = fma(-w, -c, C) equal fma(-T, alpha, T), -min(0.99, o G) and fma(w, c, C) bit for bit, so the adjoint's
+// recomputed alphas and stop decisions still match. The pair operands come from shared memory already duplicated
+// in both halves (one 16-byte load gives two pairs).
+struct FwdStaged {
+    float4 s;   // px, seam shift, c0', c1'     (per-thread dx and the exponent's dx terms)
+    float4 p0;  // py, py, c2', c2'
+    float4 p1;  // -m, -m, -o, -o              (pass interval centre, opacity)
+    float4 p2;  // -r, -r, -g, -g
+    float4 p3;  // -b, -b, h, h                (h: pass interval half-width)
+};
+
+__device__ __forceinline__ float2 lo2(const float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 v) { return make_float2(v.z, v.w); }
+
 struct Staged {
     float4 a;  // px, py, c0', c1'   (c' = conic scaled to the base-2 exponent)
     float4 b;  // c2', m, h, seam shift; the pass interval thr <= e <= 0 is written |e - m| <= h (m = thr/2, h = -m)
@@ -106,9 +123,9 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                   float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
                   uint32_t* __restrict__ out_count) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
-    __shared__ float4 s_a[NT];
-    __shared__ float4 s_b[NT];
-    __shared__ float4 s_c[NT];
+    constexpr int NP = PPT / 2;
+    static_assert(PPT % 2 == 0, "pixels are blended in pairs");
+    __shared__ FwdStaged s_e[NT];
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
@@ -119,12 +136,18 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     const uint32_t start = ranges[2 * tile_id], end = ranges[2 * tile_id + 1];
     const uint32_t* vorder = order + (size_t)v * n;
 
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    float2 T[NP], C0[NP], C1[NP], C2[NP], NY[NP];  // NY: minus the pixel centres' y
     uint32_t last[PPT], count[PPT];
     bool live[PPT];
 #pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        T[q] = make_float2(1.f, 1.f);
+        C0[q] = C1[q] = C2[q] = make_float2(0.f, 0.f);
+        NY[q] = make_float2(-(pm.y0 + 2 * q + 0.5f), -(pm.y0 + 2 * q + 1 + 0.5f));
+    }
+#pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; count[k] = 0; live[k] = true;
+        last[k] = 0; count[k] = 0; live[k] = true;
     }
     int done = 0;
     for (uint32_t b = start; b < end; b += NT) {
@@ -132,36 +155,55 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         const uint32_t s = b + threadIdx.x;
         if (s < end) {
             const Staged st = stage_entry(splats, entry_splat(keys, vorder, s, rank_mask), x_first, x_last, halfW, fW);
-            s_a[threadIdx.x] = st.a;
-            s_b[threadIdx.x] = st.b;
-            s_c[threadIdx.x] = st.c;
+            FwdStaged f;
+            f.s = make_float4(st.a.x, st.b.w, st.a.z, st.a.w);
+            f.p0 = make_float4(st.a.y, st.a.y, st.b.x, st.b.x);
+            f.p1 = make_float4(-st.b.y, -st.b.y, -st.c.x, -st.c.x);
+            f.p2 = make_float4(-st.c.y, -st.c.y, -st.c.z, -st.c.z);
+            f.p3 = make_float4(-st.c.w, -st.c.w, st.b.z, st.b.z);
+            s_e[threadIdx.x] = f;
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)NT, end - b);
         for (int j = 0; j < nb && !done; ++j) {
-            const float4 A = s_a[j];
-            const float4 B = s_b[j];
-            const float dx = entry_dx(A.x, B.w, xs, halfW, fW);
-            const float e0 = A.z * dx * dx, e1 = A.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
+            const float4 S = s_e[j].s;
+            const float4 P0 = s_e[j].p0;
+            const float4 P1 = s_e[j].p1;
+            const float dx = entry_dx(S.x, S.y, xs, halfW, fW);
+            const float e0 = S.z * dx * dx, e1 = S.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
+            const float2 E0 = make_float2(e0, e0), E1 = make_float2(e1, e1);
             const uint32_t pos1 = b - start + j + 1;        // list position after this entry
-            const float4 Cc = s_c[j];
+            const float4 P2 = s_e[j].p2;
+            const float4 P3 = s_e[j].p3;
+            const float h = P3.z;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dy = A.y - (pm.y0 + k + 0.5f);
-                const float e = fmaf(dy, fmaf(B.x, dy, e1), e0);
-                const bool pass = live[k] && (fabsf(e - B.y) <= B.z);
-                const float alpha = fminf(kAlphaMax, Cc.x * fast_ex2(e));
-                const bool stop = pass && fmaf(-T[k], alpha, T[k]) < kTStop;
-                const bool add = pass && !stop;
-                live[k] = live[k] && !stop;
-                const float a_add = add ? alpha : 0.f;  // the alpha applied: 0 when skipped or stopped
-                const float w = a_add * T[k];
-                C0[k] = fmaf(w, Cc.y, C0[k]);
-                C1[k] = fmaf(w, Cc.z, C1[k]);
-                C2[k] = fmaf(w, Cc.w, C2[k]);
-                T[k] = fmaf(-T[k], a_add, T[k]);        // T (1 - alpha), or T unchanged
-                last[k] = add ? pos1 : last[k];
-                if (kCount) count[k] += add ? 1u : 0u;
+            for (int q = 0; q < NP; ++q) {
+                const float2 dy = __fadd2_rn(lo2(P0), NY[q]);
+                const float2 e = __ffma2_rn(dy, __ffma2_rn(hi2(P0), dy, E1), E0);
+                const float2 em = __fadd2_rn(e, lo2(P1));
+                const float2 G = make_float2(fast_ex2(e.x), fast_ex2(e.y));
+                float2 na = __fmul2_rn(hi2(P1), G);  // -(o G)
+                na.x = fmaxf(-kAlphaMax, na.x);
+                na.y = fmaxf(-kAlphaMax, na.y);
+                const float2 Tn = __ffma2_rn(T[q], na, T[q]);  // T (1 - alpha) if applied
+                const int k0 = 2 * q, k1 = 2 * q + 1;
+                const bool pass0 = live[k0] && (fabsf(em.x) <= h), pass1 = live[k1] && (fabsf(em.y) <= h);
+                const bool stop0 = pass0 && Tn.x < kTStop, stop1 = pass1 && Tn.y < kTStop;
+                const bool add0 = pass0 && !stop0, add1 = pass1 && !stop1;
+                live[k0] = live[k0] && !stop0;
+                live[k1] = live[k1] && !stop1;
+                const float2 nadd = make_float2(add0 ? na.x : 0.f, add1 ? na.y : 0.f);  // -(alpha applied)
+                const float2 nw = __fmul2_rn(nadd, T[q]);
+                C0[q] = __ffma2_rn(nw, lo2(P2), C0[q]);
+                C1[q] = __ffma2_rn(nw, hi2(P2), C1[q]);
+                C2[q] = __ffma2_rn(nw, lo2(P3), C2[q]);
+                T[q] = __ffma2_rn(T[q], nadd, T[q]);
+                last[k0] = add0 ? pos1 : last[k0];
+                last[k1] = add1 ? pos1 : last[k1];
+                if (kCount) {
+                    count[k0] += add0 ? 1u : 0u;
+                    count[k1] += add1 ? 1u : 0u;
+                }
             }
             bool any = false;
 #pragma unroll
@@ -172,11 +214,15 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     const size_t HW = (size_t)H * W;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
+        const int q = k >> 1;
+        const float Tk = (k & 1) ? T[q].y : T[q].x;
+        const float c0 = (k & 1) ? C0[q].y : C0[q].x, c1 = (k & 1) ? C1[q].y : C1[q].x;
+        const float c2 = (k & 1) ? C2[q].y : C2[q].x;
         const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
-        out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(T[k], bg0, C0[k]);
-        out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(T[k], bg1, C1[k]);
-        out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(T[k], bg2, C2[k]);
-        out_T[(size_t)v * HW + pix] = T[k];
+        out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(Tk, bg0, c0);
+        out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(Tk, bg1, c1);
+        out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(Tk, bg2, c2);
+        out_T[(size_t)v * HW + pix] = Tk;
         out_nc[(size_t)v * HW + pix] = last[k];
         if (kCount) out_count[(size_t)v * HW + pix] = count[k];
     }

@@ -230,6 +230,40 @@ def test_preprocess_bwd_matches_oracle(deg):
         print(f"preprocess_bwd {name}: normwise {nw:.2e} elementwise {el:.2e}")
 
 
+@pytest.mark.parametrize("n,V", [(4000, 3), (600, 37)])
+def test_preprocess_bwd_sparse_upstream_gradient(n, V):
+    """Most (view, Gaussian) pairs of a real step pass no gradient (occluded or off every pixel). Here 60 % of the
+    rows are zero, 15 % carry one field only (each of the nine in turn), and the first 50 Gaussians get none in any
+    view; 37 views cross the 32-view chunks of the kernel's live-view mask."""
+    W, H = 512, 256
+    sc = synth.shell_scene(n, seed=17, sh_degree=3)
+    vm = np.concatenate([synth.identity_viewmats(1), synth.random_viewmats(V - 1, 19)])
+    rng = np.random.default_rng(23)
+    g2 = rng.normal(size=(V * n, 9))
+    g2[:, 2:5] *= 10.0
+    u = rng.random(V * n)
+    g2[u < 0.6] = 0.0
+    one = (u >= 0.6) & (u < 0.75)
+    keep = np.arange(V * n) % 9
+    g2[one] *= (np.arange(9)[None, :] == keep[one, None])
+    g2.reshape(V, n, 9)[:, :50] = 0.0
+    s = _settings(W, H, V=V, deg=3)
+    r = og.Rasterizer(s)
+    params = scene_to_device(sc)
+    r._ensure(n, sc.sh.shape[1])
+    grads = np.zeros((V * n, 12), np.float32)
+    grads[:, :9] = g2
+    r.grads2d.copy_(dev(grads))
+    C.omnigs_preprocess_bwd(r.cfg, n, *params, dev(vm), r.grads2d, r.d_means, r.d_scales, r.d_quats,
+                            r.d_opacity, r.d_sh, r.d_screen)
+    ref = oracle.preprocess_bwd(sc, vm, grads[:, :9].astype(np.float64), W, H)
+    for name, got in [("means", r.d_means), ("scales", r.d_scales), ("quats", r.d_quats), ("opacity", r.d_opacity),
+                      ("sh", r.d_sh), ("screen", r.d_screen)]:
+        g = got.cpu().numpy()
+        assert_grad_close(g, ref[name], name, rel=1e-4)
+        assert not np.any(g.reshape(n, -1)[:50]), name  # no gradient in any view: exactly zero
+
+
 # ------------------------------------------------------------------ S6 loss
 
 def test_l1_loss_matches_numpy():
