@@ -469,10 +469,10 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
 
 // The splats of a CTA (consecutive in depth order) own one contiguous output range. Their row items are taken
 // kRowsPerThread consecutive ones per thread at a time; a CTA scan of the kept-column counts gives every row item its
-// output offset. A thread writes the instances of its short row items itself (kDirect columns or fewer); the warp
-// writes the longer ones together, 32 consecutive columns per store, so that the rows of the nearest, widest splats
-// are written at full store width. Instances of a splat are listed row by row, columns in seam order.
-constexpr unsigned kDirect = 4;
+// output offset. The items of the chunk then go to shared memory, and the CTA writes the chunk's output slots in
+// order, thread t taking slots t, t + 256, ...: a binary search over the item offsets finds the slot's row, so every
+// store instruction writes 256 consecutive keys whatever the rows' lengths (the nearest splats have rows of hundreds
+// of tiles, most others of one to four). Instances of a splat are listed row by row, columns in seam order.
 
 template <bool kSplit>
 __global__ void __launch_bounds__(kBinThreads, 8)
@@ -486,6 +486,11 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const unsigned* __restrict__ row_count, u64* __restrict__ keys, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
+    __shared__ struct {
+        unsigned off[kRowChunk];  // output offset of each row item of the chunk, relative to the chunk
+        int cl[kRowChunk];        // its first column
+        u64 key0[kRowChunk];      // key of its first column, before the column wrap
+    } E;
     // The first max_pieces CTAs take the extra pieces of the blocks with more than `piece` instances (the
     // nearest, widest splats, which would otherwise leave one CTA writing hundreds of thousands of keys while the
     // others idle); they start first. The rest take piece 0 of every block, view-interleaved.
@@ -545,41 +550,39 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             local += cnt[k];
         }
         unsigned chunk_total;
-        const u64 base = out + block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+        unsigned rel = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);  // offset within the chunk
         if (kSplit && out + chunk_total <= plo) {  // the chunk lies before this CTA's piece
             out += chunk_total;
             continue;
         }
-        u64 off = base;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
-            if (cnt[k] <= kDirect) {
-                for (unsigned c = 0; c < cnt[k]; ++c) {
-                    int tx = cl[k] + (int)c;
-                    tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-                    const u64 at = off + c;
-                    if ((!kSplit || (at >= plo && at < phi)) && at < capacity)
-                        keys[at] = key0[k] + ((u64)tx << rank_bits);
-                }
-            }
-            unsigned long_items = __ballot_sync(0xffffffffu, cnt[k] > kDirect);
-            while (long_items) {
-                const int src = __ffs(long_items) - 1;
-                long_items &= long_items - 1;
-                const unsigned m = __shfl_sync(0xffffffffu, cnt[k], src);
-                const int c0 = __shfl_sync(0xffffffffu, cl[k], src);
-                const u64 k0 = __shfl_sync(0xffffffffu, key0[k], src);
-                const u64 o = __shfl_sync(0xffffffffu, off, src);
-                for (unsigned c = lane; c < m; c += 32) {
-                    int tx = c0 + (int)c;
-                    tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-                    const u64 at = o + c;
-                    if ((!kSplit || (at >= plo && at < phi)) && at < capacity) keys[at] = k0 + ((u64)tx << rank_bits);
-                }
-            }
-            off += cnt[k];
+            const int i = threadIdx.x * kRowsPerThread + k;
+            E.off[i] = rel;
+            E.cl[i] = cl[k];
+            E.key0[i] = key0[k];
+            rel += cnt[k];
         }
+        __syncthreads();
+        // output slot s of the chunk belongs to the last row item whose offset is <= s (items without columns share
+        // their successor's offset and are passed over)
+        unsigned s_lo = 0, s_hi = chunk_total;
+        if (kSplit) {
+            s_lo = plo > out ? (plo - out < chunk_total ? (unsigned)(plo - out) : chunk_total) : 0u;
+            s_hi = phi - out < chunk_total ? (unsigned)(phi - out) : chunk_total;
+        }
+        for (unsigned sl = s_lo + threadIdx.x; sl < s_hi; sl += kBinThreads) {
+            int i = 0;
+#pragma unroll
+            for (int step = kRowChunk / 2; step >= 1; step >>= 1)
+                if (E.off[i + step] <= sl) i += step;
+            // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
+            int tx = E.cl[i] + (int)(sl - E.off[i]);
+            tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
+            const u64 at = out + sl;
+            if (at < capacity) keys[at] = E.key0[i] + ((u64)tx << rank_bits);
+        }
+        __syncthreads();
         out += chunk_total;
     }
 }
