@@ -71,21 +71,38 @@ def _ceil_log2(x: int) -> int:
     return max(0, (int(x) - 1).bit_length())
 
 
-def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int) -> dict:
+def box_rows(splats, tile: int, H: int) -> int:
+    """Tile rows of all instance boxes (the row items bin_count stores and bin_emit reads back), from the splats'
+    centre rows and vertical half-extents."""
+    import torch
+    sp = splats.reshape(-1, 12)
+    rad = sp[:, 6].contiguous().view(torch.int32).to(torch.int64)
+    rx, ry = rad & 0xFFFF, (rad >> 16) & 0xFFFF
+    iy = torch.floor(sp[:, 1]).to(torch.int64)
+    y0 = torch.clamp(torch.div(iy - ry, tile, rounding_mode="floor"), min=0)
+    y1 = torch.clamp(torch.div(iy + ry, tile, rounding_mode="floor"), max=H // tile - 1)
+    ny = torch.clamp(y1 - y0 + 1, min=0) * (rx != 0)
+    return int(ny.sum().item())
+
+
+def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows: int, equirect: bool = True) -> dict:
     """Algorithmic HBM bytes per step of the memory-bound stages (each read or written once).
 
-    P = V n projected splats (48 B each), I instances (8 B keys), X = V H W pixels.
+    P = V n projected splats (48 B each), I instances (8 B keys), R box rows (8 B row words), X = V H W pixels.
     """
     P, X = V * n, V * H * W
     tiles = V * (W // tile) * (H // tile)
     dp = _sort_passes(32 + _ceil_log2(V))
     tp = _sort_passes(max(1, _ceil_log2(tiles)))
+    packed = equirect and _ceil_log2(V) + 32 + max(1, _ceil_log2(P)) <= 64  # splat index inside the depth key
     return {
         "preprocess_fwd": n * 236 + P * 48,               # 59 parameter floats in, one splat out per view
-        "depth_keys": P * (4 + 8 + 4),                    # depth in, (view|depth) key and index out
-        "depth_sort": dp * P * (8 + 2 * 12),              # per pass: key histogram read, key+index read and written
-        "bin_count": P * (4 + 36 + 4),                    # depth order, (p, conic, depth, radii, q), tile count out
-        "bin_emit": P * (4 + 36 + 8) + instances * 8,     # order, (p, conic, depth, radii, q), offset; one key each
+        # depth in, (view|depth|index) key out; the sorted keys read again and the splat order written
+        "depth_keys": P * (4 + 8 + 8 + 4) if packed else P * (4 + 8 + 4),
+        # per pass: key histogram read, key (and index) read and written
+        "depth_sort": dp * P * (8 + 2 * 8) if packed else dp * P * (8 + 2 * 12),
+        "bin_count": P * (4 + 36 + 4) + rows * 8,         # depth order, (p, conic, depth, radii, q), count; rows out
+        "bin_emit": rows * 8 + instances * 8,             # the stored rows in, one key per instance out
         "sort_upsweep": tp * instances * 8,               # per pass: keys read for the digit histogram
         "sort_downsweep": tp * instances * 16,            # per pass: keys read and written
         "tile_ranges": tiles * 8,                         # one [start, end) pair per tile
@@ -649,7 +666,8 @@ def main():
 
     # every stage against its own roofline (per step; a stage may span several launches)
     stages = {}
-    sb = stage_bytes(wl["n"], V, W, H, settings.tile, count)
+    sb = stage_bytes(wl["n"], V, W, H, settings.tile, count, box_rows(r.splats, settings.tile, H),
+                     equirect=not wl.get("pinhole"))
     for name, pk in per_kernel.items():
         ms_step = pk["total_ms"] / args.steps
         if name in sb:

@@ -172,6 +172,24 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
     vals[i] = (uint32_t)i;
 }
 
+// The same order from keys alone, when view, depth and splat index fit one 64-bit word: the index (gbits bits) rides
+// below the (view, depth) bits the sort orders by, and index order breaks ties as the stable sort with values does.
+__global__ void __launch_bounds__(kBinThreads)
+depth_keys_packed_kernel(int64_t total, int n, int gbits, const float4* __restrict__ splats, u64* __restrict__ keys,
+                         u64* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if (i == 0) *count = (u64)total;
+    if (i >= total) return;
+    const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 1) + 1);
+    keys[i] = ((((u64)(i / n) << 32) | (u64)__float_as_uint(d)) << gbits) | (u64)i;
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+depth_order_kernel(int64_t total, u64 gmask, const u64* __restrict__ keys, uint32_t* __restrict__ order) {
+    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if (i < total) order[i] = (uint32_t)(__ldg(keys + i) & gmask);
+}
+
 // Pinhole views see a fraction of the scene, so their splats without instances (radius_x = 0: culled, or a box off
 // the image) are left out of the depth sort: vis_count / vis_scan / depth_keys_compact write the keys of the others
 // densely (view-major; view v's from vis_start[v]), and order_scatter puts the sorted splats back at
@@ -890,7 +908,21 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     const unsigned nb = (unsigned)((total + kBinSplats - 1) / kBinSplats);  // blocks of the instance passes
     const int V = cfg.num_views;
     const unsigned* vis_start = nullptr;  // set when the depth sort ranks only the splats with instances
-    if (wrap) {
+    const int gbits = std::max(1, ceil_log2((uint64_t)total));
+    if (wrap && ceil_log2(V) + 32 + gbits <= 64) {
+        const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
+        {
+            ProfScope prof("depth_keys", stream);
+            depth_keys_packed_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, gbits, sp, dk0, &hdr->splat_count);
+        }
+        e = lsd_sort<false>(dk0, nullptr, dk1, nullptr, &hdr->splat_count, (u64)total, gbits, 32 + ceil_log2(V),
+                            sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope prof("depth_keys", stream);
+            depth_order_kernel<<<g, kBinThreads, 0, stream>>>(total, (1ull << gbits) - 1, dk0, order);
+        }
+    } else if (wrap) {
         {
             ProfScope prof("depth_keys", stream);
             const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
