@@ -97,10 +97,10 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows:
     packed = equirect and _ceil_log2(V) + 32 + max(1, _ceil_log2(P)) <= 64  # splat index inside the depth key
     return {
         "preprocess_fwd": n * 236 + P * 48,               # 59 parameter floats in, one splat out per view
-        # depth in, (view|depth|index) key out; the sorted keys read again and the splat order written
-        "depth_keys": P * (4 + 8 + 8 + 4) if packed else P * (4 + 8 + 4),
-        # per pass: key histogram read, key (and index) read and written
-        "depth_sort": dp * P * (8 + 2 * 8) if packed else dp * P * (8 + 2 * 12),
+        # depth in, (view|depth|index) key out (and the index value out when the index does not fit the key)
+        "depth_keys": P * (4 + 8) if packed else P * (4 + 8 + 4),
+        # per pass: key histogram read, key (and index) read and written; a packed sort's last pass writes the index
+        "depth_sort": dp * P * (8 + 2 * 8) - P * 4 if packed else dp * P * (8 + 2 * 12),
         "bin_count": P * (4 + 36 + 4) + rows * 8,         # depth order, (p, conic, depth, radii, q), count; rows out
         "bin_emit": rows * 8 + instances * 8,             # the stored rows in, one key per instance out
         "sort_upsweep": tp * instances * 8,               # per pass: keys read for the digit histogram

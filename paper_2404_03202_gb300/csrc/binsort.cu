@@ -174,6 +174,7 @@ depth_keys_kernel(int64_t total, int n, const float4* __restrict__ splats, u64* 
 
 // The same order from keys alone, when view, depth and splat index fit one 64-bit word: the index (gbits bits) rides
 // below the (view, depth) bits the sort orders by, and index order breaks ties as the stable sort with values does.
+// The sort's last pass writes only the index bits, which are the order.
 __global__ void __launch_bounds__(kBinThreads)
 depth_keys_packed_kernel(int64_t total, int n, int gbits, const float4* __restrict__ splats, u64* __restrict__ keys,
                          u64* __restrict__ count) {
@@ -182,12 +183,6 @@ depth_keys_packed_kernel(int64_t total, int n, int gbits, const float4* __restri
     if (i >= total) return;
     const float d = __ldg(reinterpret_cast<const float*>(splats + 3 * i + 1) + 1);
     keys[i] = ((((u64)(i / n) << 32) | (u64)__float_as_uint(d)) << gbits) | (u64)i;
-}
-
-__global__ void __launch_bounds__(kBinThreads)
-depth_order_kernel(int64_t total, u64 gmask, const u64* __restrict__ keys, uint32_t* __restrict__ order) {
-    const int64_t i = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
-    if (i < total) order[i] = (uint32_t)(__ldg(keys + i) & gmask);
 }
 
 // Pinhole views see a fraction of the scene, so their splats without instances (radius_x = 0: culled, or a box off
@@ -696,7 +691,8 @@ template <bool kVals>
 __global__ void __launch_bounds__(kSortThreads, 3)
 lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict__ vals_in, u64* __restrict__ keys_out,
                      unsigned* __restrict__ vals_out, const u64* __restrict__ count, u64 capacity, int shift, int dbits,
-                     const unsigned* __restrict__ hist, const unsigned* __restrict__ digit_start, int G) {
+                     const unsigned* __restrict__ hist, const unsigned* __restrict__ digit_start, int G,
+                     uint32_t* __restrict__ low_out, u64 low_mask) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64* s_keys = reinterpret_cast<u64*>(smem_raw);
     unsigned* s_vals = reinterpret_cast<unsigned*>(s_keys + kSortTile);
@@ -792,7 +788,8 @@ lsd_downsweep_kernel(const u64* __restrict__ keys_in, const unsigned* __restrict
             const u64 key = s_keys[i];
             const unsigned d = (unsigned)(key >> shift) & mask;
             const unsigned gpos = s_gbase[d] + (i - s_start[d]);
-            keys_out[gpos] = key;
+            if (low_out != nullptr) low_out[gpos] = (uint32_t)(key & low_mask);  // last pass: only the low bits
+            else keys_out[gpos] = key;
             if (kVals) vals_out[gpos] = s_vals[i];
         }
         __syncthreads();
@@ -841,10 +838,11 @@ Plan plan_for(int bits) {
 }
 
 // Stable sort of `count` (device) keys (and values) in (k0, v0) by key bits [lo_bit, lo_bit + bits), through (k1, v1);
-// the result lands back in (k0, v0).
+// the result lands back in (k0, v0), or, with low_out, only the sorted keys' bits under low_mask land in low_out.
 template <bool kVals>
 cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* count, u64 capacity, int lo_bit,
-                     int bits, int G, unsigned* hist, cudaStream_t stream, const char* tag_up, const char* tag_down) {
+                     int bits, int G, unsigned* hist, cudaStream_t stream, const char* tag_up, const char* tag_down,
+                     uint32_t* low_out = nullptr, u64 low_mask = 0) {
     const Plan P = plan_for(bits);
     const size_t smem = downsweep_smem<kVals>();
     cudaError_t e = cudaFuncSetAttribute(lsd_downsweep_kernel<kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -861,8 +859,10 @@ cudaError_t lsd_sort(u64* k0, unsigned* v0, u64* k1, unsigned* v1, const u64* co
         }
         {
             ProfScope prof(tag_down, stream);
+            uint32_t* lo = p + 1 == P.passes ? low_out : nullptr;
             lsd_downsweep_kernel<kVals><<<G, kSortThreads, smem, stream>>>(k0, v0, k1, v1, count, capacity, shift, db,
-                                                                            hist, hist + (size_t)kRadixMax * G, G);
+                                                                            hist, hist + (size_t)kRadixMax * G, G, lo,
+                                                                            low_mask);
         }
         std::swap(k0, k1);
         std::swap(v0, v1);
@@ -916,12 +916,9 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
             depth_keys_packed_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, gbits, sp, dk0, &hdr->splat_count);
         }
         e = lsd_sort<false>(dk0, nullptr, dk1, nullptr, &hdr->splat_count, (u64)total, gbits, 32 + ceil_log2(V),
-                            sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort");
+                            sort_grid((u64)total), hist, stream, "depth_sort", "depth_sort", order,
+                            (1ull << gbits) - 1);
         if (e != cudaSuccess) return e;
-        {
-            ProfScope prof("depth_keys", stream);
-            depth_order_kernel<<<g, kBinThreads, 0, stream>>>(total, (1ull << gbits) - 1, dk0, order);
-        }
     } else if (wrap) {
         {
             ProfScope prof("depth_keys", stream);
