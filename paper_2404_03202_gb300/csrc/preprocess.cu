@@ -343,7 +343,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
 // ---------------------------------------------------------------------------------------------------- adjoint
 
 template <int K, bool kPin>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 4)
 preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                       const float* __restrict__ scales, const float* __restrict__ quats,
                       const float* __restrict__ opacity, const float* __restrict__ sh,
@@ -359,7 +359,6 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
     float* s_view = s_dsh + kPreThreads * STRIDE;
     const int g0 = blockIdx.x * kPreThreads;
     const int cnt = min(kPreThreads, n - g0);
-    stage_sh<K>(s_sh, sh, g0, cnt);
     for (int e = threadIdx.x; e < 16 * V; e += blockDim.x) s_view[e] = __ldg(viewmats + e);
     float* dshc = s_dsh + threadIdx.x * STRIDE;
     for (int k = 0; k < KK; ++k) dshc[k] = 0.f;
@@ -369,7 +368,10 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
         float m[3], s[3], qn[4], qnorm, R[9], M3[9];
         load_params(g, means, scales, quats, m, s, qn, qnorm);
         rot_scale(qn, s, R, M3);
-        const float* shc = s_sh + threadIdx.x * STRIDE;
+        // the thread's SH row, copied to its shared-memory slot at its first view with a gradient (most Gaussians
+        // have none)
+        float* shc = s_sh + threadIdx.x * STRIDE;
+        bool sh_here = false;
         float dm[3] = {0.f, 0.f, 0.f}, dM3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float dop = 0.f, dsx = 0.f, dsy = 0.f;
         const float a = (float)W / (2.f * kPi), b = (float)H / kPi;
@@ -391,6 +393,11 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
                 const bool some = a0.x != 0.f || a0.y != 0.f || a0.z != 0.f || a0.w != 0.f || a1.x != 0.f ||
                                   a1.y != 0.f || a1.z != 0.f || a1.w != 0.f || a2 != 0.f;
                 live |= some ? 1u << i : 0u;
+            }
+            if (live && !sh_here) {
+                const float* src = sh + (size_t)g * KK;
+                for (int k = 0; k < KK; ++k) shc[k] = __ldg(src + k);
+                sh_here = true;
             }
             while (live) {
                 const int v = v0 + __ffs(live) - 1;
