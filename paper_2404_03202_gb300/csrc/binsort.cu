@@ -4,16 +4,18 @@
 // splat. Here that order is produced with short keys and coalesced passes only:
 //   1. depth_keys + LSD sort: the V * N splats are sorted once by (view, t_r bits), stable, so ties keep splat order.
 //      order[v * N + r] is the r-th nearest splat of view v (its depth rank r). Ranks are unique, so comparing ranks
-//      equals comparing (t_r, splat index). Pinhole views rank only the splats they can see (a compaction first).
+//      equals comparing (t_r, splat index). When view, t_r bits and splat index fit 64 bits the index rides in the
+//      key's low bits (keys only; the last pass writes those bits as the order); otherwise it is a value beside the
+//      key. Pinhole views rank only the splats they can see (a compaction first).
 //   2. bin_count / bin_scan / bin_emit walk the splats in depth order (through `order`), 256 per CTA: bin_count
 //      derives the kept columns of every box row (the row culling) and stores the rows, bin_scan takes a 64-bit
 //      exclusive scan of the per-CTA counts (overflow checked against the capacity), and bin_emit writes one key per
-//      instance, ((v * TILES + tile) << rank_bits) | rank, from the stored rows. The emitted stream is therefore
-//      already ordered by rank within every tile.
+//      instance, ((v * TILES + tile) << rank_bits) | rank, from the stored rows, each chunk's slots in order through
+//      a load-balanced search. The emitted stream is therefore already ordered by rank within every tile.
 //   3. A stable LSD radix sort of the instance keys over the tile bits only (ceil(log2(V * TILES)) bits above the
 //      rank, 2 passes of <= 9 bits: upsweep per-CTA digit counts; two small scans; downsweep with stable in-CTA
-//      ranking by warp match-any, staging in shared memory in digit order, runs of equal digits written to HBM). The
-//      keys carry no payload: the splat is order[v * N + rank].
+//      ranking (the lanes sharing a digit by one ballot per digit bit), staging in shared memory in digit order, runs
+//      of equal digits written to HBM). The keys carry no payload: the splat is order[v * N + rank].
 //   4. tile_ranges: [start, end) of every tile by binary search in the sorted keys.
 // No pass waits on another CTA, so there are no spin loops.
 #include <algorithm>

@@ -2,8 +2,9 @@
 // and its adjoint (Sec. 3.4, Eqs. 18-20).
 //
 // One thread per Gaussian loops over the V views, so the 59 parameter floats are read from HBM once per launch.
-// The SH block of a CTA is staged through shared memory with coalesced loads (rows padded to an odd stride so the
-// per-thread reads are bank-conflict free). The 2x2 covariance is formed as (M R S)(M R S)^T with M = J W, and its
+// The forward stages the SH block of a CTA through shared memory with coalesced loads (rows padded to an odd stride
+// so the per-thread reads are bank-conflict free). The adjoint walks only the views that passed the Gaussian a
+// gradient and copies its SH row into the same layout at the first of them. The 2x2 covariance is formed as (M R S)(M R S)^T with M = J W, and its
 // determinant as |T0 x T1|^2 + 0.3 (|T0|^2 + |T1|^2) + 0.09, a sum of non-negative terms, so that FP32 keeps full
 // relative accuracy for elongated splats (a c - b^2 would cancel). With the pinhole camera a Gaussian whose instance
 // box misses the image is culled (the frustum cull of 3DGS), and the adjoint, specialised per camera model, skips it.
