@@ -13,8 +13,8 @@ namespace omnigs {
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kDilation = 0.3f;        // low-pass dilation added to the 2x2 covariance
-constexpr float kAlphaMax = 0.99f;       // alpha clamp
-constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;       // alpha clamp (alphas below 1/255 are skipped: the factor 255 in the
+                                         // pass threshold -log2(255 o) and in the box's q = 2 ln(255 o))
 constexpr float kTStop = 1e-4f;          // stop once accumulated alpha would reach 0.9999
 constexpr float kPoleGuard = 1e-6f;      // rho is kept >= 1e-6 t_r inside J
 constexpr int kMaxRadius = 65535;        // instance-box half-extents are stored in 16 bits
