@@ -58,3 +58,17 @@ def test_stage_bytes_packed_depth_sort_only_when_the_index_fits():
     assert sb["depth_sort"] == 4 * 8_000_000 * 24 - 8_000_000 * 4
     sb = bench.stage_bytes(1_000_000, 8, 2048, 1024, 16, 10_000, 1_000, equirect=False)
     assert sb["depth_sort"] == 4 * 8_000_000 * 32
+
+
+def test_oracle_pool_times_a_bounded_sample_on_several_cores():
+    """The cpu_baseline leg: spawned workers build the workload once and each time a bounded oracle sample at the
+    same time; the step time is the mean per-core time divided by the core count."""
+    pool = bench.OraclePool("shell-small", cores=2)
+    try:
+        ms, ms_core, desc = pool.round(0.5)
+        ms2, _, _ = pool.round(0.5)
+    finally:
+        pool.close()
+    assert pool.cores == 2
+    assert ms > 0 and ms2 > 0 and abs(ms * 2 - ms_core) <= 1e-9 * ms_core
+    assert "1 of 1 views" in desc and "tiles" in desc
