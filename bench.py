@@ -595,7 +595,8 @@ def main():
 
     # ---------------------------------------------------------------- end to end through the public API
     # Every step copies its inputs (parameters, poses, targets) from pinned host memory and reads the loss and all
-    # gradients back into pinned host memory; StreamedSteps overlaps those copies with the neighbouring steps' compute.
+    # gradients back into pinned host memory; StreamedSteps overlaps those copies with the neighbouring steps' compute
+    # and replays each slot's compute from a CUDA graph after the two warm-up submits have captured them.
     e2e = None
     if not args.no_e2e:
         host_in = [torch.from_numpy(a).pin_memory() for a in scene.arrays()]
@@ -604,7 +605,7 @@ def main():
         out_shapes = {k: tuple(getattr(r, "d_" + k).shape) for k in Rasterizer.GRAD_NAMES}
         out_shapes["loss"] = (1,)
         host_out = {k: torch.empty(v, dtype=torch.float32).pin_memory() for k, v in out_shapes.items()}
-        streamed = StreamedSteps(r, lambda rr, t: loss_fn(t))
+        streamed = StreamedSteps(r, lambda rr, t: loss_fn(t), graph=not args.no_graph)
 
         for _ in range(2):
             streamed.submit(host_in, host_out)
@@ -624,7 +625,9 @@ def main():
         h2d = sum(h.numel() * h.element_size() for h in host_in)
         d2h = sum(h.numel() * h.element_size() for h in host_out.values())
         e2e = {"value": e_ms, "unit": "ms/iter", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "copies": "double-buffered: step k+1's inputs in and step k-1's results out during step k"}
+               "copies": "double-buffered: step k+1's inputs in and step k-1's results out during step k",
+               "compute": ("each slot's step captured once in a CUDA graph and replayed (StreamedSteps graph=True)"
+                           if all(g is not None for g in streamed.graphs) else "launched eagerly")}
         r.check()
 
     # ---------------------------------------------------------------- roofline of the dominant kernel

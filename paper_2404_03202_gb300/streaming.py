@@ -5,6 +5,10 @@ forward, loss and backward, and copies the loss and every gradient device -> hos
 of step k - 1 (out) run on two copy streams while step k computes: the device holds two input slots and two output
 slots, and CUDA events order each slot's copy against the compute that reads or writes it. Every step's copies are
 still made in full; only their overlap with the neighbouring steps' compute is new.
+
+With graph=True (a Rasterizer built with grow=False, and the same shapes every step) the compute of each slot is
+captured once in a CUDA graph after its first, eager, run and replayed from then on: the same kernels on the slot's
+buffers without the per-launch host cost.
 """
 from __future__ import annotations
 
@@ -22,9 +26,14 @@ class StreamedSteps:
     rasterizer.dL_drgb on the current stream (e.g. lambda r, t: r.l1_loss(t)).
     """
 
-    def __init__(self, rasterizer: Rasterizer, loss_fn: Callable[[Rasterizer, torch.Tensor], object]):
+    def __init__(self, rasterizer: Rasterizer, loss_fn: Callable[[Rasterizer, torch.Tensor], object],
+                 graph: bool = False):
+        if graph and rasterizer.grow:
+            raise ValueError("graph=True needs a Rasterizer built with grow=False (no host synchronisation)")
         self.r = rasterizer
         self.loss_fn = loss_fn
+        self.graph = graph
+        self.graphs = [None, None]    # captured compute of each slot
         dev = rasterizer.device
         self.h2d = torch.cuda.Stream(dev)
         self.d2h = torch.cuda.Stream(dev)
@@ -40,6 +49,7 @@ class StreamedSteps:
         dev = self.r.device
         if self.inputs[s] is None or any(d.shape != h.shape for d, h in zip(self.inputs[s], host_in)):
             self.inputs[s] = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in host_in]
+            self.graphs = [None, None]  # new buffers (and possibly new shapes inside the Rasterizer): capture again
 
     def _out_slot(self, s: int, means: torch.Tensor, sh: torch.Tensor):
         dev = self.r.device
@@ -50,7 +60,16 @@ class StreamedSteps:
             o = {k: torch.empty(v, dtype=torch.float32, device=dev) for k, v in shapes.items()}
             o["loss"] = torch.empty(1, dtype=torch.float32, device=dev)
             self.outputs[s] = o
+            self.graphs[s] = None
         return o
+
+    def _compute(self, s: int):
+        means, scales, quats, opacity, sh, viewmats, target = self.inputs[s]
+        self.r.forward(means, scales, quats, opacity, sh, viewmats)
+        self.loss_fn(self.r, target)
+        o = self.outputs[s]
+        self.r.backward(out=o)
+        o["loss"].copy_(self.r.loss)
 
     def begin(self):
         """Order the copy streams after everything the current stream has enqueued (e.g. a start event)."""
@@ -72,14 +91,18 @@ class StreamedSteps:
                 d.copy_(h, non_blocking=True)
             self.in_ready[s].record(self.h2d)
         cur.wait_event(self.in_ready[s])
-        means, scales, quats, opacity, sh, viewmats, target = self.inputs[s]
-        self.r.forward(means, scales, quats, opacity, sh, viewmats)
-        self.loss_fn(self.r, target)
-        o = self._out_slot(s, means, sh)
+        o = self._out_slot(s, self.inputs[s][0], self.inputs[s][4])
         if self.out_free[s] is not None:
             cur.wait_event(self.out_free[s])
-        self.r.backward(out=o)
-        o["loss"].copy_(self.r.loss)
+        if self.graphs[s] is not None:
+            self.graphs[s].replay()
+        else:
+            self._compute(s)
+            if self.graph:  # record the same work once for the next uses of this slot (capture runs nothing)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self._compute(s)
+                self.graphs[s] = g
         self.in_free[s] = torch.cuda.Event()
         self.in_free[s].record(cur)
         self.out_ready[s].record(cur)

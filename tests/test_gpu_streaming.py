@@ -25,12 +25,14 @@ def _inputs(step):
     return [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (*sc.arrays(), vm, tgt)]
 
 
-def test_streamed_steps_match_one_at_a_time():
+@pytest.mark.parametrize("graph", [False, True])
+def test_streamed_steps_match_one_at_a_time(graph):
+    """With graph=True steps 0 and 1 run eagerly and are captured, steps 2-4 replay the slots' graphs on new inputs."""
     steps = 5
     s = og.Settings(width=W, height=H, tile=16, num_views=V, sh_degree=3)
     ins = [_inputs(k) for k in range(steps)]
     r = og.Rasterizer(s, capacity=1 << 20, grow=False)
-    st = StreamedSteps(r, lambda rr, t: rr.l1_loss(t))
+    st = StreamedSteps(r, lambda rr, t: rr.l1_loss(t), graph=graph)
     outs = []
     for k in range(steps):
         n, K = ins[k][0].shape[0], ins[k][4].shape[1]
@@ -57,6 +59,13 @@ def test_streamed_steps_match_one_at_a_time():
             scale = max(np.abs(exp).max(), 1e-30)
             assert np.abs(got - exp).max() <= 1e-5 * scale, (k, name)  # the adjoint's atomics reorder sums
     assert len({float(o["loss"].item()) for o in outs}) == steps  # every step saw its own inputs
+    assert all(g is not None for g in st.graphs) == graph
+
+
+def test_graph_mode_needs_a_fixed_capacity():
+    s = og.Settings(width=W, height=H, tile=16, num_views=V, sh_degree=3)
+    with pytest.raises(ValueError):
+        StreamedSteps(og.Rasterizer(s), lambda rr, t: rr.l1_loss(t), graph=True)
 
 
 def test_backward_into_caller_buffers():
