@@ -220,88 +220,118 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_step_sample(scene, viewmats, wl: dict, target, budget_s: float, rng, tile: int | None = None):
-    """One bounded oracle sample of a step, extrapolated to the whole step (ms). Returns (ms, description)."""
-    import oracle
-    cam = oracle.pinhole(*wl["pinhole"]) if wl.get("pinhole") else None
-    W, H, V = wl["width"], wl["height"], wl["views"]
-    T = tile or (16 if wl["tile"] == "auto" else wl["tile"])
-    tiles = (W // T) * (H // T)
-    n = scene.n
-    # Gaussian fraction for the full-list stages (bin + sort, ~n log n, taken as linear) and tile sample for blending
-    frac = float(min(1.0, max(0.02, budget_s / 12.0)))
-    k_tiles = int(min(tiles, max(64, 512 * budget_s / 12.0)))
-    v = int(rng.integers(V))
-    idx = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False)) if frac < 1.0 else np.arange(n)
-    sub = scene.subset(idx)
-    t0 = time.perf_counter()
-    rec = oracle.preprocess(scene, viewmats[v:v + 1], W, H, camera=cam)
-    t_pre = time.perf_counter() - t0
-    sp = oracle.splats_from_records(rec)
-    t0 = time.perf_counter()
-    rec_s = oracle.preprocess(sub, viewmats[v:v + 1], W, H, camera=cam)
-    oracle.bin_sort(oracle.splats_from_records(rec_s), 1, W, H, T, camera=cam)
-    t_sort = (time.perf_counter() - t0) / frac
+class OracleSampler:
+    """Bounded samples of one step through the FP64 oracle, for one view of a workload. The view's full splats and
+    tile lists are computed once, untimed: they are the inputs of the sampled blend. Each sample then times
 
-    def blend(mask):
-        # bin + sort of the masked tiles is set-up here (its full cost is t_sort); only the blend calls are timed
-        rg, lst = oracle.bin_sort(sp, 1, W, H, T, tile_mask=mask, camera=cam)
+    * preprocess, bin + sort and preprocess_bwd on a random fraction of the Gaussians (scaled by 1 / fraction; the
+      sort's n log n is taken as linear),
+    * the blend forward and adjoint on random whole tile rows, cut from the full lists: a blend call costs a fixed
+      part (whole-image buffers, the splat table; measured once as a call with no tile) plus a part per tile, and only
+      the per-tile part is scaled to all tiles,
+
+    and extrapolates to the step's V views."""
+
+    def __init__(self, wl: dict, view: int, tile: int | None = None):
+        import oracle
+        self.oracle = oracle
+        self.cam = oracle.pinhole(*wl["pinhole"]) if wl.get("pinhole") else None
+        self.W, self.H, self.V = wl["width"], wl["height"], wl["views"]
+        self.T = tile or (16 if wl["tile"] == "auto" else wl["tile"])
+        self.tiles = (self.W // self.T) * (self.H // self.T)
+        self.view = view % self.V
+        self.scene = build_scene(wl)
+        self.vm = build_poses(wl, 0)[self.view:self.view + 1]
+        self.target = synth.random_image(1, self.W, self.H, 5 + self.view)
+        rec = oracle.preprocess(self.scene, self.vm, self.W, self.H, camera=self.cam)
+        self.sp = oracle.splats_from_records(rec)
+        self.rg, self.lst = oracle.bin_sort(self.sp, 1, self.W, self.H, self.T, camera=self.cam)
+        self.t_fixed = self._blend(np.zeros(0, np.int64))
+
+    def _blend(self, sel) -> float:
+        """Seconds for blend forward + adjoint over the tiles `sel` only (their lists cut from the full ones)."""
+        o = self.oracle
+        rg = np.zeros_like(self.rg)
+        parts, off = [], 0
+        for t in sel:
+            a, b = self.rg[t]
+            parts.append(self.lst[a:b])
+            rg[t] = (off, off + b - a)
+            off += b - a
+        lst = np.concatenate(parts) if parts else np.zeros(0, np.int64)
         t0 = time.perf_counter()
-        rgb, Tf, nc, _ = oracle.blend_fwd(sp, rg, lst, 1, W, H, T, camera=cam)
-        d = rgb - target[v:v + 1]
-        g = (np.sign(d) / (V * d.size)).astype(np.float64)
-        g2 = oracle.blend_bwd(sp, rg, lst, g, 1, W, H, T, camera=cam)
-        return time.perf_counter() - t0, g2
+        rgb, _, _, _ = o.blend_fwd(self.sp, rg, lst, 1, self.W, self.H, self.T, camera=self.cam)
+        d = rgb - self.target
+        o.blend_bwd(self.sp, rg, lst, np.sign(d) / (self.V * d.size), 1, self.W, self.H, self.T, camera=self.cam)
+        return time.perf_counter() - t0
 
-    # a blend call costs a fixed part (whole-image buffers, the splat table) plus a part per tile: the fixed part is
-    # the call with no tile, the per-tile part is scaled from the sampled tiles to all of them
-    mask = np.zeros(tiles, bool)
-    t_fixed, _ = blend(mask)
-    mask[rng.choice(tiles, k_tiles, replace=False)] = True
-    t_k, g2 = blend(mask)
-    t_blend = t_fixed + max(0.0, t_k - t_fixed) * tiles / k_tiles
-    t0 = time.perf_counter()
-    oracle.preprocess_bwd(scene, viewmats[v:v + 1], g2, W, H, camera=cam)
-    t_pbwd = time.perf_counter() - t0
-    ms = 1e3 * V * (t_pre + t_sort + t_blend + t_pbwd)
-    desc = (f"1 of {V} views: preprocess + preprocess_bwd of all {n} Gaussians, bin + sort of a {frac:.0%} Gaussian "
-            f"sample (scaled 1/frac), blend fwd + bwd: fixed per-call cost + {k_tiles} of {tiles} tiles (per-tile part "
-            f"scaled), times {V} views")
-    return ms, desc
+    def sample(self, budget_s: float, rng):
+        """One sample of about budget_s seconds; returns (ms per step, description)."""
+        o, n = self.oracle, self.scene.n
+        frac = float(min(1.0, max(0.02, budget_s / 12.0)))
+        k = int(min(self.tiles, max(64, 512 * budget_s / 12.0)))
+        idx = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False)) if frac < 1.0 else np.arange(n)
+        sub = self.scene.subset(idx)
+        t0 = time.perf_counter()
+        rec = o.preprocess(sub, self.vm, self.W, self.H, camera=self.cam)
+        t_pre = (time.perf_counter() - t0) / frac
+        sp = o.splats_from_records(rec)
+        t0 = time.perf_counter()
+        o.bin_sort(sp, 1, self.W, self.H, self.T, camera=self.cam)
+        t_sort = (time.perf_counter() - t0) / frac
+        # whole tile rows: the blend writes freshly zeroed whole-image arrays, whose pages are touched in proportion
+        # to the rows sampled as in the full image (scattered tiles would touch nearly every page)
+        tx, ty = self.W // self.T, self.H // self.T
+        rows = rng.choice(ty, int(min(ty, max(2, round(k / tx)))), replace=False)
+        sel = (rows[:, None] * tx + np.arange(tx)[None, :]).ravel()
+        k = len(sel)
+        t_k = self._blend(sel)
+        t_blend = self.t_fixed + max(0.0, t_k - self.t_fixed) * self.tiles / k
+        g2 = rng.standard_normal((len(idx), 9))  # the adjoint's cost does not depend on the values
+        t0 = time.perf_counter()
+        o.preprocess_bwd(sub, self.vm, g2, self.W, self.H, camera=self.cam)
+        t_pbwd = (time.perf_counter() - t0) / frac
+        ms = 1e3 * self.V * (t_pre + t_sort + t_blend + t_pbwd)
+        desc = (f"view {self.view} of {self.V}: preprocess, bin + sort and preprocess_bwd of a {frac:.0%} Gaussian "
+                f"sample of {n} (scaled 1/frac), blend fwd + bwd of {k} of {self.tiles} tiles in whole tile rows (per-tile "
+                f"part scaled, fixed per-call part once), times {self.V} views")
+        return ms, desc
 
 
 _ORACLE_STATE: dict = {}
 
 
-def _oracle_worker_init(wl_name: str, tile):
-    wl = WORKLOADS[wl_name]
-    _ORACLE_STATE.update(wl=wl, scene=build_scene(wl), vm=build_poses(wl, 0), tile=tile,
-                         target=synth.random_image(wl["views"], wl["width"], wl["height"], 5))
+def _oracle_worker_init(wl_name: str, tile, counter, barrier):
+    with counter.get_lock():
+        view = counter.value
+        counter.value += 1
+    _ORACLE_STATE.update(sampler=OracleSampler(WORKLOADS[wl_name], view, tile), barrier=barrier)
 
 
 def _oracle_worker_sample(job):
     budget, seed = job
-    st = _ORACLE_STATE
-    return oracle_step_sample(st["scene"], st["vm"], st["wl"], st["target"], budget, np.random.default_rng(seed),
-                              st["tile"])
+    _ORACLE_STATE["barrier"].wait(timeout=900)  # one job per worker, all timed at the same time
+    return _ORACLE_STATE["sampler"].sample(budget, np.random.default_rng(seed))
 
 
 class OraclePool:
-    """The FP64 oracle on every host core: one spawned process per core builds the workload once; a round runs one
-    bounded step sample per core at the same time. The step's views and tiles are independent, so the step's time on
-    C cores is the mean single-core extrapolation measured under that load, divided by C."""
+    """The FP64 oracle on every host core: one spawned process per core builds the workload and one view's full
+    splats and tile lists once; a round runs one bounded step sample per core at the same time. The step's views and
+    tiles are independent, so the step's time on C cores is the mean single-core extrapolation measured under that
+    load, divided by C."""
 
     def __init__(self, wl_name: str, tile=None, cores: int | None = None):
         import multiprocessing as mp
         self.cores = int(cores or len(os.sched_getaffinity(0)) or 1)
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
-                                                 initargs=(wl_name, tile))
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.cores, initializer=_oracle_worker_init,
+                             initargs=(wl_name, tile, ctx.Value("i", 0), ctx.Barrier(self.cores)))
         self.seed = 1000
 
     def round(self, budget_s: float):
         jobs = [(budget_s, self.seed + i) for i in range(self.cores)]
         self.seed += self.cores
-        res = self.pool.map(_oracle_worker_sample, jobs)
+        res = self.pool.map(_oracle_worker_sample, jobs, chunksize=1)
         per_core = float(np.mean([r[0] for r in res]))
         return per_core / self.cores, per_core, res[0][1]
 

@@ -71,4 +71,4 @@ def test_oracle_pool_times_a_bounded_sample_on_several_cores():
         pool.close()
     assert pool.cores == 2
     assert ms > 0 and ms2 > 0 and abs(ms * 2 - ms_core) <= 1e-9 * ms_core
-    assert "1 of 1 views" in desc and "tiles" in desc
+    assert "view 0 of 1" in desc and "tiles" in desc
