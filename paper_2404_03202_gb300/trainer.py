@@ -12,7 +12,6 @@ update have just been rebuilt), and the prune by screen-space size only starts a
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import numpy as np
 import torch

@@ -1,5 +1,4 @@
 """Autotuner of the tile size and blend schedule (gpu)."""
-import dataclasses
 
 import numpy as np
 import pytest

@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, dev, normwise, scene_to_device
+from tests.gpu_util import dev, normwise, scene_to_device
 
 pytestmark = pytest.mark.gpu
 

@@ -1,6 +1,5 @@
 """Pins of the oracle's pinhole camera (Eq. 2, the perspective model the paper contrasts with), CPU only."""
 import numpy as np
-import pytest
 
 import oracle
 import synth
