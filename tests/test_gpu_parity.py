@@ -73,9 +73,12 @@ def test_preprocess_matches_oracle(deg):
 # ------------------------------------------------------------------ S2-S4 bin, sort, ranges
 
 @pytest.mark.parametrize("tile,V,n,W,H", [(16, 2, 3000, 256, 128), (8, 1, 1500, 256, 128), (32, 3, 1000, 256, 128),
-                                         (16, 1, 60000, 512, 256), (8, 2, 20000, 128, 64)])
+                                         (16, 1, 60000, 512, 256), (8, 2, 20000, 128, 64),
+                                         (16, 4096, 300, 64, 32)])
 def test_bin_sort_bitexact(tile, V, n, W, H):
-    """Includes lists longer than one shared-memory chunk (sorted in chunks and merged) and many depth ties."""
+    """Includes lists longer than one shared-memory chunk (sorted in chunks and merged) and many depth ties. With
+    4096 views of 300 splats the (view, depth, splat index) key needs 12 + 32 + 21 bits, so the depth sort carries
+    the index as a value instead of inside the key."""
     sp = synth.random_splats(V, n, W, H, seed=100 + tile, max_radius=30)
     packed = pack_splats(sp)
     s = _settings(W, H, tile=tile, V=V)
