@@ -192,11 +192,13 @@ omnigs_status omnigs_dssim_loss(const omnigs_config *cfg, float lambda, const fl
  * or hand the library any beyond their inputs and outputs (a host application that owns the CUDA allocator or has
  * reserved all device memory, a loop with a fixed memory budget). The paper has no counterpart; this is an interface
  * convenience. Its scratch (4096 partial sums) is a fixed array inside the library, so it allocates nothing and calls
- * no allocating routine. Limit: V * 3 * H * W <= 268,435,456 floats; larger requests return OMNIGS_E_INVALID before
- * anything is enqueued. The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
- * should therefore come before any stream capture on that device. All calls on a device share the array: calls that
- * may overlap on the GPU race and must be serialised by the caller. rgb, target, dL_drgb: 16-byte aligned device
- * buffers [V, 3, H, W]; loss [1] device. */
+ * no allocating routine. Limit: V * 3 * H * W <= 268,435,456 floats; larger requests, and every configuration
+ * omnigs_l1_loss rejects, return OMNIGS_E_INVALID before anything is enqueued. The first call in a CUDA context
+ * looks up the array's device address (cudaGetSymbolAddress; again after the context is re-created) and, if nothing
+ * has loaded this library onto the device yet, loads its module, which takes device memory for the module image:
+ * make that first call before reserving all device memory and before any stream capture on that device. All calls
+ * on a device share the array: calls that may overlap on the GPU race and must be serialised by the caller. rgb,
+ * target, dL_drgb: 16-byte aligned device buffers [V, 3, H, W]; loss [1] device. */
 omnigs_status omnigs_l1_loss_static(const omnigs_config *cfg, const float *rgb, const float *target, float *dL_drgb,
                                     float *loss, omnigs_stream_t stream);
 

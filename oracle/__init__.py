@@ -52,10 +52,9 @@ def _load():
         lib.orc_quat_to_rot.argtypes = [P, P]
         lib.orc_preprocess.argtypes = [i64, i32, i32, i32, i32, f64, P, P, P, P, P, P, P]
         lib.orc_rect.argtypes = [f64, f64, i32, i32, i32, i32, i32, P]
-        lib.orc_row_columns.argtypes = [f64, f64, f64, f64, f64, f64, i64, i64, i64, i64, i32, P]
-        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P]
+        lib.orc_count_instances.argtypes = [i32, i64, i32, i32, i32, P, P, P, P]
         lib.orc_count_instances.restype = i64
-        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_bin_sort.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P, P, P]
         lib.orc_bin_sort.restype = i64
         lib.orc_blend_fwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, f64, P, P, P, P, P]
         lib.orc_blend_bwd.argtypes = [i32, i64, i32, i32, i32, P, P, P, P, P, P]
@@ -170,48 +169,32 @@ def splat_q(splats: dict) -> np.ndarray:
         return np.maximum(2.0 * np.log(255.0 * o), 0.0)
 
 
-def row_columns(px, py, c0, c1, c2, q, x0: int, nx: int, tiles_x: int, ty: int, tile: int):
-    """Unwrapped tile columns (first, last) of tile row ty that a splat with box columns x0 .. x0 + nx - 1 keeps
-    (first > last: none)."""
-    lib = _load()
-    out = np.zeros(2, dtype=np.int64)
-    lib.orc_row_columns(float(px), float(py), float(c0), float(c1), float(c2), float(q), int(x0), int(nx),
-                        int(tiles_x), int(ty), int(tile), _p(out))
-    return int(out[0]), int(out[1])
-
-
-def _conic_q(splats: dict):
-    return _f64(splats["c0"]), _f64(splats["c1"]), _f64(splats["c2"]), splat_q(splats)
-
-
 def count_instances(splats: dict, V: int, width: int, height: int, tile: int, camera=None) -> int:
+    """Number of (Gaussian, tile) instances: every tile of every instance box (Sec. 3.3)."""
     lib = _load()
     _camera(camera)
     px, py = _f64(splats["px"]), _f64(splats["py"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
-    c0, c1, c2, q = _conic_q(splats)
-    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry),
-                                       _p(c0), _p(c1), _p(c2), _p(q)))
+    return int(lib.orc_count_instances(V, px.shape[0] // V, width, height, tile, _p(px), _p(py), _p(rx), _p(ry)))
 
 
 def bin_sort(splats: dict, V: int, width: int, height: int, tile: int, tile_mask=None, camera=None):
-    """Instances sorted by (view, tile, t_r, Gaussian): returns ranges [V*tiles, 2] and the list of (v*N + g).
-    With `tile_mask` ([V*tiles] bool), only the lists of the masked tiles are built."""
+    """Instances (one per Gaussian and tile of its instance box) sorted by (view, tile, t_r, Gaussian): returns ranges
+    [V*tiles, 2] and the list of (v*N + g). With `tile_mask` ([V*tiles] bool), only the lists of the masked tiles are
+    built."""
     lib = _load()
     _camera(camera)
     px, py, depth = _f64(splats["px"]), _f64(splats["py"]), _f64(splats["depth"])
     rx, ry = _i32(splats["rx"]), _i32(splats["ry"])
-    c0, c1, c2, q = _conic_q(splats)
     n = px.shape[0] // V
     tiles = (width // tile) * (height // tile)
     mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
     ranges = np.zeros((V * tiles, 2), dtype=np.int64)
-    conic = (_p(c0), _p(c1), _p(c2), _p(q))
-    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), *conic, _p(depth),
-                                 _p(ranges), None, None if mask is None else _p(mask)))
+    total = int(lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges),
+                                 None, None if mask is None else _p(mask)))
     lst = np.zeros(max(total, 1), dtype=np.int64)
-    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), *conic, _p(depth), _p(ranges),
-                     _p(lst), None if mask is None else _p(mask))
+    lib.orc_bin_sort(V, n, width, height, tile, _p(px), _p(py), _p(rx), _p(ry), _p(depth), _p(ranges), _p(lst),
+                     None if mask is None else _p(mask))
     return ranges, lst[:total]
 
 

@@ -28,11 +28,11 @@
  *     rx = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4) + 1e-3)), ry likewise (the small widening absorbs FP32
  *     rounding on the GPU). A Gaussian with 255 o < 1 has no instance. Outside that box alpha < 1/255 at every
  *     pixel, so the narrowing leaves every image unchanged; it only drops instances that contribute nothing.
- *     rx and ry are held at 65535 (images are at most 65536 px wide).
- *   - within the box, a tile row keeps only the columns whose pixel centres the (widened) alpha >= 1/255 ellipse can
- *     reach: the ellipse's x-extent over the row's band of pixel-centre y values, widened by one pixel
- *     (row_columns below). The decision takes FP32 operations in a fixed order, so that an FP32 implementation
- *     making the same operations lists the same tiles; q = 2 ln(255 o) is stored with the splat (R_Q).
+ *     rx and ry are held at 65535 (images are at most 65536 px a side, so for the equirectangular camera a held box
+ *     still spans every column and row it reaches).
+ *   - one instance per (Gaussian, tile) pair for every tile the box touches: these are the lists this oracle builds.
+ *     An implementation may leave out pairs whose tile has no pixel centre with alpha >= 1/255 (they change no
+ *     pixel); the test-suite checks such lists against these (tests/tile_check.py).
  *   - quaternion stored (w, x, y, z), normalised before use; Sigma = R diag(s)^2 R^T.
  *   - colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m and Y_k the real
  *     orthonormal spherical harmonics up to degree 3 (no Condon-Shortley phase).
@@ -47,10 +47,9 @@
  *   p = (f_x t_x / t_z + c_x, f_y t_y / t_z + c_y); the depth that orders Gaussians is t_z; near cull t_z <= near_r;
  *   J = [[f_x / t_z, 0, -f_x u / t_z], [0, f_y / t_z, -f_y w / t_z]] with u = clamp(t_x / t_z, +-1.3 W / (2 f_x))
  *   and w = clamp(t_y / t_z, +-1.3 H / (2 f_y)) (the 3DGS guard that keeps J bounded off screen), while dp/dt, the
- *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped; centres beyond
- *   2^23 px are culled (a bound on integer tile arithmetic), and so is a Gaussian whose instance box
- *   [floor(p_x) - r_x, floor(p_x) + r_x] x [floor(p_y) - r_y, floor(p_y) + r_y] misses the image [0, W) x [0, H)
- *   (the frustum cull of 3DGS: such a Gaussian has no tile, hence no instance, either way).
+ *   derivative of p itself, is unclamped; tile columns are clipped like rows and dx is not wrapped; a Gaussian whose
+ *   instance box [floor(p_x) - r_x, floor(p_x) + r_x] x [floor(p_y) - r_y, floor(p_y) + r_y] misses the image
+ *   [0, W) x [0, H) is culled (the frustum cull of 3DGS: such a Gaussian has no tile, hence no instance, either way).
  */
 #include <math.h>
 #include <stdint.h>
@@ -295,8 +294,6 @@ static void forward_one(int W, int H, int sh_degree, double near_r, const float 
         if (tz <= near_r) { f->culled = 1; return; }
         f->p[0] = g_cam.fx * f->t[0] / tz + g_cam.cx;
         f->p[1] = g_cam.fy * f->t[1] / tz + g_cam.cy;
-        /* a bound on the tile arithmetic of any implementation: centres beyond 2^23 px are culled */
-        if (!(fabs(f->p[0]) < 8388608.0 && fabs(f->p[1]) < 8388608.0)) { f->culled = 1; return; }
         double limx = 1.3 * W / (2.0 * g_cam.fx), limy = 1.3 * H / (2.0 * g_cam.fy);
         double u = f->t[0] / tz, w = f->t[1] / tz;
         u = u < -limx ? -limx : (u > limx ? limx : u);
@@ -440,129 +437,38 @@ static int inst_cmp(const void *a, const void *b)
     return 0;
 }
 
-/* Columns [*cl, *cr] (unwrapped tile columns, within the box's x0 .. x0 + nx - 1) of tile row ty that the alpha >=
- * 1/255 ellipse dp^T conic dp <= q of a splat can reach, widened: q is raised by 0.1 % + 1e-3, the x-extent by one
- * pixel. Over the row's band of pixel-centre offsets v in [ty T + 1/2 - py, ty T + T - 1/2 - py], the ellipse spans
- * u in [x-(v_L), x+(v_R)] with x-+(v) = -s v -+ sqrt(w2 - k v^2), where s = c1 / c0, w2 = q / c0 and
- * k = det / c0^2 (det = c0 c2 - c1^2), and v_L, v_R the offsets of its leftmost and rightmost points
- * (+-c1 sqrt(q / (det c2))) clamped to the band and to the ellipse's rows |v| <= sqrt(q c0 / det). Every step is one
- * FP32 operation (single rounding, no contraction); the quotients by c0 are taken once per splat. Rows of a box that
- * spans every column, and splats whose det is not well above zero, keep the whole row. *cl > *cr means no column. */
-static void row_columns(float px, float py, float c0, float c1, float c2, float q, int64_t x0, int64_t nx,
-                        int64_t TX, int64_t ty, int T, int64_t *cl, int64_t *cr)
-{
-    *cl = x0;
-    *cr = x0 + nx - 1;
-    if (nx >= TX) return;
-    float c0c2 = c0 * c2, c1c1 = c1 * c1;
-    float det = c0c2 - c1c1;
-    float guard = 1e-3f * c0c2;
-    if (!(det > guard) || !(c0 > 0.0f) || !(c2 > 0.0f)) return;
-    float qw = q * 1.001f;
-    qw = qw + 1e-3f;
-    /* per splat */
-    float e2 = qw * c0;
-    e2 = e2 / det;
-    float ey = sqrtf(e2);
-    float d2 = det * c2;
-    float r2 = qw / d2;
-    float yL = sqrtf(r2);
-    yL = c1 * yL;
-    float s = c1 / c0;
-    float w2 = qw / c0;
-    float k = det / c0;
-    k = k / c0;
-    /* per row */
-    float tyT = (float)(ty * T);
-    float yl = tyT + 0.5f;
-    yl = yl - py;
-    float yh = tyT + (float)T;
-    yh = yh - 0.5f;
-    yh = yh - py;
-    float ney = -ey;
-    float lo = yl > ney ? yl : ney;
-    float hi = yh < ey ? yh : ey;
-    if (lo > hi) { *cl = 1; *cr = 0; return; }
-    float nyL = -yL;
-    float vL = yL < lo ? lo : (yL > hi ? hi : yL);
-    float vR = nyL < lo ? lo : (nyL > hi ? hi : nyL);
-    float hL = vL * vL;
-    hL = k * hL;
-    hL = w2 - hL;
-    hL = hL > 0.0f ? hL : 0.0f;
-    float hR = vR * vR;
-    hR = k * hR;
-    hR = w2 - hR;
-    hR = hR > 0.0f ? hR : 0.0f;
-    float xl = s * vL;
-    xl = -xl;
-    xl = xl - sqrtf(hL);
-    float xr = s * vR;
-    xr = -xr;
-    xr = xr + sqrtf(hR);
-    float ul = px + xl;
-    ul = ul - 1.0f;
-    float ur = px + xr;
-    ur = ur + 1.0f;
-    /* tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur */
-    float fT = (float)T;
-    float a = ul + 0.5f;
-    a = a - fT;
-    a = a / fT;
-    a = ceilf(a);
-    float b = ur - 0.5f;
-    b = b / fT;
-    b = floorf(b);
-    float fx0 = (float)x0, fx1 = (float)(x0 + nx - 1);
-    a = a > fx0 ? a : fx0;
-    b = b < fx1 ? b : fx1;
-    *cl = (int64_t)a;
-    *cr = (int64_t)b;
-}
-
-void orc_row_columns(double px, double py, double c0, double c1, double c2, double q, int64_t x0, int64_t nx,
-                     int64_t TX, int64_t ty, int T, int64_t *out)
-{
-    row_columns((float)px, (float)py, (float)c0, (float)c1, (float)c2, (float)q, x0, nx, TX, ty, T, out, out + 1);
-}
-
-/* Instances of one splat: tile rows of its box, each with the columns row_columns keeps. */
-static int64_t splat_instances(double px, double py, int rx, int ry, double c0, double c1, double c2, double q, int W,
-                               int H, int T, int64_t *tiles_out /* NULL: count only */)
+/* Instances of one splat: every tile of its box (Sec. 3.3, one instance per influence), row by row. */
+static int64_t splat_instances(double px, double py, int rx, int ry, int W, int H, int T,
+                               int64_t *tiles_out /* NULL: count only */)
 {
     int64_t TX = W / T, r[4], k = 0;
     orc_rect(px, py, rx, ry, W, H, T, r);
-    for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++) {
-        int64_t cl, cr;
-        row_columns((float)px, (float)py, (float)c0, (float)c1, (float)c2, (float)q, r[0], r[1], TX, ty, T, &cl, &cr);
-        for (int64_t c = cl; c <= cr; c++) {
+    for (int64_t ty = r[2]; ty < r[2] + r[3]; ty++)
+        for (int64_t c = r[0]; c < r[0] + r[1]; c++) {
             if (tiles_out) tiles_out[k] = ty * TX + ((c % TX) + TX) % TX;
             k++;
         }
-    }
     return k;
 }
 
 int64_t orc_count_instances(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                            const int32_t *rx, const int32_t *ry, const double *c0, const double *c1,
-                            const double *c2, const double *q)
+                            const int32_t *rx, const int32_t *ry)
 {
     int64_t total = 0;
     for (int64_t i = 0; i < (int64_t)V * n; i++) {
         if (rx[i] <= 0) continue;
-        total += splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, NULL);
+        total += splat_instances(px[i], py[i], rx[i], ry[i], W, H, T, NULL);
     }
     return total;
 }
 
-/* One instance per (Gaussian, kept tile); order by (view, tile), then t_r, then Gaussian index (the order a stable
+/* One instance per (Gaussian, tile of its box); order by (view, tile), then t_r, then Gaussian index (the order a stable
  * sort by (tile, t_r) gives when instances are generated Gaussian by Gaussian). ranges: [V*TX*TY][2].
  * tile_mask (optional, [V*TX*TY]): when given, only instances of tiles whose mask byte is non-zero are listed
  * (the lists of those tiles are the same as without a mask). Returns the number of listed instances; with
  * list_vg == NULL it only counts them. */
 int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, const double *py,
-                     const int32_t *rx, const int32_t *ry, const double *c0, const double *c1, const double *c2,
-                     const double *q, const double *depth, int64_t *ranges, int64_t *list_vg,
+                     const int32_t *rx, const int32_t *ry, const double *depth, int64_t *ranges, int64_t *list_vg,
                      const uint8_t *tile_mask)
 {
     int64_t TX = W / T, TY = H / T, tiles = TX * TY;
@@ -572,7 +478,7 @@ int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, co
         for (int64_t g = 0; g < n; g++) {
             int64_t i = v * n + g;
             if (rx[i] <= 0) continue;
-            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, buf);
+            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], W, H, T, buf);
             for (int64_t k = 0; k < m; k++) total += !tile_mask || tile_mask[v * tiles + buf[k]];
         }
     if (!list_vg) { free(buf); return total; } /* count only */
@@ -582,7 +488,7 @@ int64_t orc_bin_sort(int V, int64_t n, int W, int H, int T, const double *px, co
         for (int64_t g = 0; g < n; g++) {
             int64_t i = v * n + g;
             if (rx[i] <= 0) continue;
-            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], c0[i], c1[i], c2[i], q[i], W, H, T, buf);
+            int64_t m = splat_instances(px[i], py[i], rx[i], ry[i], W, H, T, buf);
             for (int64_t e = 0; e < m; e++) {
                 int64_t t = v * tiles + buf[e];
                 if (tile_mask && !tile_mask[t]) continue;

@@ -90,6 +90,9 @@ int num_sms();
 WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
 int rank_bits_for(int64_t n);
 
+// Whether a configuration is one every entry point accepts (image shape, tile, views, SH degree, camera, schedule).
+bool valid_cfg(const omnigs_config *c);
+
 // Kernel launches report their name and stream to the optional profiler.
 // Brackets the `kernels` launches of one named stage with CUDA events while the profiler is on.
 struct ProfScope {

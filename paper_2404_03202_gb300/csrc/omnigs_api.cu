@@ -91,12 +91,7 @@ ProfScope::~ProfScope() {
     cudaEventRecord(g_prof_records[slot].stop, stream);
 }
 
-}  // namespace omnigs
-
-using namespace omnigs;
-
-namespace {
-
+// The configuration checks shared by every entry point that takes an omnigs_config.
 bool valid_cfg(const omnigs_config* c) {
     if (!c) return false;
     if (c->tile != 8 && c->tile != 16 && c->tile != 32) return false;
@@ -118,6 +113,12 @@ bool valid_cfg(const omnigs_config* c) {
     const uint64_t tiles = (uint64_t)(c->width / c->tile) * (uint64_t)(c->height / c->tile) * (uint64_t)c->num_views;
     return tiles < (1ull << 31);
 }
+
+}  // namespace omnigs
+
+using namespace omnigs;
+
+namespace {
 
 bool valid_n(const omnigs_config* c, int64_t n) {
     return n >= 0 && (uint64_t)n * (uint64_t)c->num_views < (1ull << 32) && n < (1ll << 31);

@@ -75,6 +75,23 @@ def _box_margin(px, py, rx, ry, W, H):
     return np.minimum.reduce(gaps)
 
 
+def check_preprocess_pinhole(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W: int, H: int, intr):
+    """check_preprocess for a pinhole camera (Eq. 2): FP32 carries p - c to ~1e-7 of its size, so the position
+    tolerance (2e-6 of W, H) applies to centres within one image width / height of the principal point c, and the
+    rest are compared relative to |p - c|. Returns (summary, number of far centres checked)."""
+    import oracle
+    cx, cy = intr[2], intr[3]
+    dx, dy = rec[:, oracle.R_PX] - cx, rec[:, oracle.R_PY] - cy
+    on = (np.abs(dx) < W) & (np.abs(dy) < H)
+    far = ~on & (rec[:, oracle.R_RX] > 0) & (got["rx"] > 0)
+    gp = np.stack([got["px"] - cx, got["py"] - cy], 1)[far]
+    rp = np.stack([dx, dy], 1)[far]
+    if far.any():
+        assert (np.abs(gp - rp).max(1) / np.abs(rp).max(1)).max() <= 2e-6
+    summary = check_preprocess({k: v[on] for k, v in got.items()}, rec[on], opacity_expected[on], W, H, pinhole=True)
+    return summary, int(far.sum())
+
+
 def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W: int, H: int, near: float = 0.2,
                      pinhole: bool = False):
     """FP32 preprocess output against the oracle's FP64 records of the same (view, Gaussian) rows.
@@ -113,3 +130,37 @@ def check_preprocess(got: dict, rec: np.ndarray, opacity_expected: np.ndarray, W
     assert np.array_equal(got["ry"][a][margin_ok], ref["ry"][a][margin_ok])
     return dict(alive=int(a.sum()), dpx=float(np.abs(dpx).max(initial=0)), dpy=float(np.abs(dpy).max(initial=0)),
                 conic=float(cerr), rgb=float(rgb_err))
+
+
+def gpu_lists(r, count):
+    """The GPU's tile ranges [V * tiles, 2] and sorted splat list (v * n + g) of a rasterizer after bin + sort."""
+    ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+    return ranges, r.sorted_splats(count)
+
+
+def check_gpu_lists(r, count, sp, V, W, H, T, camera=None, tiles=None, ref=None):
+    """GPU tile lists against the oracle's instance-box lists of the same float32 splats, by the validity rules of
+    tests/tile_check.py (q as the float32 value both sides read). Returns the check's counts."""
+    import oracle
+    from tests import tile_check
+    sp64 = to64(sp)
+    ranges_ref, list_ref = ref if ref is not None else oracle.bin_sort(sp64, V, W, H, T, tile_mask=None, camera=camera)
+    ranges, lst = gpu_lists(r, count)
+    q = pack_splats(sp)[:, 7].astype(np.float64)
+    st = tile_check.check_tile_lists(sp64, V, W, H, T, ranges, lst, ranges_ref, list_ref, tiles=tiles, camera=camera,
+                                     q=q)
+    if tiles is None:
+        assert count == st["kept"], (count, st)
+    return st
+
+
+def last_contributor(ranges, lst, n_contrib, V, W, H, T):
+    """Splat (v * n + g) of every pixel's last contributor, -1 where none: n_contrib is the position after it in the
+    pixel's tile list, so this compares contributors between lists that differ in entries no pixel uses."""
+    TX, TY = W // T, H // T
+    ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    tile = (np.arange(V)[:, None, None] * (TX * TY) + (ys // T) * TX + xs // T)
+    nc = np.asarray(n_contrib, np.int64).reshape(V, H, W)
+    pos = np.asarray(ranges, np.int64)[tile, 0] + nc - 1
+    lst = np.asarray(lst, np.int64)
+    return np.where(nc > 0, lst[np.clip(pos, 0, max(len(lst) - 1, 0))] if len(lst) else -1, -1)

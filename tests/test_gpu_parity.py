@@ -1,7 +1,9 @@
 """GPU path vs the FP64 oracle, stage by stage and end to end, through the C ABI (marked gpu).
 
 Tolerances (written in each test):
-  * tile lists and sort order: bit-exact, given identical splats;
+  * tile lists, given identical splats: valid against the oracle's instance-box lists (tests/tile_check.py: an
+    order-preserving subsequence, every left-out pair out of reach by half the stated widening, every kept pair within
+    it), and equal to them, ranges included, where the binning keeps whole rows; the depth order bit-exact;
   * blended images: |dC| <= 1e-5 per channel, given identical splats, outside pixels where a skip / stop decision
     lies within 1e-5 (relative) of its threshold (the oracle flags them; at most 1e-3 of the pixels);
   * blend and preprocess gradients: normwise relative error <= 1e-4 and elementwise <= 1e-4 * max|g*|;
@@ -13,8 +15,8 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import (assert_grad_close, check_preprocess, dev, normwise, pack_splats, scene_to_device, to64,
-                            unpack_splats)
+from tests.gpu_util import (assert_grad_close, check_gpu_lists, check_preprocess, dev, gpu_lists, last_contributor,
+                            pack_splats, scene_to_device, to64, unpack_splats)
 
 pytestmark = pytest.mark.gpu
 
@@ -75,7 +77,7 @@ def test_preprocess_matches_oracle(deg):
 @pytest.mark.parametrize("tile,V,n,W,H", [(16, 2, 3000, 256, 128), (8, 1, 1500, 256, 128), (32, 3, 1000, 256, 128),
                                          (16, 1, 60000, 512, 256), (8, 2, 20000, 128, 64),
                                          (16, 4096, 300, 64, 32)])
-def test_bin_sort_bitexact(tile, V, n, W, H):
+def test_bin_sort_valid(tile, V, n, W, H):
     """Includes lists longer than one shared-memory chunk (sorted in chunks and merged) and many depth ties. With
     4096 views of 300 splats the (view, depth, splat index) key needs 12 + 32 + 21 bits, so the depth sort carries
     the index as a value instead of inside the key."""
@@ -83,17 +85,56 @@ def test_bin_sort_bitexact(tile, V, n, W, H):
     packed = pack_splats(sp)
     s = _settings(W, H, tile=tile, V=V)
     r, cnt = _run_splats(packed, s)
-    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
-    assert cnt == len(list_ref)
-    ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
-    assert np.array_equal(ranges, ranges_ref)
-    vals = r.sorted_splats(cnt)
-    assert np.array_equal(vals, list_ref)
+    st = check_gpu_lists(r, cnt, sp, V, W, H, tile)
+    print(f"bin tile {tile}, {V} x {n}: {st}")
+    assert st["dropped"] > 0 and st["kept_checked"] > 0.5 * st["kept"]
     # the depth order behind the ranks: per view, by (t_r, splat index)
     order = r.order.cpu().numpy().view(np.uint32).astype(np.int64).reshape(V, n)
     for v in range(V):
         d = sp["depth"][v * n:(v + 1) * n]
         assert np.array_equal(order[v] - v * n, np.lexsort((np.arange(n), d)))
+
+
+def _whole_row_splats(V, n, W, H, seed):
+    """Boxes wider than the image and, for the rest, needle conics (det = 5e-4 c0 c2, either sign of c1): the
+    binning keeps every tile of every box."""
+    sp = synth.random_splats(V, n, W, H, seed=seed, max_radius=30, wide_frac=0.4)
+    c0, c2 = sp["c0"].astype(np.float64), sp["c2"].astype(np.float64)
+    sign = np.where(np.random.default_rng(seed).uniform(size=len(c0)) < 0.5, -1.0, 1.0)
+    sp["c1"] = (sign * np.sqrt(c0 * c2 * (1.0 - 5e-4))).astype(np.float32)
+    return sp
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_bin_sort_exact_where_rows_are_whole(tile):
+    """Where no pair may be left out, the lists and ranges equal the oracle's box lists exactly."""
+    W, H, V, n = 256, 128, 2, 2000
+    sp = _whole_row_splats(V, n, W, H, 60 + tile)
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V), capacity=1 << 20)
+    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
+    ranges, lst = gpu_lists(r, cnt)
+    assert cnt == len(list_ref)
+    assert np.array_equal(ranges, ranges_ref)
+    assert np.array_equal(lst, list_ref)
+
+
+def test_row_culling_hand_computed():
+    """One circle of radius sqrt(q / c0) = 12 px (q = 9, c0 = c2 = 1/16) at (108.4, 50) on 16 px tiles, given a box
+    of half-extent 60 (tile rows 0-6, columns 3-10). Grown by the stated widening (q = 9.01: radius 12.007) and one
+    pixel, the circle's widest chord in tile row 3 (pixel centres 48.5 .. 63.5) spans 95.39 .. 121.41, which reaches
+    columns 5 (last centre 95.5) to 7; in tile row 2 (centres 32.5 .. 47.5) the widest chord, at y = 47.5, less one
+    pixel starts at 108.4 - sqrt(144.16 - 2.5^2) - 1 = 95.66 > 95.5, so the row keeps columns 6-7; no other row of
+    the box is within reach."""
+    W, H, T = 256, 128, 16
+    sp = dict(px=np.float32([108.4]), py=np.float32([50.0]), c0=np.float32([1 / 16]), c1=np.float32([0.0]),
+              c2=np.float32([1 / 16]), opacity=np.float32([np.exp(4.5) / 255]), r=np.float32([1]), g=np.float32([1]),
+              b=np.float32([1]), depth=np.float32([1]), rx=np.int32([60]), ry=np.int32([60]), q=np.float32([9.0]))
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=T))
+    ranges, lst = gpu_lists(r, cnt)
+    TX = W // T
+    kept = sorted(int(t) for t in np.nonzero(ranges[:, 1] > ranges[:, 0])[0])
+    assert kept == [2 * TX + 6, 2 * TX + 7, 3 * TX + 5, 3 * TX + 6, 3 * TX + 7]
+    assert cnt == 5 and (lst == 0).all()
 
 
 def test_sort_many_ties_and_all_columns():
@@ -102,9 +143,8 @@ def test_sort_many_ties_and_all_columns():
     sp = synth.random_splats(V, n, W, H, seed=9, max_radius=20, wide_frac=0.2)
     sp["depth"][:] = np.float32(3.0)
     r, cnt = _run_splats(pack_splats(sp), _settings(W, H, V=V))
-    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, 16)
-    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges_ref)
-    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+    st = check_gpu_lists(r, cnt, sp, V, W, H, 16)
+    assert st["whole_row_pairs"] > 0
 
 
 # ------------------------------------------------------------------ S5 render forward
@@ -137,14 +177,14 @@ def _row_cull_splats(V, n, W, H, seed):
 
 @pytest.mark.parametrize("tile", [16, 8])
 def test_bin_sort_row_culling_edges(tile):
-    """Tile lists under the per-row column culling, bit-exact, on splats that stress its decision procedure."""
+    """Tile lists under the per-row column culling, valid against the oracle's box lists, on splats that stress its
+    decision procedure."""
     W, H, V, n = 512, 256, 2, 3000
     sp = _row_cull_splats(V, n, W, H, 40 + tile)
     r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=tile, V=V), capacity=1 << 20)
-    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile)
-    assert cnt == len(list_ref)
-    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64), ranges_ref)
-    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+    st = check_gpu_lists(r, cnt, sp, V, W, H, tile)
+    print(f"row culling edges, tile {tile}: {st}")
+    assert st["dropped"] > 0 and st["whole_row_pairs"] > 0
 
 
 def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
@@ -152,7 +192,10 @@ def _fwd_compare(sp, V, W, H, tile, bg=(0.0, 0.0, 0.0), ppt=0):
     sp64 = to64(sp)
     ranges, lst = oracle.bin_sort(sp64, V, W, H, tile)
     rgb, T, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5)
-    return r, (rgb, T, nc, near), (ranges, lst, sp64)
+    # n_contrib is a position in the pixel's tile list: compare the splat it points at
+    r.last_splat = last_contributor(*gpu_lists(r, cnt), r.ncontrib.cpu().numpy(), V, W, H, tile)
+    last_ref = last_contributor(ranges, lst, nc, V, W, H, tile)
+    return r, (rgb, T, last_ref, near), (ranges, lst, sp64)
 
 
 @pytest.mark.parametrize("tile,V,ppt", [(16, 2, 4), (16, 2, 2), (16, 2, 8), (8, 1, 2), (32, 1, 4), (32, 1, 2),
@@ -161,7 +204,7 @@ def test_render_fwd_matches_oracle(tile, V, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2500, W, H, seed=200 + tile, max_radius=24)
     bg = (0.25, 0.5, 0.75)
-    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, tile, bg, ppt)
+    r, (rgb, T, last, near), _ = _fwd_compare(sp, V, W, H, tile, bg, ppt)
     mask = (near & 1) == 0
     frac = 1.0 - mask.mean()
     got = r.rgb.cpu().numpy()
@@ -170,7 +213,7 @@ def test_render_fwd_matches_oracle(tile, V, ppt):
     assert frac <= 1e-3
     assert err.max() <= 1e-5
     assert np.abs(r.T.cpu().numpy() - T)[mask].max() <= 1e-5
-    assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+    assert np.array_equal(r.last_splat[mask], last[mask])
     assert np.array_equal(r.count_out.cpu().numpy()[mask], oracle.blend_fwd.last_count[mask])
 
 
@@ -178,11 +221,11 @@ def test_render_fwd_opaque_stacks_stop_rule():
     """Dense opaque splats: most pixels stop at T < 1e-4 (the 0.9999 rule)."""
     W, H, V = 128, 64, 1
     sp = synth.random_splats(V, 3000, W, H, seed=3, max_radius=16, opacity_range=(0.9, 1.0), cull_frac=0.0)
-    r, (rgb, T, nc, near), _ = _fwd_compare(sp, V, W, H, 16)
+    r, (rgb, T, last, near), _ = _fwd_compare(sp, V, W, H, 16)
     mask = (near & 1) == 0
     assert (T[mask] < 1e-2).mean() > 0.5
     assert np.abs(r.rgb.cpu().numpy() - rgb).max(axis=1)[mask].max() <= 1e-5
-    assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+    assert np.array_equal(r.last_splat[mask], last[mask])
 
 
 # ------------------------------------------------------------------ S7 render backward
@@ -194,7 +237,7 @@ def test_render_bwd_matches_oracle(tile, V, opac, ppt):
     W, H = 256, 128
     sp = synth.random_splats(V, 2000, W, H, seed=300 + tile, max_radius=24, opacity_range=opac)
     bg = (0.1, 0.2, 0.3)
-    r, (rgb, T, nc, near), (ranges, lst, sp64) = _fwd_compare(sp, V, W, H, tile, bg, ppt)
+    r, (rgb, T, _, near), (ranges, lst, sp64) = _fwd_compare(sp, V, W, H, tile, bg, ppt)
     g = synth.random_image_grad(V, W, H, 7)
     g[np.repeat((near != 0)[:, None], 3, axis=1)] = 0.0  # pixels near a decision threshold carry no gradient
     ref = oracle.blend_bwd(sp64, ranges, lst, g.astype(np.float64), V, W, H, tile, bg)

@@ -1,7 +1,8 @@
 """The pinhole camera of Eq. 2 through the same C ABI, against the FP64 oracle (gpu).
 
-Same tolerances as the equirectangular parity tests: bit-exact tile lists on identical splats, images within 1e-5
-outside near-threshold pixels, gradients within 1e-4 (normwise and elementwise).
+Same tolerances as the equirectangular parity tests: tile lists on identical splats valid against the oracle's
+instance-box lists (tests/tile_check.py, columns clipped, no seam), images within 1e-5 outside near-threshold
+pixels, gradients within 1e-4 (normwise and elementwise).
 """
 import numpy as np
 import pytest
@@ -9,8 +10,8 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import (assert_grad_close, check_preprocess, dev, normwise, pack_splats, scene_to_device, to64,
-                            unpack_splats)
+from tests.gpu_util import (assert_grad_close, check_gpu_lists, check_preprocess_pinhole, dev, gpu_lists, last_contributor,
+                            normwise, pack_splats, scene_to_device, to64, unpack_splats)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,17 +49,9 @@ def test_preprocess_matches_oracle():
     C.omnigs_preprocess(r.cfg, sc.n, *scene_to_device(sc), dev(vm), r.splats)
     got = unpack_splats(r.splats.cpu().numpy())
     rec = oracle.preprocess(sc, vm, W, H, camera=CAM)
-    # FP32 carries p - c to ~1e-7 of its size, so the position tolerance (2e-6 of W, H) applies to centres within one
-    # image width / height of the principal point; the rest are compared relative to |p - c|
-    dx, dy = rec[:, oracle.R_PX] - INTR[2], rec[:, oracle.R_PY] - INTR[3]
-    on = (np.abs(dx) < W) & (np.abs(dy) < H)
-    far = ~on & (rec[:, oracle.R_RX] > 0)
-    gp = np.stack([got["px"] - INTR[2], got["py"] - INTR[3]], 1)[far]
-    rp = np.stack([dx, dy], 1)[far]
-    assert far.sum() > 100 and (np.abs(gp - rp).max(1) / np.abs(rp).max(1)).max() <= 2e-6
-    summary = check_preprocess({k: v[on] for k, v in got.items()}, rec[on], np.tile(sc.opacity, 2)[on], W, H,
-                               pinhole=True)
-    print("pinhole preprocess:", summary)
+    summary, far = check_preprocess_pinhole(got, rec, np.tile(sc.opacity, 2), W, H, INTR)
+    print("pinhole preprocess:", summary, "far centres", far)
+    assert far > 100
     assert summary["alive"] > 2000
 
 
@@ -72,7 +65,7 @@ def _offscreen_splats(V, n, seed):
 
 
 @pytest.mark.parametrize("tile", [16, 8])
-def test_bin_sort_bitexact(tile):
+def test_bin_sort_valid(tile):
     V, n = 2, 4000
     sp = _offscreen_splats(V, n, 3 + tile)
     s = _settings(V=V, tile=tile)
@@ -82,10 +75,9 @@ def test_bin_sort_bitexact(tile):
     C.omnigs_bin(r.cfg, n, r.splats, r.order, r.keys, r.capacity, r.ws)
     C.omnigs_sort(r.cfg, n, r.capacity, r.keys, r.ranges, r.ws)
     cnt = r.instance_count()
-    ranges_ref, list_ref = oracle.bin_sort(sp, V, W, H, tile, camera=CAM)
-    assert cnt == len(list_ref)
-    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64), ranges_ref)
-    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+    st = check_gpu_lists(r, cnt, sp, V, W, H, tile, camera=CAM)
+    print(f"pinhole bin tile {tile}: {st}")
+    assert st["dropped"] > 0
 
 
 def _fwd(sp, V, tile=16, bg=(0.0, 0.0, 0.0), ppt=0):
@@ -100,8 +92,10 @@ def _fwd(sp, V, tile=16, bg=(0.0, 0.0, 0.0), ppt=0):
     torch.cuda.synchronize()
     sp64 = to64(sp)
     ranges, lst = oracle.bin_sort(sp64, V, W, H, tile, camera=CAM)
-    ref = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5, camera=CAM)
-    return r, ref, (ranges, lst, sp64)
+    rgb, T, nc, near = oracle.blend_fwd(sp64, ranges, lst, V, W, H, tile, bg=bg, eps=1e-5, camera=CAM)
+    # n_contrib is a position in the pixel's tile list: compare the splat it points at
+    r.last_splat = last_contributor(*gpu_lists(r, r.instance_count()), r.ncontrib.cpu().numpy(), V, W, H, tile)
+    return r, (rgb, T, last_contributor(ranges, lst, nc, V, W, H, tile), near), (ranges, lst, sp64)
 
 
 @pytest.mark.parametrize("ppt", [4, 2])
@@ -109,12 +103,12 @@ def test_render_fwd_and_bwd_match_oracle(ppt):
     V = 2
     sp = _offscreen_splats(V, 2500, 11)
     bg = (0.2, 0.3, 0.4)
-    r, (rgb, T, nc, near), (ranges, lst, sp64) = _fwd(sp, V, bg=bg, ppt=ppt)
+    r, (rgb, T, last, near), (ranges, lst, sp64) = _fwd(sp, V, bg=bg, ppt=ppt)
     mask = (near & 1) == 0
     err = np.abs(r.rgb.cpu().numpy() - rgb).max(axis=1)[mask]
     print(f"pinhole render_fwd: max|dC| {err.max():.2e}, masked {1 - mask.mean():.1e}")
     assert 1 - mask.mean() <= 1e-3 and err.max() <= 1e-5
-    assert np.array_equal(r.ncontrib.cpu().numpy()[mask], nc[mask])
+    assert np.array_equal(r.last_splat[mask], last[mask])
     g = synth.random_image_grad(V, W, H, 12)
     g[np.repeat((near != 0)[:, None], 3, axis=1)] = 0.0
     got = r.backward_2d(dev(g)).cpu().numpy()
@@ -158,13 +152,16 @@ def test_end_to_end_against_oracle():
     grads = r.backward(dev(g))
     ref = oracle.render_grad(sc, vm, g.astype(np.float64), W, H, 16, fwd=f, camera=CAM)
     for name in ["means", "scales", "quats", "opacity", "sh"]:
-        assert normwise(grads[name].cpu().numpy(), ref[name]) <= 1e-2, name
+        nw = normwise(grads[name].cpu().numpy(), ref[name])
+        print(f"pinhole e2e grad {name}: normwise {nw:.2e}")
+        assert nw <= 1e-4, name
 
 
 def test_views_that_see_nothing_or_everything():
     """Three pinhole views of front-facing Gaussians: the first looks at them, the second away from them (every splat
     culled: no instance, background only), the third at them again. The depth sort ranks only what each view sees,
-    so the views must not disturb one another: lists bit-exact and images against the oracle."""
+    so the views must not disturb one another: images against the oracle, and the lists of the oracle's own splats
+    binned in one 3-view launch valid against its box lists."""
     sc = _front_scene(3000, 41)
     back = synth.identity_viewmats(1)
     back[0, :3, :3] = np.diag([-1.0, 1.0, -1.0])  # yaw by pi: everything behind the camera
@@ -180,11 +177,17 @@ def test_views_that_see_nothing_or_everything():
     ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
     tiles = (W // 16) * (H // 16)
     assert (ranges[tiles:2 * tiles] == 0).all()
-    # lists on the GPU's own splats, against the oracle's binning of the same float32 splats
-    sp = unpack_splats(r.splats.cpu().numpy())
-    ranges_ref, list_ref = oracle.bin_sort(sp, 3, W, H, 16, camera=CAM)
-    assert cnt == len(list_ref) and np.array_equal(ranges, ranges_ref)
-    assert np.array_equal(r.sorted_splats(cnt), list_ref)
+    assert cnt > 0
+    # the oracle's splats (rounded to the float32 layout) binned by the GPU in one 3-view launch
+    sp32 = unpack_splats(pack_splats(f["splats"]))
+    rb = og.Rasterizer(_settings(V=3), capacity=1 << 20)
+    rb._ensure(sc.n, 16)
+    rb.splats.copy_(dev(pack_splats(sp32)))
+    C.omnigs_bin(rb.cfg, sc.n, rb.splats, rb.order, rb.keys, rb.capacity, rb.ws)
+    C.omnigs_sort(rb.cfg, sc.n, rb.capacity, rb.keys, rb.ranges, rb.ws)
+    cb = rb.instance_count()
+    st = check_gpu_lists(rb, cb, sp32, 3, W, H, 16, camera=CAM)
+    assert (gpu_lists(rb, cb)[0][tiles:2 * tiles] == 0).all() and st["kept"] > 0
     mask = (f["near"] & 1) == 0
     err = np.abs(img - f["rgb"]).max(axis=1)[mask]
     assert np.quantile(err, 0.999) <= 1e-4 and err.max() <= 2e-6 * W * 4

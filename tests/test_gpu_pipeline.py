@@ -4,7 +4,8 @@ End to end the GPU rounds p to float32 (half an ulp of W) before blending and th
 bounded by |dC/dp| * dp rather than by the blend's own 1e-5: with the 0.3 px^2 dilation every 2D Gaussian has
 sigma >= sqrt(0.3) px, so |dG/dp| <= exp(-1/2) / sqrt(0.3) ~ 1.1 per px, and the per-pixel error stays within
 ~1e-6 * W summed over the few splats that matter. The asserts below use that bound with the pixel mask of the
-oracle's near-threshold flags (eps 1e-3, matching the FP32 alpha error of ~1e-4 relative).
+oracle's near-threshold flags (eps 1e-3, matching the FP32 alpha error of ~1e-4 relative). The gradients, with the
+near-threshold pixels' upstream gradient set to zero, are held to 1e-4 normwise per parameter tensor.
 """
 import numpy as np
 import pytest
@@ -40,7 +41,8 @@ def test_end_to_end_config1_forward_backward():
     err = np.abs(rgb - f["rgb"]).max(axis=1)
     print(f"e2e fwd: instances gpu {r.count} oracle {len(f['list'])}; max|dC| {err[mask].max():.3e} "
           f"p99.9 {np.quantile(err[mask], 0.999):.3e} mean {err[mask].mean():.3e} masked {1 - mask.mean():.2e}")
-    assert abs(r.count - len(f["list"])) <= 1e-3 * len(f["list"])
+    # the oracle lists every tile of every instance box; the GPU leaves out pairs out of reach
+    assert 0.5 * len(f["list"]) <= r.count <= len(f["list"])
     assert 1 - mask.mean() <= 1e-2
     assert err[mask].max() <= 2e-6 * W * 4
     assert np.quantile(err[mask], 0.999) <= 1e-4
@@ -52,7 +54,7 @@ def test_end_to_end_config1_forward_backward():
         got = grads[name].cpu().numpy()
         nw = normwise(got, ref[name])
         print(f"e2e grad {name}: normwise {nw:.2e}")
-        assert nw <= 1e-2, name
+        assert nw <= 1e-4, name
 
 
 def test_autograd_function_matches_direct_backward():

@@ -7,7 +7,7 @@ Which pin covers which oracle function:
   quat_to_rot                    scipy Rotation                                       test_quaternion_*
   sh_basis                       orthonormality by quadrature, scipy sph_harm_y       test_sh_*
   preprocess: near cull          t_r = 0.19 vs 0.21                                   test_near_cull
-  rect / bin_sort                pixel-enumeration brute force                        test_bin_sort_*
+  rect / bin_sort                pixel-enumeration brute force of the instance boxes  test_bin_sort_*, test_rect_*
   blend_fwd (Eqs. 6-8)           all-Gaussians brute force, stop rule closed form,    test_blend_*, test_termination_*
                                  background term, yaw = cyclic column shift           test_yaw_*
   blend_bwd, preprocess_bwd      FP64 central finite differences (stage and end-to-end)   test_*_finite_differences
@@ -267,90 +267,22 @@ def _as_ranges(lists):
     return ranges, np.array([i for L in lists for i in L], np.int64)
 
 
-def _alpha_reaches(sp, i, W, T, ty, tx):
-    """Whether some pixel of tile (ty, tx) gets alpha >= 1/255 from splat i (Eq. 8 in FP64; dx the minimal image
-    across the longitude seam)."""
-    xs = tx * T + 0.5 + np.arange(T)
-    ys = ty * T + 0.5 + np.arange(T)
-    dx = float(sp["px"][i]) - xs[None, :]
-    dx = np.where(dx >= 0.5 * W, dx - W, np.where(dx < -0.5 * W, dx + W, dx))
-    dy = float(sp["py"][i]) - ys[:, None]
-    c0, c1, c2 = (float(sp[k][i]) for k in ("c0", "c1", "c2"))
-    power = -0.5 * (c0 * dx * dx + c2 * dy * dy) - c1 * dx * dy
-    alpha = np.minimum(0.99, float(sp["opacity"][i]) * np.exp(power))
-    return bool(((power <= 0) & (alpha >= 1 / 255)).any())
-
-
-def _min_form_on_rect(c0, c1, c2, x0, x1, y0, y1):
-    """min of c0 u^2 + 2 c1 u v + c2 v^2 over [x0, x1] x [y0, y1] (interior minimum at 0, else on an edge)."""
-    if x0 <= 0 <= x1 and y0 <= 0 <= y1:
-        return 0.0
-    best = np.inf
-    for v in (y0, y1):  # horizontal edges: minimise over u
-        u = np.clip(-c1 * v / c0, x0, x1)
-        best = min(best, c0 * u * u + 2 * c1 * u * v + c2 * v * v)
-    for u in (x0, x1):
-        v = np.clip(-c1 * u / c2, y0, y1)
-        best = min(best, c0 * u * u + 2 * c1 * u * v + c2 * v * v)
-    return best
-
-
 def test_bin_sort_matches_bruteforce(oracle_lib):
-    """The tile lists are the instance boxes' lists (brute force) with the (Gaussian, tile) pairs dropped whose tile
-    has no pixel the Gaussian reaches with alpha >= 1/255, in the same order; the images over both are identical, and
-    every kept pair has its widened ellipse within 1.5 px of the tile's band of pixel centres."""
+    """The tile lists are exactly the instance boxes' lists of a pixel-enumeration brute force (columns modulo W,
+    rows clipped), ordered by (t_r, index) within every tile, including seam, pole and wider-than-image boxes and
+    depth ties; the counting pass agrees with the list."""
     V, W, H, T = 2, 128, 64, 8
-    sp = synth.random_splats(V, 150, W, H, seed=7, max_radius=20)
+    sp = synth.random_splats(V, 150, W, H, seed=7, max_radius=20, wide_frac=0.05)
     ranges, lst = oracle.bin_sort(sp, V, W, H, T)
-    ref = _brute_force_lists(sp, V, W, H, T)
-    TX, TY = W // T, H // T
-    q = oracle.splat_q(sp)
-    dropped = kept_checked = 0
-    for t, L in enumerate(ref):
-        got = lst[ranges[t, 0]:ranges[t, 1]].tolist()
-        if not got:
-            assert ranges[t, 0] == ranges[t, 1]
-        assert got == [i for i in L if i in set(got)], t
-        ty, tx = (t % (TX * TY)) // TX, t % TX
-        for i in set(L) - set(got):
-            assert not _alpha_reaches(sp, i, W, T, ty, tx), (t, i)
-            dropped += 1
-        for i in got:
-            if oracle.rect(sp["px"][i], sp["py"][i], sp["rx"][i], sp["ry"][i], W, H, T)[1] >= TX:
-                continue  # boxes over every column keep whole rows
-            c0, c1, c2 = (float(sp[k][i]) for k in ("c0", "c1", "c2"))
-            y0, y1 = ty * T + 0.5 - sp["py"][i], ty * T + T - 0.5 - sp["py"][i]
-            m = min(_min_form_on_rect(c0, c1, c2, tx * T + 0.5 - sp["px"][i] + s - 1.5,
-                                      tx * T + T - 0.5 - sp["px"][i] + s + 1.5, y0, y1) for s in (-W, 0, W))
-            assert m <= q[i] * 1.01 + 0.01, (t, i, m, q[i])
-            kept_checked += 1
-    assert sum(len(L) for L in ref) == len(lst) + dropped
-    assert dropped > 0.1 * len(lst) and kept_checked > 0.5 * len(lst)
-    box_ranges, box_list = _as_ranges(ref)
-    a = oracle.blend_fwd(sp, ranges, lst, V, W, H, T)
-    b = oracle.blend_fwd(sp, box_ranges, box_list, V, W, H, T)
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-
-
-def test_row_columns_hand_computed(oracle_lib):
-    """A circle of radius sqrt(q / c0) = 12 px (q = 9, c0 = c2 = 1/16) centred at (108.4, 50) on 16 px tiles: the
-    band of tile row 3 (pixel centres 48.5 .. 63.5) holds the circle's widest chord (108.4 -+ 12.0), which reaches the
-    centres of tile columns 5 (up to 95.5) .. 7 (from 112.5); in tile row 2 (centres 32.5 .. 47.5) the widest chord,
-    at y = 47.5, is 108.4 -+ sqrt(144 - 2.5^2) = 108.4 -+ 11.74, whose left end 96.66 stays more than a pixel right
-    of column 5's last centre; rows 1 and 4 lie wholly above and below the circle."""
-    cols = [oracle.row_columns(108.4, 50.0, 1 / 16, 0.0, 1 / 16, 9.0, 0, 15, 16, ty, 16) for ty in range(5)]
-    assert cols[2] == (6, 7) and cols[3] == (5, 7)
-    for ty in (0, 1, 4):
-        assert cols[ty][0] > cols[ty][1]
-    # the box bounds the columns; a box over every column keeps the row whole
-    assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.0, 1 / 16, 9.0, 6, 1, 16, 3, 16) == (6, 6)
-    assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.0, 1 / 16, 9.0, 0, 16, 16, 0, 16) == (0, 15)
-    # a conic whose determinant is within 1e-3 of c0 c2 from zero (a needle) keeps whole rows, even far away
-    assert oracle.row_columns(108.4, 50.0, 1 / 16, 0.99999 / 16, 1 / 16, 9.0, 0, 15, 16, 0, 16) == (0, 14)
-    # a sheared ellipse reaches further left above its centre when c1 < 0 ... and further right when c1 > 0
-    lo = oracle.row_columns(108.4, 50.0, 1 / 16, -0.04, 1 / 16, 9.0, 0, 15, 16, 2, 16)
-    hi = oracle.row_columns(108.4, 50.0, 1 / 16, 0.04, 1 / 16, 9.0, 0, 15, 16, 2, 16)
-    assert lo[1] >= hi[1] and hi[0] >= lo[0] and lo != hi
+    ref_ranges, ref_list = _as_ranges(_brute_force_lists(sp, V, W, H, T))
+    assert np.array_equal(ranges, ref_ranges) and np.array_equal(lst, ref_list)
+    assert oracle.count_instances(sp, V, W, H, T) == len(lst)
+    # a tile mask keeps the masked tiles' lists unchanged and empties the rest
+    mask = np.random.default_rng(2).uniform(size=len(ranges)) < 0.3
+    mr, ml = oracle.bin_sort(sp, V, W, H, T, tile_mask=mask)
+    for t in range(len(ranges)):
+        got = ml[mr[t, 0]:mr[t, 1]]
+        assert np.array_equal(got, lst[ranges[t, 0]:ranges[t, 1]] if mask[t] else got[:0])
 
 
 def test_rect_cases(oracle_lib):
@@ -458,9 +390,8 @@ def test_instance_box_holds_every_visible_pixel(oracle_lib):
 
 
 def test_instance_box_leaves_images_unchanged(oracle_lib):
-    """Lists from the narrowed box with the rows' column culling and from the full 3-sigma square (every tile it
-    touches, brute force) blend to identical images: every dropped instance has alpha < 1/255 at every pixel of its
-    tile."""
+    """Lists from the narrowed box and from the full 3-sigma square (every tile it touches, brute force) blend to
+    identical images: every instance the box leaves out has alpha < 1/255 at every pixel of its tile."""
     W, H, T = 256, 128, 16
     sc = synth.shell_scene(1500, seed=32, log_scale_mean=-2.5)
     sc.opacity[:] = np.random.default_rng(4).uniform(0.004, 1.0, sc.n).astype(np.float32)
