@@ -122,10 +122,10 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  * that the splat's alpha >= 1/255 ellipse can reach. Tile columns wrap modulo W / tile (the longitude seam; a box at
  * least as wide as the image covers every column once); rows are clipped to the image. Within a tile row of a box
  * narrower than the image, only the columns whose pixel centres lie within one pixel of the ellipse
- * dp^T conic dp <= q (1.001) + 1e-3, over the row's band of pixel-centre y values, are kept; the column bounds come
- * from a fixed sequence of correctly rounded FP32 operations, so that they are reproducible bit for bit. A dropped
- * tile has alpha < 1/255 at each of its pixels: no image changes. Splats with c0 c2 - c1^2 <= 1e-3 c0 c2 keep whole
- * rows.
+ * dp^T conic dp <= q (1.001) + 1e-3, over the row's band of pixel-centre y values, are kept (the widening absorbs
+ * the rounding of the single-precision bounds). A dropped tile has alpha < 1/255 at each of its pixels: no image
+ * changes. Splats with c0 c2 - c1^2 <= 1e-3 c0 c2 keep whole rows, and so, with the equirectangular camera, do
+ * splats with radius_x + tile > W / 2 (whose box offsets can differ from the minimal-image dx of the blend).
  * Splats whose centre lies outside [0, W] x [0, H] (equirectangular camera) or beyond 2^23 px (pinhole camera) are
  * ignored.
  *   splats  [V * n] input (device)

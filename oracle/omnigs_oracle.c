@@ -62,6 +62,9 @@
 #define ORC_ALPHA_MIN (1.0 / 255.0)
 #define ORC_T_STOP 1e-4
 #define ORC_POLE_GUARD 1e-6
+/* unit roundoff of single precision, 2^-24: the near-threshold flags of orc_blend_fwd widen by the rounding error a
+ * single-precision evaluation of the exponent can make (a few roundoffs of the magnitude of its terms) */
+#define ORC_F32_ROUNDOFF 5.9604644775390625e-8
 
 /* per-(view, Gaussian) record written by orc_preprocess. R_RADIUS is the square's r; R_RX, R_RY the half-extents
  * of the box the instances come from; R_RMARGIN the smallest distance of the three ceil() arguments to an integer. */
@@ -518,7 +521,9 @@ static double rel_gap(double x, double thr) { return fabs(x - thr) / fabs(thr); 
 
 /* Blend one pixel; returns the number of contributors written to `out` (which must hold the tile list length).
  * near: bit 0 = a forward decision (alpha vs 1/255, T' vs 1e-4, exponent sign) lies within eps of its threshold,
- * bit 1 = alpha lies within eps of the 0.99 clamp. */
+ * bit 1 = alpha lies within eps of the 0.99 clamp. For alpha and T' the distance allowed also includes the rounding
+ * a single-precision evaluation of the exponent -q0 - q1 - q2 can make when its terms cancel: 8 roundoffs of
+ * mag = |q0| + |q1| + |q2| (as a relative error of alpha = o e^power; times alpha / (1 - alpha) for T'). */
 static int64_t blend_pixel(int W, double xs, double ys, const double *splat, const int64_t *list, int64_t lo,
                            int64_t hi, double eps, orc_contrib *out, double *T_final, int64_t *n_contrib,
                            int *near, double *rgb_acc)
@@ -541,13 +546,14 @@ static int64_t blend_pixel(int W, double xs, double ys, const double *splat, con
         if (power > 0.0) continue;
         double G = exp(power);
         double raw = sp[5] * G;
-        if (rel_gap(raw, ORC_ALPHA_MIN) < eps) *near |= 1;
-        if (rel_gap(raw, ORC_ALPHA_MAX) < eps) *near |= 2;
+        double cond = 8.0 * ORC_F32_ROUNDOFF * mag;
+        if (rel_gap(raw, ORC_ALPHA_MIN) < eps + cond) *near |= 1;
+        if (rel_gap(raw, ORC_ALPHA_MAX) < eps + cond) *near |= 2;
         int clamped = raw > ORC_ALPHA_MAX;
         double alpha = clamped ? ORC_ALPHA_MAX : raw;
         if (alpha < ORC_ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);
-        if (rel_gap(Tn, ORC_T_STOP) < eps) *near |= 1;
+        if (rel_gap(Tn, ORC_T_STOP) < eps + cond * alpha / (1.0 - alpha)) *near |= 1;
         if (Tn < ORC_T_STOP) break;
         for (int ch = 0; ch < 3; ch++) rgb_acc[ch] += sp[6 + ch] * alpha * T;
         out[nc].vg = list[j]; out[nc].alpha = alpha; out[nc].T = T; out[nc].G = G; out[nc].raw = raw;

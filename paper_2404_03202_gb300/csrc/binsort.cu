@@ -94,17 +94,20 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
 // u in [x-(v_L), x+(v_R)], x-+(v) = -s v -+ sqrt(w2 - k v^2) with s = c1 / c0, w2 = q / c0, k = det / c0^2 and
 // det = c0 c2 - c1^2, where v_L and v_R (the v of the ellipse's leftmost and rightmost points, +-c1 sqrt(q / (det c2)))
 // are clamped to the band intersected with the ellipse's own rows |v| <= sqrt(q c0 / det). A tile column is kept when
-// its pixel centres come within one pixel of that span. Each step is a single correctly rounded FP32 operation (no
-// contraction), so that the same decision can be reproduced exactly elsewhere. The row-invariant part is computed
-// once per splat.
+// its pixel centres come within one pixel of that span; the widening of q and of the span absorbs the rounding of
+// these single-precision steps. The row-invariant part is computed once per splat. Rows keep every column of the box
+// when the box spans every column, when the conic is a needle (det <= 1e-3 c0 c2, where the bounds lose precision),
+// and, with the longitude seam, when rx + tile > W / 2: only below that do the box's unwrapped column offsets equal
+// the minimal-image offsets (|dx| < W / 2) that the blend evaluates, so the span is taken on the copy the blend uses.
 struct RowCull {
     float px, py, s, yL;  // centre, shear c1 / c0, leftmost-point offset
     float ey, w2, k;      // ey < 0: no culling (whole rows)
 };
 
-__device__ __forceinline__ RowCull row_cull_setup(const SplatPos& p, int nx, int tiles_x) {
+__device__ __forceinline__ RowCull row_cull_setup(const SplatPos& p, int nx, int tiles_x, int tile, bool wrap) {
     RowCull rc = {p.px, p.py, 0.f, 0.f, -1.f, 0.f, 0.f};
     if (nx >= tiles_x) return rc;
+    if (wrap && 2 * (p.rx + tile) > tiles_x * tile) return rc;
     const float c0c2 = __fmul_rn(p.c0, p.c2), c1c1 = __fmul_rn(p.c1, p.c1);
     const float det = __fsub_rn(c0c2, c1c1);
     const float guard = __fmul_rn(1e-3f, c0c2);
@@ -341,7 +344,7 @@ __device__ __forceinline__ unsigned stage_rows(CtaRows& S, unsigned* scratch, co
             if (p.rx > 0) {
                 r = splat_rect(p.px, p.py, p.rx, p.ry, tiles_x, tiles_y, __ffs(tile) - 1, wrap);
                 rows[u] = r.nx > 0 ? (unsigned)r.ny : 0u;
-                rc = row_cull_setup(p, r.nx, tiles_x);
+                rc = row_cull_setup(p, r.nx, tiles_x, tile, wrap);
                 const int64_t v = i / n;
                 rank = (int)(i - v * n);
                 tbase = (unsigned)v * (unsigned)(tiles_x * tiles_y);

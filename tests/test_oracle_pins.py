@@ -445,6 +445,27 @@ def test_termination_closed_form(oracle_lib):
                                + 0.01 * 0.5 * np.array([sp["r"][1], 0.5, 1.0]), atol=1e-14)
 
 
+def test_near_threshold_flag_widens_with_cancelling_exponent_terms(oracle_lib):
+    """alpha = (1 + 5e-5) / 255 at pixel (100, 60) from a splat 50 px away along the diagonal: with a diagonal conic
+    (c1 = 0, exponent terms of magnitude 5) the pixel is not flagged (5e-5 > 1e-5); with a sheared conic whose terms
+    (about 1000 in magnitude) cancel to the same exponent -5, single precision cannot place alpha within 5e-5 of
+    1/255, and the pixel is flagged."""
+    W, H, T = 256, 128, 16
+    d = 50.0
+    flags = []
+    for c, c1 in [(0.002, 0.0), (0.2, -0.2 * 0.99)]:
+        power = -0.5 * d * d * (2 * c + 2 * c1)
+        assert abs(power + 5.0) < 1e-12
+        o = (1 + 5e-5) / 255 * np.exp(5.0)
+        sp = dict(px=np.array([100.5 + d]), py=np.array([60.5 + d]), c0=np.array([c]), c1=np.array([c1]),
+                  c2=np.array([c]), opacity=np.array([o]), r=np.ones(1), g=np.ones(1), b=np.ones(1),
+                  depth=np.ones(1), rx=np.array([60], np.int32), ry=np.array([60], np.int32))
+        ranges, lst = oracle.bin_sort(sp, 1, W, H, T)
+        _, _, _, near = oracle.blend_fwd(sp, ranges, lst, 1, W, H, T, eps=1e-5)
+        flags.append(int(near[0, 60, 100] & 1))
+    assert flags == [0, 1]
+
+
 def test_yaw_equals_cyclic_column_shift(oracle_lib):
     """Yawing the camera by 2 pi k / W about its y axis shifts longitude by a constant, so the image rolls by k
     columns (Eqs. 3-5); with k a multiple of the tile size the tile lists roll with it."""

@@ -24,18 +24,22 @@ def _as_ranges(lists):
 
 def _fp64_culled(sp, V, W, H, T, ranges, lst, camera=None):
     """The box lists with the stated row culling taken in FP64: a pair stays when its splat keeps whole rows (box
-    over every column, or det <= 1e-3 c0 c2) or when the ellipse grown to q (1.001) + 1e-3 reaches the tile's
-    pixel-centre rectangle widened by one pixel in x."""
+    over every column or, equirectangular, rx + T > W / 2; or det <= 1e-3 c0 c2) or when the ellipse grown to
+    q (1.001) + 1e-3 reaches the tile's pixel-centre rectangle widened by one pixel in x."""
     TX = W // T
     tiles = np.arange(len(ranges), dtype=np.int64)
     t, _, s = tc._gather(np.asarray(ranges), lst, tiles)
     px, rx = np.asarray(sp["px"], np.float64), np.asarray(sp["rx"], np.int64)
     ix = np.floor(px).astype(np.int64)
     x0, x1 = np.floor_divide(ix - rx, T), np.floor_divide(ix + rx, T)
+    wide = x1 - x0 + 1 >= TX
     if camera is not None:
         x0, x1 = np.maximum(x0, 0), np.minimum(x1, TX - 1)
+        wide = x1 - x0 + 1 >= TX
+    else:
+        wide |= 2 * (rx + T) > W
     c0, c1, c2 = (np.asarray(sp[k], np.float64) for k in ("c0", "c1", "c2"))
-    whole = (x1 - x0 + 1 >= TX) | ~((c0 > 0) & (c2 > 0)) | (c0 * c2 - c1 * c1 <= 1e-3 * c0 * c2)
+    whole = wide | ~((c0 > 0) & (c2 > 0)) | (c0 * c2 - c1 * c1 <= 1e-3 * c0 * c2)
     q = oracle.splat_q(sp)
     keep = whole[s] | (tc.pair_reach(sp, s, t, W, H, T, 1.0, camera) <= q[s] * 1.001 + 1e-3)
     counts = np.bincount(t[keep], minlength=len(ranges))
@@ -218,3 +222,23 @@ def test_seam_copy_counts_for_the_equirectangular_camera_only(oracle_lib):
     assert not _lists(ranges_p, lst_p)[3 * TX + TX - 1]
     gr, gl = _fp64_culled(sp, 1, W, H, T, ranges_p, lst_p, camera=cam)
     tc.check_tile_lists(sp, 1, W, H, T, gr, gl, ranges_p, lst_p, camera=cam)
+
+
+def test_minimal_image_across_the_seam(oracle_lib):
+    """A splat of the egocentric workload (2048 x 1024, 16 px tiles) whose box, 1006 px either side of x = 1702.9,
+    nearly wraps: in tile row 3 its sheared ellipse reaches x = 2744, the far copy of tile column 43, but the blend
+    evaluates column 43's pixels at their minimal image dx = +999 .. +1014, out of reach, so leaving tile 43 out is
+    valid; column 41 (pixels 656 .. 671, minimal image dx = -1017 .. -1002) is reached and may not be left out."""
+    W, H, T = 2048, 1024, 16
+    TX = W // T
+    sp = _single(1702.8888, 20.02848, 2.3068576e-05, -3.3590427e-04, 0.0079759015, 10.253982, 1006, 58)
+    ranges, lst = oracle.bin_sort(sp, 1, W, H, T)
+    assert _lists(ranges, lst)[3 * TX + 43] == [0] and _lists(ranges, lst)[3 * TX + 41] == [0]
+    reach = tc.pair_reach(sp, np.array([0, 0]), np.array([3 * TX + 43, 3 * TX + 41]), W, H, T, 0.0)
+    assert reach[0] > 4 * 10.253982 and reach[1] < 10.253982
+    lists = _lists(*_fp64_culled(sp, 1, W, H, T, ranges, lst))
+    assert lists[3 * TX + 43] == [] and lists[3 * TX + 41] == [0]
+    tc.check_tile_lists(sp, 1, W, H, T, *_as_ranges(lists), ranges, lst)
+    lists[3 * TX + 41] = []
+    with pytest.raises(AssertionError, match="rule 2"):
+        tc.check_tile_lists(sp, 1, W, H, T, *_as_ranges(lists), ranges, lst)

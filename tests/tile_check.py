@@ -5,21 +5,22 @@ instance per influence"; the box is that of the alpha >= 1/255 region). A pair m
 of the tile can receive alpha >= 1/255 from the Gaussian (Eq. 8): every pixel of the tile skips it, so no image
 changes. The CUDA binning leaves pairs out row by row, with a stated widening: the ellipse dp^T conic dp <= q
 (q = 2 ln(255 o), the alpha = 1/255 level) is grown to q (1.001) + 1e-3, and by one pixel on each side in x. Rows of
-a box that spans every tile column, and Gaussians whose conic is a needle (det <= 1e-3 c0 c2, where the row bounds
-lose precision), keep the whole row.
+a box that spans every tile column, of a box with rx + T > W / 2 (equirectangular: beyond that the box's column
+offsets can differ from the blend's minimal-image dx), and Gaussians whose conic is a needle (det <= 1e-3 c0 c2,
+where the row bounds lose precision), keep the whole row.
 
 A list is valid when, tile by tile:
   1. it is an order-preserving subsequence of the oracle's list: no pair from outside the instance box, and the
      (t_r, index) order kept;
   2. every pair it leaves out is out of reach by at least half the stated widening: over the tile's rectangle of
-     pixel centres widened by 1/2 px on each side in x, min dp^T conic dp > q (1 + 5e-4) + 5e-4, the least over the
-     Gaussian's copies across the longitude seam. In particular no pixel centre of the tile gets alpha >= 1/255
-     from it;
+     pixel centres widened by 1/2 px on each side in x, min dp^T conic dp > q (1 + 5e-4) + 5e-4, with dx the minimal
+     image across the longitude seam that the blend uses. In particular no pixel centre of the tile gets
+     alpha >= 1/255 from it;
   3. every pair it keeps comes within the stated widening, up to single-precision rounding: over the rectangle
      widened by 3/2 px in x, min dp^T conic dp <= q (1.002) + 2e-3;
-  4. a Gaussian whose box spans every tile column, or whose conic is a needle, leaves out no pair, and 3 does not
-     apply to it. Within 0.1 % of the needle threshold either decision is accepted (the implementation takes it in
-     single precision).
+  4. a Gaussian whose box spans every tile column, or (equirectangular) whose box half-width rx + T exceeds W / 2,
+     or whose conic is a needle, leaves out no pair, and 3 does not apply to it. Within 0.1 % of the needle
+     threshold either decision is accepted (the implementation takes it in single precision).
 """
 from __future__ import annotations
 
@@ -58,9 +59,9 @@ def _gather(ranges, lst, tiles):
 
 
 def splat_classes(sp, W, T, camera=None):
-    """Per splat: (whole_rows, culls) booleans. whole_rows: the box spans every tile column or the conic is a needle
-    (with a 0.1 % band that is neither); culls: the rows may be culled (clearly not a needle, box narrower than the
-    image)."""
+    """Per splat: (whole_rows, culls) booleans. whole_rows: the box spans every tile column, or (equirectangular)
+    rx + T > W / 2, or the conic is a needle (with a 0.1 % band that is neither); culls: the rows may be culled
+    (clearly not a needle, box narrower than that)."""
     TX = W // T
     px = np.asarray(sp["px"], np.float64)
     rx = np.asarray(sp["rx"], np.int64)
@@ -68,7 +69,9 @@ def splat_classes(sp, W, T, camera=None):
     x0, x1 = np.floor_divide(ix - rx, T), np.floor_divide(ix + rx, T)
     if camera is not None:
         x0, x1 = np.maximum(x0, 0), np.minimum(x1, TX - 1)
-    wide = x1 - x0 + 1 >= TX
+        wide = x1 - x0 + 1 >= TX
+    else:
+        wide = (x1 - x0 + 1 >= TX) | (2 * (rx + T) > W)
     c0, c1, c2 = (np.asarray(sp[k], np.float64) for k in ("c0", "c1", "c2"))
     det = c0 * c2 - c1 * c1
     pos = (c0 > 0) & (c2 > 0)
@@ -79,9 +82,8 @@ def splat_classes(sp, W, T, camera=None):
 
 def pair_reach(sp, splat, tile, W, H, T, dx_widen, camera=None):
     """min dp^T conic dp over the pixel-centre rectangle of each (splat, tile) pair, widened by dx_widen px on each
-    side in x. Equirectangular: also over the Gaussian's copies at -W and +W for splats within 2 rx + 2 tiles of the
-    seam; farther copies are out of reach, because the alpha >= 1/255 ellipse reaches at most sqrt(q / 9) <= 1.11
-    times the 3-sigma radius from the centre (q <= 2 ln 255), and the box holds that radius or the ellipse."""
+    side in x. Equirectangular: each x offset u = x - p_x is taken as the minimal image the blend uses (u in
+    (-W/2, W/2], dx = -u in [-W/2, W/2)); a rectangle that straddles u = W/2 is split there into its two images."""
     TX, TY = W // T, H // T
     tt = tile % (TX * TY)
     ty, tx = tt // TX, tt % TX
@@ -92,12 +94,15 @@ def pair_reach(sp, splat, tile, W, H, T, dx_widen, camera=None):
     xb = tx * T + T - 0.5 + dx_widen - px
     ya = ty * T + 0.5 - py
     yb = ty * T + T - 0.5 - py
-    m = min_form_on_rect(c0, c1, c2, xa, xb, ya, yb)
-    if camera is None:
-        rx = np.asarray(sp["rx"], np.float64)[splat]
-        k = np.nonzero((px - 2 * rx - 2 * T - 8 < 0) | (px + 2 * rx + 2 * T + 8 >= W))[0]
-        for s in (-float(W), float(W)):
-            m[k] = np.minimum(m[k], min_form_on_rect(c0[k], c1[k], c2[k], xa[k] + s, xb[k] + s, ya[k], yb[k]))
+    if camera is not None:
+        return min_form_on_rect(c0, c1, c2, xa, xb, ya, yb)
+    half = 0.5 * W
+    ka = np.ceil((xa - half) / W)  # xa - ka W lies in (-W/2, W/2]
+    kb = np.ceil((xb - half) / W)
+    m = min_form_on_rect(c0, c1, c2, xa - ka * W, np.where(ka == kb, xb - ka * W, half), ya, yb)
+    k = np.nonzero(kb > ka)[0]
+    if len(k):
+        m[k] = np.minimum(m[k], min_form_on_rect(c0[k], c1[k], c2[k], -half, xb[k] - kb[k] * W, ya[k], yb[k]))
     return m
 
 
