@@ -49,15 +49,18 @@ typedef struct {
     int32_t sh_degree; /* 0..3; the SH array holds K = (sh_degree + 1)^2 coefficients per colour channel */
     float near_r;      /* a Gaussian is culled when its camera distance t_r <= near_r */
     float bg[3];       /* background colour added with the final transmittance */
-    int32_t pixels_per_thread; /* blend schedule: pixels of one image column each blend thread owns (2, 4 or 8;
-                                * 4 and 8 need tile >= 16); 0 lets the library choose. Results do not depend on
-                                * it beyond the order of floating-point additions in the gradients. */
+    int32_t pixels_per_thread; /* schedule of the forward blend (omnigs_render_fwd): pixels of one image column each
+                                * thread owns (2, 4 or 8; 4 and 8 need tile >= 16); 0 lets the library choose (4, or
+                                * 2 on 8-pixel tiles). Results do not depend on it. */
     int32_t camera;            /* OMNIGS_CAMERA_EQUIRECT (0): Eqs. 3-5, the paper's camera. OMNIGS_CAMERA_PINHOLE (1):
                                 * Eq. 2, the perspective model of 3DGS: p = (fx tx / tz + cx, fy ty / tz + cy);
                                 * Gaussians are ordered by t_z and culled when t_z <= near_r or |p| >= 2^23; J holds
                                 * t_x / t_z and t_y / t_z within 1.3 half-fields of view (W / (2 fx), H / (2 fy));
                                 * tile columns are clipped like rows and dx is not wrapped. */
     float fx, fy, cx, cy;      /* pinhole intrinsics in pixels (fx, fy > 0); ignored for the equirectangular camera */
+    int32_t adjoint_pixels_per_thread; /* schedule of the blend adjoint (omnigs_render_bwd), as pixels_per_thread;
+                                        * 0 lets the library choose (8, or 2 on 8-pixel tiles). Gradients depend on
+                                        * it only through the order of floating-point additions. */
 } omnigs_config;
 
 #define OMNIGS_CAMERA_EQUIRECT 0

@@ -522,8 +522,9 @@ static double rel_gap(double x, double thr) { return fabs(x - thr) / fabs(thr); 
 /* Blend one pixel; returns the number of contributors written to `out` (which must hold the tile list length).
  * near: bit 0 = a forward decision (alpha vs 1/255, T' vs 1e-4, exponent sign) lies within eps of its threshold,
  * bit 1 = alpha lies within eps of the 0.99 clamp. For alpha and T' the distance allowed also includes the rounding
- * a single-precision evaluation of the exponent -q0 - q1 - q2 can make when its terms cancel: 8 roundoffs of
- * mag = |q0| + |q1| + |q2| (as a relative error of alpha = o e^power; times alpha / (1 - alpha) for T'). */
+ * a single-precision evaluation of the exponent -q0 - q1 - q2 can make when its terms cancel: its three terms each
+ * carry about three roundings, and the base-2 exponential one more relative error, so 4 roundoffs of
+ * mag = |q0| + |q1| + |q2| bound it (as a relative error of alpha = o e^power; times alpha / (1 - alpha) for T'). */
 static int64_t blend_pixel(int W, double xs, double ys, const double *splat, const int64_t *list, int64_t lo,
                            int64_t hi, double eps, orc_contrib *out, double *T_final, int64_t *n_contrib,
                            int *near, double *rgb_acc)
@@ -546,7 +547,7 @@ static int64_t blend_pixel(int W, double xs, double ys, const double *splat, con
         if (power > 0.0) continue;
         double G = exp(power);
         double raw = sp[5] * G;
-        double cond = 8.0 * ORC_F32_ROUNDOFF * mag;
+        double cond = 4.0 * ORC_F32_ROUNDOFF * (mag + 1.0);
         if (rel_gap(raw, ORC_ALPHA_MIN) < eps + cond) *near |= 1;
         if (rel_gap(raw, ORC_ALPHA_MAX) < eps + cond) *near |= 2;
         int clamped = raw > ORC_ALPHA_MAX;

@@ -26,7 +26,8 @@ class omnigs_config(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("num_views", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_r", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("camera", ctypes.c_int32),
-                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("adjoint_pixels_per_thread", ctypes.c_int32)]
 
 CAMERA_EQUIRECT, CAMERA_PINHOLE = 0, 1
 
@@ -134,11 +135,14 @@ def _stream(stream):
 
 
 def make_config(width: int, height: int, tile: int = 16, num_views: int = 1, sh_degree: int = 3,
-                near_r: float = 0.2, bg=(0.0, 0.0, 0.0), pixels_per_thread: int = 0, pinhole=None) -> omnigs_config:
-    """pinhole: None for the equirectangular camera, else (fx, fy, cx, cy) in pixels (Eq. 2)."""
+                near_r: float = 0.2, bg=(0.0, 0.0, 0.0), pixels_per_thread: int = 0, pinhole=None,
+                adjoint_pixels_per_thread: int = 0) -> omnigs_config:
+    """pinhole: None for the equirectangular camera, else (fx, fy, cx, cy) in pixels (Eq. 2). pixels_per_thread and
+    adjoint_pixels_per_thread: schedules of the forward blend and of its adjoint (0: the library's choice)."""
     c = omnigs_config()
     c.width, c.height, c.tile, c.num_views, c.sh_degree, c.near_r = width, height, tile, num_views, sh_degree, near_r
     c.pixels_per_thread = pixels_per_thread
+    c.adjoint_pixels_per_thread = adjoint_pixels_per_thread
     if pinhole is not None:
         c.camera = CAMERA_PINHOLE
         c.fx, c.fy, c.cx, c.cy = (float(x) for x in pinhole)

@@ -102,9 +102,10 @@ bool valid_cfg(const omnigs_config* c) {
     if (!std::isfinite(c->near_r) || c->near_r < 0.f) return false;
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(c->bg[i])) return false;
-    const int ppt = c->pixels_per_thread;
-    if (ppt != 0 && ppt != 2 && ppt != 4 && ppt != 8) return false;
-    if (ppt > 2 && c->tile == 8) return false;
+    for (const int ppt : {c->pixels_per_thread, c->adjoint_pixels_per_thread}) {
+        if (ppt != 0 && ppt != 2 && ppt != 4 && ppt != 8) return false;
+        if (ppt > 2 && c->tile == 8) return false;
+    }
     if (c->camera != OMNIGS_CAMERA_EQUIRECT && c->camera != OMNIGS_CAMERA_PINHOLE) return false;
     if (c->camera == OMNIGS_CAMERA_PINHOLE &&
         !(std::isfinite(c->fx) && std::isfinite(c->fy) && c->fx > 0.f && c->fy > 0.f && std::isfinite(c->cx) &&

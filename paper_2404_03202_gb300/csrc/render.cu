@@ -14,9 +14,9 @@
 // list once every pixel has stopped (__syncthreads_count).
 //
 // The adjoint walks the same list back to front from each pixel's last contributor, recovers T by division by
-// (1 - alpha) and accumulates 9 sums per entry over the thread's pixels: dL/do, dL/d(r, g, b) and the exponent
-// moments sum gp, sum gp dy, sum gp dy^2 (gp = dL/d exponent; the pixels share dx, so the moments in dx follow per
-// thread). The warp then reduces them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth:
+// (1 - alpha), keeps per pixel one scalar for everything behind the current entry (the upstream gradient dotted with
+// the colour behind it), and accumulates per entry over the thread's pixels dL/do, dL/d(r, g, b) and the exponent
+// moments (the pixels share dx, so the moments in dx follow per thread). The warp then reduces them (a transposed reduce-scatter of 8 fields plus a butterfly for the ninth:
 // 14 shuffles, after which 9 lanes hold one field's total each and write it with one shared-memory atomic), the CTA
 // sums warps in shared memory, the conic turns the moments into dL/d(px, py, c0, c1, c2) once per entry, and the
 // CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
@@ -255,8 +255,71 @@ __device__ __forceinline__ float warp_sum_fields(float (&v)[kGradFields], unsign
     return t;
 }
 
+// The adjoint's entries, staged for packed pixel pairs: every pair operand sits duplicated in both halves of a
+// 16-byte word, so one shared-memory load gives two pairs.
+struct BwdStaged {
+    float4 x;   // px, seam shift, c0', c1'   (the thread's dx and the exponent's dx terms)
+    float4 p0;  // py, py, c2', c2'
+    float4 p1;  // -m, -m, -o, -o            (pass interval centre, opacity)
+    float4 p2;  // r, r, g, g
+    float4 p3;  // b, b, h, h                (h: pass interval half-width)
+    float4 d;   // raw conic c0, c1, c2, opacity (for the flush)
+};
+
+// One entry against the thread's pixel pairs, back to front: per pixel, if the entry passes (thr <= e <= 0, and the
+// pixel's last contributor is behind it) recover T in front of it, form dL/dalpha, move the entry into the colour
+// behind, and add its terms to the thread's sums. A pixel of a pair that skips the entry gets G = 0 (alpha = 0
+// leaves T and NS as they are and adds nothing). kClampable: the entry's opacity reaches the 0.99 clamp (o >= 0.99),
+// where alpha = 0.99 passes no gradient to o or the exponent; below that o G < 0.99 always. Returns whether any
+// pixel of the thread took the entry.
+template <int NP, bool kClampable>
+__device__ __forceinline__ bool bwd_entry_pairs(uint32_t pos, const uint32_t (&last)[2 * NP], float2 (&T)[NP],
+                                                float2 (&NS)[NP], const float2 (&g0)[NP], const float2 (&g1)[NP],
+                                                const float2 (&g2)[NP], const float2 (&NYS)[NP], float2 E0,
+                                                float2 E1, const float4 P0, const float4 P1, const float4 P2,
+                                                const float4 P3, float2& su, float2& suy, float2& suyy,
+                                                float2& nc0, float2& nc1, float2& nc2) {
+    const float2 kOne2 = make_float2(1.f, 1.f);
+    const float h = P3.z;
+    bool contrib = false;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const float2 dy = __fadd2_rn(lo2(P0), NYS[q]);
+        const float2 e = __ffma2_rn(dy, __ffma2_rn(hi2(P0), dy, E1), E0);
+        const float2 em = __fadd2_rn(e, lo2(P1));
+        const bool p0 = pos < last[2 * q] && fabsf(em.x) <= h;
+        const bool p1 = pos < last[2 * q + 1] && fabsf(em.y) <= h;
+        if (!(p0 || p1)) continue;
+        contrib = true;
+        const float2 G = make_float2(p0 ? fast_ex2(e.x) : 0.f, p1 ? fast_ex2(e.y) : 0.f);
+        const float2 nraw = __fmul2_rn(hi2(P1), G);  // -(o G)
+        const float2 nalpha = kClampable ? make_float2(fmaxf(-kAlphaMax, nraw.x), fmaxf(-kAlphaMax, nraw.y)) : nraw;
+        const float2 omr = __fadd2_rn(kOne2, nalpha);  // 1 - alpha
+        const float2 r = make_float2(__fdividef(1.f, omr.x), __fdividef(1.f, omr.y));
+        T[q] = __fmul2_rn(T[q], r);  // transmittance in front of this entry
+        // dL/dalpha = T (g . c) - (g . colour behind) / (1 - alpha); then this entry joins the colour behind
+        const float2 gc = __ffma2_rn(g0[q], lo2(P2), __ffma2_rn(g1[q], hi2(P2), __fmul2_rn(g2[q], lo2(P3))));
+        const float2 nw = __fmul2_rn(nalpha, T[q]);  // -(alpha T)
+        const float2 dalpha = __ffma2_rn(NS[q], r, __fmul2_rn(T[q], gc));
+        NS[q] = __ffma2_rn(nw, gc, NS[q]);
+        nc0 = __ffma2_rn(nw, g0[q], nc0);
+        nc1 = __ffma2_rn(nw, g1[q], nc1);
+        nc2 = __ffma2_rn(nw, g2[q], nc2);
+        const float2 Gu = kClampable ? make_float2(nraw.x > -kAlphaMax ? G.x : 0.f, nraw.y > -kAlphaMax ? G.y : 0.f)
+                                     : G;
+        const float2 u = __fmul2_rn(dalpha, Gu);
+        const float2 udy = __fmul2_rn(u, dy);
+        su = __fadd2_rn(su, u);
+        suy = __fadd2_rn(suy, udy);
+        suyy = __ffma2_rn(udy, dy, suyy);
+    }
+    return contrib;
+}
+
+// Register budget per schedule (measured on the 8-view egocentric frame): at 8 pixels a thread 96 registers (21 warps
+// per SM) beat both the unconstrained 123 and tighter budgets that spill.
 template <int TS, int PPT>
-__global__ void __launch_bounds__(TS * TS / PPT)
+__global__ void __launch_bounds__(TS * TS / PPT) __maxnreg__(PPT == 8 ? 96 : (PPT == 4 ? 80 : 64))
 render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0,
                   float bg1,
                   float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
@@ -265,11 +328,8 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                   const float* __restrict__ dL_drgb, float4* __restrict__ grads) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* s_a = reinterpret_cast<float4*>(smem_raw);
-    float4* s_b = s_a + NT;
-    float4* s_c = s_b + NT;
-    float4* s_d = s_c + NT;                                // raw conic c0, c1, c2
-    unsigned* s_vg = reinterpret_cast<unsigned*>(s_d + NT);
+    BwdStaged* s_e = reinterpret_cast<BwdStaged*>(smem_raw);
+    unsigned* s_vg = reinterpret_cast<unsigned*>(s_e + NT);
     float* s_acc = reinterpret_cast<float*>(s_vg + NT);  // [NT][kGradFields]
     __shared__ unsigned s_max;
 
@@ -284,38 +344,61 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     const uint32_t* vorder = order + (size_t)v * n;
     const size_t HW = (size_t)H * W;
 
+    // Pixel pairs (2q, 2q + 1) of the thread are updated together with packed FP32 (f32x2) operations. Per pixel:
+    // T, the transmittance in front of the current entry; NS, minus the upstream gradient dotted with the colour
+    // behind it (the later contributors' c alpha T plus T_final bg); g, the upstream gradient.
+    constexpr int NP = PPT / 2;
+    static_assert(PPT % 2 == 0, "pixels are updated in pairs");
     uint32_t last[PPT];
-    float T[PPT], g0[PPT], g1[PPT], g2[PPT], B0[PPT], B1[PPT], B2[PPT];
+    float2 T[NP], NS[NP], g0[NP], g1[NP], g2[NP], NYS[NP];  // NYS: minus the pixel centres' y
     uint32_t mylast = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
-        last[k] = min(ncontrib[(size_t)v * HW + pix], len);
-        T[k] = out_T[(size_t)v * HW + pix];
-        g0[k] = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
-        g1[k] = dL_drgb[(3 * (size_t)v + 1) * HW + pix];
-        g2[k] = dL_drgb[(3 * (size_t)v + 2) * HW + pix];
-        B0[k] = bg0; B1[k] = bg1; B2[k] = bg2;  // colour behind the current entry, per unit of its transmittance
-        mylast = max(mylast, last[k]);
+    for (int q = 0; q < NP; ++q) {
+        float t2[2], a0[2], a1[2], a2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * q + h;
+            const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
+            last[k] = min(ncontrib[(size_t)v * HW + pix], len);
+            t2[h] = out_T[(size_t)v * HW + pix];
+            a0[h] = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
+            a1[h] = dL_drgb[(3 * (size_t)v + 1) * HW + pix];
+            a2[h] = dL_drgb[(3 * (size_t)v + 2) * HW + pix];
+            mylast = max(mylast, last[k]);
+        }
+        T[q] = make_float2(t2[0], t2[1]);
+        g0[q] = make_float2(a0[0], a0[1]);
+        g1[q] = make_float2(a1[0], a1[1]);
+        g2[q] = make_float2(a2[0], a2[1]);
+        NS[q] = make_float2(-t2[0] * fmaf(a0[0], bg0, fmaf(a1[0], bg1, a2[0] * bg2)),
+                            -t2[1] * fmaf(a0[1], bg0, fmaf(a1[1], bg1, a2[1] * bg2)));
+        NYS[q] = make_float2(-(pm.y0 + 2 * q + 0.5f), -(pm.y0 + 2 * q + 1.5f));
     }
 
-    if (threadIdx.x == 0) s_max = 0;
+    // A CTA of one warp (PPT 8 on 16 x 16 tiles) needs no CTA barrier and no shared-memory atomics.
+    constexpr bool kOneWarp = NT == 32;
     for (int i = threadIdx.x; i < NT * kGradFields; i += NT) s_acc[i] = 0.f;
-    __syncthreads();
-    atomicMax(&s_max, mylast);
-    __syncthreads();
-    const uint32_t maxlast = s_max;
+    uint32_t maxlast;
+    if constexpr (kOneWarp) {
+        maxlast = __reduce_max_sync(0xffffffffu, mylast);
+        __syncwarp();
+    } else {
+        if (threadIdx.x == 0) s_max = 0;
+        __syncthreads();
+        atomicMax(&s_max, mylast);
+        __syncthreads();
+        maxlast = s_max;
+    }
     const unsigned lane = threadIdx.x & 31;
-    // Per-thread sums over the thread's pixels for the current entry. With gp = dL/d(exponent) per pixel, the
-    // exponent's derivatives give dL/dc0 = -1/2 sum gp dx^2, dL/dc1 = -sum gp dx dy, dL/dc2 = -1/2 sum gp dy^2,
-    // dL/dpx = -(c0 sum gp dx + c1 sum gp dy), dL/dpy = -(c1 sum gp dx + c2 sum gp dy). A thread's pixels share dx,
-    // so only sum gp, sum gp dy and sum gp dy^2 are accumulated per pixel; the warp reduces the moments
-    // (sum gp dx, sum gp dx^2, sum gp dy, sum gp dx dy, sum gp dy^2, then dL/do and dL/dc) and the conic is applied
-    // once per entry when the CTA's sums are flushed.
+    // Per-thread sums over the thread's pixels for the current entry. With gp = dL/d(exponent) = dL/dalpha o G per
+    // pixel, the exponent's derivatives give dL/dc0 = -1/2 sum gp dx^2, dL/dc1 = -sum gp dx dy, dL/dc2 =
+    // -1/2 sum gp dy^2, dL/dpx = -(c0 sum gp dx + c1 sum gp dy), dL/dpy = -(c1 sum gp dx + c2 sum gp dy). A thread's
+    // pixels share dx, and o is the entry's, so per pixel only u = dL/dalpha G (whose sum is dL/do), u dy and u dy^2
+    // are accumulated, with minus the colour weights alpha T g; the warp reduces the moments (sum gp dx,
+    // sum gp dx^2, sum gp dy, sum gp dx dy, sum gp dy^2, then dL/do and dL/dc) and the conic is applied once per
+    // entry when the CTA's sums are flushed.
+    float2 su = make_float2(0.f, 0.f), suy = su, suyy = su, nc0 = su, nc1 = su, nc2 = su;
     float gv[kGradFields];
-    float sg = 0.f, sgy = 0.f, sgyy = 0.f;
-#pragma unroll
-    for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
 
     for (int64_t bend = (int64_t)maxlast; bend > 0; bend -= NT) {
         const int64_t bbeg = bend - NT > 0 ? bend - NT : 0;
@@ -323,67 +406,58 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         if ((int)threadIdx.x < nb) {
             const unsigned vg = entry_splat(keys, vorder, (uint32_t)(start + bbeg + threadIdx.x), rank_mask);
             const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
-            s_a[threadIdx.x] = st.a;
-            s_b[threadIdx.x] = st.b;
-            s_c[threadIdx.x] = st.c;
-            s_d[threadIdx.x] = st.d;
+            BwdStaged b;
+            b.x = make_float4(st.a.x, st.b.w, st.a.z, st.a.w);
+            b.p0 = make_float4(st.a.y, st.a.y, st.b.x, st.b.x);
+            b.p1 = make_float4(-st.b.y, -st.b.y, -st.c.x, -st.c.x);
+            b.p2 = make_float4(st.c.y, st.c.y, st.c.z, st.c.z);
+            b.p3 = make_float4(st.c.w, st.c.w, st.b.z, st.b.z);
+            b.d = make_float4(st.d.x, st.d.y, st.d.z, st.c.x);
+            s_e[threadIdx.x] = b;
             s_vg[threadIdx.x] = vg;
         }
-        __syncthreads();
+        if constexpr (kOneWarp) __syncwarp(); else __syncthreads();
         for (int j = nb - 1; j >= 0; --j) {
             const uint32_t pos = (uint32_t)(bbeg + j);  // position in the tile list
             if (__all_sync(0xffffffffu, pos >= mylast)) continue;
-            const float4 A = s_a[j];
-            const float4 Bv = s_b[j];
-            const float dx = entry_dx(A.x, Bv.w, xs, halfW, fW);
-            const float e0 = A.z * dx * dx, e1 = A.w * dx;
-            bool contrib = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dy = A.y - (pm.y0 + k + 0.5f);
-                const float e = fmaf(dy, fmaf(Bv.x, dy, e1), e0);
-                if (pos >= last[k] || !(fabsf(e - Bv.y) <= Bv.z)) continue;
-                const float4 Cc = s_c[j];
-                const float G = fast_ex2(e);
-                const float raw = Cc.x * G;
-                const float alpha = fminf(kAlphaMax, raw);
-                contrib = true;
-                T[k] = __fdividef(T[k], 1.f - alpha);  // transmittance in front of this entry
-                // colour minus the colour behind, per unit of transmittance; the latter then moves to this entry
-                const float d0 = Cc.y - B0[k], d1 = Cc.z - B1[k], d2 = Cc.w - B2[k];
-                const float dalpha = T[k] * fmaf(g0[k], d0, fmaf(g1[k], d1, g2[k] * d2));
-                const float w = alpha * T[k];
-                gv[6] = fmaf(w, g0[k], gv[6]);
-                gv[7] = fmaf(w, g1[k], gv[7]);
-                gv[8] = fmaf(w, g2[k], gv[8]);
-                B0[k] = fmaf(alpha, d0, B0[k]);
-                B1[k] = fmaf(alpha, d1, B1[k]);
-                B2[k] = fmaf(alpha, d2, B2[k]);
-                if (raw < kAlphaMax) {
-                    gv[5] = fmaf(dalpha, G, gv[5]);
-                    const float gp = dalpha * raw;  // dL/d(exponent in natural units)
-                    const float gdy = gp * dy;
-                    sg += gp;
-                    sgy += gdy;
-                    sgyy = fmaf(gdy, dy, sgyy);
-                }
-            }
+            const float4 X = s_e[j].x;
+            const float4 P0 = s_e[j].p0;
+            const float4 P1 = s_e[j].p1;
+            const float4 P2 = s_e[j].p2;
+            const float4 P3 = s_e[j].p3;
+            const float dx = entry_dx(X.x, X.y, xs, halfW, fW);
+            const float e0 = X.z * dx * dx, e1 = X.w * dx;
+            const float2 E0 = make_float2(e0, e0), E1 = make_float2(e1, e1);
+            const bool contrib =
+                P1.w <= -kAlphaMax
+                    ? bwd_entry_pairs<NP, true>(pos, last, T, NS, g0, g1, g2, NYS, E0, E1, P0, P1, P2, P3, su, suy, suyy,
+                                                nc0, nc1, nc2)
+                    : bwd_entry_pairs<NP, false>(pos, last, T, NS, g0, g1, g2, NYS, E0, E1, P0, P1, P2, P3, su, suy,
+                                                 suyy, nc0, nc1, nc2);
             if (__any_sync(0xffffffffu, contrib)) {
-                gv[0] = dx * sg;        // sum gp dx
-                gv[1] = dx * gv[0];     // sum gp dx^2
-                gv[2] = sgy;            // sum gp dy
-                gv[3] = dx * sgy;       // sum gp dx dy
-                gv[4] = sgyy;           // sum gp dy^2
+                const float o = -P1.w;
+                const float s5 = su.x + su.y;
+                gv[5] = s5;                               // dL/do
+                gv[0] = dx * (o * s5);                    // sum gp dx
+                gv[1] = dx * gv[0];                       // sum gp dx^2
+                gv[2] = o * (suy.x + suy.y);              // sum gp dy
+                gv[3] = dx * gv[2];                       // sum gp dx dy
+                gv[4] = o * (suyy.x + suyy.y);            // sum gp dy^2
+                gv[6] = -(nc0.x + nc0.y);                 // dL/dc
+                gv[7] = -(nc1.x + nc1.y);
+                gv[8] = -(nc2.x + nc2.y);
                 float tot8;
                 const float tot = warp_sum_fields(gv, lane, tot8);
                 const bool quad = (lane & 3u) == 0;
-                if (quad || lane == 1u) atomicAdd(&s_acc[j * kGradFields + (quad ? (lane >> 2) : 8u)], quad ? tot : tot8);
-#pragma unroll
-                for (int q = 0; q < kGradFields; ++q) gv[q] = 0.f;
-                sg = sgy = sgyy = 0.f;
+                if (quad || lane == 1u) {
+                    float* dst = &s_acc[j * kGradFields + (quad ? (lane >> 2) : 8u)];
+                    if constexpr (kOneWarp) *dst = quad ? tot : tot8;
+                    else atomicAdd(dst, quad ? tot : tot8);
+                }
+                su = suy = suyy = nc0 = nc1 = nc2 = make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
+        if constexpr (kOneWarp) __syncwarp(); else __syncthreads();
         if ((int)threadIdx.x < nb) {
             float* acc = s_acc + threadIdx.x * kGradFields;
             bool any = false;
@@ -391,7 +465,7 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
             for (int f = 0; f < kGradFields; ++f) any |= (acc[f] != 0.f);
             if (any) {
                 // the CTA's moments -> dL/d(px, py, c0, c1, c2)
-                const float4 D = s_d[threadIdx.x];
+                const float4 D = s_e[threadIdx.x].d;
                 const float gpx = -fmaf(D.x, acc[0], D.y * acc[2]);
                 const float gpy = -fmaf(D.y, acc[0], D.z * acc[2]);
                 float4* gdst = grads + 3 * (size_t)s_vg[threadIdx.x];
@@ -402,12 +476,12 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
 #pragma unroll
             for (int f = 0; f < kGradFields; ++f) acc[f] = 0.f;
         }
-        __syncthreads();
+        if constexpr (kOneWarp) __syncwarp(); else __syncthreads();
     }
 }
 
 size_t bwd_smem(int nt) {
-    return (size_t)nt * (4 * sizeof(float4) + sizeof(unsigned) + kGradFields * sizeof(float));
+    return (size_t)nt * (sizeof(BwdStaged) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
 // Half the image width for the minimal-image dx across the longitude seam; +inf turns the wrap off (pinhole camera).
@@ -419,6 +493,15 @@ float seam_half_width(const omnigs_config& cfg) {
 int blend_ppt(const omnigs_config& cfg) {
     if (cfg.pixels_per_thread) return cfg.pixels_per_thread;
     return cfg.tile == 8 ? 2 : 4;
+}
+
+// Pixels per adjoint thread: the configured schedule, else 2 for 8x8 tiles and 8 for larger ones. Measured on the
+// egocentric (8 views), training (1 view) and roaming (4096 x 2048) frames at 16 and 32 px tiles, 8 pixels a thread
+// was the fastest adjoint everywhere (it shares the per-entry warp reduction among twice the pixels of 4), while
+// the forward, with no reduction, was fastest at 4.
+int adjoint_ppt(const omnigs_config& cfg) {
+    if (cfg.adjoint_pixels_per_thread) return cfg.adjoint_pixels_per_thread;
+    return cfg.tile == 8 ? 2 : 8;
 }
 
 template <int TS, int PPT>
@@ -536,7 +619,7 @@ cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_
                               omnigs_splat_grad* grads, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(grads, 0, sizeof(omnigs_splat_grad) * (size_t)n * cfg.num_views, stream);
     if (e != cudaSuccess) return e;
-    const int ppt = blend_ppt(cfg);
+    const int ppt = adjoint_ppt(cfg);
     switch (cfg.tile) {
         case 8: return render_bwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_T, nc, dL_drgb, grads, stream);
         case 32:

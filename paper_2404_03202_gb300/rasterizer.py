@@ -26,12 +26,13 @@ class Settings:
     sh_degree: int = 3
     near_r: float = 0.2
     bg: tuple = (0.0, 0.0, 0.0)
-    pixels_per_thread: int = 0  # blend schedule (2, 4 or 8); 0 = the library's choice
+    pixels_per_thread: int = 0  # forward blend schedule (2, 4 or 8); 0 = the library's choice
     pinhole: tuple | None = None  # (fx, fy, cx, cy) for the pinhole camera of Eq. 2; None = equirectangular
+    adjoint_pixels_per_thread: int = 0  # schedule of the blend adjoint (2, 4 or 8); 0 = the library's choice
 
     def config(self):
         return C.make_config(self.width, self.height, self.tile, self.num_views, self.sh_degree, self.near_r, self.bg,
-                             self.pixels_per_thread, self.pinhole)
+                             self.pixels_per_thread, self.pinhole, self.adjoint_pixels_per_thread)
 
     @property
     def tiles(self) -> int:

@@ -51,27 +51,34 @@ def test_host_only_calls(lib):
 
 
 def test_config_layout_and_schedule_validation(lib):
-    """omnigs_config is 60 bytes (the header's field order); invalid blend schedules, cameras and image sizes beyond
-    65536 pixels (instance-box half-extents are 16-bit) are rejected on the host."""
+    """omnigs_config is 64 bytes (the header's field order); invalid blend and adjoint schedules, cameras and image
+    sizes beyond 65536 pixels (instance-box half-extents are 16-bit) are rejected on the host."""
     spec = importlib.util.spec_from_file_location("omnigs_cabi_layout", os.path.join(ROOT, "paper_2404_03202_gb300",
                                                                                       "_cabi.py"))
     text = open(spec.origin).read()
     fields = re.findall(r'\("(\w+)", ctypes\.c_(\w+)(?: \* 3)?\)', text.split("class omnigs_config")[1].split("class ")[0])
     assert [f for f, _ in fields] == ["width", "height", "tile", "num_views", "sh_degree", "near_r", "bg",
-                                      "pixels_per_thread", "camera", "fx", "fy", "cx", "cy"]
+                                      "pixels_per_thread", "camera", "fx", "fy", "cx", "cy",
+                                      "adjoint_pixels_per_thread"]
 
     class Cfg(ctypes.Structure):
         _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32),
                     ("num_views", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_r", ctypes.c_float),
                     ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("camera", ctypes.c_int32),
-                    ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+                    ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                    ("adjoint_pixels_per_thread", ctypes.c_int32)]
 
-    assert ctypes.sizeof(Cfg) == 60
+    assert ctypes.sizeof(Cfg) == 64
     lib.omnigs_workspace_size.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_int64]
     lib.omnigs_workspace_size.restype = ctypes.c_size_t
     for tile, ppt in [(8, 4), (8, 8), (16, 3), (16, 1), (32, 16)]:
         c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), ppt)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (tile, ppt)
+        c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0, 0, 0.0, 0.0, 0.0, 0.0, ppt)
+        assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, ("adjoint", tile, ppt)
+    for tile, ppt in [(8, 2), (16, 8), (32, 4)]:
+        c = Cfg(256, 128, tile, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0, 0, 0.0, 0.0, 0.0, 0.0, ppt)
+        assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) > 0, ("adjoint", tile, ppt)
     for w, h in [(65536 + 16, 128), (256, 65536 + 16), (250, 128)]:
         c = Cfg(w, h, 16, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (w, h)

@@ -28,7 +28,9 @@ from paper_2404_03202_gb300 import _cabi as C  # noqa: E402
 
 
 def _settings(W, H, tile=16, V=1, deg=3, bg=(0.0, 0.0, 0.0), ppt=0):
-    return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=deg, bg=bg, pixels_per_thread=ppt)
+    """ppt: the schedule of both the forward blend and its adjoint (0: the library's choices)."""
+    return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=deg, bg=bg, pixels_per_thread=ppt,
+                       adjoint_pixels_per_thread=ppt)
 
 
 def _run_splats(sp_packed, s: og.Settings, capacity=1 << 16):

@@ -28,6 +28,7 @@ CAM = oracle.pinhole(*INTR)
 
 def _settings(V=1, tile=16, bg=(0.0, 0.0, 0.0), ppt=0):
     return og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=3, bg=bg, pixels_per_thread=ppt,
+                       adjoint_pixels_per_thread=ppt,
                        pinhole=INTR)
 
 
@@ -98,7 +99,7 @@ def _fwd(sp, V, tile=16, bg=(0.0, 0.0, 0.0), ppt=0):
     return r, (rgb, T, last_contributor(ranges, lst, nc, V, W, H, tile), near), (ranges, lst, sp64)
 
 
-@pytest.mark.parametrize("ppt", [4, 2])
+@pytest.mark.parametrize("ppt", [4, 2, 8])
 def test_render_fwd_and_bwd_match_oracle(ppt):
     V = 2
     sp = _offscreen_splats(V, 2500, 11)
