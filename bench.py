@@ -340,29 +340,111 @@ class OraclePool:
         self.pool.join()
 
 
+def oracle_step(wl_name: str, rows=None, with_pbwd: bool = True) -> dict:
+    """One whole step of a single-view workload through the FP64 oracle, timed stage by stage: preprocess, bin +
+    sort, blend forward and adjoint (over the tile rows `rows`, default all), preprocess adjoint. Nothing is
+    sampled or scaled."""
+    import oracle
+    wl = WORKLOADS[wl_name]
+    W, H, T = wl["width"], wl["height"], wl["tile"]
+    scene = build_scene(wl)
+    vm = build_poses(wl, 0)
+    target = synth.random_image(wl["views"], W, H, 5)
+    t = {}
+    t0 = time.perf_counter()
+    rec = oracle.preprocess(scene, vm, W, H)
+    t["preprocess"] = time.perf_counter() - t0
+    sp = oracle.splats_from_records(rec)
+    t0 = time.perf_counter()
+    rg, lst = oracle.bin_sort(sp, wl["views"], W, H, T)
+    t["bin_sort"] = time.perf_counter() - t0
+    if rows is not None:
+        tx = W // T
+        keep = np.zeros(len(rg), bool)
+        for r in rows:
+            keep[r * tx:(r + 1) * tx] = True
+        rg = np.where(keep[:, None], rg, 0)
+    t0 = time.perf_counter()
+    rgb, _, _, _ = oracle.blend_fwd(sp, rg, lst, wl["views"], W, H, T)
+    d = rgb - target
+    g2 = oracle.blend_bwd(sp, rg, lst, np.sign(d) / d.size, wl["views"], W, H, T)
+    t["blend_fwd_bwd"] = time.perf_counter() - t0
+    if with_pbwd:
+        t0 = time.perf_counter()
+        oracle.preprocess_bwd(scene, vm, g2, W, H)
+        t["preprocess_bwd"] = time.perf_counter() - t0
+    return t
+
+
+def _oracle_full_job(job):
+    kind, wl_name, part, parts, budget = job
+    if kind == "single":
+        return oracle_step(wl_name)
+    if kind == "part":
+        wl = WORKLOADS[wl_name]
+        ty = wl["height"] // wl["tile"]
+        return oracle_step(wl_name, rows=[r for r in range(ty) if r % parts == part], with_pbwd=part == 0)
+    ms, _ = OracleSampler(WORKLOADS[wl_name], 0).sample(budget, np.random.default_rng(7))
+    return ms
+
+
+def oracle_small_configs(cores: int, budget_s: float = 12.0, names=("shell-small", "training")) -> dict:
+    """The FP64 oracle on whole steps of the single-view configurations (shell-small = config 1, training =
+    config 2): single-threaded, and on `cores` cores. On C cores each process runs preprocess and bin + sort, then
+    blends (forward and adjoint) every C-th tile row; the step takes the slowest process plus the preprocess adjoint
+    (timed once; its cost does not depend on the gradient's values). Also the step sampler's estimate for training
+    against its measured whole step: the measured bias of the extrapolated egocentric figure."""
+    import multiprocessing as mp
+    out = {}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for name in names:
+            single = pool.apply(_oracle_full_job, (("single", name, 0, 1, 0.0),))
+            parts = pool.map(_oracle_full_job, [("part", name, i, cores, 0.0) for i in range(cores)], chunksize=1)
+            crit = max(sum(v for k, v in p.items() if k != "preprocess_bwd") for p in parts)
+            pbwd = parts[0]["preprocess_bwd"]
+            out[name] = {"single_thread_ms": 1e3 * sum(single.values()),
+                         "single_thread_stages_ms": {k: 1e3 * v for k, v in single.items()},
+                         "all_cores_ms": 1e3 * (crit + pbwd), "cores": cores, "measured": "whole step, unsampled"}
+        if "training" in out:
+            est = pool.apply(_oracle_full_job, (("sample", "training", 0, 1, budget_s),))
+            out["training"]["sampler_estimate_ms"] = est
+            out["training"]["sampler_bias"] = est / out["training"]["single_thread_ms"] - 1.0
+    return out
+
+
 def run_reference(args, wl):
-    """FP64 CPU oracle on bounded samples of the workload (rank 0 only)."""
+    """FP64 CPU oracle on bounded samples of the workload (rank 0 only). Each timed step is one round: every core
+    runs one bounded sample of the step at the same time. `value` is the measured wall time of a round; the step
+    time the rounds extrapolate to is reported beside it (`extrapolated_ms_per_step`), so the line's time fits in
+    its own run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     pool = OraclePool(args.workload)
     budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    times, one_core, desc = [], [], ""
+    times, one_core, walls, desc = [], [], [], ""
     try:
         for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
             ms, ms1, desc = pool.round(budget)
+            wall = 1e3 * (time.perf_counter() - t0)
             if i >= args.warmup:
                 times.append(ms)
                 one_core.append(ms1)
+                walls.append(wall)
     finally:
         pool.close()
-    value = float(np.mean(times))
-    desc += f"; {pool.cores} cores in parallel (one spawned process each), step time = per-core time / cores"
+    value = float(np.mean(walls))
+    extrapolated = float(np.mean(times))
+    desc += (f"; {pool.cores} cores in parallel (one spawned process each); value = measured wall time of one such "
+             f"round, which covers {value / extrapolated:.2%} of a step; the step extrapolates to "
+             f"{extrapolated:.0f} ms (per-core time / cores)")
     out = {"metric": "fwd+bwd ms/iter", "value": value, "unit": "ms/iter", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "impl": "reference",
            "dtype": "f64", "data": "synthetic", "config": workload_config(wl, args),
+           "extrapolated_ms_per_step": extrapolated, "sample_fraction_of_step": value / extrapolated,
            "cpu_baseline": {"value": value, "unit": "ms/iter", "cores": pool.cores, "kind": "oracle", "sample": desc,
-                            "value_per_core": float(np.mean(one_core))},
+                            "extrapolated_ms_per_step": extrapolated, "value_per_core": float(np.mean(one_core))},
            "e2e": {"value": value, "unit": "ms/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "vs_baseline": None}
     print(json.dumps(out), flush=True)
@@ -373,23 +455,30 @@ SERVING_SCENES = [100_000, 300_000, 600_000, 1_000_000, 2_000_000, 3_000_000]
 SERVING_RES = [((1024, 512), 0.3), ((2048, 1024), 0.5), ((4096, 2048), 0.2)]
 
 
-def serving_requests(names, count, rate, seed, t0=0.0):
+def serving_requests(names, count, rate, seed, t0=0.0, keys=None):
     """Poisson arrivals at `rate` per second (all at t0 when rate is None); scene uniform, resolution 0.3/0.5/0.2,
-    pose uniform within 1 m of the room centre with random yaw."""
+    pose uniform within 1 m of the room centre with random yaw. keys: optional [((scene, (w, h)), p), ...] to draw
+    (scene, resolution) from instead (a trace skewed to a few keys)."""
     from paper_2404_03202_gb300.serving import Request
     rng = np.random.default_rng(seed)
     poses = synth.room_viewmats(count, seed)
     t = np.full(count, t0) if rate is None else t0 + np.cumsum(rng.exponential(1.0 / rate, count))
     out = []
     for i in range(count):
-        (w, h), _ = SERVING_RES[rng.choice(len(SERVING_RES), p=[p for _, p in SERVING_RES])]
-        out.append(Request(i, names[rng.integers(len(names))], poses[i], w, h, float(t[i])))
+        if keys is None:
+            (w, h), _ = SERVING_RES[rng.choice(len(SERVING_RES), p=[p for _, p in SERVING_RES])]
+            name = names[rng.integers(len(names))]
+        else:
+            (name, (w, h)), _ = keys[rng.choice(len(keys), p=[p for _, p in keys])]
+        out.append(Request(i, name, poses[i], w, h, float(t[i])))
     return out
 
 
 def serving_benchmark(dev, count: int = 96, lanes: int = 4, max_batch: int = 8) -> dict:
-    """Forward-only serving of the six resident room scenes: one request at a time (closed loop, no batching, one
-    lane) gives the capacity; Poisson traces at 0.5x, 0.9x and 1.2x of it then run with continuous batching."""
+    """Forward-only serving of the six resident room scenes. One request at a time (one lane, no batching, all
+    requests queued at t = 0) gives the capacity. Each Poisson trace (0.5x to 4x of it, and one skewed to two
+    (scene, resolution) keys) is then replayed twice on the same arrivals: with continuous batching (`lanes` lanes,
+    up to `max_batch` views per batch) and one request at a time, so both see the same load."""
     from paper_2404_03202_gb300 import serving
     scenes = {f"room{n // 1000}k": synth.room_scene(n, 40 + i).arrays() for i, n in enumerate(SERVING_SCENES)}
     names = sorted(scenes)
@@ -401,12 +490,18 @@ def serving_benchmark(dev, count: int = 96, lanes: int = 4, max_batch: int = 8) 
     serving.run_trace(warm, serving_requests(names, 16, None, 1))
     seq = serving.run_trace(serving.Scheduler(ex, lanes=1, max_batch=1), serving_requests(names, count // 2, None, 2))
     out = {"scenes": SERVING_SCENES, "resolutions": [f"{w}x{h} p={p}" for (w, h), p in SERVING_RES],
-           "lanes": lanes, "max_batch": max_batch, "one_at_a_time": seq, "poisson": []}
+           "lanes": lanes, "max_batch": max_batch, "capacity_one_at_a_time": seq, "poisson": []}
     cap = seq["views_per_s"]
-    for k, f in enumerate((0.5, 0.9, 1.2)):
-        res = serving.run_trace(serving.Scheduler(ex, lanes=lanes, max_batch=max_batch),
-                                serving_requests(names, count, f * cap, 10 + k))
-        out["poisson"].append({"rate_vs_capacity": f, "offered_per_s": f * cap} | res)
+    skew = [(("room1000k", (2048, 1024)), 0.6), (("room300k", (1024, 512)), 0.4)]
+    traces = [(f, None, f"{f}x capacity, mixed keys") for f in (0.5, 0.9, 1.2, 2.0, 4.0)]
+    traces.append((2.0, skew, "2x capacity, skewed to room1000k at 2048x1024 (0.6) and room300k at 1024x512 (0.4)"))
+    for k, (f, keys, label) in enumerate(traces):
+        row = {"trace": label, "rate_vs_capacity": f, "offered_per_s": f * cap}
+        for mode, ln, mb in (("batched", lanes, max_batch), ("one_at_a_time", 1, 1)):
+            reqs = serving_requests(names, count, f * cap, 10 + k, keys=keys)
+            row[mode] = serving.run_trace(serving.Scheduler(ex, lanes=ln, max_batch=mb), reqs)
+        row["batched_vs_one_at_a_time"] = row["batched"]["views_per_s"] / row["one_at_a_time"]["views_per_s"]
+        out["poisson"].append(row)
     out["overflow_reruns"] = ex.overflows
     return out
 
@@ -461,8 +556,7 @@ def workload_config(wl, args, settings=None):
     return {"workload": f"{args.workload}: {wl['n']} Gaussians, {wl['views']} views of {wl['width']}x{wl['height']} "
                         f"{cam}, {tile}x{tile} tiles{auto}, fwd+bwd with {loss} loss",
             "gaussians": wl["n"], "views_per_step": wl["views"], "width": wl["width"], "height": wl["height"],
-            "tile": tile, "pixels_per_thread": (settings.pixels_per_thread or "default") if settings else None,
-            "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
+            "tile": tile, "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)",
             "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1",
@@ -742,9 +836,14 @@ def main():
                 ms_cpu, ms_core, desc = pool.round(12.0)
             finally:
                 pool.close()
-            cpu = {"value": ms_cpu, "unit": "ms/iter", "cores": pool.cores, "kind": "oracle",
+            small = oracle_small_configs(pool.cores)
+            cpu = {"value": ms_cpu, "unit": "ms/iter", "cores": pool.cores, "kind": "oracle", "extrapolated": True,
                    "sample": desc + f"; {pool.cores} cores in parallel (one spawned process each), step time = "
-                                    "per-core time / cores", "value_per_core": ms_core}
+                                    "per-core time / cores", "value_per_core": ms_core,
+                   "sampler_bias_measured_on_training": small["training"]["sampler_bias"],
+                   "configs": {"shell-small (config 1)": small["shell-small"], "training (config 2)": small["training"],
+                               f"{args.workload} (this line)": {"all_cores_ms": ms_cpu, "cores": pool.cores,
+                                                                 "measured": "extrapolated from bounded samples"}}}
         except Exception as e:
             cpu = {"value": None, "unit": "ms/iter", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -752,14 +851,13 @@ def main():
         out = {"metric": "fwd+bwd ms/iter", "value": ms * 1.0, "unit": "ms/iter", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": workload_config(wl, args, settings) | {"views_per_s": 1e3 * V * world / ms,
-                                                      "timing": timing,
-                                                      "autotune": tuning,
-                                                      "eager_ms_per_step": eager_ms,
-                                                      "graph_ms_per_step": graph_ms,
-                                                      "instances_per_step": count,
-                                                      "examined_pairs_per_step": examined,
-                                                      "contributing_pairs_per_step": contrib},
+               "config": workload_config(wl, args, settings),
+               "measured": {"views_per_s": 1e3 * V * world / ms, "timing": timing, "autotune": tuning,
+                            "schedule": {"pixels_per_thread": settings.pixels_per_thread or "default",
+                                         "adjoint_pixels_per_thread": settings.adjoint_pixels_per_thread or "default"},
+                            "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
+                            "instances_per_step": count, "examined_pairs_per_step": examined,
+                            "contributing_pairs_per_step": contrib},
                "gpu_launches": kernel_launches * args.steps, "stages": stages,
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "serving": serve,
                "train_loop": train_loop}

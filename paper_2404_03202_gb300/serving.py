@@ -13,11 +13,14 @@ resolutions overlap on the GPU:
 A view's image depends only on its pose and the scene (Eqs. 3-8), so a request renders to the same pixels alone or
 batched with others.
 
-The scheduler is independent of CUDA: it drives an executor with `bytes_needed`, `launch`, `done` and `collect`.
-`GpuExecutor` is the one that renders with the CUDA library.
+The scheduler is independent of CUDA: it drives an executor with `bytes_needed`, `launch`, `done` and `collect`
+(and, optionally, `wait`, a blocking wait for the next finished batch). `GpuExecutor` is the one that renders with
+the CUDA library.
 """
 from __future__ import annotations
 
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -190,8 +193,12 @@ class Scheduler:
 def run_trace(scheduler: Scheduler, requests: list, clock=time.perf_counter, sleep=time.sleep,
               spin: float = 5e-5) -> dict:
     """Replays `requests` (sorted by arrival, seconds from the start) in real time through the scheduler and
-    returns its summary: views/s over the makespan, p50 / p99 latency from arrival to image on the host."""
+    returns its summary: views/s over the makespan, p50 / p99 latency from arrival to image on the host.
+
+    Between events the loop blocks: on the executor's `wait` (until a batch finishes or the next request is due)
+    when the executor has one, else by sleeping `spin` seconds."""
     pending = sorted(requests, key=lambda r: r.arrival)
+    wait = getattr(scheduler.ex, "wait", None)
     i = 0
     t0 = clock()
     while i < len(pending) or not scheduler.idle():
@@ -201,8 +208,11 @@ def run_trace(scheduler: Scheduler, requests: list, clock=time.perf_counter, sle
             i += 1
         scheduler.poll(now)
         scheduler.pump(now)
-        if scheduler.idle() and i < len(pending):
-            sleep(max(0.0, min(pending[i].arrival - (clock() - t0), 1e-3)))
+        due = pending[i].arrival - (clock() - t0) if i < len(pending) else None
+        if scheduler.in_flight and wait is not None:
+            wait(None if due is None else max(0.0, due))
+        elif scheduler.idle() and due is not None:
+            sleep(max(0.0, min(due, 1e-3)))
         elif spin:
             sleep(spin)
     makespan = clock() - t0 - (pending[0].arrival if pending else 0.0)
@@ -233,6 +243,28 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
         self.per_view = {}
         self.overflows = 0
+        # one waiter thread per lane blocks on the lane's batches in launch order (its stream runs them in that
+        # order) and wakes `wait`; the event wait releases the interpreter lock
+        self._cv = threading.Condition()
+        self._ready = 0
+        self._queues = [queue.Queue() for _ in range(lanes)]
+        for q in self._queues:
+            threading.Thread(target=self._waiter, args=(q,), daemon=True).start()
+
+    def _waiter(self, q):
+        while True:
+            h = q.get()
+            h["ev"].synchronize()
+            with self._cv:
+                h["finished"] = True
+                self._ready += 1
+                self._cv.notify_all()
+
+    def wait(self, timeout=None) -> None:
+        """Block until some launched batch has finished and not been collected, or `timeout` seconds pass."""
+        with self._cv:
+            if self._ready == 0:
+                self._cv.wait(timeout)
 
     def _settings(self, scene, w, h, v):
         return self.og.Settings(width=w, height=h, tile=self.tile, num_views=v, sh_degree=self.scenes[scene][2],
@@ -283,12 +315,17 @@ class GpuExecutor:
             host.copy_(rast.rgb, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return {"r": rast, "host": host, "ev": ev, "stream": s, "vm": vm_dev, "requests": requests}
+        handle = {"r": rast, "host": host, "ev": ev, "stream": s, "vm": vm_dev, "requests": requests,
+                  "finished": False}
+        self._queues[lane].put(handle)
+        return handle
 
     def done(self, handle) -> bool:
-        return handle["ev"].query()
+        return handle["finished"]
 
     def collect(self, handle) -> list:
+        with self._cv:
+            self._ready -= 1
         rast, s = handle["r"], handle["stream"]
         try:
             rast.check(stream=s)

@@ -72,3 +72,13 @@ def test_oracle_pool_times_a_bounded_sample_on_several_cores():
     assert pool.cores == 2
     assert ms > 0 and ms2 > 0 and abs(ms * 2 - ms_core) <= 1e-9 * ms_core
     assert "view 0 of 1" in desc and "tiles" in desc
+
+
+def test_whole_oracle_step_on_one_and_several_cores():
+    """The unsampled leg: shell-small (config 1) as one whole oracle step, single-threaded (every stage timed) and
+    split over two spawned processes by tile rows."""
+    out = bench.oracle_small_configs(2, names=("shell-small",))
+    r = out["shell-small"]
+    assert r["single_thread_ms"] > 0 and r["all_cores_ms"] > 0 and r["cores"] == 2
+    assert set(r["single_thread_stages_ms"]) == {"preprocess", "bin_sort", "blend_fwd_bwd", "preprocess_bwd"}
+    assert abs(sum(r["single_thread_stages_ms"].values()) - r["single_thread_ms"]) <= 1e-6 * r["single_thread_ms"]
