@@ -136,17 +136,22 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  *           order[v * n + r] = v * n + g of the r-th nearest splat g of view v ("depth rank" r). With the
  *           equirectangular camera every splat is ranked; with the pinhole camera only those with instances are
  *           (a view sees a fraction of the scene), and the entries past a view's ranked splats are unspecified.
- *   keys    [capacity] output (device): one key per instance, generated view by view and splat by splat in depth
- *           order (a splat's tiles row by row, columns in seam order): ((v * TILES + tile) << R) | r, with
+ *   keys    [capacity] device buffer for one key per instance, ((v * TILES + tile) << R) | r, with
  *           TILES = (W / tile) * (H / tile), tile = ty * (W / tile) + tx, r the splat's depth rank and
- *           R = max(1, ceil(log2(n))) rank bits. Within a tile the keys are therefore already in rank order.
+ *           R = max(1, ceil(log2(n))) rank bits. The keys are generated view by view and splat by splat in depth
+ *           order (a splat's tiles row by row, columns in seam order), so within a tile they are already in rank
+ *           order. When n >= 256 and an image has at most 128 tile rows and 256 tile columns, omnigs_bin writes
+ *           them into the workspace, grouped by (view, tile row) in that order, and leaves `keys` for omnigs_sort to
+ *           fill; otherwise it writes them into `keys` in generation order. Either way omnigs_sort leaves the
+ *           sorted keys in `keys`.
  * The total instance count stays on the device (workspace); if it exceeds `capacity`, instances beyond it are dropped
  * and OMNIGS_E_CAPACITY is raised in the workspace. capacity < 2^32, the value given to omnigs_workspace_size. */
 omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
                          uint64_t *keys, int64_t capacity, void *workspace, omnigs_stream_t stream);
 
-/* Stable sort of the instance keys written by omnigs_bin by their (view, tile) bits, in place, which leaves them
- * ordered by (view, tile), then by depth rank, i.e. the blending
+/* Stable sort of the instance keys of omnigs_bin by their (view, tile) bits into `keys` (one counting pass by tile
+ * column within each (view, tile row) group when omnigs_bin grouped them, a radix sort of `keys` in place
+ * otherwise), which leaves them ordered by (view, tile), then by depth rank, i.e. the blending
  * order of Sec. 3.3 (nearest first by t_r) with equal depths in splat order, the order a stable sort of (tile, t_r)
  * keys gives to instances generated splat by splat. Writes ranges [V * TILES, 2] (device): ranges[2t], ranges[2t+1] =
  * first and one-past-last sorted position of tile t (both 0 for an empty tile). n and capacity as for omnigs_bin. */

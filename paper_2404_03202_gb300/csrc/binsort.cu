@@ -393,6 +393,75 @@ __device__ __forceinline__ u64 pack_row(int cl, unsigned cnt, int ty, int j) {
     return (u64)(unsigned short)cl | ((u64)cnt << 16) | ((u64)(unsigned)ty << 32) | ((u64)(unsigned)j << 48);
 }
 
+// ------------------------------------------------------------------------------------------- bucketed order
+// With bucketed_binning, bin_emit writes every instance straight into its (view, tile row) bucket, in depth order,
+// so that omnigs_sort only has to order each bucket by tile column. A block's row items of one bucket take
+// consecutive slots after those of the earlier blocks; within the block, the slots follow the items' order
+// (splat by splat in depth order). That order is found per chunk of row items by a stable, weighted ranking.
+constexpr int kBinWarps = kBinThreads / 32;
+constexpr int kBucketSlots = 2 * kMaxBucketRows;  // a block's buckets: the tile rows of its (at most two) views
+
+// bin_count's ranking: warp w's row items are the block's items [w * per, (w + 1) * per) in order, ranked 32 at a
+// time against the warp's own bucket counters; afterwards every warp's base in a bucket is the count of the earlier
+// warps' items there.
+struct WarpBuckets {
+    unsigned cw[kBinWarps][kBucketSlots];  // per warp: its items' instances in each bucket so far; then its base
+    unsigned run[kBucketSlots];            // the block's instances in each bucket
+    unsigned lw[kBinWarps][32];            // item weights of the current step, by warp and lane
+};
+
+struct BucketScratch {
+    unsigned run[kBucketSlots];              // the block's instances in each bucket so far
+    unsigned wt[kBinWarps][kBucketSlots];    // per-warp bucket totals of the current round (zero between rounds)
+    unsigned lw[kBinThreads];                // item weights of the current round, by thread
+    unsigned short bl[kRowChunk];            // bucket of each row item of the chunk (view in block * TY + row)
+    unsigned w[kRowChunk];                   // its instance count
+    unsigned off[kRowChunk];                 // out: its first instance's offset among the block's in the bucket
+};
+
+// Bucket offsets of the chunk's n_items row items (B.bl, B.w), in item order; advances B.run. Called by the whole
+// CTA; B.wt holds zeros on entry and on return. Round r ranks items r .. r + 255 (one per thread): the lanes of a
+// warp sharing a bucket are found by one ballot per bit of the bucket (a padding bucket for missing items
+// included), each lane adds the weights of its lower peers, and the warps' totals per bucket are added in warp
+// order.
+__device__ __forceinline__ void rank_row_buckets(BucketScratch& B, unsigned n_items) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+    for (unsigned r = 0; r < n_items; r += kBinThreads) {
+        const unsigned i = r + threadIdx.x;
+        const bool valid = i < n_items;
+        const unsigned bl = valid ? B.bl[i] : (unsigned)kBucketSlots;
+        const unsigned w = valid ? B.w[i] : 0u;
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= 8; ++b) {  // kBucketSlots = 256: 9 bits with the padding bucket
+            const unsigned bit = (bl >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        B.lw[threadIdx.x] = w;
+        __syncwarp();
+        unsigned pre = 0;
+        for (unsigned m = peers & lt; m; m &= m - 1) pre += B.lw[warp * 32 + (__ffs(m) - 1)];
+        const bool leader = valid && (peers >> lane) == 1u;  // the highest lane of its group
+        if (leader) B.wt[warp][bl] = pre + w;
+        __syncthreads();
+        if (valid) {
+            unsigned xw = 0;
+            for (unsigned q = 0; q < warp; ++q) xw += B.wt[q][bl];
+            B.off[i] = B.run[bl] + xw + pre;
+        }
+        __syncthreads();
+        if (leader) {
+            atomicAdd(&B.run[bl], pre + w);
+            B.wt[warp][bl] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int64_t view_first_block(int64_t v, int64_t n) { return v * n / kBinSplats; }
+__device__ __forceinline__ int64_t view_last_block(int64_t v, int64_t n) { return ((v + 1) * n - 1) / kBinSplats; }
+
 // A block inside one view that starts past the view's ranked splats has nothing to do.
 __device__ __forceinline__ bool block_unranked(int64_t blk, int64_t n, const unsigned* __restrict__ vis_start) {
     if (vis_start == nullptr) return false;
@@ -400,14 +469,19 @@ __device__ __forceinline__ bool block_unranked(int64_t blk, int64_t n, const uns
     return i0 + kBinSplats <= (v + 1) * n && i0 - v * n >= (int64_t)(vis_start[v + 1] - vis_start[v]);
 }
 
-__global__ void __launch_bounds__(kBinThreads, 8)
+// kBuckets: also rank every row item within its (view, tile row) bucket (the offset goes to rows_off beside the row
+// word) and write the block's instance count per bucket to bkt_counts[(v * tiles_y + ty) * nbv + block of view v].
+template <bool kBuckets>
+__global__ void __launch_bounds__(kBinThreads, kBuckets ? 6 : 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
                  int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, const unsigned* __restrict__ vis_start,
                  unsigned* __restrict__ block_sums, u64* __restrict__ rows, u64 row_cap, unsigned* __restrict__ row_base,
-                 unsigned* __restrict__ row_count, WsHeader* __restrict__ hdr) {
+                 unsigned* __restrict__ row_count, WsHeader* __restrict__ hdr, unsigned* __restrict__ rows_off,
+                 unsigned* __restrict__ bkt_counts, int nbv, unsigned* __restrict__ unstored_list) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
     __shared__ unsigned s_rbase;
+    __shared__ typename std::conditional<kBuckets, WarpBuckets, char>::type B;
     const int64_t blk = logical_block(V, n, nb, blockIdx.x);
     if (blk < 0) return;
     if (block_unranked(blk, n, vis_start)) {
@@ -424,22 +498,85 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
         s_rbase = b + rows_total <= row_cap ? (unsigned)b : 0xffffffffu;
         row_base[blk] = s_rbase;
         row_count[blk] = rows_total;
+        if (kBuckets && s_rbase == 0xffffffffu) unstored_list[atomicAdd(&hdr->unstored, 1u)] = (unsigned)blk;
     }
     __syncthreads();
     const unsigned rbase = s_rbase;
     unsigned cnt = 0;
-    for (unsigned ri0 = threadIdx.x * kRowsPerThread; ri0 < rows_total; ri0 += kRowChunk) {
-        int j = row_owner(S, ri0);
+    if constexpr (!kBuckets) {
+        for (unsigned ri0 = threadIdx.x * kRowsPerThread; ri0 < rows_total; ri0 += kRowChunk) {
+            int j = row_owner(S, ri0);
 #pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) {
-            const unsigned ri = ri0 + k;
-            if (ri < rows_total) {
-                int ty;
+            for (int k = 0; k < kRowsPerThread; ++k) {
+                const unsigned ri = ri0 + k;
+                if (ri < rows_total) {
+                    int ty;
+                    const int2 c = row_item_cols(S, ri, j, tile, &ty);
+                    const unsigned m = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                    cnt += m;
+                    if (rbase != 0xffffffffu) rows[(u64)rbase + ri] = pack_row(c.x, m, ty, j);
+                }
+            }
+        }
+    } else {
+        // warp w ranks the block's row items [seg0, seg1), 32 at a time, against warp-private bucket counters
+        for (int i = threadIdx.x; i < kBinWarps * kBucketSlots; i += kBinThreads) (&B.cw[0][0])[i] = 0u;
+        __syncthreads();
+        const int64_t p0 = blk * kBinSplats, v_lo = p0 / n, next_view = (v_lo + 1) * n - p0;
+        const unsigned lane = lane_id(), warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+        const unsigned per = (rows_total + kBinWarps - 1) / kBinWarps;
+        const unsigned seg0 = min(rows_total, warp * per), seg1 = min(rows_total, seg0 + per);
+        for (unsigned b0 = seg0; b0 < seg1; b0 += 32) {
+            const unsigned ri = b0 + lane;
+            const bool valid = ri < seg1;
+            unsigned m = 0, bl = kBucketSlots;
+            if (valid) {
+                int j = row_owner(S, ri), ty;
                 const int2 c = row_item_cols(S, ri, j, tile, &ty);
-                const unsigned m = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
-                cnt += m;
+                m = c.y >= c.x ? (unsigned)(c.y - c.x + 1) : 0u;
+                bl = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
                 if (rbase != 0xffffffffu) rows[(u64)rbase + ri] = pack_row(c.x, m, ty, j);
             }
+            cnt += m;
+            const unsigned peers = __match_any_sync(0xffffffffu, bl);
+            B.lw[warp][lane] = m;
+            __syncwarp();
+            unsigned pre = 0;
+            for (unsigned q = peers & lt; q; q &= q - 1) pre += B.lw[warp][__ffs(q) - 1];
+            if (valid) {
+                const unsigned intra = B.cw[warp][bl] + pre;
+                if (rbase != 0xffffffffu) rows_off[(u64)rbase + ri] = intra;
+            }
+            __syncwarp();
+            if (valid && (peers >> lane) == 1u) B.cw[warp][bl] += pre + m;  // the group's highest lane
+            __syncwarp();
+        }
+        __syncthreads();
+        // each warp's base in every bucket (earlier warps' items come first); the block's totals per bucket
+        for (int bl = threadIdx.x; bl < kBucketSlots; bl += kBinThreads) {
+            unsigned run = 0;
+#pragma unroll
+            for (int w = 0; w < kBinWarps; ++w) {
+                const unsigned x = B.cw[w][bl];
+                B.cw[w][bl] = run;
+                run += x;
+            }
+            B.run[bl] = run;
+        }
+        __syncthreads();
+        if (rbase != 0xffffffffu && warp > 0) {
+            for (unsigned ri = seg0 + lane; ri < seg1; ri += 32) {
+                const u64 w = rows[(u64)rbase + ri];
+                const int ty = (int)((w >> 32) & 0xffffu), j = (int)(w >> 48);
+                const unsigned bl = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
+                rows_off[(u64)rbase + ri] += B.cw[warp][bl];
+            }
+        }
+        for (int i = threadIdx.x; i < 2 * tiles_y; i += kBinThreads) {
+            const int lv = i / tiles_y, ty = i - lv * tiles_y;
+            const int64_t v = v_lo + lv;
+            if (v >= V || blk < view_first_block(v, n) || blk > view_last_block(v, n)) continue;
+            bkt_counts[((size_t)v * tiles_y + ty) * nbv + (size_t)(blk - view_first_block(v, n))] = B.run[i];
         }
     }
     unsigned tot;
@@ -492,8 +629,17 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
 // store instruction writes 256 consecutive keys whatever the rows' lengths (the nearest splats have rows of hundreds
 // of tiles, most others of one to four). Instances of a splat are listed row by row, columns in seam order.
 
-template <bool kSplit>
-__global__ void __launch_bounds__(kBinThreads, 8)
+struct EmitBuckets {
+    u64 bpos[kBucketSlots];  // output position of the block's first instance in each of its buckets
+    u64 pos[kRowChunk];      // output position of each row item's first instance
+    BucketScratch R;         // the ranking, for blocks whose rows were not stored
+};
+
+// kBuckets: each instance goes to its (view, tile row) bucket: the bucket's base, plus the block's offset in the
+// bucket (both from the bucket scans), plus the row item's offset among the block's instances of the bucket (from
+// bin_count's ranking, or ranked again here), plus its column index within the item.
+template <bool kSplit, bool kBuckets>
+__global__ void __launch_bounds__(kBinThreads, kBuckets ? 5 : 8)
 bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const uint32_t* __restrict__ order,
                 int tiles_x, int tiles_y, int tile, int wrap, int rank_bits, int V, unsigned nb, unsigned piece,
                 unsigned max_pieces,
@@ -501,7 +647,9 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const u64* __restrict__ block_offsets, const unsigned* __restrict__ piece_start,
                 const unsigned* __restrict__ piece_block, const WsHeader* __restrict__ hdr,
                 const u64* __restrict__ rows, const unsigned* __restrict__ row_base,
-                const unsigned* __restrict__ row_count, u64* __restrict__ keys, u64 capacity) {
+                const unsigned* __restrict__ row_count, u64* __restrict__ keys, u64 capacity,
+                const unsigned* __restrict__ rows_off, const unsigned* __restrict__ bkt_offsets,
+                const u64* __restrict__ bkt_base, int nbv, const unsigned* __restrict__ fallback_list) {
     __shared__ unsigned scratch[32];
     __shared__ CtaRows S;
     __shared__ struct {
@@ -509,12 +657,19 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         int cl[kRowChunk];        // its first column
         u64 key0[kRowChunk];      // key of its first column, before the column wrap
     } E;
+    __shared__ typename std::conditional<kBuckets, EmitBuckets, char>::type EB;
     // The first max_pieces CTAs take the extra pieces of the blocks with more than `piece` instances (the
     // nearest, widest splats, which would otherwise leave one CTA writing hundreds of thousands of keys while the
     // others idle); they start first. The rest take piece 0 of every block, view-interleaved.
+    // With kBuckets this kernel writes only the blocks whose row items bin_count could not store (fallback_list):
+    // the CTAs take them in turn, whole (no pieces).
     int64_t blk;
     u64 lo = 0;  // output slots [lo, lo + piece) of the block are this CTA's (all of them for a light block)
-    if (kSplit && blockIdx.x < max_pieces) {
+    unsigned e_fb = blockIdx.x;
+    if constexpr (kBuckets) {
+        if (e_fb >= hdr->unstored) return;
+        blk = fallback_list[e_fb];
+    } else if (kSplit && blockIdx.x < max_pieces) {
         const unsigned e = blockIdx.x;
         if (e >= hdr->extra_pieces) return;
         blk = piece_block[e];
@@ -523,6 +678,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         blk = logical_block(V, n, nb, blockIdx.x - max_pieces);
         if (blk < 0 || block_unranked(blk, n, vis_start)) return;
     }
+    for (;;) {
     const u64 hi = kSplit && block_sums[blk] > piece ? lo + piece : ~0ull;
     const unsigned rbase = row_base[blk];
     const bool stored = rbase != 0xffffffffu;  // block-uniform: rows from bin_count, or derived again here
@@ -533,6 +689,23 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
     const int64_t p0 = blk * kBinSplats, v0 = p0 / n, next_view = (v0 + 1) * n - p0;
     const unsigned lane = lane_id();
     const u64 first = block_offsets[blk];
+    if constexpr (kBuckets) {
+        for (int i = threadIdx.x; i < 2 * tiles_y; i += kBinThreads) {
+            const int lv = i / tiles_y, ty = i - lv * tiles_y;
+            const int64_t v = v0 + lv;
+            u64 p = 0;
+            if (v < V && blk >= view_first_block(v, n) && blk <= view_last_block(v, n)) {
+                const size_t b = (size_t)v * tiles_y + ty;
+                p = bkt_base[b] + bkt_offsets[b * nbv + (size_t)(blk - view_first_block(v, n))];
+            }
+            EB.bpos[i] = p;
+        }
+        if (!stored) {
+            for (int i = threadIdx.x; i < kBucketSlots; i += kBinThreads) EB.R.run[i] = 0u;
+            for (int i = threadIdx.x; i < kBinWarps * kBucketSlots; i += kBinThreads) (&EB.R.wt[0][0])[i] = 0u;
+        }
+        __syncthreads();
+    }
     const u64 plo = first + lo, phi = kSplit && hi != ~0ull ? first + hi : ~0ull;  // this CTA's output positions
     u64 out = first;
     for (unsigned r0 = 0; r0 < rows_total && (!kSplit || out < phi); r0 += kRowChunk) {
@@ -540,6 +713,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
         unsigned cnt[kRowsPerThread], local = 0;
         u64 key0[kRowsPerThread];  // key of the item's first column, before the column wrap
         int cl[kRowsPerThread];
+        unsigned bl[kRowsPerThread], boff[kRowsPerThread];  // bucketed order: the item's bucket and its offset
         int j = !stored && ri0 < rows_total ? row_owner(S, ri0) : 0;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
@@ -547,6 +721,8 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             cnt[k] = 0;
             cl[k] = 0;
             key0[k] = 0;
+            bl[k] = 0;
+            boff[k] = 0;
             if (ri < rows_total) {
                 int ty;
                 if (stored) {
@@ -564,8 +740,27 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const unsigned rank = (unsigned)(p0 + j - v * n);
                 const unsigned tb = (unsigned)v * (unsigned)(tiles_x * tiles_y) + (unsigned)(ty * tiles_x);
                 key0[k] = ((u64)tb << rank_bits) | (u64)rank;
+                if constexpr (kBuckets) {
+                    bl[k] = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
+                    boff[k] = stored ? __ldg(rows_off + (u64)rbase + ri) : 0u;
+                }
+            }
+            if constexpr (kBuckets) {
+                if (!stored) {
+                    const unsigned li = threadIdx.x * kRowsPerThread + k;
+                    EB.R.bl[li] = (unsigned short)bl[k];
+                    EB.R.w[li] = cnt[k];
+                }
             }
             local += cnt[k];
+        }
+        if constexpr (kBuckets) {
+            if (!stored) {  // block-uniform
+                __syncthreads();
+                rank_row_buckets(EB.R, min((unsigned)kRowChunk, rows_total - r0));
+#pragma unroll
+                for (int k = 0; k < kRowsPerThread; ++k) boff[k] = EB.R.off[threadIdx.x * kRowsPerThread + k];
+            }
         }
         unsigned chunk_total;
         unsigned rel = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);  // offset within the chunk
@@ -579,6 +774,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             E.off[i] = rel;
             E.cl[i] = cl[k];
             E.key0[i] = key0[k];
+            if constexpr (kBuckets) EB.pos[i] = EB.bpos[bl[k]] + boff[k];
             rel += cnt[k];
         }
         __syncthreads();
@@ -597,7 +793,124 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
             int tx = E.cl[i] + (int)(sl - E.off[i]);
             tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-            const u64 at = out + sl;
+            u64 at;
+            if constexpr (kBuckets) at = EB.pos[i] + (sl - E.off[i]);
+            else at = out + sl;
+            if (at < capacity) keys[at] = E.key0[i] + ((u64)tx << rank_bits);
+        }
+        __syncthreads();
+        out += chunk_total;
+    }
+    if constexpr (!kBuckets) {
+        return;
+    } else {
+        e_fb += gridDim.x;
+        if (e_fb >= hdr->unstored) return;
+        blk = fallback_list[e_fb];
+        __syncthreads();
+    }
+    }
+}
+
+// Bucketed order, blocks whose row items bin_count stored with their bucket offsets (the others are left to the
+// fallback launch of bin_emit_kernel). Same block and piece dispatch as bin_emit_kernel; each row item's first
+// instance goes to its bucket's base + the block's offset in the bucket + the item's offset within the block.
+template <bool kSplit>
+__global__ void __launch_bounds__(kBinThreads, 8)
+bin_emit_stored_kernel(int n, int tiles_x, int tiles_y, int rank_bits, int V, unsigned nb, unsigned piece,
+                       unsigned max_pieces, const unsigned* __restrict__ block_sums,
+                       const u64* __restrict__ block_offsets, const unsigned* __restrict__ piece_start,
+                       const unsigned* __restrict__ piece_block, const WsHeader* __restrict__ hdr,
+                       const u64* __restrict__ rows, const unsigned* __restrict__ rows_off,
+                       const unsigned* __restrict__ row_base, const unsigned* __restrict__ row_count,
+                       const unsigned* __restrict__ bkt_offsets, const u64* __restrict__ bkt_base, int nbv,
+                       u64* __restrict__ keys, u64 capacity) {
+    __shared__ unsigned scratch[32];
+    __shared__ struct {
+        unsigned off[kRowChunk];  // output slot of each row item of the chunk, relative to the chunk
+        int cl[kRowChunk];        // its first column
+        u64 key0[kRowChunk];      // key of its first column, before the column wrap
+        u64 pos[kRowChunk];       // output position of its first instance
+    } E;
+    __shared__ u64 s_bpos[kBucketSlots];
+    int64_t blk;
+    u64 lo = 0;
+    if (kSplit && blockIdx.x < max_pieces) {
+        const unsigned e = blockIdx.x;
+        if (e >= hdr->extra_pieces) return;
+        blk = piece_block[e];
+        lo = (u64)(1 + e - piece_start[blk]) * piece;
+    } else {
+        blk = logical_block(V, n, nb, blockIdx.x - max_pieces);
+        if (blk < 0) return;
+    }
+    const unsigned rows_total = row_count[blk];
+    if (rows_total == 0) return;
+    const unsigned rbase = row_base[blk];
+    if (rbase == 0xffffffffu) return;  // not stored: the fallback launch writes this block
+    const u64 hi = kSplit && block_sums[blk] > piece ? lo + piece : ~0ull;
+    const int64_t p0 = blk * kBinSplats, v0 = p0 / n, next_view = (v0 + 1) * n - p0;
+    for (int i = threadIdx.x; i < 2 * tiles_y; i += kBinThreads) {
+        const int lv = i / tiles_y, ty = i - lv * tiles_y;
+        const int64_t v = v0 + lv;
+        u64 p = 0;
+        if (v < V && blk >= view_first_block(v, n) && blk <= view_last_block(v, n)) {
+            const size_t b = (size_t)v * tiles_y + ty;
+            p = bkt_base[b] + bkt_offsets[b * nbv + (size_t)(blk - view_first_block(v, n))];
+        }
+        s_bpos[i] = p;
+    }
+    __syncthreads();
+    u64 out = 0;  // slots of the block before the current chunk
+    const u64 slo = lo, shi = hi;
+    for (unsigned r0 = 0; r0 < rows_total && (!kSplit || out < shi); r0 += kRowChunk) {
+        const unsigned ri0 = r0 + threadIdx.x * kRowsPerThread;
+        unsigned cnt[kRowsPerThread], local = 0;
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const unsigned ri = ri0 + k;
+            const int i = threadIdx.x * kRowsPerThread + k;
+            cnt[k] = 0;
+            if (ri < rows_total) {
+                const u64 w = __ldg(rows + (u64)rbase + ri);
+                const int cl = (int)(short)(unsigned short)(w & 0xffffu);
+                const int ty = (int)((w >> 32) & 0xffffu), j = (int)(w >> 48);
+                cnt[k] = (unsigned)(w >> 16) & 0xffffu;
+                const int64_t v = j < next_view ? v0 : v0 + 1;
+                const unsigned rank = (unsigned)(p0 + j - v * n);
+                const unsigned tb = (unsigned)v * (unsigned)(tiles_x * tiles_y) + (unsigned)(ty * tiles_x);
+                E.cl[i] = cl;
+                E.key0[i] = ((u64)tb << rank_bits) | (u64)rank;
+                E.pos[i] = s_bpos[(j < next_view ? 0 : tiles_y) + ty] + __ldg(rows_off + (u64)rbase + ri);
+            }
+            local += cnt[k];
+        }
+        unsigned chunk_total;
+        unsigned rel = block_exclusive_scan<unsigned>(local, scratch, &chunk_total);
+        if (kSplit && out + chunk_total <= slo) {
+            out += chunk_total;
+            __syncthreads();
+            continue;
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            E.off[threadIdx.x * kRowsPerThread + k] = rel;
+            rel += cnt[k];
+        }
+        __syncthreads();
+        unsigned s_lo = 0, s_hi = chunk_total;
+        if (kSplit) {
+            s_lo = slo > out ? (slo - out < chunk_total ? (unsigned)(slo - out) : chunk_total) : 0u;
+            s_hi = shi - out < chunk_total ? (unsigned)(shi - out) : chunk_total;
+        }
+        for (unsigned sl = s_lo + threadIdx.x; sl < s_hi; sl += kBinThreads) {
+            int i = 0;
+#pragma unroll
+            for (int step = kRowChunk / 2; step >= 1; step >>= 1)
+                if (E.off[i + step] <= sl) i += step;
+            int tx = E.cl[i] + (int)(sl - E.off[i]);
+            tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
+            const u64 at = E.pos[i] + (sl - E.off[i]);
             if (at < capacity) keys[at] = E.key0[i] + ((u64)tx << rank_bits);
         }
         __syncthreads();
@@ -828,6 +1141,229 @@ __global__ void ranges_kernel(const u64* __restrict__ keys, const WsHeader* __re
     ranges[2 * t + 1] = (uint32_t)(first < lo ? lo : 0);
 }
 
+// ------------------------------------------------------------------------------------------- 5: bucketed order
+
+// Per (view, tile row) bucket b = v * tiles_y + ty (one CTA each): exclusive scan, in place, of the instance counts
+// of view v's blocks; the bucket's total.
+__global__ void __launch_bounds__(256)
+bucket_scan_kernel(int tiles_y, int64_t n, int nbv, unsigned* __restrict__ counts, u64* __restrict__ totals) {
+    __shared__ u64 scratch[32];
+    const int b = blockIdx.x;
+    const int64_t v = b / tiles_y;
+    const int nblk = (int)(view_last_block(v, n) - view_first_block(v, n) + 1);
+    unsigned* c = counts + (size_t)b * nbv;
+    const int per = (nblk + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblk);
+    u64 local = 0;
+    for (int i = b0; i < b1; ++i) local += c[i];
+    u64 tot;
+    u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
+    for (int i = b0; i < b1; ++i) {
+        const unsigned x = c[i];
+        c[i] = (unsigned)run;
+        run += x;
+    }
+    if (threadIdx.x == 0) totals[b] = tot;
+}
+
+// One CTA: every bucket's base (exclusive scan of the totals, 64-bit), the part of it below the capacity (`eff`;
+// instances past the capacity were not written), and the column pass's chunks of kColChunk keys: bucket b owns
+// chunks col_start[b] .. col_start[b + 1] - 1; col_start[nbkt] is their number.
+__global__ void __launch_bounds__(1024)
+bucket_base_kernel(int nbkt, const u64* __restrict__ totals, u64* __restrict__ base, u64* __restrict__ eff,
+                   unsigned* __restrict__ col_start, u64 capacity) {
+    __shared__ u64 scratch[32];
+    __shared__ unsigned scratch32[32];
+    const int per = (nbkt + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nbkt);
+    u64 local = 0;
+    for (int b = b0; b < b1; ++b) local += totals[b];
+    u64 tot;
+    u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
+    unsigned chunks = 0;
+    for (int b = b0; b < b1; ++b) {
+        const u64 e = run < capacity ? min(totals[b], capacity - run) : 0ull;
+        base[b] = run;
+        eff[b] = e;
+        chunks += (unsigned)((e + kColChunk - 1) / kColChunk);
+        run += totals[b];
+    }
+    unsigned ctot;
+    unsigned crun = block_exclusive_scan<unsigned>(chunks, scratch32, &ctot);
+    for (int b = b0; b < b1; ++b) {
+        col_start[b] = crun;
+        crun += (unsigned)((eff[b] + kColChunk - 1) / kColChunk);
+    }
+    if (threadIdx.x == 0) col_start[nbkt] = ctot;
+}
+
+// Bucket of column-pass chunk c: the last b with col_start[b] <= c (buckets without chunks are passed over).
+__device__ __forceinline__ int chunk_bucket(const unsigned* __restrict__ col_start, int nbkt, unsigned c) {
+    int lo = 0, hi = nbkt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(col_start + mid) <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Column of every key of chunk c: hist[c][tx] (one CTA per chunk; CTAs past the last chunk return). Every key of a
+// bucket b = v * tiles_y + ty has tile key b * tiles_x + tx.
+__global__ void __launch_bounds__(kSortThreads)
+col_count_kernel(const u64* __restrict__ keys, const u64* __restrict__ base, const u64* __restrict__ eff,
+                 const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int rank_bits,
+                 unsigned* __restrict__ hist, WsHeader* __restrict__ hdr) {
+    __shared__ unsigned s_h[kMaxBucketCols];
+    const unsigned c = blockIdx.x;
+    if (c >= __ldg(col_start + nbkt)) return;
+    const int b = chunk_bucket(col_start, nbkt, c);
+    const u64 beg = base[b] + (u64)(c - col_start[b]) * kColChunk;
+    const u64 end = min(beg + kColChunk, base[b] + eff[b]);
+    const u64 tile0 = (u64)b * tiles_x;
+    for (int d = threadIdx.x; d < tiles_x; d += kSortThreads) s_h[d] = 0u;
+    __syncthreads();
+    u64 k[kSortItems];  // all loads in flight before the counting
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const u64 i = beg + threadIdx.x + (u64)j * kSortThreads;
+        k[j] = i < end ? __ldg(keys + i) : (tile0 << rank_bits);
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        if (beg + threadIdx.x + (u64)j * kSortThreads >= end) break;
+        const u64 d = (k[j] >> rank_bits) - tile0;
+        if (d < (u64)tiles_x) atomicAdd(&s_h[(unsigned)d], 1u);
+        else atomicOr(&hdr->error, kErrConsistency);  // a key outside its bucket: not counted
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < tiles_x; d += kSortThreads) hist[(size_t)c * tiles_x + d] = s_h[d];
+}
+
+// Per bucket (one CTA, thread tx per column): exclusive scan over the bucket's chunks of hist[.][tx], then over the
+// columns of their totals; hist[c][tx] becomes the output position of chunk c's first key of column tx, and the tile
+// ranges of the bucket's tiles are written ([0, 0) for an empty tile).
+__global__ void __launch_bounds__(kMaxBucketCols)
+col_scan_kernel(const u64* __restrict__ base, const unsigned* __restrict__ col_start, int tiles_x,
+                unsigned* __restrict__ hist, uint32_t* __restrict__ ranges) {
+    __shared__ unsigned scratch[32];
+    const int b = blockIdx.x;
+    const unsigned c0 = col_start[b], c1 = col_start[b + 1];
+    const int tx = threadIdx.x;
+    unsigned run = 0;
+    if (tx < tiles_x)
+        for (unsigned c = c0; c < c1; ++c) {
+            const unsigned h = hist[(size_t)c * tiles_x + tx];
+            hist[(size_t)c * tiles_x + tx] = run;
+            run += h;
+        }
+    unsigned tot;
+    const unsigned start = block_exclusive_scan<unsigned>(tx < tiles_x ? run : 0u, scratch, &tot);
+    if (tx >= tiles_x) return;
+    const unsigned first = (unsigned)base[b] + start;
+    for (unsigned c = c0; c < c1; ++c) hist[(size_t)c * tiles_x + tx] += first;
+    const size_t t = (size_t)b * tiles_x + tx;
+    ranges[2 * t] = run ? first : 0u;
+    ranges[2 * t + 1] = run ? first + run : 0u;
+}
+
+// Chunk c of a bucket, ordered by column and written to its final positions (one CTA per chunk): the keys are ranked
+// stably by column within each warp (the lanes sharing a column from one ballot per column bit, a padding column for
+// missing keys included), the warps' counts are combined in warp order, the keys are placed in column order in
+// shared memory, and each is written to hist[c][tx] + its rank within its column.
+__global__ void __launch_bounds__(kSortThreads, 3)
+col_scatter_kernel(const u64* __restrict__ keys_in, u64* __restrict__ keys_out, const u64* __restrict__ base,
+                   const u64* __restrict__ eff, const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int dbits,
+                   int rank_bits, const unsigned* __restrict__ hist, u64 capacity, WsHeader* __restrict__ hdr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64* s_keys = reinterpret_cast<u64*>(smem_raw);
+    unsigned* s_whist = reinterpret_cast<unsigned*>(s_keys + kSortTile);  // [kWarps][kHistRow]
+    unsigned* s_start = s_whist + kWarps * kHistRow;
+    unsigned* s_tot = s_start + kRadixMax;
+    unsigned* s_scratch = s_tot + kRadixMax;
+
+    const unsigned c = blockIdx.x;
+    if (c >= __ldg(col_start + nbkt)) return;
+    const int b = chunk_bucket(col_start, nbkt, c);
+    const u64 beg = base[b] + (u64)(c - col_start[b]) * kColChunk;
+    const unsigned cnt = (unsigned)(min(beg + kColChunk, base[b] + eff[b]) - beg);
+    const u64 tile0 = (u64)b * tiles_x;
+    const unsigned R = 1u << dbits;
+    const unsigned tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned* my_hist = s_whist + warp * kHistRow;
+    for (unsigned d = lane; d <= R; d += 32) my_hist[d] = 0;
+    __syncwarp();
+    const unsigned base_i = warp * (kSortItems * 32) + lane;
+    u64 k[kSortItems];
+    unsigned rk[kSortItems], dg[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const unsigned idx = base_i + j * 32;
+        k[j] = idx < cnt ? __ldg(keys_in + beg + idx) : 0ull;
+        const u64 d = (k[j] >> rank_bits) - tile0;
+        dg[j] = idx < cnt && d < (u64)tiles_x ? (unsigned)d : R;  // a key outside its bucket is left out
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const unsigned d = dg[j];
+        unsigned peers = 0xffffffffu;
+        for (int bt = 0; bt <= dbits; ++bt) {
+            const unsigned bal = __ballot_sync(0xffffffffu, (d >> bt) & 1u);
+            peers &= ((d >> bt) & 1u) ? bal : ~bal;
+        }
+        const unsigned before = my_hist[d];
+        __syncwarp();
+        if ((peers & lt_mask) == 0) my_hist[d] = before + __popc(peers);
+        __syncwarp();
+        rk[j] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    for (unsigned d = tid; d < R; d += kSortThreads) {
+        unsigned acc = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const unsigned x = s_whist[w * kHistRow + d];
+            s_whist[w * kHistRow + d] = acc;
+            acc += x;
+        }
+        s_tot[d] = acc;
+    }
+    __syncthreads();
+    {
+        constexpr int PER = kRadixMax / kSortThreads;
+        unsigned loc[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const unsigned d = tid * PER + q;
+            loc[q] = d < R ? s_tot[d] : 0u;
+            sum += loc[q];
+        }
+        unsigned tile_total;
+        unsigned run = block_exclusive_scan<unsigned>(sum, s_scratch, &tile_total);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const unsigned d = tid * PER + q;
+            if (d < R) s_start[d] = run;
+            run += loc[q];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j)
+        if (dg[j] < R) s_keys[s_start[dg[j]] + my_hist[dg[j]] + rk[j]] = k[j];
+    __syncthreads();
+    const unsigned placed = s_start[R - 1] + s_tot[R - 1];  // keys with a column (all, unless one was left out)
+    if (tid == 0 && placed != cnt) atomicOr(&hdr->error, kErrConsistency);
+    const unsigned* h = hist + (size_t)c * tiles_x;
+    for (unsigned i = tid; i < placed; i += kSortThreads) {
+        const u64 key = s_keys[i];
+        const unsigned d = (unsigned)((key >> rank_bits) - tile0);
+        const u64 at = (u64)__ldg(h + d) + (i - s_start[d]);
+        if (at < capacity) keys_out[at] = key;
+    }
+}
+
 // Radix-sort geometry: `bits` key bits in an even number of passes of <= 9 bits.
 struct Plan {
     int passes, digit;
@@ -963,7 +1499,6 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     }
     const unsigned grid = per_view * (unsigned)V;
     unsigned* pstart = reinterpret_cast<unsigned*>(ws + L.piece_start);
-    u64* rows = reinterpret_cast<u64*>(ws + L.alt_keys);  // free until the tile sort
     unsigned* rbase = reinterpret_cast<unsigned*>(ws + L.row_base);
     unsigned* rcount = reinterpret_cast<unsigned*>(ws + L.row_count);
     unsigned* pblock = reinterpret_cast<unsigned*>(ws + L.piece_block);
@@ -971,20 +1506,65 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     // overlaps their heavy first blocks, and the pieces' repeated row work would cost more than it saves.
     const unsigned piece = V <= 2 ? (unsigned)kEmitPiece : 0u;
     const unsigned max_pieces = piece ? (unsigned)((u64)capacity / piece + 1) : 0u;
+    const int rb = rank_bits_for(n);
+    if (!bucketed_binning(cfg, n)) {
+        // instances in emission order into keys; the row words use the tile sort's spare buffer meanwhile
+        u64* rows = reinterpret_cast<u64*>(ws + L.alt_keys);
+        {
+            ProfScope prof("bin_count", stream, 2);
+            bin_count_kernel<false><<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n,
+                                                                      nb, vis_start, bsums, rows, (u64)capacity,
+                                                                      rbase, rcount, hdr, nullptr, nullptr, 0,
+                                                                      nullptr);
+            bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, piece, pstart, pblock, max_pieces, hdr,
+                                                    (u64)capacity);
+        }
+        if (capacity > 0) {
+            ProfScope prof("bin_emit", stream);
+            auto emit = piece ? bin_emit_kernel<true, false> : bin_emit_kernel<false, false>;
+            emit<<<grid + max_pieces, kBinThreads, 0, stream>>>(
+                total, (int)n, sp, order, tx, ty, cfg.tile, wrap, rb, V, nb, piece, max_pieces, vis_start, bsums,
+                boffs, pstart, pblock, hdr, rows, rbase, rcount, reinterpret_cast<u64*>(keys), (u64)capacity, nullptr,
+                nullptr, nullptr, 0, nullptr);
+        }
+        return cudaGetLastError();
+    }
+    // bucketed: instances go to their (view, tile row) bucket in the spare buffer; omnigs_sort orders each bucket
+    // by column into keys
+    u64* rows = reinterpret_cast<u64*>(ws + L.rows);
+    unsigned* rows_off = reinterpret_cast<unsigned*>(ws + L.rows_off);
+    unsigned* bcounts = reinterpret_cast<unsigned*>(ws + L.bkt_counts);
+    u64* btotal = reinterpret_cast<u64*>(ws + L.bkt_total);
+    u64* bbase = reinterpret_cast<u64*>(ws + L.bkt_base);
+    u64* beff = reinterpret_cast<u64*>(ws + L.bkt_eff);
+    unsigned* cstart = reinterpret_cast<unsigned*>(ws + L.col_start);
+    unsigned* unstored = reinterpret_cast<unsigned*>(ws + L.unstored_list);
+    const int nbkt = V * ty;
+    const int nbv = (int)blocks_per_view_max(n);
+    e = cudaMemsetAsync(bcounts, 0, sizeof(unsigned) * (size_t)nbkt * nbv, stream);
+    if (e != cudaSuccess) return e;
     {
-        ProfScope prof("bin_count", stream, 2);
-        bin_count_kernel<<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb,
-                                                           vis_start, bsums, rows, (u64)capacity, rbase, rcount,
-                                                           hdr);
+        ProfScope prof("bin_count", stream, 4);
+        bin_count_kernel<true><<<grid, kBinThreads, 0, stream>>>(total, sp, order, tx, ty, cfg.tile, wrap, V, n, nb,
+                                                                 vis_start, bsums, rows, (u64)L.row_cap, rbase, rcount,
+                                                                 hdr, rows_off, bcounts, nbv, unstored);
         bin_scan_kernel<<<1, 1024, 0, stream>>>((int)nb, bsums, boffs, piece, pstart, pblock, max_pieces, hdr,
                                                 (u64)capacity);
+        bucket_scan_kernel<<<nbkt, 256, 0, stream>>>(ty, n, nbv, bcounts, btotal);
+        bucket_base_kernel<<<1, 1024, 0, stream>>>(nbkt, btotal, bbase, beff, cstart, (u64)capacity);
     }
     if (capacity > 0) {
-        ProfScope prof("bin_emit", stream);
-        auto emit = piece ? bin_emit_kernel<true> : bin_emit_kernel<false>;
-        emit<<<grid + max_pieces, kBinThreads, 0, stream>>>(
-            total, (int)n, sp, order, tx, ty, cfg.tile, wrap, rank_bits_for(n), V, nb, piece, max_pieces, vis_start,
-            bsums, boffs, pstart, pblock, hdr, rows, rbase, rcount, reinterpret_cast<u64*>(keys), (u64)capacity);
+        ProfScope prof("bin_emit", stream, 2);
+        u64* out = reinterpret_cast<u64*>(ws + L.alt_keys);
+        auto emit = piece ? bin_emit_stored_kernel<true> : bin_emit_stored_kernel<false>;
+        emit<<<grid + max_pieces, kBinThreads, 0, stream>>>((int)n, tx, ty, rb, V, nb, piece, max_pieces, bsums, boffs,
+                                                            pstart, pblock, hdr, rows, rows_off, rbase, rcount, bcounts,
+                                                            bbase, nbv, out, (u64)capacity);
+        // the blocks whose row items did not fit: derived again and ranked here, a few CTAs taking them in turn
+        const unsigned fb_grid = std::min<unsigned>(nb, (unsigned)num_sms() * 2);
+        bin_emit_kernel<false, true><<<fb_grid, kBinThreads, 0, stream>>>(
+            total, (int)n, sp, order, tx, ty, cfg.tile, wrap, rb, V, nb, 0u, 0u, vis_start, bsums, boffs, pstart,
+            pblock, hdr, rows, rbase, rcount, out, (u64)capacity, rows_off, bcounts, bbase, nbv, unstored);
     }
     return cudaGetLastError();
 }
@@ -996,6 +1576,33 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
     cudaError_t e;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
     u64* alt = reinterpret_cast<u64*>(ws + L.alt_keys);
+    if (bucketed_binning(cfg, n)) {
+        // one counting pass by tile column within every (view, tile row) bucket, from the spare buffer into keys
+        const int tx = cfg.width / cfg.tile, nbkt = cfg.num_views * (cfg.height / cfg.tile), rb = rank_bits_for(n);
+        const u64* bbase = reinterpret_cast<const u64*>(ws + L.bkt_base);
+        const u64* beff = reinterpret_cast<const u64*>(ws + L.bkt_eff);
+        const unsigned* cstart = reinterpret_cast<const unsigned*>(ws + L.col_start);
+        unsigned* chist = reinterpret_cast<unsigned*>(ws + L.col_hist);
+        const unsigned chunks = (unsigned)((u64)capacity / kColChunk + nbkt + 1);
+        const size_t smem = sizeof(u64) * kSortTile + sizeof(unsigned) * (kWarps * kHistRow + 2 * kRadixMax + 32);
+        e = cudaFuncSetAttribute(col_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope prof("tile_count", stream);
+            col_count_kernel<<<chunks, kSortThreads, 0, stream>>>(alt, bbase, beff, cstart, nbkt, tx, rb, chist, hdr);
+        }
+        {
+            ProfScope prof("tile_ranges", stream);
+            col_scan_kernel<<<nbkt, kMaxBucketCols, 0, stream>>>(bbase, cstart, tx, chist, ranges);
+        }
+        {
+            ProfScope prof("tile_scatter", stream);
+            col_scatter_kernel<<<chunks, kSortThreads, smem, stream>>>(alt, reinterpret_cast<u64*>(keys), bbase, beff,
+                                                                       cstart, nbkt, tx, std::max(1, ceil_log2(tx)),
+                                                                       rb, chist, (u64)capacity, hdr);
+        }
+        return cudaGetLastError();
+    }
     unsigned* hist = reinterpret_cast<unsigned*>(ws + L.hist);
     e = lsd_sort<false>(reinterpret_cast<u64*>(keys), nullptr, alt, nullptr, &hdr->count, (u64)capacity,
                         rank_bits_for(n), tile_key_bits(cfg), sort_grid((u64)capacity), hist, stream, "sort_upsweep",

@@ -20,6 +20,7 @@ constexpr float kPoleGuard = 1e-6f;      // rho is kept >= 1e-6 t_r inside J
 constexpr int kMaxRadius = 65535;        // instance-box half-extents are stored in 16 bits
 
 constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrConsistency = 2u;  // a device-side consistency check failed (the access was skipped)
 
 // Workspace header (first 256 bytes of every workspace).
 struct WsHeader {
@@ -28,7 +29,7 @@ struct WsHeader {
     unsigned int error;              // sticky device-side error bits
     unsigned int extra_pieces;       // bin_emit CTAs beyond one per block (blocks with many instances)
     float loss;
-    unsigned int pad1;
+    unsigned int unstored;           // blocks whose row items did not fit the rows region (bucketed order)
     unsigned long long rows_used;    // row items bin_count has stored for bin_emit
 };
 
@@ -69,7 +70,11 @@ __device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_
 // n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
     size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
-        block_offsets, piece_start, piece_block, row_base, row_count, vis_sums, vis_start, vis_mask, total;
+        block_offsets, piece_start, piece_block, row_base, row_count, vis_sums, vis_start, vis_mask,
+        // bucketed instance order (see bucketed_binning): stored row words and their bucket offsets, per-block
+        // bucket counts, bucket totals and bases, chunk starts and the column pass's per-chunk histograms
+        rows, rows_off, bkt_counts, bkt_total, bkt_base, bkt_eff, col_start, col_hist, unstored_list, total;
+    size_t row_cap;  // row words the rows region holds
     int loss_blocks;
 };
 
@@ -83,11 +88,24 @@ constexpr int kVisPerThread = 4;                      // slots per thread of the
 constexpr int kVisSlots = kBinThreads * kVisPerThread;
 constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
 constexpr int kSortCtasPerSm = 12;   // radix-sort grid: up to this many CTAs per SM
+constexpr int kMaxBucketRows = 128;  // tile rows per view of the bucketed instance order
+constexpr int kMaxBucketCols = 256;  // tile columns per view of its column pass (digits of at most 8 bits)
+constexpr int kColChunk = 4096;      // keys per CTA of the column pass
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocks = 1024;
 
 int num_sms();
 WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
+
+// Whether omnigs_bin emits the instances bucketed by (view, tile row), so that omnigs_sort orders them with one
+// counting pass over the tile column within each bucket (instead of a radix sort over all tile-key bits): when every
+// CTA of 256 consecutive splats of the (view, depth) order spans at most two views (n >= 256) and a view has at most
+// kMaxBucketRows tile rows and kMaxBucketCols tile columns.
+inline bool bucketed_binning(const omnigs_config &cfg, int64_t n) {
+    return n >= kBinSplats && cfg.height / cfg.tile <= kMaxBucketRows && cfg.width / cfg.tile <= kMaxBucketCols;
+}
+// Blocks of 256 positions a view's splats can share: its own, plus one straddling the next view.
+inline int64_t blocks_per_view_max(int64_t n) { return (n + kBinSplats - 1) / kBinSplats + 1; }
 int rank_bits_for(int64_t n);
 
 // Whether a configuration is one every entry point accepts (image shape, tile, views, SH degree, camera, schedule).

@@ -45,6 +45,20 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.vis_sums = off;       off += align256(sizeof(unsigned) * nbv * cfg.num_views);
     L.vis_start = off;      off += align256(sizeof(unsigned) * ((size_t)cfg.num_views + 1));
     L.vis_mask = off;       off += align256(sizeof(unsigned) * (kVisSlots / 32) * nbv * cfg.num_views);
+    // bucketed instance order: row words in their own region (the emission fills alt_keys)
+    const bool bk = bucketed_binning(cfg, n);
+    const size_t nbkt = bk ? (size_t)cfg.num_views * (cfg.height / cfg.tile) : 0;
+    const size_t chunks = bk ? (size_t)capacity / kColChunk + nbkt + 1 : 0;
+    L.row_cap = bk ? (size_t)capacity / 2 + 1 : 0;
+    L.rows = off;           off += align256(sizeof(unsigned long long) * L.row_cap);
+    L.rows_off = off;       off += align256(sizeof(unsigned) * L.row_cap);
+    L.bkt_counts = off;     off += align256(sizeof(unsigned) * nbkt * (bk ? blocks_per_view_max(n) : 0));
+    L.bkt_total = off;      off += align256(sizeof(unsigned long long) * nbkt);
+    L.bkt_base = off;       off += align256(sizeof(unsigned long long) * nbkt);
+    L.bkt_eff = off;        off += align256(sizeof(unsigned long long) * nbkt);
+    L.col_start = off;      off += align256(sizeof(unsigned) * (nbkt + 1));
+    L.col_hist = off;       off += align256(sizeof(unsigned) * chunks * (bk ? cfg.width / cfg.tile : 0));
+    L.unstored_list = off;  off += align256(sizeof(unsigned) * (bk ? nb : 0));
     L.total = off;
     return L;
 }
@@ -357,6 +371,7 @@ omnigs_status omnigs_last_error(void* workspace, omnigs_stream_t stream) {
                         (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (h.error & kErrCapacity) return OMNIGS_E_CAPACITY;
+    if (h.error & kErrConsistency) return OMNIGS_E_CUDA;
     return OMNIGS_E_TIMEOUT;
 }
 

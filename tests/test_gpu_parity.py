@@ -78,11 +78,14 @@ def test_preprocess_matches_oracle(deg):
 
 @pytest.mark.parametrize("tile,V,n,W,H", [(16, 2, 3000, 256, 128), (8, 1, 1500, 256, 128), (32, 3, 1000, 256, 128),
                                          (16, 1, 60000, 512, 256), (8, 2, 20000, 128, 64),
-                                         (16, 4096, 300, 64, 32)])
+                                         (16, 4096, 300, 64, 32), (16, 2, 3000, 4096, 64), (16, 2, 3000, 64, 2304),
+                                         (8, 3, 200, 256, 128)])
 def test_bin_sort_valid(tile, V, n, W, H):
     """Includes lists longer than one shared-memory chunk (sorted in chunks and merged) and many depth ties. With
     4096 views of 300 splats the (view, depth, splat index) key needs 12 + 32 + 21 bits, so the depth sort carries
-    the index as a value instead of inside the key."""
+    the index as a value instead of inside the key. 4096 x 64 px on 16 px tiles has the most tile columns (256) of
+    the instance order bucketed by (view, tile row); 64 x 2304 px (144 tile rows) and 200 splats a view (a 256-splat
+    block spans three views) take the radix sort over all tile-key bits instead."""
     sp = synth.random_splats(V, n, W, H, seed=100 + tile, max_radius=30)
     packed = pack_splats(sp)
     s = _settings(W, H, tile=tile, V=V)

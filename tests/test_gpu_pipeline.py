@@ -173,7 +173,18 @@ def test_profiler_collects_kernel_times():
     finally:
         C.omnigs_profiler_enable(False)
     names = {t[0] for t in times}
-    for k in ["preprocess_fwd", "depth_keys", "depth_sort", "bin_count", "bin_emit", "sort_upsweep",
-              "sort_downsweep", "tile_ranges", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd"]:
+    # 1000 splats (a 256-splat block spans two views at most) and 8 x 4 tiles: the bucketed order
+    for k in ["preprocess_fwd", "depth_keys", "depth_sort", "bin_count", "bin_emit", "tile_count", "tile_scatter",
+              "tile_ranges", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd"]:
         assert k in names, k
     assert all(t[2] >= 0 for t in times)
+    # fewer than 256 splats: the radix sort over the tile bits
+    r = og.Rasterizer(_settings(W, H))
+    C.omnigs_profiler_enable(True)
+    try:
+        r.forward(*scene_to_device(synth.shell_scene(200, seed=6)), dev(synth.identity_viewmats(1)))
+        torch.cuda.synchronize()
+        names = {t[0] for t in C.omnigs_profiler_collect()}
+    finally:
+        C.omnigs_profiler_enable(False)
+    assert {"sort_upsweep", "sort_downsweep", "tile_ranges"} <= names and "tile_scatter" not in names
