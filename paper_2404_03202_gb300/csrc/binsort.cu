@@ -9,14 +9,22 @@
 //      key. Pinhole views rank only the splats they can see (a compaction first).
 //   2. bin_count / bin_scan / bin_emit walk the splats in depth order (through `order`), 256 per CTA: bin_count
 //      derives the kept columns of every box row (the row culling) and stores the rows, bin_scan takes a 64-bit
-//      exclusive scan of the per-CTA counts (overflow checked against the capacity), and bin_emit writes one key per
-//      instance, ((v * TILES + tile) << rank_bits) | rank, from the stored rows, each chunk's slots in order through
-//      a load-balanced search. The emitted stream is therefore already ordered by rank within every tile.
-//   3. A stable LSD radix sort of the instance keys over the tile bits only (ceil(log2(V * TILES)) bits above the
-//      rank, 2 passes of <= 9 bits: upsweep per-CTA digit counts; two small scans; downsweep with stable in-CTA
-//      ranking (the lanes sharing a digit by one ballot per digit bit), staging in shared memory in digit order, runs
-//      of equal digits written to HBM). The keys carry no payload: the splat is order[v * N + rank].
+//      exclusive scan of the per-CTA counts (overflow checked against the capacity), and bin_emit writes one entry
+//      per instance from the stored rows, each chunk's slots in order through a load-balanced search.
+//   Bucketed order (the usual case, see bucketed_binning):
+//   3. bin_count also ranks every row item within its (view, tile row) bucket among the CTA's items; small scans give
+//      each bucket its base and each CTA its offset in the bucket, and bin_emit writes every instance straight to its
+//      bucket as a 32-bit entry (tx << rank_bits) | rank. Every bucket is then in rank order.
+//   4. omnigs_sort: one stable counting pass by tile column within every bucket (tile_count: per-chunk column counts;
+//      tile_ranges: their scans, which are also the tile ranges; tile_scatter: in-CTA stable ranking by column, the
+//      lanes sharing a column found by ballots, written out as keys ((v * TILES + tile) << rank_bits) | rank).
+//   Otherwise:
+//   3. bin_emit writes the keys ((v * TILES + tile) << rank_bits) | rank in generation order, already in rank order
+//      within every tile, and a stable LSD radix sort orders them over the tile bits only (ceil(log2(V * TILES))
+//      bits above the rank, 2 passes of <= 9 bits: upsweep per-CTA digit counts; two small scans; downsweep with
+//      stable in-CTA ranking, staging in shared memory in digit order, runs of equal digits written to HBM).
 //   4. tile_ranges: [start, end) of every tile by binary search in the sorted keys.
+// The keys carry no payload: the splat is order[v * N + rank].
 // No pass waits on another CTA, so there are no spin loops.
 #include <algorithm>
 
@@ -647,7 +655,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const u64* __restrict__ block_offsets, const unsigned* __restrict__ piece_start,
                 const unsigned* __restrict__ piece_block, const WsHeader* __restrict__ hdr,
                 const u64* __restrict__ rows, const unsigned* __restrict__ row_base,
-                const unsigned* __restrict__ row_count, u64* __restrict__ keys, u64 capacity,
+                const unsigned* __restrict__ row_count, void* __restrict__ keys_out, u64 capacity,
                 const unsigned* __restrict__ rows_off, const unsigned* __restrict__ bkt_offsets,
                 const u64* __restrict__ bkt_base, int nbv, const unsigned* __restrict__ fallback_list) {
     __shared__ unsigned scratch[32];
@@ -739,7 +747,7 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
                 const int64_t v = j < next_view ? v0 : v0 + 1;
                 const unsigned rank = (unsigned)(p0 + j - v * n);
                 const unsigned tb = (unsigned)v * (unsigned)(tiles_x * tiles_y) + (unsigned)(ty * tiles_x);
-                key0[k] = ((u64)tb << rank_bits) | (u64)rank;
+                key0[k] = kBuckets ? (u64)rank : ((u64)tb << rank_bits) | (u64)rank;  // a bucket entry: no tile bits
                 if constexpr (kBuckets) {
                     bl[k] = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
                     boff[k] = stored ? __ldg(rows_off + (u64)rbase + ri) : 0u;
@@ -793,10 +801,14 @@ bin_emit_kernel(int64_t total, int n, const float4* __restrict__ splats, const u
             // a box narrower than the image has columns in (-tiles_x, 2 tiles_x): one wrap at most
             int tx = E.cl[i] + (int)(sl - E.off[i]);
             tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
-            u64 at;
-            if constexpr (kBuckets) at = EB.pos[i] + (sl - E.off[i]);
-            else at = out + sl;
-            if (at < capacity) keys[at] = E.key0[i] + ((u64)tx << rank_bits);
+            if constexpr (kBuckets) {
+                const u64 at = EB.pos[i] + (sl - E.off[i]);
+                if (at < capacity)
+                    static_cast<unsigned*>(keys_out)[at] = (unsigned)E.key0[i] | ((unsigned)tx << rank_bits);
+            } else {
+                const u64 at = out + sl;
+                if (at < capacity) static_cast<u64*>(keys_out)[at] = E.key0[i] + ((u64)tx << rank_bits);
+            }
         }
         __syncthreads();
         out += chunk_total;
@@ -824,12 +836,12 @@ bin_emit_stored_kernel(int n, int tiles_x, int tiles_y, int rank_bits, int V, un
                        const u64* __restrict__ rows, const unsigned* __restrict__ rows_off,
                        const unsigned* __restrict__ row_base, const unsigned* __restrict__ row_count,
                        const unsigned* __restrict__ bkt_offsets, const u64* __restrict__ bkt_base, int nbv,
-                       u64* __restrict__ keys, u64 capacity) {
+                       unsigned* __restrict__ entries, u64 capacity) {
     __shared__ unsigned scratch[32];
     __shared__ struct {
         unsigned off[kRowChunk];  // output slot of each row item of the chunk, relative to the chunk
         int cl[kRowChunk];        // its first column
-        u64 key0[kRowChunk];      // key of its first column, before the column wrap
+        unsigned rank[kRowChunk];  // its splat's depth rank
         u64 pos[kRowChunk];       // output position of its first instance
     } E;
     __shared__ u64 s_bpos[kBucketSlots];
@@ -877,10 +889,8 @@ bin_emit_stored_kernel(int n, int tiles_x, int tiles_y, int rank_bits, int V, un
                 const int ty = (int)((w >> 32) & 0xffffu), j = (int)(w >> 48);
                 cnt[k] = (unsigned)(w >> 16) & 0xffffu;
                 const int64_t v = j < next_view ? v0 : v0 + 1;
-                const unsigned rank = (unsigned)(p0 + j - v * n);
-                const unsigned tb = (unsigned)v * (unsigned)(tiles_x * tiles_y) + (unsigned)(ty * tiles_x);
                 E.cl[i] = cl;
-                E.key0[i] = ((u64)tb << rank_bits) | (u64)rank;
+                E.rank[i] = (unsigned)(p0 + j - v * n);
                 E.pos[i] = s_bpos[(j < next_view ? 0 : tiles_y) + ty] + __ldg(rows_off + (u64)rbase + ri);
             }
             local += cnt[k];
@@ -911,7 +921,7 @@ bin_emit_stored_kernel(int n, int tiles_x, int tiles_y, int rank_bits, int V, un
             int tx = E.cl[i] + (int)(sl - E.off[i]);
             tx += tx < 0 ? tiles_x : (tx >= tiles_x ? -tiles_x : 0);
             const u64 at = E.pos[i] + (sl - E.off[i]);
-            if (at < capacity) keys[at] = E.key0[i] + ((u64)tx << rank_bits);
+            if (at < capacity) entries[at] = E.rank[i] | ((unsigned)tx << rank_bits);
         }
         __syncthreads();
         out += chunk_total;
@@ -1208,10 +1218,10 @@ __device__ __forceinline__ int chunk_bucket(const unsigned* __restrict__ col_sta
     return lo;
 }
 
-// Column of every key of chunk c: hist[c][tx] (one CTA per chunk; CTAs past the last chunk return). Every key of a
-// bucket b = v * tiles_y + ty has tile key b * tiles_x + tx.
+// Column count of chunk c: hist[c][tx] (one CTA per chunk; CTAs past the last chunk return). A bucket entry is
+// (tx << rank_bits) | depth rank; its bucket b = v * tiles_y + ty gives the rest of the tile key, b * tiles_x + tx.
 __global__ void __launch_bounds__(kSortThreads)
-col_count_kernel(const u64* __restrict__ keys, const u64* __restrict__ base, const u64* __restrict__ eff,
+col_count_kernel(const unsigned* __restrict__ entries, const u64* __restrict__ base, const u64* __restrict__ eff,
                  const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int rank_bits,
                  unsigned* __restrict__ hist, WsHeader* __restrict__ hdr) {
     __shared__ unsigned s_h[kMaxBucketCols];
@@ -1220,20 +1230,19 @@ col_count_kernel(const u64* __restrict__ keys, const u64* __restrict__ base, con
     const int b = chunk_bucket(col_start, nbkt, c);
     const u64 beg = base[b] + (u64)(c - col_start[b]) * kColChunk;
     const u64 end = min(beg + kColChunk, base[b] + eff[b]);
-    const u64 tile0 = (u64)b * tiles_x;
     for (int d = threadIdx.x; d < tiles_x; d += kSortThreads) s_h[d] = 0u;
     __syncthreads();
-    u64 k[kSortItems];  // all loads in flight before the counting
+    unsigned k[kSortItems];  // all loads in flight before the counting
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const u64 i = beg + threadIdx.x + (u64)j * kSortThreads;
-        k[j] = i < end ? __ldg(keys + i) : (tile0 << rank_bits);
+        k[j] = i < end ? __ldg(entries + i) : 0u;
     }
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         if (beg + threadIdx.x + (u64)j * kSortThreads >= end) break;
-        const u64 d = (k[j] >> rank_bits) - tile0;
-        if (d < (u64)tiles_x) atomicAdd(&s_h[(unsigned)d], 1u);
+        const unsigned d = k[j] >> rank_bits;
+        if (d < (unsigned)tiles_x) atomicAdd(&s_h[d], 1u);
         else atomicOr(&hdr->error, kErrConsistency);  // a key outside its bucket: not counted
     }
     __syncthreads();
@@ -1267,17 +1276,17 @@ col_scan_kernel(const u64* __restrict__ base, const unsigned* __restrict__ col_s
     ranges[2 * t + 1] = run ? first + run : 0u;
 }
 
-// Chunk c of a bucket, ordered by column and written to its final positions (one CTA per chunk): the keys are ranked
-// stably by column within each warp (the lanes sharing a column from one ballot per column bit, a padding column for
-// missing keys included), the warps' counts are combined in warp order, the keys are placed in column order in
-// shared memory, and each is written to hist[c][tx] + its rank within its column.
-__global__ void __launch_bounds__(kSortThreads, 3)
-col_scatter_kernel(const u64* __restrict__ keys_in, u64* __restrict__ keys_out, const u64* __restrict__ base,
+// Chunk c of a bucket, ordered by column and written to its final positions as tile keys (one CTA per chunk): the
+// entries are ranked stably by column within each warp (the lanes sharing a column found by one ballot per column
+// bit, a padding column for missing entries included), the warps' counts are combined in warp order, the entries are placed in
+// column order in shared memory, and each is written to hist[c][tx] + its rank within its column.
+__global__ void __launch_bounds__(kSortThreads, 4)
+col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_out, const u64* __restrict__ base,
                    const u64* __restrict__ eff, const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int dbits,
                    int rank_bits, const unsigned* __restrict__ hist, u64 capacity, WsHeader* __restrict__ hdr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    u64* s_keys = reinterpret_cast<u64*>(smem_raw);
-    unsigned* s_whist = reinterpret_cast<unsigned*>(s_keys + kSortTile);  // [kWarps][kHistRow]
+    unsigned* s_ent = reinterpret_cast<unsigned*>(smem_raw);
+    unsigned* s_whist = s_ent + kSortTile;  // [kWarps][kHistRow]
     unsigned* s_start = s_whist + kWarps * kHistRow;
     unsigned* s_tot = s_start + kRadixMax;
     unsigned* s_scratch = s_tot + kRadixMax;
@@ -1288,21 +1297,20 @@ col_scatter_kernel(const u64* __restrict__ keys_in, u64* __restrict__ keys_out, 
     const u64 beg = base[b] + (u64)(c - col_start[b]) * kColChunk;
     const unsigned cnt = (unsigned)(min(beg + kColChunk, base[b] + eff[b]) - beg);
     const u64 tile0 = (u64)b * tiles_x;
-    const unsigned R = 1u << dbits;
+    const unsigned R = 1u << dbits, rank_mask = (1u << rank_bits) - 1u;
     const unsigned tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     const unsigned lt_mask = (1u << lane) - 1u;
     unsigned* my_hist = s_whist + warp * kHistRow;
     for (unsigned d = lane; d <= R; d += 32) my_hist[d] = 0;
     __syncwarp();
     const unsigned base_i = warp * (kSortItems * 32) + lane;
-    u64 k[kSortItems];
-    unsigned rk[kSortItems], dg[kSortItems];
+    unsigned k[kSortItems], rk[kSortItems], dg[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const unsigned idx = base_i + j * 32;
-        k[j] = idx < cnt ? __ldg(keys_in + beg + idx) : 0ull;
-        const u64 d = (k[j] >> rank_bits) - tile0;
-        dg[j] = idx < cnt && d < (u64)tiles_x ? (unsigned)d : R;  // a key outside its bucket is left out
+        k[j] = idx < cnt ? __ldg(entries + beg + idx) : 0u;
+        const unsigned d = k[j] >> rank_bits;
+        dg[j] = idx < cnt && d < (unsigned)tiles_x ? d : R;  // an entry outside its bucket's columns is left out
     }
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
@@ -1351,16 +1359,15 @@ col_scatter_kernel(const u64* __restrict__ keys_in, u64* __restrict__ keys_out, 
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j)
-        if (dg[j] < R) s_keys[s_start[dg[j]] + my_hist[dg[j]] + rk[j]] = k[j];
+        if (dg[j] < R) s_ent[s_start[dg[j]] + my_hist[dg[j]] + rk[j]] = k[j];
     __syncthreads();
-    const unsigned placed = s_start[R - 1] + s_tot[R - 1];  // keys with a column (all, unless one was left out)
+    const unsigned placed = s_start[R - 1] + s_tot[R - 1];  // entries with a column (all, unless one was left out)
     if (tid == 0 && placed != cnt) atomicOr(&hdr->error, kErrConsistency);
     const unsigned* h = hist + (size_t)c * tiles_x;
     for (unsigned i = tid; i < placed; i += kSortThreads) {
-        const u64 key = s_keys[i];
-        const unsigned d = (unsigned)((key >> rank_bits) - tile0);
+        const unsigned e = s_ent[i], d = e >> rank_bits;
         const u64 at = (u64)__ldg(h + d) + (i - s_start[d]);
-        if (at < capacity) keys_out[at] = key;
+        if (at < capacity) keys_out[at] = ((tile0 + d) << rank_bits) | (u64)(e & rank_mask);
     }
 }
 
@@ -1529,8 +1536,8 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
         }
         return cudaGetLastError();
     }
-    // bucketed: instances go to their (view, tile row) bucket in the spare buffer; omnigs_sort orders each bucket
-    // by column into keys
+    // bucketed: instances go to their (view, tile row) bucket in the spare buffer, as 32-bit entries; omnigs_sort
+    // orders each bucket by column into keys
     u64* rows = reinterpret_cast<u64*>(ws + L.rows);
     unsigned* rows_off = reinterpret_cast<unsigned*>(ws + L.rows_off);
     unsigned* bcounts = reinterpret_cast<unsigned*>(ws + L.bkt_counts);
@@ -1555,7 +1562,7 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     }
     if (capacity > 0) {
         ProfScope prof("bin_emit", stream, 2);
-        u64* out = reinterpret_cast<u64*>(ws + L.alt_keys);
+        unsigned* out = reinterpret_cast<unsigned*>(ws + L.alt_keys);  // bucket entries, 32 bits
         auto emit = piece ? bin_emit_stored_kernel<true> : bin_emit_stored_kernel<false>;
         emit<<<grid + max_pieces, kBinThreads, 0, stream>>>((int)n, tx, ty, rb, V, nb, piece, max_pieces, bsums, boffs,
                                                             pstart, pblock, hdr, rows, rows_off, rbase, rcount, bcounts,
@@ -1584,12 +1591,13 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
         const unsigned* cstart = reinterpret_cast<const unsigned*>(ws + L.col_start);
         unsigned* chist = reinterpret_cast<unsigned*>(ws + L.col_hist);
         const unsigned chunks = (unsigned)((u64)capacity / kColChunk + nbkt + 1);
-        const size_t smem = sizeof(u64) * kSortTile + sizeof(unsigned) * (kWarps * kHistRow + 2 * kRadixMax + 32);
+        const unsigned* ent = reinterpret_cast<const unsigned*>(ws + L.alt_keys);
+        const size_t smem = sizeof(unsigned) * (kSortTile + kWarps * kHistRow + 2 * kRadixMax + 32);
         e = cudaFuncSetAttribute(col_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         {
             ProfScope prof("tile_count", stream);
-            col_count_kernel<<<chunks, kSortThreads, 0, stream>>>(alt, bbase, beff, cstart, nbkt, tx, rb, chist, hdr);
+            col_count_kernel<<<chunks, kSortThreads, 0, stream>>>(ent, bbase, beff, cstart, nbkt, tx, rb, chist, hdr);
         }
         {
             ProfScope prof("tile_ranges", stream);
@@ -1597,7 +1605,7 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
         }
         {
             ProfScope prof("tile_scatter", stream);
-            col_scatter_kernel<<<chunks, kSortThreads, smem, stream>>>(alt, reinterpret_cast<u64*>(keys), bbase, beff,
+            col_scatter_kernel<<<chunks, kSortThreads, smem, stream>>>(ent, reinterpret_cast<u64*>(keys), bbase, beff,
                                                                        cstart, nbkt, tx, std::max(1, ceil_log2(tx)),
                                                                        rb, chist, (u64)capacity, hdr);
         }

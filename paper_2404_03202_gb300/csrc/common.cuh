@@ -90,7 +90,8 @@ constexpr int kRadixMax = 512;       // radix-sort digits of up to 9 bits
 constexpr int kSortCtasPerSm = 12;   // radix-sort grid: up to this many CTAs per SM
 constexpr int kMaxBucketRows = 128;  // tile rows per view of the bucketed instance order
 constexpr int kMaxBucketCols = 256;  // tile columns per view of its column pass (digits of at most 8 bits)
-constexpr int kColChunk = 4096;      // keys per CTA of the column pass
+constexpr int kColChunk = 4096;        // keys per CTA of the column pass
+constexpr int kBucketRankBitsMax = 24;  // bucket entries: 8 tile-column bits + up to 24 rank bits
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocks = 1024;
 
@@ -99,14 +100,16 @@ WsLayout ws_layout(const omnigs_config &cfg, int64_t n, int64_t capacity);
 
 // Whether omnigs_bin emits the instances bucketed by (view, tile row), so that omnigs_sort orders them with one
 // counting pass over the tile column within each bucket (instead of a radix sort over all tile-key bits): when every
-// CTA of 256 consecutive splats of the (view, depth) order spans at most two views (n >= 256) and a view has at most
-// kMaxBucketRows tile rows and kMaxBucketCols tile columns.
+// CTA of 256 consecutive splats of the (view, depth) order spans at most two views (n >= 256), a view has at most
+// kMaxBucketRows tile rows and kMaxBucketCols tile columns, and a bucket entry (tile column << rank bits | depth rank)
+// fits 32 bits (n <= 2^24).
+int rank_bits_for(int64_t n);
 inline bool bucketed_binning(const omnigs_config &cfg, int64_t n) {
-    return n >= kBinSplats && cfg.height / cfg.tile <= kMaxBucketRows && cfg.width / cfg.tile <= kMaxBucketCols;
+    return n >= kBinSplats && n <= (int64_t(1) << kBucketRankBitsMax) && cfg.height / cfg.tile <= kMaxBucketRows &&
+           cfg.width / cfg.tile <= kMaxBucketCols;
 }
 // Blocks of 256 positions a view's splats can share: its own, plus one straddling the next view.
 inline int64_t blocks_per_view_max(int64_t n) { return (n + kBinSplats - 1) / kBinSplats + 1; }
-int rank_bits_for(int64_t n);
 
 // Whether a configuration is one every entry point accepts (image shape, tile, views, SH degree, camera, schedule).
 bool valid_cfg(const omnigs_config *c);

@@ -30,7 +30,8 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.header = off;         off += align256(sizeof(WsHeader));
     L.loss_partials = off;  off += align256(sizeof(float) * L.loss_blocks);
     L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * ((size_t)num_sms() * kSortCtasPerSm + 1));
-    L.alt_keys = off;       off += align256(sizeof(unsigned long long) * (size_t)capacity);
+    const bool bk = bucketed_binning(cfg, n);  // bucket entries are 32 bits, radix-sort keys 64
+    L.alt_keys = off;       off += align256((bk ? sizeof(unsigned) : sizeof(unsigned long long)) * (size_t)capacity);
     L.depth_keys = off;     off += align256(sizeof(unsigned long long) * total);
     L.depth_keys_alt = off; off += align256(sizeof(unsigned long long) * total);
     L.depth_vals_alt = off; off += align256(sizeof(uint32_t) * total);
@@ -46,7 +47,6 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.vis_start = off;      off += align256(sizeof(unsigned) * ((size_t)cfg.num_views + 1));
     L.vis_mask = off;       off += align256(sizeof(unsigned) * (kVisSlots / 32) * nbv * cfg.num_views);
     // bucketed instance order: row words in their own region (the emission fills alt_keys)
-    const bool bk = bucketed_binning(cfg, n);
     const size_t nbkt = bk ? (size_t)cfg.num_views * (cfg.height / cfg.tile) : 0;
     const size_t chunks = bk ? (size_t)capacity / kColChunk + nbkt + 1 : 0;
     L.row_cap = bk ? (size_t)capacity / 2 + 1 : 0;
