@@ -1251,7 +1251,11 @@ col_count_kernel(const unsigned* __restrict__ entries, const u64* __restrict__ b
 
 // Per bucket (one CTA, thread tx per column): exclusive scan over the bucket's chunks of hist[.][tx], then over the
 // columns of their totals; hist[c][tx] becomes the output position of chunk c's first key of column tx, and the tile
-// ranges of the bucket's tiles are written ([0, 0) for an empty tile).
+// ranges of the bucket's tiles are written ([0, 0) for an empty tile). The chunk counts are read kScanBatch at a time,
+// all in flight together: a bucket has tens of chunks, and one dependent load after another would take a memory
+// latency each.
+constexpr int kScanBatch = 16;
+
 __global__ void __launch_bounds__(kMaxBucketCols)
 col_scan_kernel(const u64* __restrict__ base, const unsigned* __restrict__ col_start, int tiles_x,
                 unsigned* __restrict__ hist, uint32_t* __restrict__ ranges) {
@@ -1259,18 +1263,31 @@ col_scan_kernel(const u64* __restrict__ base, const unsigned* __restrict__ col_s
     const int b = blockIdx.x;
     const unsigned c0 = col_start[b], c1 = col_start[b + 1];
     const int tx = threadIdx.x;
+    const bool col = tx < tiles_x;
     unsigned run = 0;
-    if (tx < tiles_x)
-        for (unsigned c = c0; c < c1; ++c) {
-            const unsigned h = hist[(size_t)c * tiles_x + tx];
-            hist[(size_t)c * tiles_x + tx] = run;
-            run += h;
+    if (col)
+        for (unsigned c = c0; c < c1; c += kScanBatch) {
+            unsigned h[kScanBatch];
+#pragma unroll
+            for (int q = 0; q < kScanBatch; ++q) h[q] = c + q < c1 ? hist[(size_t)(c + q) * tiles_x + tx] : 0u;
+#pragma unroll
+            for (int q = 0; q < kScanBatch; ++q) run += h[q];
         }
     unsigned tot;
-    const unsigned start = block_exclusive_scan<unsigned>(tx < tiles_x ? run : 0u, scratch, &tot);
-    if (tx >= tiles_x) return;
+    const unsigned start = block_exclusive_scan<unsigned>(col ? run : 0u, scratch, &tot);
+    if (!col) return;
     const unsigned first = (unsigned)base[b] + start;
-    for (unsigned c = c0; c < c1; ++c) hist[(size_t)c * tiles_x + tx] += first;
+    unsigned at = first;
+    for (unsigned c = c0; c < c1; c += kScanBatch) {
+        unsigned h[kScanBatch];
+#pragma unroll
+        for (int q = 0; q < kScanBatch; ++q) h[q] = c + q < c1 ? hist[(size_t)(c + q) * tiles_x + tx] : 0u;
+#pragma unroll
+        for (int q = 0; q < kScanBatch; ++q) {
+            if (c + q < c1) hist[(size_t)(c + q) * tiles_x + tx] = at;
+            at += h[q];
+        }
+    }
     const size_t t = (size_t)b * tiles_x + tx;
     ranges[2 * t] = run ? first : 0u;
     ranges[2 * t + 1] = run ? first + run : 0u;

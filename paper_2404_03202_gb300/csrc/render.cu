@@ -20,9 +20,10 @@
 // 14 shuffles, after which 9 lanes hold one field's total each and write it with one shared-memory atomic), the CTA
 // sums warps in shared memory, the conic turns the moments into dL/d(px, py, c0, c1, c2) once per entry, and the
 // CTA's sum goes to the splat's gradient with 16-byte vector atomics (red.global.add.v4.f32).
-// A thread owns PPT = 2, 4 or 8 pixels (the blend schedule of the config): more pixels per thread share more of the
-// per-entry work and the warp reduction, fewer give more threads per tile. At 8 pixels one warp covers a 16 x 16
-// tile. Forward and adjoint evaluate alpha with identical
+// A thread owns PPT = 2, 4 or 8 pixels of one column (the blend schedule of the config): more pixels per thread share
+// more of the per-entry work and the warp reduction, fewer give more threads per tile. At 8 pixels one warp covers a
+// 16 x 16 tile. The adjoint interleaves the rows of a column's threads within the warp (InterleavedRows), so that
+// the pixel pairs it may skip together are bands of adjacent rows. Forward and adjoint evaluate alpha with identical
 // arithmetic, so their skip / stop decisions agree.
 #include "common.cuh"
 
@@ -111,6 +112,24 @@ struct PixelMap {
     __device__ PixelMap(int txi, int tyi) {
         x = txi * TS + (int)threadIdx.x % TS;
         y0 = tyi * TS + ((int)threadIdx.x / TS) * PPT;
+    }
+};
+
+// The adjoint's pixels: within each warp, the threads of a column interleave their rows. A warp covers
+// RW = 32 / TS threads per column; its thread l / TS of column l % TS takes rows l / TS + RW k of the warp's band
+// of RW PPT rows, so the warp's k-th pixels (and its pixel pairs) form one band of RW (2 RW) adjacent rows. The
+// adjoint skips a pixel pair when no pixel of the warp's pair passes the entry, and a splat's footprint in the tile
+// is a compact blob: it meets fewer of the warp's pair bands than with each thread's pixels stacked.
+template <int TS, int PPT>
+struct InterleavedRows {
+    static constexpr int NT = TS * TS / PPT;
+    static constexpr int RW = 32 / TS;
+    static_assert(TS <= 32 && NT % 32 == 0, "a warp holds whole rows of threads");
+    int x, y0;  // column; row of the thread's pixel k is y0 + RW k
+    __device__ InterleavedRows(int txi, int tyi) {
+        const int l = (int)threadIdx.x & 31, w = (int)threadIdx.x >> 5;
+        x = txi * TS + l % TS;
+        y0 = tyi * TS + w * RW * PPT + l / TS;
     }
 };
 
@@ -326,7 +345,7 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                   const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
                   const float* __restrict__ out_T, const uint32_t* __restrict__ ncontrib,
                   const float* __restrict__ dL_drgb, float4* __restrict__ grads) {
-    constexpr int NT = PixelMap<TS, PPT>::NT;
+    constexpr int NT = InterleavedRows<TS, PPT>::NT, RW = InterleavedRows<TS, PPT>::RW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdStaged* s_e = reinterpret_cast<BwdStaged*>(smem_raw);
     unsigned* s_vg = reinterpret_cast<unsigned*>(s_e + NT);
@@ -336,7 +355,7 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     const int tile_id = blockIdx.x;
     const int v = tile_id / tiles, t = tile_id - v * tiles;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    const PixelMap<TS, PPT> pm(txi, tyi);
+    const InterleavedRows<TS, PPT> pm(txi, tyi);
     const float xs = pm.x + 0.5f;
     const float fW = (float)W;  // halfW: W / 2, or +inf for the pinhole camera (no seam)
     const float x_first = txi * TS + 0.5f, x_last = txi * TS + TS - 0.5f;
@@ -358,7 +377,7 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * q + h;
-            const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
+            const size_t pix = (size_t)(pm.y0 + RW * k) * W + pm.x;
             last[k] = min(ncontrib[(size_t)v * HW + pix], len);
             t2[h] = out_T[(size_t)v * HW + pix];
             a0[h] = dL_drgb[(3 * (size_t)v + 0) * HW + pix];
@@ -372,7 +391,7 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         g2[q] = make_float2(a2[0], a2[1]);
         NS[q] = make_float2(-t2[0] * fmaf(a0[0], bg0, fmaf(a1[0], bg1, a2[0] * bg2)),
                             -t2[1] * fmaf(a0[1], bg0, fmaf(a1[1], bg1, a2[1] * bg2)));
-        NYS[q] = make_float2(-(pm.y0 + 2 * q + 0.5f), -(pm.y0 + 2 * q + 1.5f));
+        NYS[q] = make_float2(-(pm.y0 + RW * (2 * q) + 0.5f), -(pm.y0 + RW * (2 * q + 1) + 0.5f));
     }
 
     // A CTA of one warp (PPT 8 on 16 x 16 tiles) needs no CTA barrier and no shared-memory atomics.
