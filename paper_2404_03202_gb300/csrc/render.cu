@@ -413,9 +413,9 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
     // pixel, the exponent's derivatives give dL/dc0 = -1/2 sum gp dx^2, dL/dc1 = -sum gp dx dy, dL/dc2 =
     // -1/2 sum gp dy^2, dL/dpx = -(c0 sum gp dx + c1 sum gp dy), dL/dpy = -(c1 sum gp dx + c2 sum gp dy). A thread's
     // pixels share dx, and o is the entry's, so per pixel only u = dL/dalpha G (whose sum is dL/do), u dy and u dy^2
-    // are accumulated, with minus the colour weights alpha T g; the warp reduces the moments (sum gp dx,
-    // sum gp dx^2, sum gp dy, sum gp dx dy, sum gp dy^2, then dL/do and dL/dc) and the conic is applied once per
-    // entry when the CTA's sums are flushed.
+    // are accumulated, with minus the colour weights alpha T g; the warp reduces the moments of u (sum u dx,
+    // sum u dx^2, sum u dy, sum u dx dy, sum u dy^2, sum u = dL/do) and -dL/dc, and o, the signs and the conic are
+    // applied once per entry when the CTA's sums are flushed.
     float2 su = make_float2(0.f, 0.f), suy = su, suyy = su, nc0 = su, nc1 = su, nc2 = su;
     float gv[kGradFields];
 
@@ -454,17 +454,16 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
                     : bwd_entry_pairs<NP, false>(pos, last, T, NS, g0, g1, g2, NYS, E0, E1, P0, P1, P2, P3, su, suy,
                                                  suyy, nc0, nc1, nc2);
             if (__any_sync(0xffffffffu, contrib)) {
-                const float o = -P1.w;
-                const float s5 = su.x + su.y;
-                gv[5] = s5;                               // dL/do
-                gv[0] = dx * (o * s5);                    // sum gp dx
-                gv[1] = dx * gv[0];                       // sum gp dx^2
-                gv[2] = o * (suy.x + suy.y);              // sum gp dy
-                gv[3] = dx * gv[2];                       // sum gp dx dy
-                gv[4] = o * (suyy.x + suyy.y);            // sum gp dy^2
-                gv[6] = -(nc0.x + nc0.y);                 // dL/dc
-                gv[7] = -(nc1.x + nc1.y);
-                gv[8] = -(nc2.x + nc2.y);
+                // the moments of u (gp = o u; o and the signs are applied once per entry in the flush)
+                gv[5] = su.x + su.y;                      // sum u = dL/do
+                gv[0] = dx * gv[5];                       // sum u dx
+                gv[1] = dx * gv[0];                       // sum u dx^2
+                gv[2] = suy.x + suy.y;                    // sum u dy
+                gv[3] = dx * gv[2];                       // sum u dx dy
+                gv[4] = suyy.x + suyy.y;                  // sum u dy^2
+                gv[6] = nc0.x + nc0.y;                    // -dL/dc
+                gv[7] = nc1.x + nc1.y;
+                gv[8] = nc2.x + nc2.y;
                 float tot8;
                 const float tot = warp_sum_fields(gv, lane, tot8);
                 const bool quad = (lane & 3u) == 0;
@@ -483,14 +482,14 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
 #pragma unroll
             for (int f = 0; f < kGradFields; ++f) any |= (acc[f] != 0.f);
             if (any) {
-                // the CTA's moments -> dL/d(px, py, c0, c1, c2)
-                const float4 D = s_e[threadIdx.x].d;
-                const float gpx = -fmaf(D.x, acc[0], D.y * acc[2]);
-                const float gpy = -fmaf(D.y, acc[0], D.z * acc[2]);
+                // the CTA's moments of u -> dL/d(px, py, c0, c1, c2) (gp = o u), dL/do and dL/dc
+                const float4 D = s_e[threadIdx.x].d;  // c0, c1, c2, o
+                const float gpx = -D.w * fmaf(D.x, acc[0], D.y * acc[2]);
+                const float gpy = -D.w * fmaf(D.y, acc[0], D.z * acc[2]);
                 float4* gdst = grads + 3 * (size_t)s_vg[threadIdx.x];
-                atomicAdd(gdst, make_float4(gpx, gpy, -0.5f * acc[1], -acc[3]));
-                atomicAdd(gdst + 1, make_float4(-0.5f * acc[4], acc[5], acc[6], acc[7]));
-                atomicAdd(reinterpret_cast<float*>(gdst + 2), acc[8]);
+                atomicAdd(gdst, make_float4(gpx, gpy, -0.5f * D.w * acc[1], -D.w * acc[3]));
+                atomicAdd(gdst + 1, make_float4(-0.5f * D.w * acc[4], acc[5], -acc[6], -acc[7]));
+                atomicAdd(reinterpret_cast<float*>(gdst + 2), -acc[8]);
             }
 #pragma unroll
             for (int f = 0; f < kGradFields; ++f) acc[f] = 0.f;
