@@ -546,6 +546,8 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
                 if (rbase != 0xffffffffu) rows[(u64)rbase + ri] = pack_row(c.x, m, ty, j);
             }
             cnt += m;
+            // the lanes sharing a bucket (measured faster here than one ballot per bucket bit; the column pass,
+            // with more keys per warp, is the other way round)
             const unsigned peers = __match_any_sync(0xffffffffu, bl);
             B.lw[warp][lane] = m;
             __syncwarp();
@@ -1321,17 +1323,18 @@ col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_
     for (unsigned d = lane; d <= R; d += 32) my_hist[d] = 0;
     __syncwarp();
     const unsigned base_i = warp * (kSortItems * 32) + lane;
-    unsigned k[kSortItems], rk[kSortItems], dg[kSortItems];
+    unsigned k[kSortItems], rd[kSortItems];  // rd: rank within the warp's column << 16 | column
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const unsigned idx = base_i + j * 32;
         k[j] = idx < cnt ? __ldg(entries + beg + idx) : 0u;
-        const unsigned d = k[j] >> rank_bits;
-        dg[j] = idx < cnt && d < (unsigned)tiles_x ? d : R;  // an entry outside its bucket's columns is left out
     }
+    unsigned* s_h = s_scratch + 32;  // the chunk's output positions per column, hist[c][.]
+    for (int d = tid; d < tiles_x; d += kSortThreads) s_h[d] = __ldg(hist + (size_t)c * tiles_x + d);
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const unsigned d = dg[j];
+        const unsigned idx = base_i + j * 32, dk = k[j] >> rank_bits;
+        const unsigned d = idx < cnt && dk < (unsigned)tiles_x ? dk : R;  // an entry outside its columns: left out
         unsigned peers = 0xffffffffu;
         for (int bt = 0; bt <= dbits; ++bt) {
             const unsigned bal = __ballot_sync(0xffffffffu, (d >> bt) & 1u);
@@ -1341,7 +1344,7 @@ col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_
         __syncwarp();
         if ((peers & lt_mask) == 0) my_hist[d] = before + __popc(peers);
         __syncwarp();
-        rk[j] = before + __popc(peers & lt_mask);
+        rd[j] = (before + __popc(peers & lt_mask)) << 16 | d;
     }
     __syncthreads();
     for (unsigned d = tid; d < R; d += kSortThreads) {
@@ -1375,15 +1378,16 @@ col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j)
-        if (dg[j] < R) s_ent[s_start[dg[j]] + my_hist[dg[j]] + rk[j]] = k[j];
+    for (int j = 0; j < kSortItems; ++j) {
+        const unsigned d = rd[j] & 0xffffu;
+        if (d < R) s_ent[s_start[d] + my_hist[d] + (rd[j] >> 16)] = k[j];
+    }
     __syncthreads();
     const unsigned placed = s_start[R - 1] + s_tot[R - 1];  // entries with a column (all, unless one was left out)
     if (tid == 0 && placed != cnt) atomicOr(&hdr->error, kErrConsistency);
-    const unsigned* h = hist + (size_t)c * tiles_x;
     for (unsigned i = tid; i < placed; i += kSortThreads) {
         const unsigned e = s_ent[i], d = e >> rank_bits;
-        const u64 at = (u64)__ldg(h + d) + (i - s_start[d]);
+        const u64 at = (u64)s_h[d] + (i - s_start[d]);
         if (at < capacity) keys_out[at] = ((tile0 + d) << rank_bits) | (u64)(e & rank_mask);
     }
 }
@@ -1609,7 +1613,7 @@ cudaError_t launch_sort(const omnigs_config& cfg, int64_t n, int64_t capacity, u
         unsigned* chist = reinterpret_cast<unsigned*>(ws + L.col_hist);
         const unsigned chunks = (unsigned)((u64)capacity / kColChunk + nbkt + 1);
         const unsigned* ent = reinterpret_cast<const unsigned*>(ws + L.alt_keys);
-        const size_t smem = sizeof(unsigned) * (kSortTile + kWarps * kHistRow + 2 * kRadixMax + 32);
+        const size_t smem = sizeof(unsigned) * (kSortTile + kWarps * kHistRow + 2 * kRadixMax + 32 + kMaxBucketCols);
         e = cudaFuncSetAttribute(col_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         {
