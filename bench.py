@@ -59,6 +59,7 @@ FLOP_EXAMINED = 10
 FWD_FLOP_CONTRIB = 13
 BWD_FLOP_CONTRIB = 54
 SORT_BYTES_PER_KEY = 16      # sort_downsweep: one 8 B key read and written per instance and pass
+TILE_SCATTER_BYTES_PER_KEY = 12  # tile_scatter: one 4 B bucket entry read and one 8 B key written per instance
 
 
 def _sort_passes(bits: int) -> int:
@@ -88,9 +89,11 @@ def box_rows(splats, tile: int, H: int) -> int:
 def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows: int, equirect: bool = True) -> dict:
     """Algorithmic HBM bytes per step of the memory-bound stages (each read or written once).
 
-    P = V n projected splats (48 B each), I instances (8 B keys), R box rows (8 B row words), X = V H W pixels.
+    P = V n projected splats (48 B each), I instances (8 B keys; 4 B bucket entries in the bucketed order), R box
+    rows (8 B row words, plus a 4 B bucket offset in the bucketed order), X = V H W pixels.
     """
     P, X = V * n, V * H * W
+    bucketed = n >= 256 and H // tile <= 128 and W // tile <= 256 and n <= 1 << 24  # as the library decides
     tiles = V * (W // tile) * (H // tile)
     dp = _sort_passes(32 + _ceil_log2(V))
     tp = _sort_passes(max(1, _ceil_log2(tiles)))
@@ -101,14 +104,16 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows:
         "depth_keys": P * (4 + 8) if packed else P * (4 + 8 + 4),
         # per pass: key histogram read, key (and index) read and written; a packed sort's last pass writes the index
         "depth_sort": dp * P * (8 + 2 * 8) - P * 4 if packed else dp * P * (8 + 2 * 12),
-        "bin_count": P * (4 + 36 + 4) + rows * 8,         # depth order, (p, conic, depth, radii, q), count; rows out
-        "bin_emit": rows * 8 + instances * 8,             # the stored rows in, one key per instance out
+        # depth order, (p, conic, depth, radii, q), count in; rows (and their bucket offsets) out
+        "bin_count": P * (4 + 36 + 4) + rows * (12 if bucketed else 8),
+        # the stored rows (and offsets) in, one bucket entry (or key) per instance out
+        "bin_emit": rows * 12 + instances * 4 if bucketed else rows * 8 + instances * 8,
         "sort_upsweep": tp * instances * 8,               # per pass: keys read for the digit histogram
         "sort_downsweep": tp * instances * 16,            # per pass: keys read and written
         "tile_ranges": tiles * 8,                         # one [start, end) pair per tile
-        # bucketed order: one column pass (histogram read, then keys read and written)
-        "tile_count": instances * 8,
-        "tile_scatter": instances * 16,
+        # bucketed order: one column pass (entries read for the column counts, then read again and keys written)
+        "tile_count": instances * 4,
+        "tile_scatter": instances * (4 + 8),
         "l1_loss": X * 3 * 12,                            # image and target in, dL/dC out
         "dssim_fwd": X * 3 * (8 + 12),                    # image and target in, three sensitivity maps out
         "dssim_bwd": X * 3 * (12 + 8 + 4),                # sensitivity maps, image and target in, dL/dC out
@@ -120,8 +125,8 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows:
 # 1-view workload; the 8-view launch processes 8 such views), with the SHA-256 of the adjoint's source (the kernel
 # and the helpers it uses) it was taken on: once that source changes the figure no longer applies and the bench
 # reports traffic as null.
-RENDER_BWD_TRAFFIC = {"bytes_per_view": 50_062_848,
-                      "source_sha256": "d1b1e32a8056dac2a84129d7cc664140e23f63e3ac791756056b2f0be4ddef17"}
+RENDER_BWD_TRAFFIC = {"bytes_per_view": 50_073_344,
+                      "source_sha256": "ad640b00e4a93ec02dc0be1d2ee90af2ce199a5197f6136710be45c15532eaae"}
 
 
 def render_bwd_source(text: str) -> str:
@@ -788,8 +793,11 @@ def main():
                 src = render_bwd_source(f.read())
             if hashlib.sha256(src.encode()).hexdigest() == RENDER_BWD_TRAFFIC["source_sha256"]:
                 traffic = RENDER_BWD_TRAFFIC["bytes_per_view"] * V
-    elif dom in ("sort_downsweep", "tile_scatter"):
+    elif dom == "sort_downsweep":
         roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    elif dom == "tile_scatter":
+        roof = {"bound": "hbm", "achieved": count * TILE_SCATTER_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
