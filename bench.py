@@ -495,13 +495,19 @@ def serving_benchmark(dev, count: int = 192, lanes: int = 4, max_batch: int = 8)
         for (w, h), _ in SERVING_RES:
             ex.bytes_needed(nm, w, h, 1)
     # warm-up: every (scene, resolution) key once alone and once in a full batch, so that no timed trace pays a
-    # first use (allocator growth, capacity probes)
+    # first use (allocator growth, capacity probes). Every scheduler delivers and drops each image as it completes,
+    # as a server does: held images would keep their pinned host buffers, and each trace would then pin new ones.
+    def sched(ln, mb):
+        return serving.Scheduler(ex, lanes=ln, max_batch=mb, keep_results=False)
     every = [((nm, wh), 1.0) for nm in names for wh, _ in SERVING_RES]
     for key in every:
-        serving.run_trace(serving.Scheduler(ex, lanes=1, max_batch=1), serving_requests(names, 1, None, 1, keys=[key]))
-        serving.run_trace(serving.Scheduler(ex, lanes=lanes, max_batch=max_batch),
-                          serving_requests(names, max_batch, None, 1, keys=[key]))
-    seq = serving.run_trace(serving.Scheduler(ex, lanes=1, max_batch=1), serving_requests(names, count // 2, None, 2))
+        serving.run_trace(sched(1, 1), serving_requests(names, 1, None, 1, keys=[key]))
+        serving.run_trace(sched(lanes, max_batch), serving_requests(names, max_batch, None, 1, keys=[key]))
+    # and every batch size at every resolution once (the pinned result buffer of each size)
+    for wh, _ in SERVING_RES:
+        for v in range(2, max_batch):
+            serving.run_trace(sched(1, v), serving_requests(names, v, None, 1, keys=[((names[0], wh), 1.0)]))
+    seq = serving.run_trace(sched(1, 1), serving_requests(names, count // 2, None, 2))
     out = {"scenes": SERVING_SCENES, "resolutions": [f"{w}x{h} p={p}" for (w, h), p in SERVING_RES],
            "lanes": lanes, "max_batch": max_batch, "capacity_one_at_a_time": seq, "poisson": []}
     cap = seq["views_per_s"]
@@ -512,7 +518,7 @@ def serving_benchmark(dev, count: int = 192, lanes: int = 4, max_batch: int = 8)
         row = {"trace": label, "rate_vs_capacity": f, "offered_per_s": f * cap}
         for mode, ln, mb in (("batched", lanes, max_batch), ("one_at_a_time", 1, 1)):
             reqs = serving_requests(names, count, f * cap, 10 + k, keys=keys)
-            row[mode] = serving.run_trace(serving.Scheduler(ex, lanes=ln, max_batch=mb), reqs)
+            row[mode] = serving.run_trace(sched(ln, mb), reqs)
         row["batched_vs_one_at_a_time"] = row["batched"]["views_per_s"] / row["one_at_a_time"]["views_per_s"]
         out["poisson"].append(row)
     out["overflow_reruns"] = ex.overflows

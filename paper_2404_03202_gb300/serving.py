@@ -78,7 +78,7 @@ class Stats:
 
 class Scheduler:
     def __init__(self, executor, lanes: int = 4, max_batch: int = 8, mem_budget: int | None = None,
-                 max_wait: float = 0.25):
+                 max_wait: float = 0.25, keep_results: bool = True):
         if lanes < 1 or max_batch < 1:
             raise ValueError("lanes and max_batch must be >= 1")
         self.ex = executor
@@ -86,6 +86,9 @@ class Scheduler:
         self.max_batch = max_batch
         self.mem_budget = mem_budget if mem_budget is not None else executor.memory_budget()
         self.max_wait = max_wait
+        # keep_results=False: a completed request's image is delivered and dropped at once (a server that hands it
+        # on), so its host buffer goes back to the allocator instead of being held until the caller lets go
+        self.keep_results = keep_results
         self.waiting: list[Request] = []
         self.in_flight: dict[int, Batch] = {}
         self.free_lanes = list(range(lanes))
@@ -175,7 +178,7 @@ class Scheduler:
             images = self.ex.collect(b.handle)
             t = now
             for r, img in zip(b.requests, images):
-                r.result = img
+                r.result = img if self.keep_results else None
                 r.done = t
                 self.stats.completed += 1
                 self.stats.latencies.append(t - r.arrival)

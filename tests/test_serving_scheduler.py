@@ -96,6 +96,17 @@ def test_every_request_completes_with_its_own_image():
     assert summary["p50_ms"] <= summary["p99_ms"]
 
 
+def test_delivered_images_are_dropped_when_results_are_not_kept():
+    """keep_results=False: every request still completes (and is timed), but its image is not held."""
+    reqs = _trace(100, 2000.0, 5)
+    clk = SimClock()
+    ex = FakeExecutor(clk, budget=10_000)
+    sch = S.Scheduler(ex, lanes=3, max_batch=4, keep_results=False)
+    summary = S.run_trace(sch, reqs, clock=clk, sleep=clk.sleep)
+    assert summary["requests"] == 100 and summary["rejected"] == 0
+    assert all(r.result is None and r.done is not None and r.arrival <= r.admitted <= r.done for r in reqs)
+
+
 def test_batches_hold_one_key_and_respect_lanes_and_memory():
     reqs = _trace(400, 5000.0, 2)
     sch, ex, summary = _run(reqs, lanes=3, max_batch=4, budget=2500)
