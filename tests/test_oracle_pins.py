@@ -161,6 +161,39 @@ def test_aligned_covariance_and_quaternion_order(oracle_lib):
             assert rec[key] == expect
 
 
+def test_instance_box_is_bounded_by_the_radius(oracle_lib):
+    """At opacity 0.99 the alpha >= 1/255 ellipse (q = 2 ln(252.45) = 11.06) reaches past 3 sigma: for an isotropic
+    Sigma~ both box half-extents are the 3-sigma radius ceil(3 sqrt(lambda)) of reading 6, not the ellipse's
+    ceil(sqrt(q var)); at opacity 0.1 the ellipse's box is the narrower one."""
+    W, H = 1024, 512
+    for o, binds in ((0.99, True), (0.1, False)):
+        sc = _one_gaussian([0, 0, 3.0], [0.05] * 3, [1, 0, 0, 0], opacity=o)
+        rec = oracle.preprocess(sc, synth.identity_viewmats(1), W, H)[0]
+        lam = max(rec[oracle.R_COV00], rec[oracle.R_COV11])
+        r = np.ceil(3 * np.sqrt(lam))
+        assert rec[oracle.R_RADIUS] == r
+        q = 2 * np.log(255 * float(sc.opacity[0]))
+        for key, var in ((oracle.R_RX, rec[oracle.R_COV00]), (oracle.R_RY, rec[oracle.R_COV11])):
+            ellipse = np.ceil(np.sqrt(q * var) * (1 + 1e-4) + 1e-3)
+            assert (ellipse > r) == binds
+            assert rec[key] == min(r, ellipse)
+
+
+def test_gaussian_on_the_pole_projects_to_finite_values(oracle_lib):
+    """A Gaussian straight above the camera (t_x = t_z = 0, lat = pi/2): the projection is finite, and with the pole
+    guard so is J (its entries are those at rho = 1e-6 t_r), hence the covariance, conic and box."""
+    W, H = 512, 256
+    t = np.array([0.0, 2.0, 0.0])
+    J = oracle.jacobian(t, W, H)
+    assert np.isfinite(J).all()
+    sc = _one_gaussian(t, [0.05] * 3, [1, 0, 0, 0])
+    rec = oracle.preprocess(sc, synth.identity_viewmats(1), W, H)[0]
+    fields = [oracle.R_PX, oracle.R_PY, oracle.R_COV00, oracle.R_COV01, oracle.R_COV11, oracle.R_C0, oracle.R_C1,
+              oracle.R_C2, oracle.R_RX, oracle.R_RY]
+    assert np.isfinite(rec[fields]).all()
+    assert rec[oracle.R_PY] == H
+
+
 def test_quaternion_matches_scipy(oracle_lib):
     for _ in range(100):
         q = RNG.normal(size=4) * RNG.uniform(0.1, 3)
@@ -540,6 +573,41 @@ def test_blend_bwd_matches_finite_differences(oracle_lib, case):
             assert abs(fd - g[i, j]) <= 1e-6 * max(1.0, abs(fd)), (fld, i, fd, g[i, j])
             checked += 1
     assert checked >= 50 and skipped < 0.05 * checked
+
+
+def test_screen_gradient_matches_finite_differences(oracle_lib):
+    """dL/ds (Sec. 4's densification signal), s the screen coordinates of Eq. 4 with p = (s + 1) (W, H) / 2, summed
+    over the views: moving s_x by h in every view moves p_x by h W / 2 there (and s_y, p_y by h H / 2). Central
+    differences of the blend on a W != H image, the lists held fixed."""
+    V, W, H, T = 2, 64, 32, 8
+    sc = synth.shell_scene(60, seed=3)
+    vm = synth.random_viewmats(V, 7)
+    wgt = synth.random_image_grad(V, W, H, 11).astype(np.float64)
+    f0 = oracle.render(sc, vm, W, H, T)
+    g = oracle.render_grad(sc, vm, wgt, W, H, T, fwd=f0)
+    sp, n = f0["splats"], sc.n
+
+    def loss(s):
+        rgb, _, nc, _ = oracle.blend_fwd(s, f0["ranges"], f0["list"], V, W, H, T)
+        return float((rgb * wgt).sum()), nc
+
+    checked = 0
+    for gi in range(n):
+        for axis, fld, half in ((0, "px", W / 2), (1, "py", H / 2)):
+            h = 1e-7
+            sp_p = {k: v.copy() for k, v in sp.items()}
+            sp_m = {k: v.copy() for k, v in sp.items()}
+            for v in range(V):
+                sp_p[fld][v * n + gi] += h * half
+                sp_m[fld][v * n + gi] -= h * half
+            lp, ncp = loss(sp_p)
+            lm, ncm = loss(sp_m)
+            if not (np.array_equal(ncp, f0["n_contrib"]) and np.array_equal(ncm, f0["n_contrib"])):
+                continue
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g["screen"][gi, axis]) <= 1e-5 * max(1.0, abs(fd)), (gi, fld, fd, g["screen"][gi, axis])
+            checked += fd != 0.0
+    assert checked >= 20
 
 
 def test_preprocess_bwd_matches_finite_differences(oracle_lib):

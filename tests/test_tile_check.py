@@ -204,6 +204,55 @@ def test_whole_row_splats_may_not_drop(oracle_lib):
         tc.check_tile_lists(wide, 1, W, H, T, *_as_ranges(lists), ranges, lst)
 
 
+def test_half_width_boxes_keep_whole_rows(oracle_lib):
+    """Equirectangular: a box of half-width rx = 114 on a 256 px image (16 px tiles) spans 15 of the 16 tile columns
+    (x = 6 .. 234), yet rx + T > W / 2, so its column offsets can differ from the blend's minimal-image dx: its rows
+    are kept whole (rule 4). The uncut box lists pass; leaving out a far column does not."""
+    W, H, T = 256, 128, 16
+    TX = W // T
+    sp = _single(120.3, 60.0, 1 / 16, 0.0, 1 / 16, 9.0, 114, 20)
+    ranges, lst = oracle.bin_sort(sp, 1, W, H, T)
+    lists = _lists(ranges, lst)
+    assert sum(len(L) for L in lists) == 15 * 4  # columns 0 .. 14; pixel rows 40 .. 80: tile rows 2 .. 5
+    tc.check_tile_lists(sp, 1, W, H, T, ranges, lst, ranges, lst)
+    lists[3 * TX + 0] = []
+    with pytest.raises(AssertionError, match="rule 4"):
+        tc.check_tile_lists(sp, 1, W, H, T, *_as_ranges(lists), ranges, lst)
+
+
+def test_a_flat_ellipse_short_of_the_needle_threshold_is_culled(oracle_lib):
+    """det = 5e-3 c0 c2 is a flat ellipse but no needle (the threshold is 1e-3): its rows are culled like any other,
+    so its FP64-culled lists pass and drop pairs of its box."""
+    W, H, T = 256, 128, 16
+    c0, c2 = 1 / 16, 1 / 64
+    c1 = np.sqrt(c0 * c2 * (1 - 5e-3))
+    sp = _single(128.3, 64.0, c0, c1, c2, 9.0, 80, 40)
+    ranges, lst = oracle.bin_sort(sp, 1, W, H, T)
+    gr, gl = _fp64_culled(sp, 1, W, H, T, ranges, lst)
+    st = tc.check_tile_lists(sp, 1, W, H, T, gr, gl, ranges, lst)
+    assert st["dropped"] > 0 and st["whole_row_pairs"] == 0, st
+
+
+@pytest.mark.parametrize("side", [-1, 1])
+def test_half_pixel_widening_on_either_side(oracle_lib, side):
+    """A circle (radius 12, q = 9) whose edge stops 0.3 px short of a tile's outer pixel centres, on its left
+    (side -1: the circle lies left of column 6, whose first centre is x = 96.5) or on its right (side 1: right of
+    column 5, last centre 95.5). No pixel centre of that tile reaches alpha >= 1/255 (form 9.46 > q (1 + 5e-4) +
+    5e-4), but the tile's rectangle grown by 1/2 px does: leaving the pair out breaks rule 2."""
+    W, H, T = 256, 128, 16
+    TX = W // T
+    col, centre = (6, 96.5 - 12.3) if side < 0 else (5, 95.5 + 12.3)
+    sp = _single(centre, 56.0, 1 / 16, 0.0, 1 / 16, 9.0, 14, 14)
+    ranges, lst = oracle.bin_sort(sp, 1, W, H, T)
+    lists = _lists(ranges, lst)
+    assert lists[3 * TX + col] == [0]
+    reach = tc.pair_reach(sp, np.array([0]), np.array([3 * TX + col]), W, H, T, 0.0)[0]
+    assert reach > 9.0 * (1 + 5e-4) + 5e-4
+    lists[3 * TX + col] = []
+    with pytest.raises(AssertionError, match="rule 2"):
+        tc.check_tile_lists(sp, 1, W, H, T, *_as_ranges(lists), ranges, lst)
+
+
 def test_seam_copy_counts_for_the_equirectangular_camera_only(oracle_lib):
     """A circle centred 2 px right of the seam reaches the last tile column through its copy at -W: leaving that tile
     out breaks rule 2 on the equirectangular camera; with a pinhole camera (no wrap) the box is clipped at column 0
