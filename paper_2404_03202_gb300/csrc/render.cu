@@ -45,11 +45,11 @@ __device__ __forceinline__ float fast_ex2(float x) {
 // recomputed alphas and stop decisions still match. The pair operands come from shared memory already duplicated
 // in both halves (one 16-byte load gives two pairs).
 struct FwdStaged {
-    float4 s;   // px + seam shift, per-pixel wrap flag, c0', c1'   (per-thread dx and the exponent's dx terms)
+    float4 s;   // px, seam shift, c0', c1'     (per-thread dx and the exponent's dx terms)
     float4 p0;  // py, py, c2', c2'
     float4 p1;  // -m, -m, -o, -o              (pass interval centre, opacity)
     float4 p2;  // -r, -r, -g, -g
-    float4 p3;  // -b, -b, h, h                (h: pass interval half-width)
+    float4 p3;  // -b, -b, h, per-pixel wrap flag   (h: pass interval half-width)
 };
 
 __device__ __forceinline__ float2 lo2(const float4 v) { return make_float2(v.x, v.y); }
@@ -90,15 +90,13 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ splats,
     return s;
 }
 
-// The entry's px with the tile's seam shift applied (px itself when the shift is decided per pixel), and the flag
-// (1) of a per-pixel wrap.
-__device__ __forceinline__ float shifted_px(const Staged& st) {
-    return st.b.w != kPerPixelWrap ? st.a.x + st.b.w : st.a.x;
-}
+// The tile's seam shift of the entry (0 when the shift is decided per pixel), and the flag (1) of a per-pixel wrap.
+// dx = (px - xs) + shift rounds like the per-pixel wrap (px - xs) -+ W, so a pixel's dx, and its alpha, do not depend
+// on which of the two its tile took (nor, then, on the tile size); px - xs is exact for the nearby pixels.
+__device__ __forceinline__ float seam_shift(const Staged& st) { return st.b.w != kPerPixelWrap ? st.b.w : 0.f; }
 __device__ __forceinline__ float wrap_flag(const Staged& st) { return st.b.w != kPerPixelWrap ? 0.f : 1.f; }
 
-// Minimal-image dx of the thread's column for a staged entry: dx = (px + shift) - xs, wrapped per pixel if flagged.
-// Both passes compute it this way, so their alphas agree bit for bit.
+// Minimal-image wrap of a per-pixel dx.
 __device__ __forceinline__ float wrap_dx(float dx, float halfW, float fW) {
     if (dx >= halfW) dx -= fW;
     else if (dx < -halfW) dx += fW;
@@ -178,11 +176,11 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         if (s < end) {
             const Staged st = stage_entry(splats, entry_splat(keys, vorder, s, rank_mask), x_first, x_last, halfW, fW);
             FwdStaged f;
-            f.s = make_float4(shifted_px(st), wrap_flag(st), st.a.z, st.a.w);
+            f.s = make_float4(st.a.x, seam_shift(st), st.a.z, st.a.w);
             f.p0 = make_float4(st.a.y, st.a.y, st.b.x, st.b.x);
             f.p1 = make_float4(-st.b.y, -st.b.y, -st.c.x, -st.c.x);
             f.p2 = make_float4(-st.c.y, -st.c.y, -st.c.z, -st.c.z);
-            f.p3 = make_float4(-st.c.w, -st.c.w, st.b.z, st.b.z);
+            f.p3 = make_float4(-st.c.w, -st.c.w, st.b.z, wrap_flag(st));
             s_e[threadIdx.x] = f;
         }
         __syncthreads();
@@ -191,13 +189,13 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
             const float4 S = s_e[j].s;
             const float4 P0 = s_e[j].p0;
             const float4 P1 = s_e[j].p1;
-            float dx = S.x - xs;
-            if (S.y != 0.f) dx = wrap_dx(dx, halfW, fW);
+            const float4 P2 = s_e[j].p2;
+            const float4 P3 = s_e[j].p3;
+            float dx = (S.x - xs) + S.y;
+            if (P3.w != 0.f) dx = wrap_dx(dx, halfW, fW);
             const float e0 = S.z * dx * dx, e1 = S.w * dx;  // exponent = e0 + dy (e1 + c2' dy)
             const float2 E0 = make_float2(e0, e0), E1 = make_float2(e1, e1);
             const uint32_t pos1 = b - start + j + 1;        // list position after this entry
-            const float4 P2 = s_e[j].p2;
-            const float4 P3 = s_e[j].p3;
             const float h = P3.z;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -281,11 +279,11 @@ __device__ __forceinline__ float warp_sum_fields(float (&v)[kGradFields], unsign
 // The adjoint's entries, staged for packed pixel pairs: every pair operand sits duplicated in both halves of a
 // 16-byte word, so one shared-memory load gives two pairs.
 struct BwdStaged {
-    float4 x;   // px + seam shift, per-pixel wrap flag, c0', c1'   (the thread's dx and the exponent's dx terms)
+    float4 x;   // px, seam shift, c0', c1'   (the thread's dx and the exponent's dx terms)
     float4 p0;  // py, py, c2', c2'
     float4 p1;  // -m, -m, -o, -o            (pass interval centre, opacity)
     float4 p2;  // r, r, g, g
-    float4 p3;  // b, b, h, h                (h: pass interval half-width)
+    float4 p3;  // b, b, h, per-pixel wrap flag   (h: pass interval half-width)
     float4 d;   // raw conic c0, c1, c2, opacity (for the flush)
 };
 
@@ -430,11 +428,11 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
             const unsigned vg = entry_splat(keys, vorder, (uint32_t)(start + bbeg + threadIdx.x), rank_mask);
             const Staged st = stage_entry(splats, vg, x_first, x_last, halfW, fW);
             BwdStaged b;
-            b.x = make_float4(shifted_px(st), wrap_flag(st), st.a.z, st.a.w);
+            b.x = make_float4(st.a.x, seam_shift(st), st.a.z, st.a.w);
             b.p0 = make_float4(st.a.y, st.a.y, st.b.x, st.b.x);
             b.p1 = make_float4(-st.b.y, -st.b.y, -st.c.x, -st.c.x);
             b.p2 = make_float4(st.c.y, st.c.y, st.c.z, st.c.z);
-            b.p3 = make_float4(st.c.w, st.c.w, st.b.z, st.b.z);
+            b.p3 = make_float4(st.c.w, st.c.w, st.b.z, wrap_flag(st));
             b.d = make_float4(st.d.x, st.d.y, st.d.z, st.c.x);
             s_e[threadIdx.x] = b;
             s_vg[threadIdx.x] = vg;
@@ -449,8 +447,8 @@ render_bwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
             const float4 P1 = s_e[j].p1;
             const float4 P2 = s_e[j].p2;
             const float4 P3 = s_e[j].p3;
-            float dx = X.x - xs;
-            if (X.y != 0.f) dx = wrap_dx(dx, halfW, fW);
+            float dx = (X.x - xs) + X.y;
+            if (P3.w != 0.f) dx = wrap_dx(dx, halfW, fW);
             const float e0 = X.z * dx * dx, e1 = X.w * dx;
             const float2 E0 = make_float2(e0, e0), E1 = make_float2(e1, e1);
             const bool contrib =
