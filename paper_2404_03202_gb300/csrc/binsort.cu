@@ -409,13 +409,17 @@ __device__ __forceinline__ u64 pack_row(int cl, unsigned cnt, int ty, int j) {
 constexpr int kBinWarps = kBinThreads / 32;
 constexpr int kBucketSlots = 2 * kMaxBucketRows;  // a block's buckets: the tile rows of its (at most two) views
 
+constexpr int kPendRows = 2048;  // row items whose in-warp offsets wait in shared memory for their warp's base
+
 // bin_count's ranking: warp w's row items are the block's items [w * per, (w + 1) * per) in order, ranked 32 at a
 // time against the warp's own bucket counters; afterwards every warp's base in a bucket is the count of the earlier
 // warps' items there.
+
 struct WarpBuckets {
     unsigned cw[kBinWarps][kBucketSlots];  // per warp: its items' instances in each bucket so far; then its base
     unsigned run[kBucketSlots];            // the block's instances in each bucket
     unsigned lw[kBinWarps][32];            // item weights of the current step, by warp and lane
+    unsigned pend[kPendRows];              // row item ri < kPendRows: bucket << 24 | offset within its warp's items
 };
 
 struct BucketScratch {
@@ -555,7 +559,8 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
             for (unsigned q = peers & lt; q; q &= q - 1) pre += B.lw[warp][__ffs(q) - 1];
             if (valid) {
                 const unsigned intra = B.cw[warp][bl] + pre;
-                if (rbase != 0xffffffffu) rows_off[(u64)rbase + ri] = intra;
+                if (ri < (unsigned)kPendRows) B.pend[ri] = bl << 24 | intra;
+                else if (rbase != 0xffffffffu) rows_off[(u64)rbase + ri] = intra;
             }
             __syncwarp();
             if (valid && (peers >> lane) == 1u) B.cw[warp][bl] += pre + m;  // the group's highest lane
@@ -574,12 +579,18 @@ bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_
             B.run[bl] = run;
         }
         __syncthreads();
-        if (rbase != 0xffffffffu && warp > 0) {
+        if (rbase != 0xffffffffu) {
+            // the first kPendRows items from shared memory, written once; the rest (blocks of many rows) read back
             for (unsigned ri = seg0 + lane; ri < seg1; ri += 32) {
-                const u64 w = rows[(u64)rbase + ri];
-                const int ty = (int)((w >> 32) & 0xffffu), j = (int)(w >> 48);
-                const unsigned bl = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
-                rows_off[(u64)rbase + ri] += B.cw[warp][bl];
+                if (ri < (unsigned)kPendRows) {
+                    const unsigned e = B.pend[ri];
+                    rows_off[(u64)rbase + ri] = (e & 0xffffffu) + B.cw[warp][e >> 24];
+                } else if (warp > 0) {
+                    const u64 w = rows[(u64)rbase + ri];
+                    const int ty = (int)((w >> 32) & 0xffffu), j = (int)(w >> 48);
+                    const unsigned bl = (j < next_view ? 0u : (unsigned)tiles_y) + (unsigned)ty;
+                    rows_off[(u64)rbase + ri] += B.cw[warp][bl];
+                }
             }
         }
         for (int i = threadIdx.x; i < 2 * tiles_y; i += kBinThreads) {
