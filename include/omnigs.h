@@ -37,7 +37,7 @@ typedef enum {
     OMNIGS_E_INVALID = 1,  /* bad argument; nothing was enqueued */
     OMNIGS_E_CAPACITY = 2, /* more tile instances than the capacity given to omnigs_bin */
     OMNIGS_E_CUDA = 3,     /* a CUDA launch or call failed */
-    OMNIGS_E_TIMEOUT = 4   /* a bounded device-side wait ran out */
+    OMNIGS_E_TIMEOUT = 4   /* a bounded device-side wait ran out (the tile sort's bulk copies; 2 s each) */
 } omnigs_status;
 
 /* Image and camera set-up shared by all calls of one frame. */

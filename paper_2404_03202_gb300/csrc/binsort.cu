@@ -1220,6 +1220,61 @@ bucket_base_kernel(int nbkt, const u64* __restrict__ totals, u64* __restrict__ b
     if (threadIdx.x == 0) col_start[nbkt] = ctot;
 }
 
+// One column-pass chunk of bucket entries copied into shared memory by the bulk-copy engine (cp.async.bulk, TMA's
+// untiled form): one thread arms an mbarrier with the byte count and issues the copy; every thread waits on the
+// barrier's first phase. A bulk copy wants 16-byte aligned addresses and a multiple of 16 bytes, so the window starts
+// at the chunk's first entry rounded down to 4 entries and ends at its last rounded up: entry i of the chunk is
+// window entry lead + i (lead = first entry mod 4). The window may run up to 3 entries past the chunk; the
+// workspace region holding the entries is padded for that. The wait is bounded in time (kBulkWaitNs of the global
+// nanosecond timer): on timeout the CTA flags kErrTimeout and reports failure, and the caller skips the chunk.
+constexpr int kColWindow = kColChunk + 8;  // entries of the shared-memory window (chunk, lead and rounding)
+constexpr unsigned long long kBulkWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool bulk_load_window(unsigned* s_win, unsigned long long* s_bar,
+                                                 const unsigned* __restrict__ entries, u64 first, u64 last,
+                                                 unsigned* lead, WsHeader* __restrict__ hdr) {
+    const u64 a0 = first & ~3ull, a1 = (last + 3) & ~3ull;  // [first, last): the chunk's entries
+    const unsigned bytes = (unsigned)(a1 - a0) * 4u;
+    *lead = (unsigned)(first - a0);
+    const unsigned bar = smem_u32(s_bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(s_win)), "l"(entries + a0), "r"(bytes), "r"(bar)
+                     : "memory");
+    }
+    unsigned done = 0;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar)
+                     : "memory");
+        if (done || global_ns() - t0 > kBulkWaitNs) break;
+    }
+    if (!done) {
+        atomicOr(&hdr->error, kErrTimeout);
+        return false;
+    }
+    return true;
+}
+
 // Bucket of column-pass chunk c: the last b with col_start[b] <= c (buckets without chunks are passed over).
 __device__ __forceinline__ int chunk_bucket(const unsigned* __restrict__ col_start, int nbkt, unsigned c) {
     int lo = 0, hi = nbkt - 1;
@@ -1238,23 +1293,19 @@ col_count_kernel(const unsigned* __restrict__ entries, const u64* __restrict__ b
                  const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int rank_bits,
                  unsigned* __restrict__ hist, WsHeader* __restrict__ hdr) {
     __shared__ unsigned s_h[kMaxBucketCols];
+    __shared__ __align__(128) unsigned s_win[kColWindow];
+    __shared__ __align__(8) unsigned long long s_bar;
     const unsigned c = blockIdx.x;
     if (c >= __ldg(col_start + nbkt)) return;
     const int b = chunk_bucket(col_start, nbkt, c);
     const u64 beg = base[b] + (u64)(c - col_start[b]) * kColChunk;
     const u64 end = min(beg + kColChunk, base[b] + eff[b]);
     for (int d = threadIdx.x; d < tiles_x; d += kSortThreads) s_h[d] = 0u;
-    __syncthreads();
-    unsigned k[kSortItems];  // all loads in flight before the counting
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const u64 i = beg + threadIdx.x + (u64)j * kSortThreads;
-        k[j] = i < end ? __ldg(entries + i) : 0u;
-    }
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        if (beg + threadIdx.x + (u64)j * kSortThreads >= end) break;
-        const unsigned d = k[j] >> rank_bits;
+    unsigned lead;
+    const bool ok = bulk_load_window(s_win, &s_bar, entries, beg, end, &lead, hdr);  // syncs the CTA
+    const unsigned cnt = ok ? (unsigned)(end - beg) : 0u;
+    for (unsigned i = threadIdx.x; i < cnt; i += kSortThreads) {
+        const unsigned d = s_win[lead + i] >> rank_bits;
         if (d < (unsigned)tiles_x) atomicAdd(&s_h[d], 1u);
         else atomicOr(&hdr->error, kErrConsistency);  // a key outside its bucket: not counted
     }
@@ -1334,6 +1385,7 @@ col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_
     for (unsigned d = lane; d <= R; d += 32) my_hist[d] = 0;
     __syncwarp();
     const unsigned base_i = warp * (kSortItems * 32) + lane;
+    // (plain loads, all in flight at once: staging the chunk by bulk copy, as col_count does, measured slower here)
     unsigned k[kSortItems], rd[kSortItems];  // rd: rank within the warp's column << 16 | column
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {

@@ -21,6 +21,7 @@ constexpr int kMaxRadius = 65535;        // instance-box half-extents are stored
 
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrConsistency = 2u;  // a device-side consistency check failed (the access was skipped)
+constexpr uint32_t kErrTimeout = 4u;      // a bounded device-side wait ran out (the data it guarded was skipped)
 
 // Workspace header (first 256 bytes of every workspace).
 struct WsHeader {
