@@ -157,7 +157,8 @@ def test_sort_many_ties_and_all_columns():
 def _row_cull_splats(V, n, W, H, seed):
     """Large, strongly sheared ellipses (correlations up to and past the 1 - 1e-3 determinant guard), opacities down
     to just above 1/255 (q near 0), centres on pixel centres and tile corners; the nearest (first in depth order) are
-    the largest, so that one CTA's splats span many more than 1024 tile rows."""
+    the largest, so that one CTA's splats span several thousand box rows (past the 2048 whose bucket offsets bin_count
+    keeps in shared memory; the rest take its global-memory fix-up)."""
     rng = np.random.default_rng(seed)
     m = V * n
     sx, sy = rng.uniform(0.4, 50.0, m), rng.uniform(0.4, 50.0, m)
