@@ -405,7 +405,8 @@ __device__ __forceinline__ u64 pack_row(int cl, unsigned cnt, int ty, int j) {
 // With bucketed_binning, bin_emit writes every instance straight into its (view, tile row) bucket, in depth order,
 // so that omnigs_sort only has to order each bucket by tile column. A block's row items of one bucket take
 // consecutive slots after those of the earlier blocks; within the block, the slots follow the items' order
-// (splat by splat in depth order). That order is found per chunk of row items by a stable, weighted ranking.
+// (splat by splat in depth order). bin_count finds that order by a stable, weighted ranking of the block's row items
+// (WarpBuckets); the fallback emission of blocks whose rows were not stored ranks each chunk again (BucketScratch).
 constexpr int kBinWarps = kBinThreads / 32;
 constexpr int kBucketSlots = 2 * kMaxBucketRows;  // a block's buckets: the tile rows of its (at most two) views
 
@@ -414,7 +415,6 @@ constexpr int kPendRows = 2048;  // row items whose in-warp offsets wait in shar
 // bin_count's ranking: warp w's row items are the block's items [w * per, (w + 1) * per) in order, ranked 32 at a
 // time against the warp's own bucket counters; afterwards every warp's base in a bucket is the count of the earlier
 // warps' items there.
-
 struct WarpBuckets {
     unsigned cw[kBinWarps][kBucketSlots];  // per warp: its items' instances in each bucket so far; then its base
     unsigned run[kBucketSlots];            // the block's instances in each bucket
