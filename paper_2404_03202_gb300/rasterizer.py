@@ -49,11 +49,15 @@ class Rasterizer:
     capacity: room for tile instances. With `grow=True` (default) the forward pass reads the instance count back
     (one synchronisation) and re-bins with a larger capacity when needed. With `grow=False` the pass never
     synchronises (it can be captured in a CUDA graph); an overflow is then reported by `check()`.
+    alloc: optional allocator `(shape, dtype, device) -> tensor` for every device buffer (default torch.empty);
+    forward_only: leave out the buffers of the backward pass (the adjoint's outputs and dL/dC).
     """
 
     def __init__(self, settings: Settings, device="cuda", capacity: int = 1 << 20, grow: bool = True,
-                 headroom: float = 1.25):
+                 headroom: float = 1.25, alloc=None, forward_only: bool = False):
         C.load()
+        self._empty = alloc if alloc is not None else _empty
+        self.forward_only = forward_only
         self.s = settings
         self.cfg = settings.config()
         self.device = torch.device(device)
@@ -63,20 +67,20 @@ class Rasterizer:
         self.n = -1
         self.count = None
         V, H, W = settings.num_views, settings.height, settings.width
-        self.rgb = _empty((V, 3, H, W), torch.float32, self.device)
-        self.T = _empty((V, H, W), torch.float32, self.device)
-        self.ncontrib = _empty((V, H, W), torch.int32, self.device)
+        self.rgb = self._empty((V, 3, H, W), torch.float32, self.device)
+        self.T = self._empty((V, H, W), torch.float32, self.device)
+        self.ncontrib = self._empty((V, H, W), torch.int32, self.device)
         self.count_out = None  # set to an int32 [V, H, W] tensor to receive per-pixel contributor counts
-        self.dL_drgb = _empty((V, 3, H, W), torch.float32, self.device)
+        self.dL_drgb = None if forward_only else self._empty((V, 3, H, W), torch.float32, self.device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
-        self.ranges = _empty((V * settings.tiles * 2,), torch.int32, self.device)
+        self.ranges = self._empty((V * settings.tiles * 2,), torch.int32, self.device)
         self._alloc_instances(self.capacity)
 
     # ---------------------------------------------------------------- buffers
     def _alloc_instances(self, capacity: int):
         self.capacity = int(capacity)
         cap = max(self.capacity, 1)
-        self.keys = _empty((cap,), torch.int64, self.device)
+        self.keys = self._empty((cap,), torch.int64, self.device)
         self.ws = None
 
     def _ensure(self, n: int, K: int):
@@ -84,22 +88,24 @@ class Rasterizer:
         if n != self.n:
             self.n = n
             m = max(V * n, 1)
-            self.splats = _empty((m, C.SPLAT_FLOATS), torch.float32, self.device)
-            self.order = _empty((m,), torch.int32, self.device)
-            self.grads2d = _empty((m, C.GRAD_FLOATS), torch.float32, self.device)
-            self.d_means = _empty((max(n, 1), 3), torch.float32, self.device)
-            self.d_scales = _empty((max(n, 1), 3), torch.float32, self.device)
-            self.d_quats = _empty((max(n, 1), 4), torch.float32, self.device)
-            self.d_opacity = _empty((max(n, 1),), torch.float32, self.device)
-            self.d_screen = _empty((max(n, 1), 2), torch.float32, self.device)
+            self.splats = self._empty((m, C.SPLAT_FLOATS), torch.float32, self.device)
+            self.order = self._empty((m,), torch.int32, self.device)
+            if not self.forward_only:
+                self.grads2d = self._empty((m, C.GRAD_FLOATS), torch.float32, self.device)
+                self.d_means = self._empty((max(n, 1), 3), torch.float32, self.device)
+                self.d_scales = self._empty((max(n, 1), 3), torch.float32, self.device)
+                self.d_quats = self._empty((max(n, 1), 4), torch.float32, self.device)
+                self.d_opacity = self._empty((max(n, 1),), torch.float32, self.device)
+                self.d_screen = self._empty((max(n, 1), 2), torch.float32, self.device)
             self.ws = None
-        if getattr(self, "d_sh", None) is None or self.d_sh.shape[0] != max(n, 1) or self.d_sh.shape[1] != K:
-            self.d_sh = _empty((max(n, 1), K, 3), torch.float32, self.device)
+        if not self.forward_only and (getattr(self, "d_sh", None) is None or self.d_sh.shape[0] != max(n, 1)
+                                      or self.d_sh.shape[1] != K):
+            self.d_sh = self._empty((max(n, 1), K, 3), torch.float32, self.device)
         if self.ws is None:
             nbytes = C.omnigs_workspace_size(self.cfg, max(n, 0), self.capacity)
             if nbytes == 0:
                 raise C.OmnigsError(C.OMNIGS_E_INVALID, "omnigs_workspace_size")
-            self.ws = _empty((nbytes,), torch.uint8, self.device)
+            self.ws = self._empty((nbytes,), torch.uint8, self.device)
 
     # ---------------------------------------------------------------- forward
     def forward(self, means, scales, quats, opacity, sh, viewmats, stream=None):

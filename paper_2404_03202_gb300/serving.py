@@ -222,6 +222,37 @@ def run_trace(scheduler: Scheduler, requests: list, clock=time.perf_counter, sle
     return scheduler.stats.summary(makespan)
 
 
+class _LaneArena:
+    """Device memory of one lane, carved into a batch's buffers. A lane runs one batch at a time and its next batch
+    is launched only after the previous one was collected, so each launch starts carving from the beginning again.
+    The arena grows (one allocation) when a batch needs more than it holds, which the warm-up of every key brings
+    about before any timed work; in steady state a batch allocates no device memory, so no allocation of the
+    framework's caching allocator can stall the other lanes."""
+
+    def __init__(self, torch, device):
+        self.torch, self.device = torch, device
+        self.buf = None
+        self.off = 0
+
+    def reset(self, nbytes: int) -> None:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = self.torch.empty((nbytes,), dtype=self.torch.uint8, device=self.device)
+        self.off = 0
+
+    def alloc(self, shape, dtype, device):
+        torch = self.torch
+        count = 1
+        for d in shape:
+            count *= int(d)
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        if self.buf is not None and self.off + nbytes <= self.buf.numel():
+            t = self.buf[self.off:self.off + nbytes].view(dtype).view(tuple(shape))
+            self.off += (nbytes + 255) // 256 * 256
+            return t
+        return torch.empty(tuple(shape), dtype=dtype, device=device)  # past the arena (a capacity re-run)
+
+
 class GpuExecutor:
     """Renders batches with the CUDA library; every scene stays resident on the device.
 
@@ -244,6 +275,7 @@ class GpuExecutor:
             k = int(t[4].shape[1])
             self.scenes[name] = (t, int(t[0].shape[0]), int(round(k ** 0.5)) - 1)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
+        self.arenas = [_LaneArena(torch, self.device) for _ in range(lanes)]
         self.per_view = {}
         self.overflows = 0
         # one waiter thread per lane blocks on the lane's batches in launch order (its stream runs them in that
@@ -309,9 +341,12 @@ class GpuExecutor:
         v = len(requests)
         params = self.scenes[r0.scene][0]
         vm = np.stack([np.asarray(r.viewmat, np.float32) for r in requests])
+        arena = self.arenas[lane]
+        arena.reset(self.bytes_needed(r0.scene, r0.width, r0.height, v))
         with torch.cuda.stream(s):
             rast = self.og.Rasterizer(self._settings(r0.scene, r0.width, r0.height, v), device=self.device,
-                                      capacity=self._capacity(r0.scene, r0.width, r0.height, v), grow=False)
+                                      capacity=self._capacity(r0.scene, r0.width, r0.height, v), grow=False,
+                                      alloc=arena.alloc, forward_only=True)
             vm_dev = torch.from_numpy(vm).to(self.device, non_blocking=True)
             rast.forward(*params, vm_dev, stream=s)
             host = torch.empty(tuple(rast.rgb.shape), dtype=torch.float32, pin_memory=True)
