@@ -172,3 +172,25 @@ def test_max_wait_stops_backfill():
 def test_bad_scheduler_arguments():
     with pytest.raises(ValueError):
         S.Scheduler(FakeExecutor(SimClock()), lanes=0)
+
+
+def test_lane_arena_carves_aligned_disjoint_buffers_and_falls_back_past_its_end():
+    """The serving executor's per-lane arena (CPU tensors here): buffers in order, each at a 256-byte boundary,
+    disjoint, of the asked shape and type; a request past the arena's end gets an ordinary tensor; reset starts over
+    and grows the arena when asked for more."""
+    torch = pytest.importorskip("torch")
+    ar = S._LaneArena(torch, torch.device("cpu"))
+    ar.reset(4096)
+    a = ar.alloc((3, 5), torch.float32, "cpu")
+    b = ar.alloc((7,), torch.int64, "cpu")
+    c = ar.alloc((100,), torch.uint8, "cpu")
+    base = ar.buf.data_ptr()
+    assert [a.data_ptr() - base, b.data_ptr() - base, c.data_ptr() - base] == [0, 256, 512]
+    assert a.shape == (3, 5) and a.dtype == torch.float32 and b.dtype == torch.int64 and c.shape == (100,)
+    a.fill_(1.0), b.fill_(2), c.fill_(3)
+    assert float(a.sum()) == 15.0 and int(b.sum()) == 14 and int(c.sum()) == 300
+    big = ar.alloc((4096,), torch.float32, "cpu")  # does not fit: a tensor of its own
+    assert not (base <= big.data_ptr() < base + ar.buf.numel())
+    ar.reset(1 << 16)
+    assert ar.buf.numel() >= 1 << 16 and ar.off == 0
+    assert ar.alloc((2,), torch.float32, "cpu").data_ptr() == ar.buf.data_ptr()
