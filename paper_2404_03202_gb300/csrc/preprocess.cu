@@ -348,7 +348,10 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
 // ---------------------------------------------------------------------------------------------------- adjoint
 
 template <int K, bool kPin>
-__global__ void __launch_bounds__(kPreBwdThreads, 512 / kPreBwdThreads)
+// 20 one-warp CTAs per SM: 96 registers a thread (12 bytes spilled), against 128 at 16 CTAs: the kernel waits on
+// memory, and the extra warps cover it (0.168 ms against 0.180 on the 8-view egocentric step; 80 registers spill
+// 136 bytes and measured 0.188)
+__global__ void __launch_bounds__(kPreBwdThreads, 20)
 preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                       const float* __restrict__ scales, const float* __restrict__ quats,
                       const float* __restrict__ opacity, const float* __restrict__ sh,
