@@ -100,6 +100,23 @@ def test_bin_sort_valid(tile, V, n, W, H):
         assert np.array_equal(order[v] - v * n, np.lexsort((np.arange(n), d)))
 
 
+def test_bin_sort_valid_when_rows_overflow_the_row_store():
+    """The instance capacity set to the count itself, with splats of one or two tiles per box row: the box rows
+    outnumber what the row store holds (capacity / 2 + 1 rows), so bin_count stores the first blocks' rows and the
+    fallback emission derives and ranks the other blocks' rows again. The lists stay valid and complete."""
+    W, H, V, n, T = 512, 256, 2, 4000, 16
+    sp = synth.random_splats(V, n, W, H, seed=77, max_radius=6, wide_frac=0.0)
+    ry = np.asarray(sp["ry"], np.int64)
+    iy = np.floor(np.asarray(sp["py"], np.float64)).astype(np.int64)
+    y0 = np.maximum(np.floor_divide(iy - ry, T), 0)
+    y1 = np.minimum(np.floor_divide(iy + ry, T), H // T - 1)
+    rows = int(np.where(np.asarray(sp["rx"]) > 0, np.maximum(y1 - y0 + 1, 0), 0).sum())
+    r, cnt = _run_splats(pack_splats(sp), _settings(W, H, tile=T, V=V), capacity=1)
+    assert r.capacity == cnt and rows > cnt // 2 + 1, (rows, cnt)
+    st = check_gpu_lists(r, cnt, sp, V, W, H, T)
+    print(f"row store overflow: {rows} box rows, {cnt} instances: {st}")
+
+
 def _whole_row_splats(V, n, W, H, seed):
     """Boxes wider than the image and, for the rest, needle conics (det = 5e-4 c0 c2, either sign of c1): the
     binning keeps every tile of every box."""
