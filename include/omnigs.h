@@ -142,8 +142,8 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
  *           order (a splat's tiles row by row, columns in seam order), so within a tile they are already in rank
  *           order. When 256 <= n <= 2^24 and an image has at most 128 tile rows and 256 tile columns,
  *           omnigs_bin writes them into the workspace, grouped by (view, tile row) in that order (as 32-bit entries),
- *           and leaves `keys` for omnigs_sort to fill; otherwise it writes them into `keys` in generation order. Either way omnigs_sort leaves the
- *           sorted keys in `keys`.
+ *           and leaves `keys` for omnigs_sort to fill; otherwise it writes them into `keys` in generation order.
+ *           Either way omnigs_sort leaves the sorted keys in `keys`.
  * The total instance count stays on the device (workspace); if it exceeds `capacity`, instances beyond it are dropped
  * and OMNIGS_E_CAPACITY is raised in the workspace. capacity < 2^32, the value given to omnigs_workspace_size. */
 omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,

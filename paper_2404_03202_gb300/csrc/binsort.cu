@@ -487,7 +487,8 @@ template <bool kBuckets>
 __global__ void __launch_bounds__(kBinThreads, kBuckets ? 6 : 8)
 bin_count_kernel(int64_t total, const float4* __restrict__ splats, const uint32_t* __restrict__ order, int tiles_x,
                  int tiles_y, int tile, int wrap, int V, int64_t n, unsigned nb, const unsigned* __restrict__ vis_start,
-                 unsigned* __restrict__ block_sums, u64* __restrict__ rows, u64 row_cap, unsigned* __restrict__ row_base,
+                 unsigned* __restrict__ block_sums, u64* __restrict__ rows, u64 row_cap,
+                 unsigned* __restrict__ row_base,
                  unsigned* __restrict__ row_count, WsHeader* __restrict__ hdr, unsigned* __restrict__ rows_off,
                  unsigned* __restrict__ bkt_counts, int nbv, unsigned* __restrict__ unstored_list) {
     __shared__ unsigned scratch[32];
@@ -1359,12 +1360,13 @@ col_scan_kernel(const u64* __restrict__ base, const unsigned* __restrict__ col_s
 
 // Chunk c of a bucket, ordered by column and written to its final positions as tile keys (one CTA per chunk): the
 // entries are ranked stably by column within each warp (the lanes sharing a column found by one ballot per column
-// bit, a padding column for missing entries included), the warps' counts are combined in warp order, the entries are placed in
-// column order in shared memory, and each is written to hist[c][tx] + its rank within its column.
+// bit, a padding column for missing entries included), the warps' counts are combined in warp order, the entries are
+// placed in column order in shared memory, and each is written to hist[c][tx] + its rank within its column.
 __global__ void __launch_bounds__(kSortThreads, 4)
 col_scatter_kernel(const unsigned* __restrict__ entries, u64* __restrict__ keys_out, const u64* __restrict__ base,
-                   const u64* __restrict__ eff, const unsigned* __restrict__ col_start, int nbkt, int tiles_x, int dbits,
-                   int rank_bits, const unsigned* __restrict__ hist, u64 capacity, WsHeader* __restrict__ hdr) {
+                   const u64* __restrict__ eff, const unsigned* __restrict__ col_start, int nbkt, int tiles_x,
+                   int dbits, int rank_bits, const unsigned* __restrict__ hist, u64 capacity,
+                   WsHeader* __restrict__ hdr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned* s_ent = reinterpret_cast<unsigned*>(smem_raw);
     unsigned* s_whist = s_ent + kSortTile;  // [kWarps][kHistRow]

@@ -32,7 +32,8 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * ((size_t)num_sms() * kSortCtasPerSm + 1));
     const bool bk = bucketed_binning(cfg, n);  // bucket entries are 32 bits, radix-sort keys 64
     // (+16 bytes: the column pass's bulk copies read whole 16-byte words, up to 12 bytes past the last entry)
-    L.alt_keys = off;       off += align256((bk ? sizeof(unsigned) : sizeof(unsigned long long)) * (size_t)capacity + 16);
+    const size_t alt_bytes = (bk ? sizeof(unsigned) : sizeof(unsigned long long)) * (size_t)capacity + 16;
+    L.alt_keys = off;       off += align256(alt_bytes);
     L.depth_keys = off;     off += align256(sizeof(unsigned long long) * total);
     L.depth_keys_alt = off; off += align256(sizeof(unsigned long long) * total);
     L.depth_vals_alt = off; off += align256(sizeof(uint32_t) * total);
