@@ -615,27 +615,42 @@ bin_scan_kernel(int nblocks, const unsigned* __restrict__ block_sums, u64* __res
                 unsigned max_pieces, WsHeader* __restrict__ hdr, u64 capacity) {
     __shared__ u64 scratch[32];
     __shared__ unsigned scratch32[32];
+    constexpr int kLoads = 8;  // a thread's sums are read 8 at a time, all in flight (one latency per 8, not per sum)
     const int per = (nblocks + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblocks);
     u64 local = 0;
     unsigned extra = 0;
-    for (int b = b0; b < b1; ++b) {
-        local += block_sums[b];
-        if (piece) extra += (block_sums[b] + piece - 1) / piece - (block_sums[b] > 0 ? 1u : 0u);
+    for (int b = b0; b < b1; b += kLoads) {
+        unsigned v[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) v[q] = b + q < b1 ? block_sums[b + q] : 0u;
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+            local += v[q];
+            if (piece) extra += (v[q] + piece - 1) / piece - (v[q] > 0 ? 1u : 0u);
+        }
     }
     u64 tot;
     u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
     unsigned extra_tot;
     unsigned erun = block_exclusive_scan<unsigned>(extra, scratch32, &extra_tot);
-    for (int b = b0; b < b1; ++b) {
-        block_offsets[b] = run;
-        run += block_sums[b];
-        if (!piece) continue;
-        const unsigned eb = (block_sums[b] + piece - 1) / piece - (block_sums[b] > 0 ? 1u : 0u);
-        piece_start[b] = erun;
-        for (unsigned k = 0; k < eb; ++k)
-            if (erun + k < max_pieces) piece_block[erun + k] = (unsigned)b;
-        erun += eb;
+    for (int b0q = b0; b0q < b1; b0q += kLoads) {
+        unsigned v[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) v[q] = b0q + q < b1 ? block_sums[b0q + q] : 0u;
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+            const int b = b0q + q;
+            if (b >= b1) break;
+            block_offsets[b] = run;
+            run += v[q];
+            if (!piece) continue;
+            const unsigned eb = (v[q] + piece - 1) / piece - (v[q] > 0 ? 1u : 0u);
+            piece_start[b] = erun;
+            for (unsigned k = 0; k < eb; ++k)
+                if (erun + k < max_pieces) piece_block[erun + k] = (unsigned)b;
+            erun += eb;
+        }
     }
     if (threadIdx.x == 0) {
         hdr->count = tot;
@@ -1176,16 +1191,28 @@ bucket_scan_kernel(int tiles_y, int64_t n, int nbv, unsigned* __restrict__ count
     const int64_t v = b / tiles_y;
     const int nblk = (int)(view_last_block(v, n) - view_first_block(v, n) + 1);
     unsigned* c = counts + (size_t)b * nbv;
+    constexpr int kLoads = 8;  // read 8 at a time, all in flight
     const int per = (nblk + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblk);
     u64 local = 0;
-    for (int i = b0; i < b1; ++i) local += c[i];
+    for (int i = b0; i < b1; i += kLoads) {
+        unsigned v[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) v[q] = i + q < b1 ? c[i + q] : 0u;
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) local += v[q];
+    }
     u64 tot;
     u64 run = block_exclusive_scan<u64>(local, scratch, &tot);
-    for (int i = b0; i < b1; ++i) {
-        const unsigned x = c[i];
-        c[i] = (unsigned)run;
-        run += x;
+    for (int i = b0; i < b1; i += kLoads) {
+        unsigned v[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) v[q] = i + q < b1 ? c[i + q] : 0u;
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+            if (i + q < b1) c[i + q] = (unsigned)run;
+            run += v[q];
+        }
     }
     if (threadIdx.x == 0) totals[b] = tot;
 }
