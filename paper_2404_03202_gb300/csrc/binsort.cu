@@ -107,6 +107,15 @@ __device__ __forceinline__ SplatPos load_pos(const float4* __restrict__ sp, size
 // when the box spans every column, when the conic is a needle (det <= 1e-3 c0 c2, where the bounds lose precision),
 // and, with the longitude seam, when rx + tile > W / 2: only below that do the box's unwrapped column offsets equal
 // the minimal-image offsets (|dx| < W / 2) that the blend evaluates, so the span is taken on the copy the blend uses.
+// The quotients and square roots are the hardware approximations (relative error a few units in the last place):
+// against the widening (one pixel; 0.1 % of q) their error is negligible, and they took bin_count from 0.484 to
+// 0.464 ms on the 8-view egocentric frame (the conic entries are far below 2^126, where the fast quotient fails).
+__device__ __forceinline__ float approx_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct RowCull {
     float px, py, s, yL;  // centre, shear c1 / c0, leftmost-point offset
     float ey, w2, k;      // ey < 0: no culling (whole rows)
@@ -121,11 +130,11 @@ __device__ __forceinline__ RowCull row_cull_setup(const SplatPos& p, int nx, int
     const float guard = __fmul_rn(1e-3f, c0c2);
     if (!(det > guard) || !(p.c0 > 0.f) || !(p.c2 > 0.f)) return rc;
     const float qw = __fadd_rn(__fmul_rn(p.q, 1.001f), 1e-3f);
-    rc.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(qw, p.c0), det));
-    rc.yL = __fmul_rn(p.c1, __fsqrt_rn(__fdiv_rn(qw, __fmul_rn(det, p.c2))));
-    rc.s = __fdiv_rn(p.c1, p.c0);
-    rc.w2 = __fdiv_rn(qw, p.c0);
-    rc.k = __fdiv_rn(__fdiv_rn(det, p.c0), p.c0);
+    rc.ey = approx_sqrt(__fdividef(__fmul_rn(qw, p.c0), det));
+    rc.yL = __fmul_rn(p.c1, approx_sqrt(__fdividef(qw, __fmul_rn(det, p.c2))));
+    rc.s = __fdividef(p.c1, p.c0);
+    rc.w2 = __fdividef(qw, p.c0);
+    rc.k = __fdividef(__fdividef(det, p.c0), p.c0);
     return rc;
 }
 
@@ -146,13 +155,13 @@ __device__ __forceinline__ int2 row_cols(const RowCull& rc, int x0, int nx, int 
     hL = hL > 0.f ? hL : 0.f;
     float hR = __fsub_rn(rc.w2, __fmul_rn(rc.k, __fmul_rn(vR, vR)));
     hR = hR > 0.f ? hR : 0.f;
-    const float xl = __fsub_rn(-__fmul_rn(rc.s, vL), __fsqrt_rn(hL));
-    const float xr = __fadd_rn(-__fmul_rn(rc.s, vR), __fsqrt_rn(hR));
+    const float xl = __fsub_rn(-__fmul_rn(rc.s, vL), approx_sqrt(hL));
+    const float xr = __fadd_rn(-__fmul_rn(rc.s, vR), approx_sqrt(hR));
     const float ul = __fsub_rn(__fadd_rn(rc.px, xl), 1.f);
     const float ur = __fadd_rn(__fadd_rn(rc.px, xr), 1.f);
     // tile column c reaches the band when c T + T - 1/2 >= ul and c T + 1/2 <= ur; T is a power of two, so the
-    // product with 1 / T equals the correctly rounded quotient by T
-    const float inv_T = 1.f / fT;
+    // product with 1 / T (built from its exponent) equals the correctly rounded quotient by T
+    const float inv_T = __int_as_float((127 - (__ffs(tile) - 1)) << 23);
     float a = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(ul, 0.5f), fT), inv_T));
     float b = floorf(__fmul_rn(__fsub_rn(ur, 0.5f), inv_T));
     const float fx0 = (float)x0, fx1 = (float)(x0 + nx - 1);
