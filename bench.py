@@ -132,7 +132,7 @@ RENDER_BWD_TRAFFIC = {"bytes_per_view": 49_962_496,
 def render_bwd_source(text: str) -> str:
     """The part of render.cu the adjoint kernel is built from: the staging helpers and the adjoint itself."""
     a = text.index("struct Staged {")
-    f = text.rindex("template <", 0, text.index("render_fwd_kernel("))
+    f = text.rindex("template <", 0, text.index("render_fwd_body("))
     g = text.index("constexpr int kGradFields")
     h = text.index("size_t bwd_smem(")
     return text[a:f] + text[g:h]
@@ -578,7 +578,8 @@ def workload_config(wl, args, settings=None):
             "tile": tile, "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)",
-            "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1",
+            "loss": ("L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim"
+                     else ("L1 over the loss rows" if wl.get("loss_rows") else "L1, fused into the forward blend")),
             "camera": f"pinhole fx, fy, cx, cy = {wl['pinhole']}" if wl.get("pinhole") else "equirectangular"}
 
 
@@ -662,9 +663,15 @@ def main():
         else:
             r.l1_loss(tgt, rows=loss_rows)
 
+    # the full-image L1 loss is computed by the forward blend itself (omnigs_render_fwd_l1)
+    fused_l1 = dssim_scratch is None and loss_rows is None
+
     def step():
-        r.forward(*params, vm)
-        loss_fn(target)
+        if fused_l1:
+            r.forward(*params, vm, l1_target=target)
+        else:
+            r.forward(*params, vm)
+            loss_fn(target)
         r.backward()
 
     for _ in range(args.warmup):
@@ -748,7 +755,7 @@ def main():
         out_shapes = {k: tuple(getattr(r, "d_" + k).shape) for k in Rasterizer.GRAD_NAMES}
         out_shapes["loss"] = (1,)
         host_out = {k: torch.empty(v, dtype=torch.float32).pin_memory() for k, v in out_shapes.items()}
-        streamed = StreamedSteps(r, lambda rr, t: loss_fn(t), graph=not args.no_graph)
+        streamed = StreamedSteps(r, None if fused_l1 else (lambda rr, t: loss_fn(t)), graph=not args.no_graph)
 
         for _ in range(2):
             streamed.submit(host_in, host_out)

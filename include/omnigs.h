@@ -171,6 +171,19 @@ omnigs_status omnigs_render_fwd(const omnigs_config *cfg, int64_t n, const omnig
                                 const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
                                 float *out_T, uint32_t *out_ncontrib, uint32_t *out_count, omnigs_stream_t stream);
 
+/* omnigs_render_fwd followed by omnigs_l1_loss in one pass over the image: the forward blend's epilogue compares
+ * each pixel's colour with target [V, 3, H, W] (device) and writes dL_drgb [V, 3, H, W] = sign(rgb - target) /
+ * (V * 3 * H * W), bit for bit what omnigs_l1_loss writes for this out_rgb, and per tile the sum of |rgb - target|,
+ * which a second kernel adds up in double precision into loss [1] (device) = mean |rgb - target|. The loss differs
+ * from omnigs_l1_loss's only in the order of the additions (a few units in the last place of the float result).
+ * This saves the loss kernel's read of the image (Eq. 17's L1 term and Eqs. 6-8, fused; the paper has no such
+ * interface). Other arguments as for omnigs_render_fwd (no per-pixel count); workspace as for omnigs_l1_loss (the
+ * per-tile sums sit at a fixed offset of it). Calls sharing a workspace must not overlap on the GPU. */
+omnigs_status omnigs_render_fwd_l1(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats,
+                                   const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
+                                   const float *target, float *out_rgb, float *out_T, uint32_t *out_ncontrib,
+                                   float *dL_drgb, float *loss, void *workspace, omnigs_stream_t stream);
+
 /* L1 term of the photometric loss (Eq. 17 with lambda = 0): loss = mean |rgb - target| over [V, 3, H, W];
  * dL_drgb = sign(rgb - target) / (V * 3 * H * W) (0 where equal). rgb, target: inputs; dL_drgb [V, 3, H, W] and
  * loss [1]: outputs (device). */

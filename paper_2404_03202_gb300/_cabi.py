@@ -75,6 +75,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P]
         lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
         lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
+        lib.omnigs_render_fwd_l1.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.omnigs_l1_loss.argtypes = [cfgp, P, P, P, P, P, P]
         lib.omnigs_l1_loss_rows.argtypes = [cfgp, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
         lib.omnigs_l1_loss_static.argtypes = [cfgp, P, P, P, P, P]
@@ -99,7 +100,8 @@ def load() -> ctypes.CDLL:
         lib.omnigs_profiler_enable.argtypes = [ctypes.c_int]
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
-        for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_l1_loss",
+        for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_render_fwd_l1",
+                     "omnigs_l1_loss",
                      "omnigs_l1_loss_rows", "omnigs_dssim_loss", "omnigs_adam_step", "omnigs_publish_params",
                      "omnigs_densify_stats", "omnigs_densify", "omnigs_reset_opacity", "omnigs_equirect_crop",
                      "omnigs_render_bwd", "omnigs_preprocess_bwd", "omnigs_instance_count", "omnigs_last_error",
@@ -180,6 +182,13 @@ def omnigs_render_fwd(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_n
     _check(load().omnigs_render_fwd(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(keys), _ptr(order),
                                     _ptr(out_rgb), _ptr(out_T), _ptr(out_ncontrib), _ptr(out_count), _stream(stream)),
            "omnigs_render_fwd")
+
+
+def omnigs_render_fwd_l1(cfg, n, splats, ranges, keys, order, target, out_rgb, out_T, out_ncontrib, dL_drgb, loss,
+                         workspace, stream=None):
+    _check(load().omnigs_render_fwd_l1(ctypes.byref(cfg), n, _ptr(splats), _ptr(ranges), _ptr(keys), _ptr(order),
+                                       _ptr(target), _ptr(out_rgb), _ptr(out_T), _ptr(out_ncontrib), _ptr(dL_drgb),
+                                       _ptr(loss), _ptr(workspace), _stream(stream)), "omnigs_render_fwd_l1")
 
 
 def omnigs_l1_loss(cfg, rgb, target, dL_drgb, loss, workspace, stream=None):

@@ -70,7 +70,7 @@ __device__ inline Rect splat_rect(float px, float py, int rx, int ry, int tiles_
 // Order: fixed-size regions, then those sized by the capacity, then those sized by n, so that calls which do not take
 // n or the capacity find their regions at the same offsets as omnigs_bin.
 struct WsLayout {
-    size_t header, loss_partials, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
+    size_t header, loss_partials, loss_tiles, hist, alt_keys, depth_keys, depth_keys_alt, depth_vals_alt, block_sums,
         block_offsets, piece_start, piece_block, row_base, row_count, vis_sums, vis_start, vis_mask,
         // bucketed instance order (see bucketed_binning): stored row words and their bucket offsets, per-block
         // bucket counts, bucket totals and bases, chunk starts and the column pass's per-chunk histograms
@@ -136,9 +136,18 @@ cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *
                        uint64_t *keys, int64_t capacity, const WsLayout &L, char *ws, cudaStream_t stream);
 cudaError_t launch_sort(const omnigs_config &cfg, int64_t n, int64_t capacity, uint64_t *keys, uint32_t *ranges,
                         const WsLayout &L, char *ws, cudaStream_t stream);
+// The L1 loss fused into the forward blend (omnigs_render_fwd_l1): the target image, the gradient and loss outputs,
+// and the per-tile partial sums [V * TILES] in the workspace.
+struct FwdL1 {
+    const float *target;
+    float *dL_drgb;
+    float *loss;
+    float *tile_sums;
+};
 cudaError_t launch_render_fwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
                               const uint32_t *ranges, const uint64_t *keys, const uint32_t *order, float *out_rgb,
-                              float *out_T, uint32_t *out_nc, uint32_t *out_count, cudaStream_t stream);
+                              float *out_T, uint32_t *out_nc, uint32_t *out_count, const FwdL1 *l1,
+                              cudaStream_t stream);
 cudaError_t launch_render_bwd(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats,
                               const uint32_t *ranges, const uint64_t *keys, const uint32_t *order,
                               const float *out_T, const uint32_t *nc, const float *dL_drgb,

@@ -29,6 +29,9 @@ WsLayout ws_layout(const omnigs_config& cfg, int64_t n, int64_t capacity) {
     size_t off = 0;
     L.header = off;         off += align256(sizeof(WsHeader));
     L.loss_partials = off;  off += align256(sizeof(float) * L.loss_blocks);
+    // per-tile sums of the forward with the L1 loss fused in (omnigs_render_fwd_l1)
+    L.loss_tiles = off;     off += align256(sizeof(float) * (size_t)cfg.num_views * (cfg.width / cfg.tile) *
+                                            (cfg.height / cfg.tile));
     L.hist = off;           off += align256(sizeof(unsigned) * kRadixMax * ((size_t)num_sms() * kSortCtasPerSm + 1));
     const bool bk = bucketed_binning(cfg, n);  // bucket entries are 32 bits, radix-sort keys 64
     // (+16 bytes: the column pass's bulk copies read whole 16-byte words, up to 12 bytes past the last entry)
@@ -204,7 +207,21 @@ omnigs_status omnigs_render_fwd(const omnigs_config* cfg, int64_t n, const omnig
     if (!ranges || !out_rgb || !out_T || !out_ncontrib) return OMNIGS_E_INVALID;
     if (n > 0 && (!splats || !keys || !order || !aligned(splats, 16))) return OMNIGS_E_INVALID;
     return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, out_count,
-                                       (cudaStream_t)stream));
+                                       nullptr, (cudaStream_t)stream));
+}
+
+omnigs_status omnigs_render_fwd_l1(const omnigs_config* cfg, int64_t n, const omnigs_splat* splats,
+                                   const uint32_t* ranges, const uint64_t* keys, const uint32_t* order,
+                                   const float* target, float* out_rgb, float* out_T, uint32_t* out_ncontrib,
+                                   float* dL_drgb, float* loss, void* workspace, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n)) return OMNIGS_E_INVALID;
+    if (!ranges || !out_rgb || !out_T || !out_ncontrib) return OMNIGS_E_INVALID;
+    if (n > 0 && (!splats || !keys || !order || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    if (!target || !dL_drgb || !loss || !workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, 0, 0);  // the per-tile sums sit at a fixed offset
+    const FwdL1 l1 = {target, dL_drgb, loss, reinterpret_cast<float*>((char*)workspace + L.loss_tiles)};
+    return from_cuda(launch_render_fwd(*cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_ncontrib, nullptr,
+                                       &l1, (cudaStream_t)stream));
 }
 
 omnigs_status omnigs_l1_loss(const omnigs_config* cfg, const float* rgb, const float* target, float* dL_drgb,

@@ -134,14 +134,16 @@ struct InterleavedRows {
     }
 };
 
-template <int TS, int PPT, bool kCount>
-__global__ void __launch_bounds__(TS * TS / PPT)
-render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0,
-                  float bg1,
-                  float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
-                  const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
-                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
-                  uint32_t* __restrict__ out_count) {
+template <int TS, int PPT, bool kCount, bool kL1>
+__device__ __forceinline__ void render_fwd_body(int W, int H, float halfW, int tiles_x, int tiles, int n,
+                                                unsigned long long rank_mask, float bg0, float bg1, float bg2,
+                                                const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                                                const unsigned long long* __restrict__ keys,
+                                                const uint32_t* __restrict__ order, float* __restrict__ out_rgb,
+                                                float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
+                                                uint32_t* __restrict__ out_count, const float* __restrict__ target,
+                                                float* __restrict__ dL, float* __restrict__ tile_sums,
+                                                float inv_total) {
     constexpr int NT = PixelMap<TS, PPT>::NT;
     constexpr int NP = PPT / 2;
     static_assert(PPT % 2 == 0, "pixels are blended in pairs");
@@ -233,6 +235,7 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         }
     }
     const size_t HW = (size_t)H * W;
+    float l1 = 0.f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int q = k >> 1;
@@ -240,13 +243,66 @@ render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsi
         const float c0 = (k & 1) ? C0[q].y : C0[q].x, c1 = (k & 1) ? C1[q].y : C1[q].x;
         const float c2 = (k & 1) ? C2[q].y : C2[q].x;
         const size_t pix = (size_t)(pm.y0 + k) * W + pm.x;
-        out_rgb[(3 * (size_t)v + 0) * HW + pix] = fmaf(Tk, bg0, c0);
-        out_rgb[(3 * (size_t)v + 1) * HW + pix] = fmaf(Tk, bg1, c1);
-        out_rgb[(3 * (size_t)v + 2) * HW + pix] = fmaf(Tk, bg2, c2);
+        const float rgb[3] = {fmaf(Tk, bg0, c0), fmaf(Tk, bg1, c1), fmaf(Tk, bg2, c2)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t i = (3 * (size_t)v + c) * HW + pix;
+            out_rgb[i] = rgb[c];
+            if constexpr (kL1) {
+                const float d = rgb[c] - __ldg(target + i);
+                l1 += fabsf(d);
+                dL[i] = d > 0.f ? inv_total : (d < 0.f ? -inv_total : 0.f);
+            }
+        }
         out_T[(size_t)v * HW + pix] = Tk;
         out_nc[(size_t)v * HW + pix] = last[k];
         if (kCount) out_count[(size_t)v * HW + pix] = count[k];
     }
+    if constexpr (kL1) {
+        __shared__ float s_l1[NT / 32];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        if ((threadIdx.x & 31) == 0) s_l1[threadIdx.x >> 5] = l1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) t += s_l1[w];
+            tile_sums[tile_id] = t;
+        }
+    }
+}
+
+template <int TS, int PPT, bool kCount>
+__global__ void __launch_bounds__(TS * TS / PPT)
+render_fwd_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask, float bg0,
+                  float bg1, float bg2, const float4* __restrict__ splats, const uint32_t* __restrict__ ranges,
+                  const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ order,
+                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_nc,
+                  uint32_t* __restrict__ out_count) {
+    render_fwd_body<TS, PPT, kCount, false>(W, H, halfW, tiles_x, tiles, n, rank_mask, bg0, bg1, bg2, splats, ranges,
+                                            keys, order, out_rgb, out_T, out_nc, out_count, nullptr, nullptr, nullptr,
+                                            0.f);
+}
+
+// The forward with the L1 loss fused into its epilogue (omnigs_render_fwd_l1). Each pixel's colour, already in
+// registers, is compared with the target: dL = sign(rgb - target) * inv_total is written beside it, and the CTA's sum
+// of |rgb - target| (in pixel order within each thread, then thread and warp order) goes to tile_sums[tile], which
+// l1_tiles_finish_kernel adds up. The epilogue needs a few more registers than the plain forward's; at 16 x 16 tiles
+// and 4 pixels a thread the budget is held at the plain kernel's 64 (16 CTAs per SM) without spilling. Measured on
+// the 8-view egocentric frame: 0.977 ms against 0.979 for the plain forward (plus 0.105 for the separate loss and its
+// finish); prefetching the targets to L2 when the CTA starts cost 0.014 ms more.
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT, TS * TS / PPT == 64 ? 16 : 1)
+render_fwd_l1_kernel(int W, int H, float halfW, int tiles_x, int tiles, int n, unsigned long long rank_mask,
+                     float bg0, float bg1, float bg2, const float4* __restrict__ splats,
+                     const uint32_t* __restrict__ ranges, const unsigned long long* __restrict__ keys,
+                     const uint32_t* __restrict__ order, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                     uint32_t* __restrict__ out_nc, const float* __restrict__ target, float* __restrict__ dL,
+                     float* __restrict__ tile_sums, float inv_total) {
+    render_fwd_body<TS, PPT, false, true>(W, H, halfW, tiles_x, tiles, n, rank_mask, bg0, bg1, bg2, splats, ranges,
+                                          keys, order, out_rgb, out_T, out_nc, nullptr, target, dL, tile_sums,
+                                          inv_total);
 }
 
 constexpr int kGradFields = 9;
@@ -526,6 +582,41 @@ size_t bwd_smem(int nt) {
     return (size_t)nt * (sizeof(BwdStaged) + sizeof(unsigned) + kGradFields * sizeof(float));
 }
 
+// Sum of the forward's per-tile L1 sums, then the mean, by one CTA of kLossBlocks threads. Each thread adds its
+// tiles (16 loads in flight at a time) in FP32 with Kahan's compensation, and the threads' sums are added in double
+// precision: GB300's FP64 rate is a small fraction of its FP32 rate, and 65,536 double additions on one SM took
+// 43 us where this takes a few. The order of the additions is fixed, so the loss is reproducible.
+__global__ void __launch_bounds__(kLossBlocks)
+l1_tiles_finish_kernel(const float* __restrict__ tile_sums, int nt, float inv_total, float* __restrict__ loss) {
+    __shared__ double red[kLossBlocks / 32];
+    constexpr int kBatch = 16;
+    float sum = 0.f, comp = 0.f;  // the running sum and minus its lost low-order part
+    for (int i0 = (int)threadIdx.x; i0 < nt; i0 += kBatch * kLossBlocks) {
+        float x[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q)
+            x[q] = i0 + q * kLossBlocks < nt ? __ldg(tile_sums + i0 + q * kLossBlocks) : 0.f;
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+            const float y = x[q] - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+    }
+    double s = (double)sum - (double)comp;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = red[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *loss = (float)(s * (double)inv_total);
+    }
+}
+
 // Half the image width for the minimal-image dx across the longitude seam; +inf turns the wrap off (pinhole camera).
 float seam_half_width(const omnigs_config& cfg) {
     return cfg.camera == OMNIGS_CAMERA_EQUIRECT ? 0.5f * (float)cfg.width : INFINITY;
@@ -549,15 +640,30 @@ int adjoint_ppt(const omnigs_config& cfg) {
 template <int TS, int PPT>
 cudaError_t render_fwd_t(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, const uint32_t* ranges,
                          const uint64_t* keys, const uint32_t* order, float* out_rgb, float* out_T, uint32_t* out_nc,
-                         uint32_t* out_count, cudaStream_t stream) {
+                         uint32_t* out_count, const FwdL1* l1, cudaStream_t stream) {
     const int tx = cfg.width / TS, tiles = tx * (cfg.height / TS);
     const unsigned long long mask = (1ull << rank_bits_for(n)) - 1ull;
-    ProfScope prof("render_fwd", stream);
-    auto kern = out_count ? render_fwd_kernel<TS, PPT, true> : render_fwd_kernel<TS, PPT, false>;
-    kern<<<tiles * cfg.num_views, PixelMap<TS, PPT>::NT, 0, stream>>>(
-        cfg.width, cfg.height, seam_half_width(cfg), tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
-        reinterpret_cast<const float4*>(splats), ranges, reinterpret_cast<const unsigned long long*>(keys), order,
-        out_rgb, out_T, out_nc, out_count);
+    const float inv_total = l1 ? (float)(1.0 / ((double)cfg.num_views * 3.0 * cfg.height * cfg.width)) : 0.f;
+    {
+        ProfScope prof("render_fwd", stream);
+        const unsigned grid = (unsigned)(tiles * cfg.num_views), block = PixelMap<TS, PPT>::NT;
+        const float4* sp = reinterpret_cast<const float4*>(splats);
+        const unsigned long long* ks = reinterpret_cast<const unsigned long long*>(keys);
+        if (l1) {
+            render_fwd_l1_kernel<TS, PPT><<<grid, block, 0, stream>>>(
+                cfg.width, cfg.height, seam_half_width(cfg), tx, tiles, (int)n, mask, cfg.bg[0], cfg.bg[1], cfg.bg[2],
+                sp, ranges, ks, order, out_rgb, out_T, out_nc, l1->target, l1->dL_drgb, l1->tile_sums, inv_total);
+        } else {
+            auto kern = out_count ? render_fwd_kernel<TS, PPT, true> : render_fwd_kernel<TS, PPT, false>;
+            kern<<<grid, block, 0, stream>>>(cfg.width, cfg.height, seam_half_width(cfg), tx, tiles, (int)n, mask,
+                                             cfg.bg[0], cfg.bg[1], cfg.bg[2], sp, ranges, ks, order, out_rgb, out_T,
+                                             out_nc, out_count);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !l1) return e;
+    ProfScope prof("l1_finish", stream);
+    l1_tiles_finish_kernel<<<1, kLossBlocks, 0, stream>>>(l1->tile_sums, tiles * cfg.num_views, inv_total, l1->loss);
     return cudaGetLastError();
 }
 
@@ -638,21 +744,17 @@ l1_finish_kernel(const float* __restrict__ partials, int nb, float inv_total, fl
 
 cudaError_t launch_render_fwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,
                               const uint32_t* ranges, const uint64_t* keys, const uint32_t* order, float* out_rgb,
-                              float* out_T, uint32_t* out_nc, uint32_t* out_count, cudaStream_t stream) {
+                              float* out_T, uint32_t* out_nc, uint32_t* out_count, const FwdL1* l1,
+                              cudaStream_t stream) {
     const int ppt = blend_ppt(cfg);
+#define OMNIGS_FWD(TS, PPT) render_fwd_t<TS, PPT>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, \
+                                                  out_count, l1, stream)
     switch (cfg.tile) {
-        case 8: return render_fwd_t<8, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-        case 32:
-            if (ppt == 8)
-                return render_fwd_t<32, 8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-            return ppt == 4 ? render_fwd_t<32, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
-                            : render_fwd_t<32, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-        default:
-            if (ppt == 8)
-                return render_fwd_t<16, 8>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
-            return ppt == 4 ? render_fwd_t<16, 4>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream)
-                            : render_fwd_t<16, 2>(cfg, n, splats, ranges, keys, order, out_rgb, out_T, out_nc, out_count, stream);
+        case 8: return OMNIGS_FWD(8, 2);
+        case 32: return ppt == 8 ? OMNIGS_FWD(32, 8) : (ppt == 4 ? OMNIGS_FWD(32, 4) : OMNIGS_FWD(32, 2));
+        default: return ppt == 8 ? OMNIGS_FWD(16, 8) : (ppt == 4 ? OMNIGS_FWD(16, 4) : OMNIGS_FWD(16, 2));
     }
+#undef OMNIGS_FWD
 }
 
 cudaError_t launch_render_bwd(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats,

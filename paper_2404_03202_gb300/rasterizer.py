@@ -108,9 +108,11 @@ class Rasterizer:
             self.ws = self._empty((nbytes,), torch.uint8, self.device)
 
     # ---------------------------------------------------------------- forward
-    def forward(self, means, scales, quats, opacity, sh, viewmats, stream=None):
+    def forward(self, means, scales, quats, opacity, sh, viewmats, stream=None, l1_target=None):
         """Render every view. Inputs are contiguous float32 device tensors; returns rgb [V, 3, H, W] (a buffer of
-        this Rasterizer, overwritten by the next forward)."""
+        this Rasterizer, overwritten by the next forward). With l1_target (a [V, 3, H, W] float32 device tensor) the
+        L1 loss is computed by the blend itself (omnigs_render_fwd_l1): self.loss and self.dL_drgb are then set as
+        l1_loss(l1_target) would set them, without a second pass over the image."""
         n = int(means.shape[0])
         K = int(sh.shape[1]) if n > 0 else (self.s.sh_degree + 1) ** 2
         self._ensure(n, K)
@@ -124,8 +126,14 @@ class Rasterizer:
                 self._ensure(n, K)
                 C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
         C.omnigs_sort(self.cfg, n, self.capacity, self.keys, self.ranges, self.ws, stream)
-        C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.keys, self.order, self.rgb, self.T,
-                            self.ncontrib, self.count_out, stream)
+        if l1_target is not None:
+            if self.forward_only or self.count_out is not None:
+                raise ValueError("l1_target needs a Rasterizer with gradients and without per-pixel counts")
+            C.omnigs_render_fwd_l1(self.cfg, n, self.splats, self.ranges, self.keys, self.order, l1_target,
+                                   self.rgb, self.T, self.ncontrib, self.dL_drgb, self.loss, self.ws, stream)
+        else:
+            C.omnigs_render_fwd(self.cfg, n, self.splats, self.ranges, self.keys, self.order, self.rgb, self.T,
+                                self.ncontrib, self.count_out, stream)
         return self.rgb
 
     def l1_loss(self, target, stream=None, rows=None):

@@ -23,10 +23,11 @@ class StreamedSteps:
     """Double-buffered fwd + loss + bwd steps of one Rasterizer.
 
     loss_fn(rasterizer, target) computes the loss into rasterizer.loss and its image gradient into
-    rasterizer.dL_drgb on the current stream (e.g. lambda r, t: r.l1_loss(t)).
+    rasterizer.dL_drgb on the current stream (e.g. lambda r, t: r.l1_loss(t)). loss_fn=None: the L1 loss, computed
+    by the forward blend itself (Rasterizer.forward with l1_target).
     """
 
-    def __init__(self, rasterizer: Rasterizer, loss_fn: Callable[[Rasterizer, torch.Tensor], object],
+    def __init__(self, rasterizer: Rasterizer, loss_fn: Callable[[Rasterizer, torch.Tensor], object] | None,
                  graph: bool = False):
         if graph and rasterizer.grow:
             raise ValueError("graph=True needs a Rasterizer built with grow=False (no host synchronisation)")
@@ -65,8 +66,11 @@ class StreamedSteps:
 
     def _compute(self, s: int):
         means, scales, quats, opacity, sh, viewmats, target = self.inputs[s]
-        self.r.forward(means, scales, quats, opacity, sh, viewmats)
-        self.loss_fn(self.r, target)
+        if self.loss_fn is None:
+            self.r.forward(means, scales, quats, opacity, sh, viewmats, l1_target=target)
+        else:
+            self.r.forward(means, scales, quats, opacity, sh, viewmats)
+            self.loss_fn(self.r, target)
         o = self.outputs[s]
         self.r.backward(out=o)
         o["loss"].copy_(self.r.loss)

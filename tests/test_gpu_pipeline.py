@@ -188,3 +188,60 @@ def test_profiler_collects_kernel_times():
     finally:
         C.omnigs_profiler_enable(False)
     assert {"sort_upsweep", "sort_downsweep", "tile_ranges"} <= names and "tile_scatter" not in names
+
+
+@pytest.mark.parametrize("tile,ppt", [(16, 4), (16, 2), (16, 8), (32, 4), (8, 2)])
+def test_forward_with_fused_l1_matches_forward_then_l1(tile, ppt):
+    """omnigs_render_fwd_l1 against omnigs_render_fwd followed by omnigs_l1_loss: the image, T, n_contrib and the
+    gradient bit for bit, the loss (the same sum in another order) within 1e-6 relative, and against float64 numpy
+    over the rendered image; pixels equal to the target get a zero gradient. The graph-captured fused step repeats
+    the loss exactly."""
+    W, H, V = 256, 128, 2
+    sc = synth.shell_scene(6000, seed=11)
+    vm = dev(synth.random_viewmats(V, 4))
+    params = scene_to_device(sc)
+    s = og.Settings(width=W, height=H, tile=tile, num_views=V, sh_degree=3, pixels_per_thread=ppt)
+    a = og.Rasterizer(s)
+    rgb = a.forward(*params, vm).clone()
+    tgt = dev(synth.random_image(V, W, H, 12))
+    tgt[0, :, :8, :8] = rgb[0, :, :8, :8]  # equal pixels: zero gradient
+    a.l1_loss(tgt)
+    b = og.Rasterizer(s, capacity=int(a.count * 1.5) + 1024, grow=False)
+    b.forward(*params, vm, l1_target=tgt)
+    torch.cuda.synchronize()
+    b.check()
+    assert torch.equal(b.rgb, a.rgb) and torch.equal(b.T, a.T) and torch.equal(b.ncontrib, a.ncontrib)
+    assert torch.equal(b.dL_drgb, a.dL_drgb)
+    assert not torch.any(b.dL_drgb[0, :, :8, :8])
+    d = rgb.cpu().numpy().astype(np.float64) - tgt.cpu().numpy()
+    ref = np.abs(d).mean()
+    print(f"fused L1 {tile}x{tile}/{ppt}: {b.loss.item():.9g} unfused {a.loss.item():.9g} float64 {ref:.9g}")
+    assert abs(b.loss.item() - a.loss.item()) <= 1e-6 * ref
+    assert abs(b.loss.item() - ref) <= 1e-6 * ref
+
+    def step():
+        b.forward(*params, vm, l1_target=tgt)
+        return b.backward()
+
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        step()
+    torch.cuda.current_stream().wait_stream(st)
+    torch.cuda.synchronize()
+    first = b.loss.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.loss, first)
+
+
+def test_fused_l1_rejects_a_forward_only_rasterizer():
+    W, H = 64, 32
+    sc = synth.shell_scene(200, seed=2)
+    r = og.Rasterizer(_settings(W, H), forward_only=True)
+    with pytest.raises(ValueError):
+        r.forward(*scene_to_device(sc), dev(synth.identity_viewmats(1)), l1_target=torch.zeros(1, 3, H, W,
+                                                                                               device="cuda"))
