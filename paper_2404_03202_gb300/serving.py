@@ -283,17 +283,38 @@ class GpuExecutor:
         self._cv = threading.Condition()
         self._ready = 0
         self._queues = [queue.Queue() for _ in range(lanes)]
-        for q in self._queues:
-            threading.Thread(target=self._waiter, args=(q,), daemon=True).start()
+        self._threads = [threading.Thread(target=self._waiter, args=(q,), daemon=True) for q in self._queues]
+        for t in self._threads:
+            t.start()
 
     def _waiter(self, q):
         while True:
             h = q.get()
+            if h is None:  # close()
+                return
             h["ev"].synchronize()
             with self._cv:
                 h["finished"] = True
                 self._ready += 1
                 self._cv.notify_all()
+
+    def reserve(self, keys, max_views: int) -> int:
+        """Grow every lane's arena to the largest batch of up to max_views views of the given (scene, (w, h)) keys,
+        so that no lane allocates device memory once requests are served. Returns the bytes per lane."""
+        nbytes = max(self.bytes_needed(scene, w, h, max_views) for scene, (w, h) in keys)
+        for a in self.arenas:
+            a.reset(nbytes)
+        return nbytes
+
+    def close(self) -> None:
+        """Stop the waiter threads (after the batches already launched) and release the lanes' arenas and the
+        resident scenes. The threads hold the executor, so without close() its device memory stays allocated."""
+        for q in self._queues:
+            q.put(None)
+        for t in self._threads:
+            t.join()
+        self.arenas = []
+        self.scenes = {}
 
     def wait(self, timeout=None) -> None:
         """Block until some launched batch has finished and not been collected, or `timeout` seconds pass."""

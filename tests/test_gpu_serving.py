@@ -56,3 +56,26 @@ def test_oversize_request_is_rejected_not_run():
     r = serving.Request(0, "room3k", np.eye(4, dtype=np.float32), 512, 256, 0.0)
     summary = serving.run_trace(sch, [r])
     assert summary["rejected"] == 1 and r.error and r.result is None
+
+
+def test_reserved_arenas_serve_without_growing_and_close_stops_the_lanes():
+    """reserve() sizes every lane's arena for the largest batch: a trace afterwards allocates no arena memory, its
+    images equal those of an unreserved executor, and close() ends the waiter threads and frees the arenas."""
+    scenes = _scenes()
+    arrays = {k: s.arrays() for k, s in scenes.items()}
+    res = [(256, 128), (512, 256)]
+    ex = serving.GpuExecutor(arrays, lanes=2)
+    nbytes = ex.reserve([(nm, wh) for nm in sorted(arrays) for wh in res], 4)
+    bufs = [a.buf for a in ex.arenas]
+    assert all(b is not None and b.numel() >= nbytes for b in bufs)
+    reqs = _requests(scenes, 24, 4000.0, 7)
+    serving.run_trace(serving.Scheduler(ex, lanes=2, max_batch=4), reqs)
+    assert all(a.buf is b for a, b in zip(ex.arenas, bufs))  # no lane grew its arena
+    ref = serving.GpuExecutor(arrays, lanes=1)
+    again = _requests(scenes, 24, 4000.0, 7)
+    serving.run_trace(serving.Scheduler(ref, lanes=1, max_batch=1), again)
+    for a, b in zip(reqs, again):
+        assert np.array_equal(a.result, b.result), a.rid
+    for e in (ex, ref):
+        e.close()
+        assert not any(t.is_alive() for t in e._threads) and e.arenas == []
