@@ -639,7 +639,8 @@ def main():
             serve = serving_benchmark(dev)
         except Exception as e:  # reported, never hidden
             serve = {"failed": f"{type(e).__name__}: {e}"}
-        torch.cuda.empty_cache()
+        # (its freed arenas stay in the framework's cache: returning them to the driver made the later phases'
+        # first device allocations slow, e.g. the timed densify-and-prune pass)
 
     scene = build_scene(wl)
     vm_np = build_poses(wl, rank, world)
