@@ -149,6 +149,16 @@ omnigs_status omnigs_preprocess(const omnigs_config *cfg, int64_t n, const float
 omnigs_status omnigs_bin(const omnigs_config *cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
                          uint64_t *keys, int64_t capacity, void *workspace, omnigs_stream_t stream);
 
+/* omnigs_preprocess followed by omnigs_bin, with the same arguments and the same results (splats, order, keys, the
+ * instance count and the errors in the workspace). With the equirectangular camera the projection kernel also writes
+ * the depth sort's keys into the workspace, so that the binning does not read every splat record back for its depth
+ * (the fused form of Sec. 3.3's depth ordering of the splats of Eqs. 3-5; the paper has no such interface); with the
+ * pinhole camera the two calls simply run one after the other. */
+omnigs_status omnigs_preprocess_bin(const omnigs_config *cfg, int64_t n, const float *means, const float *scales,
+                                    const float *quats, const float *opacity, const float *sh, const float *viewmats,
+                                    omnigs_splat *splats, uint32_t *order, uint64_t *keys, int64_t capacity,
+                                    void *workspace, omnigs_stream_t stream);
+
 /* Stable sort of the instance keys of omnigs_bin by their (view, tile) bits into `keys` (one counting pass by tile
  * column within each (view, tile row) group when omnigs_bin grouped them, a radix sort of `keys` in place
  * otherwise), which leaves them ordered by (view, tile), then by depth rank, i.e. the blending

@@ -73,6 +73,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_workspace_size.restype = ctypes.c_size_t
         lib.omnigs_preprocess.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P]
         lib.omnigs_bin.argtypes = [cfgp, i64, P, P, P, i64, P, P]
+        lib.omnigs_preprocess_bin.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, i64, P, P]
         lib.omnigs_sort.argtypes = [cfgp, i64, i64, P, P, P, P]
         lib.omnigs_render_fwd.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P]
         lib.omnigs_render_fwd_l1.argtypes = [cfgp, i64, P, P, P, P, P, P, P, P, P, P, P, P]
@@ -100,7 +101,7 @@ def load() -> ctypes.CDLL:
         lib.omnigs_profiler_enable.argtypes = [ctypes.c_int]
         lib.omnigs_profiler_collect.argtypes = [ctypes.POINTER(omnigs_kernel_time), ctypes.c_int]
         lib.omnigs_profiler_collect.restype = ctypes.c_int
-        for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_render_fwd_l1",
+        for name in ("omnigs_preprocess", "omnigs_bin", "omnigs_preprocess_bin", "omnigs_sort", "omnigs_render_fwd", "omnigs_render_fwd_l1",
                      "omnigs_l1_loss",
                      "omnigs_l1_loss_rows", "omnigs_dssim_loss", "omnigs_adam_step", "omnigs_publish_params",
                      "omnigs_densify_stats", "omnigs_densify", "omnigs_reset_opacity", "omnigs_equirect_crop",
@@ -171,6 +172,13 @@ def omnigs_preprocess(cfg, n, means, scales, quats, opacity, sh, viewmats, splat
 def omnigs_bin(cfg, n, splats, order, keys, capacity, workspace, stream=None):
     _check(load().omnigs_bin(ctypes.byref(cfg), n, _ptr(splats), _ptr(order), _ptr(keys), capacity, _ptr(workspace),
                              _stream(stream)), "omnigs_bin")
+
+
+def omnigs_preprocess_bin(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, order, keys, capacity,
+                          workspace, stream=None):
+    _check(load().omnigs_preprocess_bin(ctypes.byref(cfg), n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity),
+                                        _ptr(sh), _ptr(viewmats), _ptr(splats), _ptr(order), _ptr(keys), capacity,
+                                        _ptr(workspace), _stream(stream)), "omnigs_preprocess_bin")
 
 
 def omnigs_sort(cfg, n, capacity, keys, ranges, workspace, stream=None):

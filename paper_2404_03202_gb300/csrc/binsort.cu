@@ -1560,13 +1560,22 @@ int tile_key_bits(const omnigs_config& cfg) {
     return std::max(1, ceil_log2(tiles));
 }
 
+bool packed_depth_keys(const omnigs_config& cfg, int64_t n, int* gbits) {
+    const int64_t total = n * cfg.num_views;
+    *gbits = std::max(1, ceil_log2((uint64_t)std::max<int64_t>(total, 1)));
+    return cfg.camera == OMNIGS_CAMERA_EQUIRECT && ceil_log2(cfg.num_views) + 32 + *gbits <= 64;
+}
+
+// depth_keys_ready: the caller zeroed the header and wrote the packed depth keys and the splat count (the fused
+// preprocess of omnigs_preprocess_bin; only where packed_depth_keys holds).
 cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* splats, uint32_t* order,
-                       uint64_t* keys, int64_t capacity, const WsLayout& L, char* ws, cudaStream_t stream) {
+                       uint64_t* keys, int64_t capacity, const WsLayout& L, char* ws, cudaStream_t stream,
+                       bool depth_keys_ready) {
     const int64_t total = n * cfg.num_views;
     const int tx = cfg.width / cfg.tile, ty = cfg.height / cfg.tile;
     const int wrap = cfg.camera == OMNIGS_CAMERA_EQUIRECT;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
-    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
+    cudaError_t e = depth_keys_ready ? cudaSuccess : cudaMemsetAsync(hdr, 0, sizeof(WsHeader), stream);
     if (e != cudaSuccess || total == 0) return e;
     const float4* sp = reinterpret_cast<const float4*>(splats);
     u64* dk0 = reinterpret_cast<u64*>(ws + L.depth_keys);
@@ -1578,10 +1587,10 @@ cudaError_t launch_bin(const omnigs_config& cfg, int64_t n, const omnigs_splat* 
     const unsigned nb = (unsigned)((total + kBinSplats - 1) / kBinSplats);  // blocks of the instance passes
     const int V = cfg.num_views;
     const unsigned* vis_start = nullptr;  // set when the depth sort ranks only the splats with instances
-    const int gbits = std::max(1, ceil_log2((uint64_t)total));
-    if (wrap && ceil_log2(V) + 32 + gbits <= 64) {
-        const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
-        {
+    int gbits = 0;
+    if (packed_depth_keys(cfg, n, &gbits)) {
+        if (!depth_keys_ready) {
+            const unsigned g = (unsigned)((total + kBinThreads - 1) / kBinThreads);
             ProfScope prof("depth_keys", stream);
             depth_keys_packed_kernel<<<g, kBinThreads, 0, stream>>>(total, (int)n, gbits, sp, dk0, &hdr->splat_count);
         }

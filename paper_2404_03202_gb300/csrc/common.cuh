@@ -125,15 +125,21 @@ struct ProfScope {
 };
 
 // Stage launchers (defined in preprocess.cu, binsort.cu, render.cu). Each returns cudaGetLastError().
+// depth_keys (optional): also write the depth sort's packed keys (see packed_depth_keys) and the splat count.
 cudaError_t launch_preprocess(const omnigs_config &cfg, int64_t n, const float *means, const float *scales,
                               const float *quats, const float *opacity, const float *sh, const float *viewmats,
-                              omnigs_splat *splats, cudaStream_t stream);
+                              omnigs_splat *splats, cudaStream_t stream, uint64_t *depth_keys = nullptr, int gbits = 0,
+                              uint64_t *splat_count = nullptr);
+// Whether the depth sort of omnigs_bin orders packed keys ((view << 32 | t_r bits) << gbits | splat index, which the
+// equirectangular camera uses when they fit 64 bits); *gbits: the index bits.
+bool packed_depth_keys(const omnigs_config &cfg, int64_t n, int *gbits);
 cudaError_t launch_preprocess_bwd(const omnigs_config &cfg, int64_t n, const float *means, const float *scales,
                                   const float *quats, const float *opacity, const float *sh, const float *viewmats,
                                   const omnigs_splat_grad *grads, float *d_means, float *d_scales, float *d_quats,
                                   float *d_opacity, float *d_sh, float *d_screen, cudaStream_t stream);
 cudaError_t launch_bin(const omnigs_config &cfg, int64_t n, const omnigs_splat *splats, uint32_t *order,
-                       uint64_t *keys, int64_t capacity, const WsLayout &L, char *ws, cudaStream_t stream);
+                       uint64_t *keys, int64_t capacity, const WsLayout &L, char *ws, cudaStream_t stream,
+                       bool depth_keys_ready = false);
 cudaError_t launch_sort(const omnigs_config &cfg, int64_t n, int64_t capacity, uint64_t *keys, uint32_t *ranges,
                         const WsLayout &L, char *ws, cudaStream_t stream);
 // The L1 loss fused into the forward blend (omnigs_render_fwd_l1): the target image, the gradient and loss outputs,

@@ -191,6 +191,35 @@ omnigs_status omnigs_bin(const omnigs_config* cfg, int64_t n, const omnigs_splat
     return from_cuda(launch_bin(*cfg, n, splats, order, keys, capacity, L, (char*)workspace, (cudaStream_t)stream));
 }
 
+omnigs_status omnigs_preprocess_bin(const omnigs_config* cfg, int64_t n, const float* means, const float* scales,
+                                    const float* quats, const float* opacity, const float* sh, const float* viewmats,
+                                    omnigs_splat* splats, uint32_t* order, uint64_t* keys, int64_t capacity,
+                                    void* workspace, omnigs_stream_t stream) {
+    if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;
+    if (!workspace || !aligned(workspace, 256)) return OMNIGS_E_INVALID;
+    if (n > 0 && (!means || !scales || !quats || !opacity || !sh || !viewmats || !splats || !order))
+        return OMNIGS_E_INVALID;
+    if (n > 0 && (!aligned(quats, 16) || !aligned(splats, 16))) return OMNIGS_E_INVALID;
+    if (capacity > 0 && (!keys || !aligned(keys, 8))) return OMNIGS_E_INVALID;
+    const WsLayout L = ws_layout(*cfg, n, capacity);
+    char* ws = (char*)workspace;
+    const cudaStream_t st = (cudaStream_t)stream;
+    int gbits = 0;
+    if (n == 0 || !packed_depth_keys(*cfg, n, &gbits)) {  // the two calls one after the other
+        cudaError_t e = launch_preprocess(*cfg, n, means, scales, quats, opacity, sh, viewmats, splats, st);
+        if (e != cudaSuccess) return from_cuda(e);
+        return from_cuda(launch_bin(*cfg, n, splats, order, keys, capacity, L, ws, st));
+    }
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.header);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+    if (e == cudaSuccess)
+        e = launch_preprocess(*cfg, n, means, scales, quats, opacity, sh, viewmats, splats, st,
+                              reinterpret_cast<uint64_t*>(ws + L.depth_keys), gbits,
+                              reinterpret_cast<uint64_t*>(&hdr->splat_count));
+    if (e == cudaSuccess) e = launch_bin(*cfg, n, splats, order, keys, capacity, L, ws, st, true);
+    return from_cuda(e);
+}
+
 omnigs_status omnigs_sort(const omnigs_config* cfg, int64_t n, int64_t capacity, uint64_t* keys, uint32_t* ranges,
                           void* workspace, omnigs_stream_t stream) {
     if (!valid_cfg(cfg) || !valid_n(cfg, n) || capacity < 0 || capacity >= (1ll << 32)) return OMNIGS_E_INVALID;

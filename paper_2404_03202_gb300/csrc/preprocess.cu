@@ -282,11 +282,15 @@ __device__ __forceinline__ bool box_off_image(float px, float py, int rx, int ry
     return ix + rx < 0 || ix - rx >= W || iy + ry < 0 || iy - ry >= H;
 }
 
-template <int K>
+// kKeys: also write the depth sort's packed key of every splat, ((view << 32 | t_r bits) << gbits) | splat index, and
+// the splat count (omnigs_preprocess_bin), so that the binning does not read every splat record back for its depth.
+template <int K, bool kKeys>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float* __restrict__ means,
                   const float* __restrict__ scales, const float* __restrict__ quats, const float* __restrict__ opacity,
-                  const float* __restrict__ sh, const float* __restrict__ viewmats, float4* __restrict__ splats) {
+                  const float* __restrict__ sh, const float* __restrict__ viewmats, float4* __restrict__ splats,
+                  unsigned long long* __restrict__ depth_keys, int gbits,
+                  unsigned long long* __restrict__ splat_count) {
     constexpr int STRIDE = 3 * K + 1;
     extern __shared__ float smem[];
     float* s_sh = smem;
@@ -298,6 +302,7 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
     __syncthreads();
     const int g = g0 + threadIdx.x;
     if (threadIdx.x >= cnt) return;
+    if (kKeys && g == 0) *splat_count = (unsigned long long)n * V;
 
     float m[3], s[3], qn[4], qnorm, R[9], M3[9];
     load_params(g, means, scales, quats, m, s, qn, qnorm);
@@ -310,7 +315,12 @@ preprocess_kernel(int n, int V, int W, int H, float near_r, Cam cam, const float
         Proj P;
         float px, py;
         float4* out = splats + 3 * ((size_t)v * n + g);
-        if (!project(w, cam, m, M3, W, H, near_r, P, px, py)) {
+        const bool visible = project(w, cam, m, M3, W, H, near_r, P, px, py);  // sets t_r either way
+        if constexpr (kKeys) {
+            const unsigned long long i = (unsigned long long)v * n + g;
+            depth_keys[i] = ((((unsigned long long)v << 32) | __float_as_uint(P.tr)) << gbits) | i;
+        }
+        if (!visible) {
             out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             out[1] = make_float4(0.f, P.tr, __uint_as_float(0u), 0.f);
             out[2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -589,16 +599,19 @@ preprocess_bwd_kernel(int n, int V, int W, int H, float near_r, Cam cam, const f
 template <int K>
 cudaError_t preprocess_k(const omnigs_config& cfg, int64_t n, const float* means, const float* scales,
                          const float* quats, const float* opacity, const float* sh, const float* viewmats,
-                         omnigs_splat* splats, cudaStream_t stream) {
+                         omnigs_splat* splats, uint64_t* depth_keys, int gbits, uint64_t* splat_count,
+                         cudaStream_t stream) {
     const size_t smem = sizeof(float) * (kPreThreads * (3 * K + 1) + 16 * cfg.num_views);
-    auto kern = preprocess_kernel<K>;
+    auto kern = depth_keys ? preprocess_kernel<K, true> : preprocess_kernel<K, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((n + kPreThreads - 1) / kPreThreads);
     ProfScope prof("preprocess_fwd", stream);
     kern<<<blocks, kPreThreads, smem, stream>>>((int)n, cfg.num_views, cfg.width, cfg.height, cfg.near_r, make_cam(cfg),
                                                 means, scales, quats, opacity, sh, viewmats,
-                                                reinterpret_cast<float4*>(splats));
+                                                reinterpret_cast<float4*>(splats),
+                                                reinterpret_cast<unsigned long long*>(depth_keys), gbits,
+                                                reinterpret_cast<unsigned long long*>(splat_count));
     return cudaGetLastError();
 }
 
@@ -625,14 +638,18 @@ cudaError_t preprocess_bwd_k(const omnigs_config& cfg, int64_t n, const float* m
 
 cudaError_t launch_preprocess(const omnigs_config& cfg, int64_t n, const float* means, const float* scales,
                               const float* quats, const float* opacity, const float* sh, const float* viewmats,
-                              omnigs_splat* splats, cudaStream_t stream) {
+                              omnigs_splat* splats, cudaStream_t stream, uint64_t* depth_keys, int gbits,
+                              uint64_t* splat_count) {
     if (n == 0) return cudaSuccess;
+#define OMNIGS_PRE(K) preprocess_k<K>(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, depth_keys, gbits, \
+                                      splat_count, stream)
     switch (cfg.sh_degree) {
-        case 0: return preprocess_k<1>(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, stream);
-        case 1: return preprocess_k<4>(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, stream);
-        case 2: return preprocess_k<9>(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, stream);
-        default: return preprocess_k<16>(cfg, n, means, scales, quats, opacity, sh, viewmats, splats, stream);
+        case 0: return OMNIGS_PRE(1);
+        case 1: return OMNIGS_PRE(4);
+        case 2: return OMNIGS_PRE(9);
+        default: return OMNIGS_PRE(16);
     }
+#undef OMNIGS_PRE
 }
 
 cudaError_t launch_preprocess_bwd(const omnigs_config& cfg, int64_t n, const float* means, const float* scales,

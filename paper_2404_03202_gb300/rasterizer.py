@@ -117,8 +117,10 @@ class Rasterizer:
         K = int(sh.shape[1]) if n > 0 else (self.s.sh_degree + 1) ** 2
         self._ensure(n, K)
         self._params = (means, scales, quats, opacity, sh, viewmats)
-        C.omnigs_preprocess(self.cfg, n, means, scales, quats, opacity, sh, viewmats, self.splats, stream)
-        C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
+        # (omnigs_preprocess then omnigs_bin, in one call: with the equirectangular camera the projection also
+        # writes the depth sort's keys)
+        C.omnigs_preprocess_bin(self.cfg, n, means, scales, quats, opacity, sh, viewmats, self.splats, self.order,
+                                self.keys, self.capacity, self.ws, stream)
         if self.grow:
             self.count = C.omnigs_instance_count(self.ws, stream)
             if self.count > self.capacity:

@@ -173,10 +173,12 @@ def test_profiler_collects_kernel_times():
     finally:
         C.omnigs_profiler_enable(False)
     names = {t[0] for t in times}
-    # 1000 splats (a 256-splat block spans two views at most) and 8 x 4 tiles: the bucketed order
-    for k in ["preprocess_fwd", "depth_keys", "depth_sort", "bin_count", "bin_emit", "tile_count", "tile_scatter",
+    # 1000 splats (a 256-splat block spans two views at most) and 8 x 4 tiles: the bucketed order; the projection
+    # writes the depth sort's keys itself (omnigs_preprocess_bin), so there is no separate depth_keys stage
+    for k in ["preprocess_fwd", "depth_sort", "bin_count", "bin_emit", "tile_count", "tile_scatter",
               "tile_ranges", "render_fwd", "l1_loss", "render_bwd", "preprocess_bwd"]:
         assert k in names, k
+    assert "depth_keys" not in names
     assert all(t[2] >= 0 for t in times)
     # fewer than 256 splats: the radix sort over the tile bits
     r = og.Rasterizer(_settings(W, H))
@@ -245,3 +247,42 @@ def test_fused_l1_rejects_a_forward_only_rasterizer():
     with pytest.raises(ValueError):
         r.forward(*scene_to_device(sc), dev(synth.identity_viewmats(1)), l1_target=torch.zeros(1, 3, H, W,
                                                                                                device="cuda"))
+
+
+@pytest.mark.parametrize("camera", ["equirect", "pinhole"])
+def test_preprocess_bin_equals_preprocess_then_bin(camera):
+    """omnigs_preprocess_bin (the projection also writing the depth sort's keys, equirectangular camera) against
+    omnigs_preprocess followed by omnigs_bin: splats, order, the instance count and, after omnigs_sort, the sorted
+    keys and the tile ranges bit for bit; and the same capacity-overflow error."""
+    W, H, V = 256, 128, 3
+    sc = synth.shell_scene(5000, seed=21)
+    vm = dev(synth.random_viewmats(V, 9))
+    params = scene_to_device(sc)
+    pin = (200.0, 200.0, 128.0, 64.0) if camera == "pinhole" else None
+    s = og.Settings(width=W, height=H, tile=16, num_views=V, sh_degree=3, pinhole=pin)
+    a = og.Rasterizer(s)
+    a.forward(*params, vm)  # sizes the buffers (capacity) and the workspace
+    cap = int(a.count * 1.2) + 64
+    outs = []
+    for fused in (False, True):
+        r = og.Rasterizer(s, capacity=cap, grow=False)
+        r._ensure(sc.n, sc.sh.shape[1])
+        r.order.fill_(-1)  # (pinhole: the entries past a view's ranked splats are left as they are)
+        if fused:
+            C.omnigs_preprocess_bin(r.cfg, sc.n, *params, vm, r.splats, r.order, r.keys, r.capacity, r.ws)
+        else:
+            C.omnigs_preprocess(r.cfg, sc.n, *params, vm, r.splats)
+            C.omnigs_bin(r.cfg, sc.n, r.splats, r.order, r.keys, r.capacity, r.ws)
+        count = C.omnigs_instance_count(r.ws)
+        C.omnigs_sort(r.cfg, sc.n, r.capacity, r.keys, r.ranges, r.ws)  # (the bucketed bin leaves keys to the sort)
+        outs.append((r.splats.clone(), r.order.clone(), count, r.keys[:count].clone(), r.ranges.clone()))
+    (s0, o0, c0, k0, g0), (s1, o1, c1, k1, g1) = outs
+    assert torch.equal(s0, s1) and torch.equal(o0, o1) and c0 == c1 == a.count
+    assert torch.equal(k0, k1) and torch.equal(g0, g1)
+    small = og.Rasterizer(s, capacity=max(a.count // 2, 1), grow=False)
+    small._ensure(sc.n, sc.sh.shape[1])
+    C.omnigs_preprocess_bin(small.cfg, sc.n, *params, vm, small.splats, small.order, small.keys, small.capacity,
+                            small.ws)
+    with pytest.raises(og.OmnigsError) as ei:
+        small.check()
+    assert ei.value.status == C.OMNIGS_E_CAPACITY
