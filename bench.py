@@ -99,7 +99,8 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows:
     tp = _sort_passes(max(1, _ceil_log2(tiles)))
     packed = equirect and _ceil_log2(V) + 32 + max(1, _ceil_log2(P)) <= 64  # splat index inside the depth key
     return {
-        "preprocess_fwd": n * 236 + P * 48,               # 59 parameter floats in, one splat out per view
+        # 59 parameter floats in, one splat out per view (and its packed depth key, which the projection writes)
+        "preprocess_fwd": n * 236 + P * (48 + 8 if packed else 48),
         # depth in, (view|depth|index) key out (and the index value out when the index does not fit the key)
         "depth_keys": P * (4 + 8) if packed else P * (4 + 8 + 4),
         # per pass: key histogram read, key (and index) read and written; a packed sort's last pass writes the index
