@@ -68,8 +68,8 @@ typedef struct {
 
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned). The fields binning reads
  * (position, conic, depth, box, q) fill the first 32 bytes, the colour fields the last 16.
- * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the image). (c0, c1, c2): inverse of the 2x2 covariance
- * Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
+ * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the
+ * image). (c0, c1, c2): inverse of the 2x2 covariance Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
  * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
  * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
  * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
@@ -110,7 +110,8 @@ size_t omnigs_workspace_size(const omnigs_config *cfg, int64_t n, int64_t capaci
 
 /* Per-(view, Gaussian) projection, Sec. 3.2-3.3: t = W m + t_cw (Eq. 1); lon, lat (Eq. 3); s (Eq. 4); p (Eq. 5);
  * J (Eqs. 10-16); Sigma~ = J W Sigma W^T J^T + 0.3 I (Eq. 9), Sigma = R(q) diag(s)^2 R(q)^T; conic = Sigma~^-1;
- * the instance box (radius_x, radius_y); colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from the camera centre to m (Sec. 3.1).
+ * the instance box (radius_x, radius_y); colour c = max(sum_k Y_k(d) sh_k + 0.5, 0) with d the unit vector from
+ * the camera centre to m (Sec. 3.1).
  *   means   [n, 3]  world positions m                     scales  [n, 3]  linear scales S (> 0)
  *   quats   [n, 4]  rotations q as (w, x, y, z), any norm  opacity [n]     opacities o in [0, 1]
  *   sh      [n, K, 3] SH coefficients                     viewmats [V, 4, 4] row-major world-to-camera T_cw
@@ -202,8 +203,8 @@ omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const f
 
 /* L1 loss restricted to the image rows [row_begin, row_end), for captures whose band of rows shows the capture rig
  * rather than the scene (Sec. 5.2: in the 360Roam captures the bottom rows, which show the robot carrying the
- * camera, are left out of the loss and its gradient): loss = mean |rgb - target| over [V, 3, row_begin:row_end, W]; dL_drgb = sign(rgb - target) / (V * 3 *
- * (row_end - row_begin) * W) inside those rows and 0 outside. Requires 0 <= row_begin < row_end <= H (else
+ * camera, are left out of the loss and its gradient): loss = mean |rgb - target| over [V, 3, row_begin:row_end, W];
+ * dL_drgb = sign(rgb - target) / (V * 3 * (row_end - row_begin) * W) inside those rows and 0 outside. Requires 0 <= row_begin < row_end <= H (else
  * OMNIGS_E_INVALID). Buffers as for omnigs_l1_loss. */
 omnigs_status omnigs_l1_loss_rows(const omnigs_config *cfg, int32_t row_begin, int32_t row_end, const float *rgb,
                                   const float *target, float *dL_drgb, float *loss, void *workspace,
