@@ -69,8 +69,8 @@ typedef struct {
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned). The fields binning reads
  * (position, conic, depth, box, q) fill the first 32 bytes, the colour fields the last 16.
  * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the
- * image). (c0, c1, c2): inverse of the 2x2 covariance Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in pixels of the box
- * around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
+ * image). (c0, c1, c2): inverse of the 2x2 covariance Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|.
+ * (radius_x, radius_y): half-extents in pixels of the box around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
  * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
  * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
  * + 1e-3)) and radius_y likewise with Sigma~_11, both held at 65535. Outside that ellipse alpha < 1/255, so the
@@ -204,8 +204,8 @@ omnigs_status omnigs_l1_loss(const omnigs_config *cfg, const float *rgb, const f
 /* L1 loss restricted to the image rows [row_begin, row_end), for captures whose band of rows shows the capture rig
  * rather than the scene (Sec. 5.2: in the 360Roam captures the bottom rows, which show the robot carrying the
  * camera, are left out of the loss and its gradient): loss = mean |rgb - target| over [V, 3, row_begin:row_end, W];
- * dL_drgb = sign(rgb - target) / (V * 3 * (row_end - row_begin) * W) inside those rows and 0 outside. Requires 0 <= row_begin < row_end <= H (else
- * OMNIGS_E_INVALID). Buffers as for omnigs_l1_loss. */
+ * dL_drgb = sign(rgb - target) / (V * 3 * (row_end - row_begin) * W) inside those rows and 0 outside. Requires
+ * 0 <= row_begin < row_end <= H (else OMNIGS_E_INVALID). Buffers as for omnigs_l1_loss. */
 omnigs_status omnigs_l1_loss_rows(const omnigs_config *cfg, int32_t row_begin, int32_t row_end, const float *rgb,
                                   const float *target, float *dL_drgb, float *loss, void *workspace,
                                   omnigs_stream_t stream);
