@@ -67,16 +67,16 @@ typedef struct {
 #define OMNIGS_CAMERA_PINHOLE 1
 
 /* One projected Gaussian in one view (48 bytes; arrays of it must be 16-byte aligned). The fields binning reads
- * (position, conic, depth, box, q) fill the first 32 bytes, the colour fields the last 16.
- * (px, py): Eq. 5 pixel position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the
- * image). (c0, c1, c2): inverse of the 2x2 covariance Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|.
- * (radius_x, radius_y): half-extents in pixels of the box around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view. The box is the
- * square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per axis to the
- * box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00) (1 + 1e-4)
- * + 1e-3)) and radius_y likewise with Sigma~_11, both held at 65535. Outside that ellipse alpha < 1/255, so the
- * narrowing removes only instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled, and with the
- * pinhole camera so is one whose box misses the image (it has no tile either way). q = 2 ln(255 o)
- * (0 when culled) is the level of that ellipse, dp^T conic dp <= q, which omnigs_bin uses to cull tiles row by row. */
+ * (position, conic, depth, box, q) fill the first 32 bytes, the colour fields the last 16. (px, py): Eq. 5 pixel
+ * position, px in [0, W], py in [0, H] (Eq. 2 for the pinhole camera: may lie off the image). (c0, c1, c2): inverse of
+ * the 2x2 covariance Sigma~ of Eq. 9 (entries 00, 01, 11). depth = t_r = |t|. (radius_x, radius_y): half-extents in
+ * pixels of the box around pixel floor(p) whose tiles receive an instance; 0 when the Gaussian is culled in this view.
+ * The box is the square of half-side r = ceil(3 sqrt(lambda_max)) (the radius of influence, Sec. 3.3), narrowed per
+ * axis to the box of the ellipse where alpha >= 1/255: with q = 2 ln(255 o), radius_x = min(r, ceil(sqrt(q Sigma~_00)
+ * (1 + 1e-4) + 1e-3)) and radius_y likewise with Sigma~_11, both held at 65535. Outside that ellipse alpha < 1/255, so
+ * the narrowing removes only instances that contribute to no pixel. A Gaussian with 255 o < 1 is culled, and with the
+ * pinhole camera so is one whose box misses the image (it has no tile either way). q = 2 ln(255 o) (0 when culled) is
+ * the level of that ellipse, dp^T conic dp <= q, which omnigs_bin uses to cull tiles row by row. */
 typedef struct {
     float px, py;
     float c0, c1, c2;
