@@ -25,14 +25,15 @@ def _inputs(step):
     return [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (*sc.arrays(), vm, tgt)]
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_streamed_steps_match_one_at_a_time(graph):
-    """With graph=True steps 0 and 1 run eagerly and are captured, steps 2-4 replay the slots' graphs on new inputs."""
+@pytest.mark.parametrize("graph,fused", [(False, False), (True, False), (True, True)])
+def test_streamed_steps_match_one_at_a_time(graph, fused):
+    """With graph=True steps 0 and 1 run eagerly and are captured, steps 2-4 replay the slots' graphs on new inputs.
+    fused: loss_fn=None, the L1 loss computed by the forward blend (omnigs_render_fwd_l1)."""
     steps = 5
     s = og.Settings(width=W, height=H, tile=16, num_views=V, sh_degree=3)
     ins = [_inputs(k) for k in range(steps)]
     r = og.Rasterizer(s, capacity=1 << 20, grow=False)
-    st = StreamedSteps(r, lambda rr, t: rr.l1_loss(t), graph=graph)
+    st = StreamedSteps(r, None if fused else (lambda rr, t: rr.l1_loss(t)), graph=graph)
     outs = []
     for k in range(steps):
         n, K = ins[k][0].shape[0], ins[k][4].shape[1]
@@ -49,8 +50,11 @@ def test_streamed_steps_match_one_at_a_time(graph):
     ref = og.Rasterizer(s, capacity=1 << 20, grow=False)
     for k in range(steps):
         dev = [t.cuda() for t in ins[k]]
-        ref.forward(*dev[:6])
-        ref.l1_loss(dev[6])
+        if fused:
+            ref.forward(*dev[:6], l1_target=dev[6])
+        else:
+            ref.forward(*dev[:6])
+            ref.l1_loss(dev[6])
         g = ref.backward()
         torch.cuda.synchronize()
         assert outs[k]["loss"].item() == ref.loss.item(), k  # the loss reduction is deterministic
