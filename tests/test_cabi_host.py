@@ -85,3 +85,27 @@ def test_config_layout_and_schedule_validation(lib):
     for cam, fx, fy in [(2, 100.0, 100.0), (1, 0.0, 100.0), (1, 100.0, -1.0), (1, float("nan"), 100.0)]:
         c = Cfg(256, 128, 16, 1, 3, 0.2, (ctypes.c_float * 3)(0, 0, 0), 0, cam, fx, fy, 128.0, 64.0)
         assert lib.omnigs_workspace_size(ctypes.byref(c), 10, 100) == 0, (cam, fx, fy)
+
+
+def test_fused_calls_reject_invalid_arguments_on_the_host(lib):
+    """omnigs_preprocess_bin and omnigs_render_fwd_l1 validate their arguments before any CUDA call: no config, and
+    a valid config with a missing workspace or target."""
+    P = ctypes.c_void_p
+    lib.omnigs_preprocess_bin.argtypes = [P, ctypes.c_int64] + [P] * 9 + [ctypes.c_int64, P, P]
+    lib.omnigs_render_fwd_l1.argtypes = [P, ctypes.c_int64] + [P] * 12
+    assert lib.omnigs_preprocess_bin(None, 10, *([None] * 9), 100, None, None) == 1
+    assert lib.omnigs_render_fwd_l1(None, 10, *([None] * 12)) == 1
+    cfg = (ctypes.c_int32 * 16)()
+    for i, v in enumerate([256, 128, 16, 1, 3]):
+        cfg[i] = v
+    ctypes.cast(ctypes.byref(cfg, 20), ctypes.POINTER(ctypes.c_float))[0] = 0.2  # near_r
+    buf = (ctypes.c_float * 128)()
+    p = ctypes.c_void_p((ctypes.addressof(buf) + 255) // 256 * 256)  # 256-byte aligned: only the tested argument fails
+    # n = 10 with every array given but no workspace; a negative capacity
+    assert lib.omnigs_preprocess_bin(ctypes.byref(cfg), 10, *([p] * 9), 100, None, None) == 1
+    assert lib.omnigs_preprocess_bin(ctypes.byref(cfg), 10, *([p] * 9), -1, p, None) == 1
+    # render_fwd_l1: no target, then no workspace
+    args = [p] * 4 + [None] + [p] * 5
+    assert lib.omnigs_render_fwd_l1(ctypes.byref(cfg), 10, *args, p, None) == 1
+    args = [p] * 10
+    assert lib.omnigs_render_fwd_l1(ctypes.byref(cfg), 10, *args, None, None) == 1
