@@ -86,6 +86,23 @@ def test_empty_scene_renders_background():
     assert (r.T == 1).all() and (r.ncontrib == 0).all()
 
 
+def test_empty_scene_with_the_fused_loss():
+    """No Gaussians: the fused blend writes the background, its L1 loss against a target and the sign gradient."""
+    W, H = 128, 64
+    bg = (0.2, 0.4, 0.6)
+    r = og.Rasterizer(_settings(W, H, bg=bg))
+    z = torch.zeros((0, 3), device="cuda")
+    tgt = dev(synth.random_image(1, W, H, 4))
+    rgb = r.forward(z, z.clone(), torch.zeros((0, 4), device="cuda"), torch.zeros((0,), device="cuda"),
+                    torch.zeros((0, 16, 3), device="cuda"), dev(synth.identity_viewmats(1)), l1_target=tgt)
+    torch.cuda.synchronize()
+    d = np.broadcast_to(np.asarray(bg, np.float32).reshape(1, 3, 1, 1), (1, 3, H, W)).astype(np.float64) \
+        - tgt.cpu().numpy()
+    assert r.count == 0 and torch.equal(rgb, torch.tensor(bg, device="cuda").view(1, 3, 1, 1).expand_as(rgb))
+    assert abs(r.loss.item() - np.abs(d).mean()) <= 1e-6 * np.abs(d).mean()
+    assert np.array_equal(r.dL_drgb.cpu().numpy(), (np.sign(d) / d.size).astype(np.float32))
+
+
 def test_all_culled_inside_near_sphere():
     W, H = 128, 64
     sc = synth.shell_scene(500, seed=2, r_min=0.01, r_max=0.15)
