@@ -113,6 +113,10 @@ class Rasterizer:
         this Rasterizer, overwritten by the next forward). With l1_target (a [V, 3, H, W] float32 device tensor) the
         L1 loss is computed by the blend itself (omnigs_render_fwd_l1): self.loss and self.dL_drgb are then set as
         l1_loss(l1_target) would set them, without a second pass over the image."""
+        if l1_target is not None:
+            if self.forward_only or self.count_out is not None:
+                raise ValueError("l1_target needs a Rasterizer with gradients and without per-pixel counts")
+            self._check_target(l1_target)
         n = int(means.shape[0])
         K = int(sh.shape[1]) if n > 0 else (self.s.sh_degree + 1) ** 2
         self._ensure(n, K)
@@ -129,8 +133,6 @@ class Rasterizer:
                 C.omnigs_bin(self.cfg, n, self.splats, self.order, self.keys, self.capacity, self.ws, stream)
         C.omnigs_sort(self.cfg, n, self.capacity, self.keys, self.ranges, self.ws, stream)
         if l1_target is not None:
-            if self.forward_only or self.count_out is not None:
-                raise ValueError("l1_target needs a Rasterizer with gradients and without per-pixel counts")
             C.omnigs_render_fwd_l1(self.cfg, n, self.splats, self.ranges, self.keys, self.order, l1_target,
                                    self.rgb, self.T, self.ncontrib, self.dL_drgb, self.loss, self.ws, stream)
         else:
@@ -138,9 +140,16 @@ class Rasterizer:
                                 self.ncontrib, self.count_out, stream)
         return self.rgb
 
+    def _check_target(self, target) -> None:
+        """The loss kernels read a [V, 3, H, W] float32 image through a raw pointer: anything else is refused here."""
+        if (not isinstance(target, torch.Tensor) or target.dtype != torch.float32 or not target.is_cuda
+                or tuple(target.shape) != tuple(self.rgb.shape) or not target.is_contiguous()):
+            raise ValueError(f"target must be a contiguous float32 CUDA tensor of shape {tuple(self.rgb.shape)}")
+
     def l1_loss(self, target, stream=None, rows=None):
         """mean |rgb - target| (device scalar) and its gradient in self.dL_drgb; with rows = (begin, end) only those
         image rows count (the others get a zero gradient)."""
+        self._check_target(target)
         if rows is None:
             C.omnigs_l1_loss(self.cfg, self.rgb, target, self.dL_drgb, self.loss, self.ws, stream)
         else:

@@ -257,13 +257,21 @@ def test_forward_with_fused_l1_matches_forward_then_l1(tile, ppt):
     assert torch.equal(b.loss, first)
 
 
-def test_fused_l1_rejects_a_forward_only_rasterizer():
+def test_fused_l1_rejects_a_forward_only_rasterizer_and_a_mismatched_target():
     W, H = 64, 32
     sc = synth.shell_scene(200, seed=2)
+    params, vm = scene_to_device(sc), dev(synth.identity_viewmats(1))
     r = og.Rasterizer(_settings(W, H), forward_only=True)
     with pytest.raises(ValueError):
-        r.forward(*scene_to_device(sc), dev(synth.identity_viewmats(1)), l1_target=torch.zeros(1, 3, H, W,
-                                                                                               device="cuda"))
+        r.forward(*params, vm, l1_target=torch.zeros(1, 3, H, W, device="cuda"))
+    g = og.Rasterizer(_settings(W, H))
+    for bad in (torch.zeros(2, 3, H, W, device="cuda"), torch.zeros(1, 3, H, W, device="cuda", dtype=torch.float64),
+                torch.zeros(1, 3, W, H, device="cuda").transpose(2, 3), torch.zeros(1, 3, H, W)):
+        with pytest.raises(ValueError):
+            g.forward(*params, vm, l1_target=bad)
+        g.forward(*params, vm)
+        with pytest.raises(ValueError):
+            g.l1_loss(bad)
 
 
 @pytest.mark.parametrize("camera", ["equirect", "pinhole"])
