@@ -56,8 +56,10 @@ def test_sort_pass_counts():
 def test_stage_bytes_packed_depth_sort_only_when_the_index_fits():
     sb = bench.stage_bytes(1_000_000, 8, 2048, 1024, 16, 10_000, 1_000)
     assert sb["depth_sort"] == 4 * 8_000_000 * 24 - 8_000_000 * 4
+    assert sb["preprocess_fwd"] == 1_000_000 * 236 + 8_000_000 * (48 + 8)  # the projection writes the packed keys
     sb = bench.stage_bytes(1_000_000, 8, 2048, 1024, 16, 10_000, 1_000, equirect=False)
     assert sb["depth_sort"] == 4 * 8_000_000 * 32
+    assert sb["preprocess_fwd"] == 1_000_000 * 236 + 8_000_000 * 48
 
 
 def test_oracle_pool_times_a_bounded_sample_on_several_cores():
