@@ -491,11 +491,11 @@ def serving_benchmark(dev, count: int = 192, lanes: int = 4, max_batch: int = 8)
     from paper_2404_03202_gb300 import serving
     scenes = {f"room{n // 1000}k": synth.room_scene(n, 40 + i).arrays() for i, n in enumerate(SERVING_SCENES)}
     names = sorted(scenes)
-    ex = serving.GpuExecutor(scenes, lanes=lanes, device=dev)
+    ex = serving.GpuExecutor(scenes, lanes=lanes, device=dev, host_buffers="per_lane")
     for nm in names:  # probes (capacity per scene and resolution) and allocator warm-up, outside the timings
         for (w, h), _ in SERVING_RES:
             ex.bytes_needed(nm, w, h, 1)
-    # every lane's arena sized for the largest batch up front
+    # every lane's arena (and pinned result buffer) sized for the largest batch up front
     lane_bytes = ex.reserve([(nm, wh) for nm in names for wh, _ in SERVING_RES], max_batch)
     # warm-up: every (scene, resolution) key once alone and once in a full batch, so that no timed trace pays a
     # first use (allocator growth, capacity probes). Every scheduler delivers and drops each image as it completes,
@@ -506,7 +506,7 @@ def serving_benchmark(dev, count: int = 192, lanes: int = 4, max_batch: int = 8)
     for key in every:
         serving.run_trace(sched(1, 1), serving_requests(names, 1, None, 1, keys=[key]))
         serving.run_trace(sched(lanes, max_batch), serving_requests(names, max_batch, None, 1, keys=[key]))
-    # and every batch size at every resolution once (the pinned result buffer of each size)
+    # and every batch size at every resolution once
     for wh, _ in SERVING_RES:
         for v in range(2, max_batch):
             serving.run_trace(sched(1, v), serving_requests(names, v, None, 1, keys=[((names[0], wh), 1.0)]))

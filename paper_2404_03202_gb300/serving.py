@@ -78,9 +78,11 @@ class Stats:
 
 class Scheduler:
     def __init__(self, executor, lanes: int = 4, max_batch: int = 8, mem_budget: int | None = None,
-                 max_wait: float = 0.25, keep_results: bool = True):
+                 max_wait: float = 0.25, keep_results: bool = True, on_result=None):
         if lanes < 1 or max_batch < 1:
             raise ValueError("lanes and max_batch must be >= 1")
+        if keep_results and getattr(executor, "host_buffers", "per_batch") == "per_lane":
+            raise ValueError("an executor with per-lane host buffers reuses each image's memory: keep_results=False")
         self.ex = executor
         self.lanes = lanes
         self.max_batch = max_batch
@@ -89,6 +91,7 @@ class Scheduler:
         # keep_results=False: a completed request's image is delivered and dropped at once (a server that hands it
         # on), so its host buffer goes back to the allocator instead of being held until the caller lets go
         self.keep_results = keep_results
+        self.on_result = on_result  # called with (request, image) as each request completes, before it is dropped
         self.waiting: list[Request] = []
         self.in_flight: dict[int, Batch] = {}
         self.free_lanes = list(range(lanes))
@@ -178,6 +181,8 @@ class Scheduler:
             images = self.ex.collect(b.handle)
             t = now
             for r, img in zip(b.requests, images):
+                if self.on_result is not None:
+                    self.on_result(r, img)
                 r.result = img if self.keep_results else None
                 r.done = t
                 self.stats.completed += 1
@@ -260,10 +265,18 @@ class GpuExecutor:
     scene. Instance capacity per batch is sized from the largest per-view count seen for that scene and resolution
     (a probe render on first use) times `headroom`; a batch that still overflows is re-rendered once with growing
     capacity when it is collected, and counted in `overflows`.
+
+    host_buffers: where a batch's images land on the host. "per_batch" (default): a new pinned buffer per batch,
+    from the framework's caching host allocator; the images stay valid as long as they are held. "per_lane": one
+    pinned buffer per lane, sized by `reserve` and reused by the lane's next batch, so that serving pins no host
+    memory (pinning a buffer of hundreds of MB takes far longer than rendering into it); the images a batch returns
+    are then valid only until its lane's next batch, and only a Scheduler that does not keep results accepts it.
     """
 
     def __init__(self, scenes: dict, lanes: int, device="cuda", tile: int = 16, headroom: float = 1.3,
-                 bg=(0.0, 0.0, 0.0)):
+                 bg=(0.0, 0.0, 0.0), host_buffers: str = "per_batch"):
+        if host_buffers not in ("per_batch", "per_lane"):
+            raise ValueError("host_buffers must be 'per_batch' or 'per_lane'")
         import torch
         import paper_2404_03202_gb300 as og
         self.torch, self.og = torch, og
@@ -276,6 +289,8 @@ class GpuExecutor:
             self.scenes[name] = (t, int(t[0].shape[0]), int(round(k ** 0.5)) - 1)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(lanes)]
         self.arenas = [_LaneArena(torch, self.device) for _ in range(lanes)]
+        self.host_buffers = host_buffers
+        self._lane_host = [None] * lanes  # per_lane: each lane's pinned result buffer (float32, flat)
         self.per_view = {}
         self.overflows = 0
         # one waiter thread per lane blocks on the lane's batches in launch order (its stream runs them in that
@@ -304,7 +319,19 @@ class GpuExecutor:
         nbytes = max(self.bytes_needed(scene, w, h, max_views) for scene, (w, h) in keys)
         for a in self.arenas:
             a.reset(nbytes)
+        if self.host_buffers == "per_lane":
+            floats = max_views * 3 * max(w * h for _, (w, h) in keys)
+            for lane in range(len(self._lane_host)):
+                self._lane_host[lane] = self._pinned(lane, floats)
         return nbytes
+
+    def _pinned(self, lane: int, floats: int):
+        """The lane's pinned result buffer, grown to hold `floats` values."""
+        buf = self._lane_host[lane]
+        if buf is None or buf.numel() < floats:
+            buf = None
+            self._lane_host[lane] = buf = self.torch.empty((floats,), dtype=self.torch.float32, pin_memory=True)
+        return buf
 
     def close(self) -> None:
         """Stop the waiter threads (after the batches already launched) and release the lanes' arenas and the
@@ -314,6 +341,7 @@ class GpuExecutor:
         for t in self._threads:
             t.join()
         self.arenas = []
+        self._lane_host = []
         self.scenes = {}
 
     def wait(self, timeout=None) -> None:
@@ -370,7 +398,12 @@ class GpuExecutor:
                                       alloc=arena.alloc, forward_only=True)
             vm_dev = torch.from_numpy(vm).to(self.device, non_blocking=True)
             rast.forward(*params, vm_dev, stream=s)
-            host = torch.empty(tuple(rast.rgb.shape), dtype=torch.float32, pin_memory=True)
+            shape = tuple(rast.rgb.shape)
+            if self.host_buffers == "per_lane":
+                # the lane's previous batch was collected before this launch, so its buffer is free
+                host = self._pinned(lane, v * 3 * r0.width * r0.height)[:v * 3 * r0.width * r0.height].view(shape)
+            else:
+                host = torch.empty(shape, dtype=torch.float32, pin_memory=True)
             host.copy_(rast.rgb, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)

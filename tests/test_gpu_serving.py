@@ -79,3 +79,26 @@ def test_reserved_arenas_serve_without_growing_and_close_stops_the_lanes():
     for e in (ex, ref):
         e.close()
         assert not any(t.is_alive() for t in e._threads) and e.arenas == []
+
+
+def test_per_lane_host_buffers_deliver_the_same_images():
+    """host_buffers='per_lane': each lane reuses one pinned buffer; the images handed to on_result as requests
+    complete equal those of the default per-batch buffers (one request at a time)."""
+    scenes = _scenes()
+    arrays = {k: s.arrays() for k, s in scenes.items()}
+    res = [(256, 128), (512, 256)]
+    ex = serving.GpuExecutor(arrays, lanes=3, host_buffers="per_lane")
+    ex.reserve([(nm, wh) for nm in sorted(arrays) for wh in res], 4)
+    got = {}
+    sch = serving.Scheduler(ex, lanes=3, max_batch=4, keep_results=False,
+                            on_result=lambda r, img: got.__setitem__(r.rid, np.array(img, copy=True)))
+    reqs = _requests(scenes, 40, 4000.0, 11)
+    summary = serving.run_trace(sch, reqs)
+    assert summary["requests"] == len(reqs) and summary["mean_batch"] > 1.0
+    ref = serving.GpuExecutor(arrays, lanes=1)
+    again = _requests(scenes, 40, 4000.0, 11)
+    serving.run_trace(serving.Scheduler(ref, lanes=1, max_batch=1), again)
+    for r in again:
+        assert np.array_equal(got[r.rid], r.result), r.rid
+    for e in (ex, ref):
+        e.close()

@@ -107,6 +107,23 @@ def test_delivered_images_are_dropped_when_results_are_not_kept():
     assert all(r.result is None and r.done is not None and r.arrival <= r.admitted <= r.done for r in reqs)
 
 
+def test_results_reach_the_delivery_hook_and_per_lane_buffers_need_dropped_results():
+    """on_result sees every request with its own image as it completes, also when results are not kept; an
+    executor that reuses each lane's host buffer is refused by a scheduler that keeps results."""
+    reqs = _trace(120, 2000.0, 9)
+    clk = SimClock()
+    ex = FakeExecutor(clk, budget=10_000)
+    seen = {}
+    sch = S.Scheduler(ex, lanes=3, max_batch=4, keep_results=False,
+                      on_result=lambda r, img: seen.__setitem__(r.rid, float(img[0, 0, 0])))
+    S.run_trace(sch, reqs, clock=clk, sleep=clk.sleep)
+    assert seen == {r.rid: float(r.rid) for r in reqs} and all(r.result is None for r in reqs)
+    ex.host_buffers = "per_lane"
+    with pytest.raises(ValueError):
+        S.Scheduler(ex, lanes=3, max_batch=4)
+    S.Scheduler(ex, lanes=3, max_batch=4, keep_results=False)
+
+
 def test_batches_hold_one_key_and_respect_lanes_and_memory():
     reqs = _trace(400, 5000.0, 2)
     sch, ex, summary = _run(reqs, lanes=3, max_batch=4, budget=2500)
