@@ -584,8 +584,7 @@ def workload_config(wl, args, settings=None):
             "tile": tile, "loss_rows": list(wl["loss_rows"]) if wl.get("loss_rows") else None,
             "parallelism": f"replica x{args.gpus} (views per rank)",
             "l2": "inputs larger than L2 (several GB touched per step)",
-            "loss": ("L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim"
-                     else ("L1 over the loss rows" if wl.get("loss_rows") else "L1, fused into the forward blend")),
+            "loss": "L1 + D-SSIM, lambda 0.2" if getattr(args, "loss", "l1") == "dssim" else "L1",
             "camera": f"pinhole fx, fy, cx, cy = {wl['pinhole']}" if wl.get("pinhole") else "equirectangular"}
 
 
@@ -896,7 +895,9 @@ def main():
                                          "adjoint_pixels_per_thread": settings.adjoint_pixels_per_thread or "default"},
                             "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
                             "instances_per_step": count, "examined_pairs_per_step": examined,
-                            "contributing_pairs_per_step": contrib},
+                            "contributing_pairs_per_step": contrib,
+                            "loss_path": ("fused into the forward blend (omnigs_render_fwd_l1)" if fused_l1
+                                          else "separate loss call")},
                "gpu_launches": kernel_launches * args.steps, "stages": stages,
                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "serving": serve,
                "train_loop": train_loop}
