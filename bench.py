@@ -122,11 +122,10 @@ def stage_bytes(n: int, V: int, W: int, H: int, tile: int, instances: int, rows:
     }
 
 
-# DRAM traffic of render_bwd per view (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
-# 1-view workload; the 8-view launch processes 8 such views), with the SHA-256 of the adjoint's source (the kernel
-# and the helpers it uses) it was taken on: once that source changes the figure no longer applies and the bench
-# reports traffic as null.
-RENDER_BWD_TRAFFIC = {"bytes_per_view": 49_962_496,
+# DRAM traffic of one render_bwd launch of the egocentric step (8 views: dram__bytes_read.sum + dram__bytes_write.sum
+# of one ncu capture of that launch), with the SHA-256 of the adjoint's source (the kernel and the helpers it uses) it
+# was taken on: once that source changes the figure no longer applies and the bench reports traffic as null.
+RENDER_BWD_TRAFFIC = {"bytes_per_launch": 407_923_456, "views": 8,
                       "source_sha256": "463372f855ce567f74c6d51bc7e69662edac2a25b762c2bd3f76f5b93375e88e"}
 
 
@@ -822,8 +821,9 @@ def main():
         if dom == "render_bwd" and args.workload == "egocentric":
             with open(os.path.join(ROOT, "paper_2404_03202_gb300", "csrc", "render.cu")) as f:
                 src = render_bwd_source(f.read())
-            if hashlib.sha256(src.encode()).hexdigest() == RENDER_BWD_TRAFFIC["source_sha256"]:
-                traffic = RENDER_BWD_TRAFFIC["bytes_per_view"] * V
+            if (hashlib.sha256(src.encode()).hexdigest() == RENDER_BWD_TRAFFIC["source_sha256"]
+                    and V == RENDER_BWD_TRAFFIC["views"]):
+                traffic = RENDER_BWD_TRAFFIC["bytes_per_launch"]
     elif dom == "sort_downsweep":
         roof = {"bound": "hbm", "achieved": count * SORT_BYTES_PER_KEY / (k["avg_ms"] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s"}

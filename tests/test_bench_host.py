@@ -84,3 +84,13 @@ def test_whole_oracle_step_on_one_and_several_cores():
     assert r["single_thread_ms"] > 0 and r["all_cores_ms"] > 0 and r["cores"] == 2
     assert set(r["single_thread_stages_ms"]) == {"preprocess", "bin_sort", "blend_fwd_bwd", "preprocess_bwd"}
     assert abs(sum(r["single_thread_stages_ms"].values()) - r["single_thread_ms"]) <= 1e-6 * r["single_thread_ms"]
+
+
+def test_render_bwd_traffic_figure_belongs_to_the_current_adjoint():
+    """The bench reports the adjoint's measured DRAM traffic only while the adjoint's source is the one it was
+    measured on; this fails when the kernel changes without a new capture."""
+    import hashlib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "paper_2404_03202_gb300", "csrc", "render.cu")) as f:
+        src = bench.render_bwd_source(f.read())
+    assert hashlib.sha256(src.encode()).hexdigest() == bench.RENDER_BWD_TRAFFIC["source_sha256"]
